@@ -1,0 +1,285 @@
+/*
+ * dist.h -- C ABI of libdist: differentiable sphere tracing of a DeepSDF-style
+ * latent-conditioned MLP signed distance function on one NVIDIA B300 (sm_103a).
+ *
+ * Method: DIST (Liu et al., CVPR 2020, arXiv 1911.13225).  The problem
+ * statement (Sec. 3.4 and Eq. 3 of Sec. 4.2.1): given a decoder f_theta(p, z),
+ * a latent code z, a camera (intrinsics K, extrinsics) and an image size,
+ * render depth, surface normal and soft silhouette by sphere tracing every
+ * pixel's ray with at most `max_steps` queries and convergence threshold
+ * `eps`, then back-propagate image-plane losses to z.
+ *
+ * Conventions for every entry point:
+ *  - All functions return a dist_status and never abort, trap or print.
+ *    On failure dist_last_error() returns a message for the calling thread.
+ *  - "device" pointers are CUDA global-memory pointers on the current device;
+ *    "host" pointers are ordinary CPU memory.  The caller owns every buffer it
+ *    passes; the library owns decoders, workspaces and servers it creates.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Trace/loss/backward calls are stream-ordered: they enqueue
+ *    work and return without synchronising and without allocating memory.
+ *  - Pixels of several cameras are concatenated in camera order, each camera's
+ *    pixels row-major (index = offset + y * W + x).  Cameras use OpenCV axes:
+ *    x right, y down, z forward (the depth formula of Sec. 3.3).
+ *  - Background pixels have depth +inf (Sec. 3.2, "Initialization").
+ */
+#ifndef DIST_H
+#define DIST_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  DIST_OK = 0,
+  DIST_E_INVALID = 1,     /* bad argument: NULL pointer, size out of range,
+                             camera inside the bounding sphere, ...       */
+  DIST_E_NOMEM = 2,       /* allocation failed, workspace too small, or a
+                             serving request refused by the memory budget  */
+  DIST_E_CUDA = 3,        /* a CUDA runtime call failed                   */
+  DIST_E_TIMEOUT = 4,     /* a bounded wait ran out                       */
+  DIST_E_BUSY = 5,        /* serving: result not ready / no free slot     */
+  DIST_E_UNSUPPORTED = 6  /* e.g. BF16 tensor-core path asked for a decoder
+                             shape it does not cover                      */
+} dist_status;
+
+typedef enum { DIST_PREC_FP32 = 0, DIST_PREC_BF16 = 1 } dist_precision;
+typedef enum { DIST_GRAD_EXACT = 0, DIST_GRAD_PAPER = 1 } dist_grad_mode;
+
+/* Ray outcome codes written to dist_trace_out.status. */
+enum { DIST_RAY_INIT_MISS = 0, DIST_RAY_HIT = 1, DIST_RAY_LEFT = 2, DIST_RAY_MAX_STEPS = 3 };
+
+/* ---------------------------------------------------------------- decoder */
+
+/* Shape of the DeepSDF decoder (Sec. B.1: 9 FC layers, hidden 512, latent
+ * 256, DeepSDF's skip concatenation).  Layer 0 reads [z (latent_dim), x, y, z];
+ * layer `skip` reads [h, z, x, y, z] where h is the output of layer skip-1
+ * (width - latent_dim - 3 values); hidden layers use ReLU; layer n_hidden is
+ * the head (width -> 1) followed by tanh.  skip = -1: no skip layer. */
+typedef struct {
+  int latent_dim;
+  int width;       /* 128, 256, 384 or 512 */
+  int n_hidden;    /* 2..16 */
+  int skip;        /* -1 or 1..n_hidden-1 */
+} dist_decoder_desc;
+
+typedef struct dist_decoder dist_decoder;
+
+/* Upload a decoder.  W[l] (host, float32, row-major [out_l][in_l]) and b[l]
+ * (host, float32, [out_l]) for l = 0..n_hidden.  The library copies and
+ * repacks the weights (FP32 copies in both orientations, and BF16 tensor-core
+ * tiles when the shape is the DeepSDF one: width 512, 8 hidden, skip 4);
+ * the host arrays may be freed on return.  Synchronous; allocates.
+ * Errors: DIST_E_INVALID (bad desc / NULL), DIST_E_NOMEM, DIST_E_CUDA. */
+dist_status dist_decoder_create(const dist_decoder_desc* desc,
+                                const float* const* W, const float* const* b,
+                                dist_decoder** out);
+dist_status dist_decoder_destroy(dist_decoder* dec);
+/* 1 if the BF16 tensor-core MLP covers this decoder, else 0. */
+int dist_decoder_has_bf16(const dist_decoder* dec);
+
+/* ----------------------------------------------------------------- camera */
+
+typedef struct {
+  float fx, fy, cx, cy;  /* pinhole intrinsics K (pixels) */
+  float R[9];            /* camera-to-world rotation, row-major; its columns
+                            are the camera x, y, z axes in world frame    */
+  float c[3];            /* camera centre in world frame                  */
+  int H, W;              /* image size                                     */
+  int shape;             /* index of this camera's latent code            */
+} dist_camera;
+
+/* ------------------------------------------------------------- parameters */
+
+typedef struct {
+  int max_steps;       /* queries per ray (Sec. B.4 uses 100; Tab. 1 50)   */
+  float eps;           /* convergence threshold on |f| (Sec. 3.2: 5e-5)    */
+  float alpha;         /* aggressive marching factor (Sec. 3.2: 1.5)       */
+  int k_min;           /* samples with the smallest |f| kept per ray for the
+                          paper's gradient (Sec. B.4: K = 1 or 3); 1..3    */
+  float normal_delta;  /* 0: analytic normals; > 0: central differences
+                          with this step (Sec. 3.3)                         */
+  int grad_mode;       /* dist_grad_mode for the depth term                */
+  int precision;       /* dist_precision of the marching queries           */
+  float eps_bf16;      /* BF16 path: |f_bf16| below which a ray switches
+                          to FP32 queries (then converges on eps)          */
+  float radius;        /* bounding sphere radius (Sec. 3.2: unit sphere)   */
+} dist_trace_params;
+
+/* Fill `p` with the paper's defaults: max_steps 50, eps 5e-5, alpha 1.5,
+ * k_min 1, normal_delta 0, exact gradients, FP32, eps_bf16 1e-3, radius 1. */
+void dist_trace_params_default(dist_trace_params* p);
+
+/* -------------------------------------------------------------- workspace */
+
+typedef struct dist_workspace dist_workspace;
+
+/* Library-owned device scratch for up to `max_rays` pixels per call: ray
+ * state (32 B/ray), active-ray lists and per-step counters.  Allocates
+ * (synchronous).  One workspace must not be used by two calls that overlap
+ * on the device. */
+dist_status dist_workspace_create(int64_t max_rays, int max_steps,
+                                  dist_workspace** out);
+dist_status dist_workspace_destroy(dist_workspace* ws);
+
+/* ----------------------------------------------------------------- tracing */
+
+/* Per-pixel results, caller-owned DEVICE buffers of n_pixels (= sum H*W)
+ * entries unless stated.  Pointers marked "optional" may be NULL. */
+typedef struct {
+  float* depth;      /* z_c = d / sqrt(x~^2+y~^2+1) (Sec. 3.3); +inf = bg  */
+  float* sil;        /* soft silhouette: min_n |f(p_n)| - eps, or
+                        dist(origin, ray) - radius for rays missing the
+                        bounding sphere (Sec. A.3); < 0 <=> hit             */
+  uint8_t* mask;     /* 1 = converged hit                                   */
+  int32_t* steps;    /* queries made for the ray                            */
+  int32_t* status;   /* DIST_RAY_* outcome (optional)                       */
+  float* d_hit;      /* ray distance after the unit final step (Eq. 1);
+                        +inf when not a hit                                 */
+  float* d_min;      /* [n_pixels][k_min] ray distances of the k samples
+                        with the smallest |f| (ascending |f|), NaN if fewer */
+  float* f_min;      /* [n_pixels][k_min] signed f at those samples         */
+  float* normal;     /* [n_pixels][3] (optional): filled by dist_trace_fwd
+                        when non-NULL, else by dist_render_normals          */
+  unsigned long long* queries;  /* optional, device [2]: += MLP queries made
+                        while marching, [0] BF16, [1] FP32                  */
+} dist_trace_out;
+
+/* Forward render: unit-sphere initialisation (Sec. 3.2), then up to
+ * max_steps iterations of {compact the unfinished rays, query the MLP,
+ * converge/step} (Alg. 1 with aggressive marching and dynamic synchronized
+ * inference, Sec. 3.2 and B.2), then depth / silhouette / mask (Sec. 3.3).
+ * z: device float [n_shapes][latent_dim].  cams: HOST array of n_cams.
+ * Errors: DIST_E_INVALID (NULL/sizes, n_pixels > workspace, camera inside
+ * the bounding sphere, shape index out of range, k_min outside 1..3),
+ * DIST_E_UNSUPPORTED (BF16 asked, decoder not covered), DIST_E_CUDA. */
+dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes,
+                           const dist_camera* cams, int n_cams,
+                           const dist_trace_params* params,
+                           const dist_trace_out* out, dist_workspace* ws,
+                           void* stream);
+
+/* Surface normals at the hits of a previous dist_trace_fwd (same arguments;
+ * reads out->mask and out->d_hit): the normalised analytic gradient of f
+ * (normal_delta = 0) or the paper's central differences (Sec. 3.3).
+ * normal: device float [n_pixels][3]; zero for non-hit pixels. */
+dist_status dist_render_normals(const dist_decoder* dec, const float* z, int n_shapes,
+                                const dist_camera* cams, int n_cams,
+                                const dist_trace_params* params,
+                                const dist_trace_out* fwd, float* normal,
+                                dist_workspace* ws, void* stream);
+
+/* Evaluate the decoder f(p, z_shape) (Sec. 3.4: f_theta(p, z)) at n points:
+ * pts: device float [n][3]; shape: device int32 [n] latent index per point;
+ * f: device float [n]; grad: device float [n][3] = grad_p f, or NULL.
+ * precision DIST_PREC_FP32 (SIMT kernels; grad allowed) or DIST_PREC_BF16
+ * (tensor-core kernel; grad must be NULL).  n <= 10 * workspace max_rays.
+ * Shape indices outside [0, n_shapes) are clamped into range.
+ * Errors: DIST_E_INVALID, DIST_E_UNSUPPORTED, DIST_E_CUDA. */
+dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
+                          const float* pts, const int32_t* shape, int64_t n, int precision,
+                          float* f, float* grad, dist_workspace* ws, void* stream);
+
+/* ------------------------------------------------------------------- loss */
+
+typedef struct {
+  float w_depth;   /* L1 depth (Sec. 4.2.1, B.3)                         */
+  float w_normal;  /* negative dot product of normals (Sec. B.3)         */
+  float w_sil;     /* silhouette loss, Eq. 4 of Sec. A.3                  */
+  float w_reg;     /* ||z||^2 regulariser (Sec. B.4)                      */
+} dist_loss_weights;
+
+/* Image-plane loss of a rendered batch and its per-pixel upstream gradients.
+ * Depth and normal terms are means over M = (rendered hit) and (target depth
+ * finite) (Sec. B.3: over the rendered foreground); the silhouette term is a
+ * mean over all pixels; the regulariser is w_reg * sum ||z||^2.
+ * Inputs (device): depth, mask, sil, normal (NULL if w_normal == 0), targets
+ * tgt_depth [n] (+inf = background), tgt_normal [n][3] (NULL if unused),
+ * tgt_sil [n] (1 = foreground; NULL if unused), z [n_shapes][latent_dim].
+ * Outputs (device): loss (double, 1 value, overwritten), g_depth [n],
+ * g_normal [n][3] (may be NULL if w_normal == 0), g_sil [n] (may be NULL if
+ * w_sil == 0), dz [n_shapes][latent_dim] OVERWRITTEN with 2 w_reg z, so that
+ * dist_trace_bwd can accumulate into it.  The workspace provides the small
+ * reduction scratch. */
+dist_status dist_loss(int64_t n_pixels, const float* depth, const uint8_t* mask,
+                      const float* sil, const float* normal,
+                      const float* tgt_depth, const float* tgt_normal,
+                      const float* tgt_sil, const float* z, int n_shapes, int latent_dim,
+                      const dist_loss_weights* w, double* loss,
+                      float* g_depth, float* g_normal, float* g_sil, float* dz,
+                      dist_workspace* ws, void* stream);
+
+/* --------------------------------------------------------------- backward */
+
+/* dL/dz += sum over pixels of upstream gradients times the latent Jacobians
+ * of the rendered depth, normal and silhouette (device dz [n_shapes][L],
+ * ACCUMULATED).  Depth: grad_mode EXACT differentiates the converged root
+ * implicitly, dd/dz = -(df/dz)/(grad_p f . v) at the hit (grazing rays,
+ * |grad_p f . v| < 1e-3 |grad_p f|, contribute 0); PAPER keeps the first term
+ * of Eq. 2 over the k_min smallest-|f| samples, alpha * sum_k df(p_k)/dz
+ * (Sec. 3.4, B.2).  Silhouette: sign(f_min) df(p_min)/dz (Sec. A.3 with the
+ * first-term rule).  Normal: needs normal_delta > 0; VJP of the central-
+ * difference normal with the hit point held fixed.  The decoder is
+ * re-evaluated at these points only (no per-step graph is stored).
+ * Upstream gradients g_depth [n], g_normal [n][3], g_sil [n] are device
+ * arrays or NULL.  Per-ray sums are reduced in FP64. */
+dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes,
+                           const dist_camera* cams, int n_cams,
+                           const dist_trace_params* params,
+                           const dist_trace_out* fwd,
+                           const float* g_depth, const float* g_normal,
+                           const float* g_sil, float* dz,
+                           dist_workspace* ws, void* stream);
+
+/* ---------------------------------------------------------------- serving */
+
+typedef struct dist_server dist_server;
+
+typedef enum { DIST_REQ_RENDER = 0, DIST_REQ_RENDER_BACKWARD = 1 } dist_request_kind;
+
+/* One request.  All pointers are HOST memory owned by the caller and must
+ * stay valid until dist_serve_poll reports the request done. */
+typedef struct {
+  int kind;                  /* dist_request_kind                          */
+  dist_camera cam;           /* cam.shape is ignored                       */
+  const float* z;            /* [latent_dim] latent code                   */
+  const float* tgt_depth;    /* [H*W], RENDER_BACKWARD only (L1 depth)     */
+  float* depth;              /* [H*W] out                                  */
+  float* sil;                /* [H*W] out (optional)                       */
+  uint8_t* mask;             /* [H*W] out (optional)                       */
+  float* dz;                 /* [latent_dim] out, RENDER_BACKWARD only     */
+  double* loss;              /* out, RENDER_BACKWARD only                  */
+} dist_request;
+
+/* A continuous-batching render server on its own thread and stream: requests
+ * are admitted while the ray pool (max_rays) and the device-memory budget
+ * allow, their rays march together with those already in flight, and each
+ * request completes as soon as its own rays finish.  Allocates. */
+dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* params,
+                              int64_t max_rays, size_t mem_budget_bytes,
+                              int max_requests, dist_server** out);
+/* Non-blocking.  DIST_E_INVALID for a malformed request, DIST_E_NOMEM if the
+ * request alone exceeds the pool or the budget, DIST_E_BUSY if the queue of
+ * pending requests is full. */
+dist_status dist_serve_submit(dist_server* s, const dist_request* req, uint64_t* ticket);
+/* Non-blocking: *done = 1 once the request's outputs are in its host buffers
+ * (the ticket is then retired), else 0. DIST_E_INVALID for an unknown
+ * ticket; a failed request returns its error status. */
+dist_status dist_serve_poll(dist_server* s, uint64_t ticket, int* done);
+/* Stops the server thread (bounded wait) and frees its memory. */
+dist_status dist_serve_destroy(dist_server* s);
+
+/* ------------------------------------------------------------------- misc */
+
+/* Message of the last error on the calling thread ("" if none). */
+const char* dist_last_error(void);
+/* Library version string. */
+const char* dist_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIST_H */

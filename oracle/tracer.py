@@ -58,11 +58,13 @@ def unit_sphere_init(c, v, radius=1.0):
     return enters, t_in, t_out, dist
 
 
-def march(f, c, v, shape, t_in, t_out, enters, max_steps, eps, alpha, k_min=1):
+def march(f, c, v, shape, t_in, t_out, enters, max_steps, eps, alpha, k_min=1,
+          record=False):
     """Sphere-trace every ray (vectorised over rays, looped over steps).
 
     ``c`` is (3,) or (n, 3); ``f(p, shape)`` returns the SDF for points p.
-    Returns a dict of per-ray arrays."""
+    Returns a dict of per-ray arrays; with ``record`` also every sample's
+    ray distance and f as (n, max_steps) arrays (NaN past the last query)."""
     n = v.shape[0]
     c = np.broadcast_to(np.asarray(c, dtype=np.float64), (n, 3))
     d = np.where(enters, t_in, 0.0).astype(np.float64)
@@ -75,12 +77,17 @@ def march(f, c, v, shape, t_in, t_out, enters, max_steps, eps, alpha, k_min=1):
     topk_f = np.full((n, k_min), np.inf)      # |f| of the k smallest samples
     topk_d = np.full((n, k_min), np.nan)      # their ray distances
     topk_s = np.full((n, k_min), np.nan)      # their signed f
-    for _ in range(max_steps):
+    rec_d = np.full((n, max_steps), np.nan) if record else None
+    rec_f = np.full((n, max_steps), np.nan) if record else None
+    for it in range(max_steps):
         idx = np.nonzero(active)[0]
         if idx.size == 0:
             break
         p = c[idx] + d[idx, None] * v[idx]
         s = np.asarray(f(p, shape[idx]), dtype=np.float64)
+        if record:
+            rec_d[idx, it] = d[idx]
+            rec_f[idx, it] = s
         steps[idx] += 1
         f_last[idx] = s
         d_last[idx] = d[idx]
@@ -115,11 +122,12 @@ def march(f, c, v, shape, t_in, t_out, enters, max_steps, eps, alpha, k_min=1):
         "f_last": f_last, "d_last": d_last,
         "min_abs_f": topk_f[:, 0], "d_at_min": topk_d[:, 0], "f_at_min": topk_s[:, 0],
         "topk_f": topk_f, "topk_d": topk_d, "topk_s": topk_s,
+        "rec_d": rec_d, "rec_f": rec_f,
     }
 
 
 def render(sdf, cams, max_steps=50, eps=5e-5, alpha=1.5, normal_delta=0.0,
-           k_min=1, radius=1.0, with_normals=True):
+           k_min=1, radius=1.0, with_normals=True, record=False):
     """Trace all pixels of all cameras; outputs are concatenated in camera
     order, each camera's pixels row-major.  ``cam["shape"]`` selects the
     latent (the SDF's ``shape`` argument)."""
@@ -139,7 +147,7 @@ def render(sdf, cams, max_steps=50, eps=5e-5, alpha=1.5, normal_delta=0.0,
     shape = np.concatenate(shapes)
     enters, t_in, t_out, dist = unit_sphere_init(c, v, radius)
 
-    out = march(sdf, c, v, shape, t_in, t_out, enters, max_steps, eps, alpha, k_min)
+    out = march(sdf, c, v, shape, t_in, t_out, enters, max_steps, eps, alpha, k_min, record)
     hit = out["status"] == HIT
     depth = np.where(hit, depth_from_distance(out["d_hit"], inv_norm), np.inf)
     sil = np.where(enters, out["min_abs_f"] - eps, dist - radius)

@@ -1,0 +1,171 @@
+// Internal definitions shared by the libdist translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/dist.h"
+
+namespace dist {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string& msg);
+
+#define DIST_CUDA_TRY(call)                                                   \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) {                                                  \
+      ::dist::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));  \
+      return DIST_E_CUDA;                                                     \
+    }                                                                         \
+  } while (0)
+
+#define DIST_CHECK(cond, code, msg)                                           \
+  do {                                                                        \
+    if (!(cond)) {                                                            \
+      ::dist::set_error(msg);                                                 \
+      return code;                                                            \
+    }                                                                         \
+  } while (0)
+
+constexpr int kMaxShapes = 1024;    // folded-bias capacity of a workspace
+constexpr int kMaxK = 3;            // k_min upper bound (Sec. B.4 uses 1 or 3)
+constexpr int kProbesPerRay = 10;   // probe capacity per pixel in a workspace:
+                                    // <= 4 depth/silhouette + 6 normal probes
+
+// ------------------------------------------------------------- camera table
+
+// One camera as the kernels see it.
+struct CamDev {
+  float c[3];
+  float R[9];
+  float fx, fy, cx, cy;
+  int H, W;
+  int shape;
+  int pad;
+  long long offset;   // first pixel index of this camera
+};
+
+// ------------------------------------------------------------------ decoder
+
+// Weights repacked for the FP32 SIMT kernels.  Every hidden layer is padded
+// to a square WIDTH x WIDTH block with zeros so that all layers share one
+// tiling; padded outputs have zero weight and bias and so stay 0 after ReLU.
+struct DecoderF32 {
+  int width, n_hidden, skip, latent;
+  int kh[16];          // h-part input count of each hidden layer (0 for layer 0)
+  int nout[16];        // real output count of each hidden layer
+  const float* Wt[16];   // [WIDTH k][WIDTH j] = W_l[j][h-col k]   (forward)
+  const float* Wb[16];   // [WIDTH j][WIDTH k] = W_l[j][h-col k]   (backward)
+  const float* b[16];    // [WIDTH]
+  const float* Wx0;      // [WIDTH][4]  xyz columns of layer 0
+  const float* Wxs;      // [WIDTH][4]  xyz columns of the skip layer (or null)
+  const float* Wz0;      // [WIDTH][latent] latent columns of layer 0
+  const float* Wzs;      // [WIDTH][latent] latent columns of the skip layer
+  const float* w_head;   // [WIDTH]
+  float b_head;
+};
+
+// BF16 tensor-core packing of the DeepSDF shape (width 512, 8 hidden, skip 4).
+struct DecoderTC {
+  bool ok;
+  const __nv_bfloat16* W[8];     // GEMM layers 1..7: [N rows][K cols] K-major bf16
+  int n_rows[8], k_cols[8];
+};
+
+}  // namespace dist
+
+struct dist_decoder {
+  dist_decoder_desc desc;
+  dist::DecoderF32 f32;
+  dist::DecoderTC tc;
+  std::vector<void*> allocations;
+};
+
+struct dist_workspace {
+  int64_t max_rays;
+  int max_steps;
+  // ray state
+  float4* dir;        // (vx, vy, vz, 1/sqrt(x~^2+y~^2+1))
+  float4* st;         // (d, t_in, t_out, camera index as int bits)
+  int* act[2][2];     // [parity][0 = BF16 list, 1 = FP32 list] active ray ids
+  float* fbuf[2];     // MLP outputs for the two lists
+  int* counts;        // [(max_steps + 2) * 2] list lengths per step
+  dist::CamDev* cams; // camera table (device)
+  int max_cams;
+  float* bfold;       // [2][kMaxShapes][512] folded latent biases
+  double* gacc;       // [2][kMaxShapes][512] FP64 latent-gradient accumulators
+  float4* probe_p;    // [max_rays * kProbesPerRay] (x, y, z, shape bits)
+  float4* probe_q;    // (vx, vy, vz, coefficient)
+  int* probe_pix;     // pixel of each probe
+  float* probe_out;   // [max_rays * kProbesPerRay][4] f and grad_p per probe
+  int* probe_count;   // [4]
+  double* red;        // [8] small FP64 reduction scratch
+  int* ired;          // [8] small integer scratch
+  std::vector<void*> allocations;
+};
+
+namespace dist {
+
+// ------------------------------------------------------- device helpers
+
+__device__ __forceinline__ float3 cam_origin(const CamDev& c) {
+  return make_float3(c.c[0], c.c[1], c.c[2]);
+}
+
+// Row sources for the MLP kernels: rays of an active list, or explicit points.
+struct RowSrc {
+  const int* count;        // device: number of rows (null -> n_rows)
+  int n_rows;
+  const int* idx;          // active list of ray ids (rays mode)
+  const float4* st;
+  const float4* dir;
+  const CamDev* cams;
+  const float4* pts;       // points mode: (x, y, z, shape as int bits)
+};
+
+__device__ __forceinline__ int rowsrc_count(const RowSrc& s) {
+  return s.count ? *s.count : s.n_rows;
+}
+
+__device__ __forceinline__ void rowsrc_load(const RowSrc& s, int j, float3& p, int& shape) {
+  if (s.pts) {
+    float4 q = s.pts[j];
+    p = make_float3(q.x, q.y, q.z);
+    shape = __float_as_int(q.w);
+  } else {
+    int i = s.idx[j];
+    float4 st = s.st[i];
+    float4 dv = s.dir[i];
+    const CamDev& c = s.cams[__float_as_int(st.w)];
+    p = make_float3(fmaf(st.x, dv.x, c.c[0]), fmaf(st.x, dv.y, c.c[1]), fmaf(st.x, dv.z, c.c[2]));
+    shape = c.shape;
+  }
+}
+
+// ------------------------------------------------------------ launchers
+
+int num_sms();
+
+// FP32 SIMT decoder forward over `src` rows: fout[j] = f(p_j, z_shape_j).
+cudaError_t mlp_fp32_forward(const DecoderF32& d, const RowSrc& src, const float* bfold0,
+                             const float* bfolds, float* fout, cudaStream_t st);
+
+// FP32 SIMT adjoint over probes: f and grad_p f per probe (out4, optional) and
+// FP64 accumulation of coef * (pre-activation gradients at layer 0 and the
+// skip layer) into gacc0 / gaccs [shape][WIDTH] (when accumulate != 0).
+cudaError_t mlp_fp32_adjoint(const DecoderF32& d, const float4* pp, const float4* pq,
+                             const int* count, const float* bfold0, const float* bfolds,
+                             float* out4, double* gacc0, double* gaccs, int accumulate,
+                             cudaStream_t st);
+
+// BF16 tcgen05 decoder forward (DeepSDF shape only).
+cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
+                           const float* bfolds, float* fout, cudaStream_t st);
+
+}  // namespace dist

@@ -1,0 +1,856 @@
+// Sphere tracing on the device: ray generation with unit-sphere
+// initialisation, the per-step converge/step/compact update, normals, the
+// backward probes and the image-plane losses, plus their C-ABI entry points.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace dist {
+
+namespace {
+
+constexpr float kInf = __builtin_huge_valf();
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Warp-aggregated append: lanes with `pred` get consecutive slots of `list`
+// (one atomic per warp).  Must be called by all 32 lanes.
+__device__ __forceinline__ int warp_append(bool pred, int* counter) {
+  const unsigned m = __ballot_sync(0xffffffffu, pred);
+  if (m == 0) return -1;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane_id() == leader) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  return pred ? base + __popc(m & ((1u << lane_id()) - 1u)) : -1;
+}
+
+// Warp-aggregated append of `k` consecutive slots per lane (k may be 0).
+__device__ __forceinline__ int warp_append_n(int k, int* counter) {
+  int incl = k;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane_id() >= o) incl += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int base = 0;
+  if (total > 0 && lane_id() == 31) base = atomicAdd(counter, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + incl - k;
+}
+
+__device__ __forceinline__ int find_cam(const CamDev* cams, int n_cams, long long i) {
+  int lo = 0, hi = n_cams - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cams[mid].offset <= i) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------- cameras
+
+constexpr int kCamChunk = 40;
+struct CamChunk {
+  CamDev c[kCamChunk];
+  int n, first;
+};
+
+// Cameras travel as kernel parameters, so no host staging buffer has to
+// outlive the call.
+__global__ void write_cams_kernel(CamChunk ch, CamDev* dst) {
+  const int t = threadIdx.x;
+  if (t < ch.n) dst[ch.first + t] = ch.c[t];
+}
+
+// --------------------------------------------------------- latent folding
+
+// b'[s][j] = b[j] + sum_k W_z[j][k] z[s][k] for layer 0 (y = 0) and the skip
+// layer (y = 1): the latent part of the concatenated input [z, p] is the same
+// for every query of a shape, so it is applied once per shape.
+__global__ void fold_bias_kernel(DecoderF32 d, const float* __restrict__ z, int n_shapes,
+                                 float* bfold0, float* bfolds) {
+  const int s = blockIdx.x;
+  const int which = blockIdx.y;
+  if (which == 1 && d.skip < 0) return;
+  const float* Wz = which == 0 ? d.Wz0 : d.Wzs;
+  const float* b = which == 0 ? d.b[0] : d.b[d.skip];
+  float* out = (which == 0 ? bfold0 : bfolds) + (size_t)s * d.width;
+  const int warp = threadIdx.x >> 5, lane = lane_id();
+  for (int j = blockIdx.z * 8 + warp; j < d.width; j += gridDim.z * 8) {
+    double acc = 0.0;
+    for (int k = lane; k < d.latent; k += 32)
+      acc += (double)Wz[(size_t)j * d.latent + k] * (double)z[(size_t)s * d.latent + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) out[j] = (float)(acc + (double)b[j]);
+  }
+}
+
+// -------------------------------------------------------------- ray setup
+
+struct TraceArgs {
+  const CamDev* cams;
+  int n_cams;
+  long long n_pix;
+  float radius;
+  int K;
+  float eps, alpha, eps_bf16;
+  int max_steps;
+  dist_trace_out o;
+  float4* st;
+  float4* dir;
+};
+
+// One thread per pixel (Sec. 3.2 "Initialization"): the ray through the
+// pixel centre, its entry/exit distances into the bounding sphere, and the
+// background outputs of rays that miss it (depth +inf, silhouette =
+// distance from the origin to the ray minus the radius, Sec. A.3).
+__global__ void raygen_kernel(TraceArgs a, int* list0, int* count0) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
+       base < a.n_pix; base += stride) {
+    const long long i = base + lane_id();
+    bool enters = false;
+    if (i < a.n_pix) {
+      const int ci = find_cam(a.cams, a.n_cams, i);
+      const CamDev& c = a.cams[ci];
+      const long long li = i - c.offset;
+      const int x = (int)(li % c.W), y = (int)(li / c.W);
+      const float xt = ((float)x + 0.5f - c.cx) / c.fx;
+      const float yt = ((float)y + 0.5f - c.cy) / c.fy;
+      const float inv = 1.0f / sqrtf(xt * xt + yt * yt + 1.0f);
+      const float vx0 = xt * inv, vy0 = yt * inv, vz0 = inv;
+      float vx = c.R[0] * vx0 + c.R[1] * vy0 + c.R[2] * vz0;
+      float vy = c.R[3] * vx0 + c.R[4] * vy0 + c.R[5] * vz0;
+      float vz = c.R[6] * vx0 + c.R[7] * vy0 + c.R[8] * vz0;
+      const float vn = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
+      vx *= vn; vy *= vn; vz *= vn;
+      const float b = vx * c.c[0] + vy * c.c[1] + vz * c.c[2];
+      // squared distance from the origin to the line, without cancellation
+      const float qx = c.c[0] - b * vx, qy = c.c[1] - b * vy, qz = c.c[2] - b * vz;
+      const float qq = qx * qx + qy * qy + qz * qz;
+      const float disc = a.radius * a.radius - qq;
+      const float sq = sqrtf(fmaxf(disc, 0.f));
+      const float t_in = -b - sq, t_out = -b + sq;
+      enters = disc > 0.f && t_out > 0.f;
+      a.dir[i] = make_float4(vx, vy, vz, inv);
+      a.o.steps[i] = 0;
+      for (int k = 0; k < a.K; ++k) {
+        a.o.d_min[i * a.K + k] = __int_as_float(0x7fc00000);
+        a.o.f_min[i * a.K + k] = kInf;
+      }
+      if (enters) {
+        a.st[i] = make_float4(t_in, t_in, t_out, __int_as_float(ci));
+      } else {
+        const float cc = c.c[0] * c.c[0] + c.c[1] * c.c[1] + c.c[2] * c.c[2];
+        const float dist = b < 0.f ? sqrtf(qq) : sqrtf(cc);
+        a.o.depth[i] = kInf;
+        a.o.d_hit[i] = kInf;
+        a.o.mask[i] = 0;
+        a.o.sil[i] = dist - a.radius;
+        if (a.o.status) a.o.status[i] = DIST_RAY_INIT_MISS;
+      }
+    }
+    const int slot = warp_append(enters, count0);
+    if (slot >= 0) list0[slot] = (int)i;
+  }
+}
+
+// ------------------------------------------------------------- march step
+
+struct StepLists {
+  const int* cnt_in;      // [2]: BF16 list, FP32 list
+  int* cnt_out;           // [2]
+  const int* in[2];
+  const float* f[2];
+  int* out[2];
+};
+
+// One march step for every ray that was queried this step (Alg. 1 with the
+// aggressive update of Sec. 3.2 and the stopping rules of Sec. 3.2 / B.2):
+//  * track the k smallest |f| (Sec. 3.4, B.2) -- ties keep the earlier sample;
+//  * |f| < eps: hit; the last query is a unit step, d_hit = d + f (Eq. 1);
+//  * else d += alpha f; leaving [t_in, t_out] or using the last query makes
+//    the ray background (Sec. B.2, A.2);
+//  * survivors are appended to the next step's list (dynamic synchronized
+//    inference, Sec. 3.2) with a warp-aggregated atomic.
+// BF16-phase rays (list 0) use eps_bf16 to switch to FP32 queries at the
+// same point; their samples enter the |f| tracking as max(|f|, eps) so that
+// only FP32 samples can make the silhouette negative.
+__global__ void step_kernel(TraceArgs a, StepLists L, unsigned long long* queries) {
+  const int n0 = L.cnt_in[0], n1 = L.cnt_in[1];
+  const int n = n0 + n1;
+  if (queries && blockIdx.x == 0 && threadIdx.x == 0) {
+    atomicAdd(queries + 0, (unsigned long long)n0);
+    atomicAdd(queries + 1, (unsigned long long)n1);
+  }
+  const int stride = gridDim.x * blockDim.x;
+  for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < n; base += stride) {
+    const int j = base + lane_id();
+    int keep = -1, ray = -1;
+    if (j < n) {
+      const int list = j < n0 ? 0 : 1;
+      const int jj = list == 0 ? j : j - n0;
+      const int i = L.in[list][jj];
+      const float f = L.f[list][jj];
+      ray = i;
+      float4 s = a.st[i];
+      const float d = s.x;
+      const int steps = a.o.steps[i] + 1;
+      a.o.steps[i] = steps;
+      const float af = fabsf(f);
+      const float track = list == 0 ? fmaxf(af, a.eps) : af;
+      // k smallest |f|, ascending
+      float* fm = a.o.f_min + (size_t)i * a.K;
+      float* dm = a.o.d_min + (size_t)i * a.K;
+      {
+        float cf = copysignf(track, f), cd = d;
+        for (int k = 0; k < a.K; ++k) {
+          const float ok = fm[k];
+          if (fabsf(cf) < fabsf(ok)) {
+            const float od = dm[k];
+            fm[k] = cf; dm[k] = cd;
+            cf = ok; cd = od;
+          }
+        }
+      }
+      int outcome = -1;   // -1 keep marching
+      float dn = d;
+      if (list == 1 && af < a.eps) {
+        outcome = DIST_RAY_HIT;
+      } else if (list == 0 && af < a.eps_bf16) {
+        keep = 1;       // switch to FP32 queries at the same point
+      } else {
+        dn = fmaf(a.alpha, f, d);
+        if (dn > s.z || dn < s.y) outcome = DIST_RAY_LEFT;
+        else keep = list;
+      }
+      if (outcome < 0 && steps >= a.max_steps) { outcome = DIST_RAY_MAX_STEPS; keep = -1; }
+      if (outcome == DIST_RAY_HIT) {
+        const float dh = d + f;
+        a.o.d_hit[i] = dh;
+        a.o.depth[i] = dh * a.dir[i].w;
+        a.o.mask[i] = 1;
+        a.o.sil[i] = fabsf(fm[0]) - a.eps;
+      } else if (outcome >= 0) {
+        a.o.d_hit[i] = kInf;
+        a.o.depth[i] = kInf;
+        a.o.mask[i] = 0;
+        a.o.sil[i] = fabsf(fm[0]) - a.eps;
+      } else if (keep == list) {
+        s.x = dn;
+        a.st[i] = s;
+      }
+      if (outcome >= 0 && a.o.status) a.o.status[i] = outcome;
+    }
+    const int s0 = warp_append(keep == 0, L.cnt_out + 0);
+    if (s0 >= 0) L.out[0][s0] = ray;
+    const int s1 = warp_append(keep == 1, L.cnt_out + 1);
+    if (s1 >= 0) L.out[1][s1] = ray;
+  }
+}
+
+// ---------------------------------------------------------------- probes
+
+struct ProbeArgs {
+  const CamDev* cams;
+  const float4* st;       // unused after the trace except for the camera id
+  const float4* dir;
+  long long n_pix;
+  int n_cams;
+  int K;
+  dist_trace_out o;
+  float4* pp;
+  float4* pq;
+  int* pix;
+  int* count;
+};
+
+__device__ __forceinline__ float4 ray_point(const CamDev& c, const float4& v, float d, int shape) {
+  return make_float4(fmaf(d, v.x, c.c[0]), fmaf(d, v.y, c.c[1]), fmaf(d, v.z, c.c[2]),
+                     __int_as_float(shape));
+}
+
+// Hit points of the trace (normals): one probe per hit pixel.
+__global__ void probes_hits_kernel(ProbeArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
+       base < a.n_pix; base += stride) {
+    const long long i = base + lane_id();
+    const bool hit = i < a.n_pix && a.o.mask[i];
+    const int slot = warp_append(hit, a.count);
+    if (slot >= 0) {
+      const CamDev& c = a.cams[find_cam(a.cams, a.n_cams, i)];
+      a.pp[slot] = ray_point(c, a.dir[i], a.o.d_hit[i], c.shape);
+      a.pq[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.pix[slot] = (int)i;
+    }
+  }
+}
+
+// Six probes per hit pixel at p_hit +- delta e_a (Sec. 3.3 central
+// differences), in the order +x, -x, +y, -y, +z, -z.  With `g_normal`
+// non-null only pixels with a non-zero normal gradient get probes.
+__global__ void probes_fd_kernel(ProbeArgs a, float delta, const float* g_normal) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
+       base < a.n_pix; base += stride) {
+    const long long i = base + lane_id();
+    bool take = i < a.n_pix && a.o.mask[i];
+    if (take && g_normal)
+      take = g_normal[3 * i] != 0.f || g_normal[3 * i + 1] != 0.f || g_normal[3 * i + 2] != 0.f;
+    const int slot = warp_append_n(take ? 6 : 0, a.count);
+    if (take) {
+      const CamDev& c = a.cams[find_cam(a.cams, a.n_cams, i)];
+      const float4 p = ray_point(c, a.dir[i], a.o.d_hit[i], c.shape);
+      for (int e = 0; e < 6; ++e) {
+        float4 q = p;
+        const float dlt = (e & 1) ? -delta : delta;
+        if (e < 2) q.x += dlt; else if (e < 4) q.y += dlt; else q.z += dlt;
+        a.pp[slot + e] = q;
+        a.pq[slot + e] = make_float4(0.f, 0.f, 0.f, 0.f);
+        a.pix[slot + e] = (int)i;
+      }
+    }
+  }
+}
+
+__global__ void normals_from_grad_kernel(const float* out4, const int* pix, const int* count,
+                                         float* normal) {
+  const int n = *count;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const float4 g = out4 ? reinterpret_cast<const float4*>(out4)[j] : make_float4(0, 0, 0, 0);
+    const float nn = sqrtf(g.y * g.y + g.z * g.z + g.w * g.w);
+    const float s = nn > 0.f ? 1.f / nn : 0.f;
+    const int i = pix[j];
+    normal[3 * i] = g.y * s; normal[3 * i + 1] = g.z * s; normal[3 * i + 2] = g.w * s;
+  }
+}
+
+__global__ void normals_from_fd_kernel(const float* f6, const int* pix, const int* count,
+                                       float delta, float* normal) {
+  const int n = *count / 6;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+    const float* f = f6 + 6 * h;
+    const float inv = 1.f / (2.f * delta);
+    const float gx = (f[0] - f[1]) * inv, gy = (f[2] - f[3]) * inv, gz = (f[4] - f[5]) * inv;
+    const float nn = sqrtf(gx * gx + gy * gy + gz * gz);
+    const float s = nn > 0.f ? 1.f / nn : 0.f;
+    const int i = pix[6 * h];
+    normal[3 * i] = gx * s; normal[3 * i + 1] = gy * s; normal[3 * i + 2] = gz * s;
+  }
+}
+
+// Backward probes for the depth and silhouette terms.
+//  exact depth: the hit point, q = (v, g_depth * inv_norm); the adjoint
+//    turns it into -q.w / (grad f . v) (implicit differentiation);
+//  paper depth: the k smallest-|f| samples, coefficient alpha g_depth inv_norm
+//    (first term of Eq. 2);
+//  silhouette: the smallest-|f| sample, coefficient g_sil sign(f_min).
+__global__ void probes_bwd_kernel(ProbeArgs a, const float* g_depth, const float* g_sil,
+                                  int paper, float alpha) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
+       base < a.n_pix; base += stride) {
+    const long long i = base + lane_id();
+    int nd = 0, ns = 0;
+    float gd = 0.f, gs = 0.f;
+    if (i < a.n_pix) {
+      gd = g_depth ? g_depth[i] : 0.f;
+      gs = g_sil ? g_sil[i] : 0.f;
+      if (a.o.mask[i] && gd != 0.f) {
+        if (!paper) nd = 1;
+        else
+          for (int k = 0; k < a.K; ++k) nd += isnan(a.o.d_min[i * a.K + k]) ? 0 : 1;
+      }
+      const float fm0 = a.o.f_min[i * a.K];
+      if (gs != 0.f && !isnan(a.o.d_min[i * a.K]) && fm0 != 0.f) ns = 1;
+    }
+    int slot = warp_append_n(nd + ns, a.count);
+    if (nd + ns > 0) {
+      const CamDev& c = a.cams[find_cam(a.cams, a.n_cams, i)];
+      const float4 v = a.dir[i];
+      if (nd > 0 && !paper) {
+        a.pp[slot] = ray_point(c, v, a.o.d_hit[i], c.shape);
+        a.pq[slot] = make_float4(v.x, v.y, v.z, gd * v.w);
+        a.pix[slot] = (int)i;
+        ++slot;
+      } else if (nd > 0) {
+        for (int k = 0; k < a.K; ++k) {
+          const float dk = a.o.d_min[i * a.K + k];
+          if (isnan(dk)) continue;
+          a.pp[slot] = ray_point(c, v, dk, c.shape);
+          a.pq[slot] = make_float4(0.f, 0.f, 0.f, alpha * gd * v.w);
+          a.pix[slot] = (int)i;
+          ++slot;
+        }
+      }
+      if (ns) {
+        const float fm0 = a.o.f_min[i * a.K];
+        a.pp[slot] = ray_point(c, v, a.o.d_min[i * a.K], c.shape);
+        a.pq[slot] = make_float4(0.f, 0.f, 0.f, fm0 > 0.f ? gs : -gs);
+        a.pix[slot] = (int)i;
+      }
+    }
+  }
+}
+
+// Normal-loss coefficients: with g = FD gradient from the six probe values
+// and n = g / |g|, dL/dg = (g_n - n (n . g_n)) / |g|; probe +a gets
+// dL/dg_a / (2 delta), probe -a its negative (hit point held fixed).
+__global__ void fd_coef_kernel(const float* f6, const int* pix, const int* count, float delta,
+                               const float* g_normal, float4* pq) {
+  const int n = *count / 6;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+    const float* f = f6 + 6 * h;
+    const double inv = 1.0 / (2.0 * (double)delta);
+    const double g[3] = {(f[0] - f[1]) * inv, (f[2] - f[3]) * inv, (f[4] - f[5]) * inv};
+    const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    const int i = pix[6 * h];
+    const double up[3] = {g_normal[3 * i], g_normal[3 * i + 1], g_normal[3 * i + 2]};
+    double c[3] = {0, 0, 0};
+    if (gn > 0) {
+      const double nv[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
+      const double nu = nv[0] * up[0] + nv[1] * up[1] + nv[2] * up[2];
+      for (int e = 0; e < 3; ++e) c[e] = (up[e] - nv[e] * nu) / gn * inv;
+    }
+    for (int e = 0; e < 3; ++e) {
+      pq[6 * h + 2 * e] = make_float4(0.f, 0.f, 0.f, (float)c[e]);
+      pq[6 * h + 2 * e + 1] = make_float4(0.f, 0.f, 0.f, (float)-c[e]);
+    }
+  }
+}
+
+// dz[s][k] += sum_j Wz0[j][k] G0[s][j] + sum_j Wzs[j][k] Gs[s][j]  (FP64).
+__global__ void latent_finalize_kernel(DecoderF32 d, const double* G0, const double* Gs,
+                                       int n_shapes, float* dz) {
+  const int s = blockIdx.y;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.latent; k += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < d.width; ++j) {
+      acc += (double)d.Wz0[(size_t)j * d.latent + k] * G0[(size_t)s * d.width + j];
+      if (d.skip > 0) acc += (double)d.Wzs[(size_t)j * d.latent + k] * Gs[(size_t)s * d.width + j];
+    }
+    dz[(size_t)s * d.latent + k] += (float)acc;
+  }
+}
+
+// ------------------------------------------------------------------ losses
+
+__device__ __forceinline__ double block_sum_d(double v, double* sh) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5;
+  if (lane_id() == 0) sh[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += sh[k];
+  __syncthreads();
+  return t;
+}
+
+__global__ void loss_count_kernel(long long n, const uint8_t* mask, const float* tgt, int* cnt) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll; base < n;
+       base += stride) {
+    const long long i = base + lane_id();
+    const bool m = i < n && mask[i] && isfinite(tgt[i]);
+    const unsigned b = __ballot_sync(0xffffffffu, m);
+    if (lane_id() == 0 && b) atomicAdd(cnt, __popc(b));
+  }
+}
+
+struct LossArgs {
+  long long n;
+  const float *depth, *sil, *normal, *tgt_depth, *tgt_normal, *tgt_sil;
+  const uint8_t* mask;
+  dist_loss_weights w;
+  const int* cnt;
+  double* loss;
+  float *g_depth, *g_normal, *g_sil;
+};
+
+// Per-pixel loss terms and upstream gradients (Sec. B.3; silhouette Eq. 4 of
+// Sec. A.3); FP64 block sums.
+__global__ void loss_terms_kernel(LossArgs a) {
+  __shared__ double sh[32];
+  const double nM = (double)max(*a.cnt, 1);
+  const double nA = (double)a.n;
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const bool M = a.mask[i] && isfinite(a.tgt_depth[i]);
+    if (a.w.w_depth != 0.f) {
+      const double r = M ? (double)a.depth[i] - (double)a.tgt_depth[i] : 0.0;
+      acc += a.w.w_depth * fabs(r) / nM;
+      a.g_depth[i] = (float)(a.w.w_depth * (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / nM);
+    } else if (a.g_depth) {
+      a.g_depth[i] = 0.f;
+    }
+    if (a.w.w_normal != 0.f) {
+      double dot = 0.0;
+      for (int e = 0; e < 3; ++e) dot += (double)a.normal[3 * i + e] * (double)a.tgt_normal[3 * i + e];
+      if (M) acc += -a.w.w_normal * dot / nM;
+      for (int e = 0; e < 3; ++e)
+        a.g_normal[3 * i + e] = M ? (float)(-a.w.w_normal * a.tgt_normal[3 * i + e] / nM) : 0.f;
+    } else if (a.g_normal) {
+      for (int e = 0; e < 3; ++e) a.g_normal[3 * i + e] = 0.f;
+    }
+    if (a.w.w_sil != 0.f) {
+      const double S = a.sil[i], Sg = a.tgt_sil[i];
+      acc += a.w.w_sil * (Sg * fmax(0.0, S) + (1.0 - Sg) * fmax(0.0, -S)) / nA;
+      a.g_sil[i] = (float)(a.w.w_sil * (Sg * (S > 0 ? 1.0 : 0.0) - (1.0 - Sg) * (S < 0 ? 1.0 : 0.0)) / nA);
+    } else if (a.g_sil) {
+      a.g_sil[i] = 0.f;
+    }
+  }
+  const double t = block_sum_d(acc, sh);
+  if (threadIdx.x == 0 && t != 0.0) atomicAdd(a.loss, t);
+}
+
+// ||z||^2 regulariser (Sec. B.4): loss += w sum z^2, dz = 2 w z.
+__global__ void loss_reg_kernel(const float* z, long long nz, float w, double* loss, float* dz) {
+  __shared__ double sh[32];
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nz;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double zi = z[i];
+    acc += (double)w * zi * zi;
+    if (dz) dz[i] = (float)(2.0 * w * zi);
+  }
+  const double t = block_sum_d(acc, sh);
+  if (threadIdx.x == 0 && t != 0.0) atomicAdd(loss, t);
+}
+
+// Shape indices are clamped into [0, n_shapes) so no kernel reads outside the
+// folded-bias table.
+__global__ void pack_points_kernel(const float* __restrict__ pts, const int* __restrict__ shape,
+                                   long long n, int n_shapes, float4* out, int* count) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *count = (int)n;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int s = min(max(shape[i], 0), n_shapes - 1);
+    out[i] = make_float4(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], __int_as_float(s));
+  }
+}
+
+__global__ void unpack_grad_kernel(const float* out4, long long n, float* f, float* grad) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const float4 v = reinterpret_cast<const float4*>(out4)[i];
+    f[i] = v.x;
+    grad[3 * i] = v.y; grad[3 * i + 1] = v.z; grad[3 * i + 2] = v.w;
+  }
+}
+
+// -------------------------------------------------------------- host side
+
+int grid_for(long long n, int threads) {
+  long long g = (n + threads - 1) / threads;
+  const long long cap = (long long)num_sms() * 8;
+  if (g > cap) g = cap;
+  return (int)(g < 1 ? 1 : g);
+}
+
+struct Prepared {
+  long long n_pix;
+  cudaStream_t st;
+};
+
+dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_shapes,
+                                const dist_camera* cams, int n_cams,
+                                const dist_trace_params* p, const dist_trace_out* o,
+                                dist_workspace* ws, void* stream, Prepared* out) {
+  DIST_CHECK(dec && z && cams && p && o && ws, DIST_E_INVALID, "NULL argument");
+  DIST_CHECK(n_cams >= 1 && n_cams <= ws->max_cams, DIST_E_INVALID, "n_cams out of range");
+  DIST_CHECK(n_shapes >= 1 && n_shapes <= kMaxShapes, DIST_E_INVALID, "n_shapes out of range");
+  DIST_CHECK(p->max_steps >= 1 && p->max_steps <= ws->max_steps, DIST_E_INVALID,
+             "max_steps must be 1..workspace max_steps");
+  DIST_CHECK(p->k_min >= 1 && p->k_min <= kMaxK, DIST_E_INVALID, "k_min must be 1..3");
+  DIST_CHECK(p->eps > 0.f && p->alpha > 0.f && p->radius > 0.f && p->normal_delta >= 0.f,
+             DIST_E_INVALID, "eps, alpha, radius must be > 0 and normal_delta >= 0");
+  DIST_CHECK(p->precision == DIST_PREC_FP32 || p->precision == DIST_PREC_BF16, DIST_E_INVALID,
+             "bad precision");
+  DIST_CHECK(p->grad_mode == DIST_GRAD_EXACT || p->grad_mode == DIST_GRAD_PAPER, DIST_E_INVALID,
+             "bad grad_mode");
+  DIST_CHECK(p->precision != DIST_PREC_BF16 || dec->tc.ok, DIST_E_UNSUPPORTED,
+             "BF16 tensor-core MLP covers only the DeepSDF decoder shape (512 x 8, skip 4, latent 256)");
+  DIST_CHECK(o->depth && o->sil && o->mask && o->steps && o->d_hit && o->d_min && o->f_min,
+             DIST_E_INVALID, "dist_trace_out: NULL required buffer");
+  long long n_pix = 0;
+  CamChunk ch;
+  std::memset(&ch, 0, sizeof(ch));
+  cudaStream_t st = (cudaStream_t)stream;
+  for (int c = 0; c < n_cams; ++c) {
+    const dist_camera& k = cams[c];
+    DIST_CHECK(k.H > 0 && k.W > 0 && (long long)k.H * k.W <= (1ll << 31), DIST_E_INVALID,
+               "camera image size out of range");
+    DIST_CHECK(k.shape >= 0 && k.shape < n_shapes, DIST_E_INVALID, "camera shape index out of range");
+    DIST_CHECK(k.fx != 0.f && k.fy != 0.f, DIST_E_INVALID, "zero focal length");
+    const double cc = (double)k.c[0] * k.c[0] + (double)k.c[1] * k.c[1] + (double)k.c[2] * k.c[2];
+    DIST_CHECK(cc > (double)p->radius * p->radius, DIST_E_INVALID,
+               "camera inside the bounding sphere");
+    CamDev& d = ch.c[c % kCamChunk];
+    std::memcpy(d.c, k.c, sizeof(d.c));
+    std::memcpy(d.R, k.R, sizeof(d.R));
+    d.fx = k.fx; d.fy = k.fy; d.cx = k.cx; d.cy = k.cy;
+    d.H = k.H; d.W = k.W; d.shape = k.shape; d.pad = 0;
+    d.offset = n_pix;
+    n_pix += (long long)k.H * k.W;
+    if (c % kCamChunk == kCamChunk - 1 || c == n_cams - 1) {
+      ch.n = c % kCamChunk + 1;
+      ch.first = c - (c % kCamChunk);
+      write_cams_kernel<<<1, 64, 0, st>>>(ch, ws->cams);
+      DIST_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  DIST_CHECK(n_pix <= ws->max_rays, DIST_E_INVALID, "more pixels than the workspace holds");
+  const DecoderF32& d = dec->f32;
+  dim3 g(n_shapes, 2, (d.width + 63) / 64);
+  fold_bias_kernel<<<g, 256, 0, st>>>(d, z, n_shapes, ws->bfold, ws->bfold + kMaxShapes * 512);
+  DIST_CUDA_TRY(cudaGetLastError());
+  out->n_pix = n_pix;
+  out->st = st;
+  return DIST_OK;
+}
+
+TraceArgs make_args(const dist_trace_params* p, const dist_trace_out* o, dist_workspace* ws,
+                    int n_cams, long long n_pix) {
+  TraceArgs a;
+  a.cams = ws->cams; a.n_cams = n_cams; a.n_pix = n_pix; a.radius = p->radius; a.K = p->k_min;
+  a.eps = p->eps; a.alpha = p->alpha; a.eps_bf16 = p->eps_bf16; a.max_steps = p->max_steps;
+  a.o = *o; a.st = ws->st; a.dir = ws->dir;
+  return a;
+}
+
+ProbeArgs make_probe_args(const dist_trace_params* p, const dist_trace_out* o, dist_workspace* ws,
+                          int n_cams, long long n_pix, long long offset, int count_slot) {
+  ProbeArgs a;
+  a.cams = ws->cams; a.st = ws->st; a.dir = ws->dir; a.n_pix = n_pix; a.n_cams = n_cams;
+  a.K = p->k_min; a.o = *o;
+  a.pp = ws->probe_p + offset; a.pq = ws->probe_q + offset; a.pix = ws->probe_pix + offset;
+  a.count = ws->probe_count + count_slot;
+  return a;
+}
+
+dist_status normals_impl(const dist_decoder* dec, const dist_trace_params* p,
+                         const dist_trace_out* o, float* normal, dist_workspace* ws,
+                         int n_cams, long long n_pix, cudaStream_t st) {
+  const float* b0 = ws->bfold;
+  const float* bs = ws->bfold + kMaxShapes * 512;
+  DIST_CUDA_TRY(cudaMemsetAsync(normal, 0, (size_t)n_pix * 3 * sizeof(float), st));
+  DIST_CUDA_TRY(cudaMemsetAsync(ws->probe_count, 0, 8 * sizeof(int), st));
+  const int g = grid_for(n_pix, 256);
+  if (p->normal_delta == 0.f) {
+    ProbeArgs a = make_probe_args(p, o, ws, n_cams, n_pix, 0, 0);
+    probes_hits_kernel<<<g, 256, 0, st>>>(a);
+    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_CUDA_TRY(mlp_fp32_adjoint(dec->f32, ws->probe_p, nullptr, ws->probe_count, b0, bs,
+                                   ws->probe_out, nullptr, nullptr, 0, st));
+    normals_from_grad_kernel<<<g, 256, 0, st>>>(ws->probe_out, ws->probe_pix, ws->probe_count,
+                                                 normal);
+    DIST_CUDA_TRY(cudaGetLastError());
+  } else {
+    ProbeArgs a = make_probe_args(p, o, ws, n_cams, n_pix, 0, 0);
+    probes_fd_kernel<<<g, 256, 0, st>>>(a, p->normal_delta, nullptr);
+    DIST_CUDA_TRY(cudaGetLastError());
+    RowSrc src{};
+    src.count = ws->probe_count;
+    src.pts = ws->probe_p;
+    DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->probe_out, st));
+    normals_from_fd_kernel<<<g, 256, 0, st>>>(ws->probe_out, ws->probe_pix, ws->probe_count,
+                                               p->normal_delta, normal);
+    DIST_CUDA_TRY(cudaGetLastError());
+  }
+  return DIST_OK;
+}
+
+}  // namespace
+}  // namespace dist
+
+using namespace dist;
+
+extern "C" {
+
+dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes,
+                           const dist_camera* cams, int n_cams, const dist_trace_params* p,
+                           const dist_trace_out* o, dist_workspace* ws, void* stream) {
+  Prepared pr;
+  dist_status s = validate_and_upload(dec, z, n_shapes, cams, n_cams, p, o, ws, stream, &pr);
+  if (s != DIST_OK) return s;
+  cudaStream_t st = pr.st;
+  const long long n_pix = pr.n_pix;
+  TraceArgs a = make_args(p, o, ws, n_cams, n_pix);
+  DIST_CUDA_TRY(cudaMemsetAsync(ws->counts, 0, (size_t)(p->max_steps + 2) * 2 * sizeof(int), st));
+  const int first = p->precision == DIST_PREC_BF16 ? 0 : 1;
+  raygen_kernel<<<grid_for(n_pix, 256), 256, 0, st>>>(a, ws->act[0][first], ws->counts + first);
+  DIST_CUDA_TRY(cudaGetLastError());
+  const float* b0 = ws->bfold;
+  const float* bs = ws->bfold + kMaxShapes * 512;
+  const int step_grid = num_sms() * 4;
+  for (int s = 0; s < p->max_steps; ++s) {
+    const int par = s & 1;
+    int* cin = ws->counts + 2 * s;
+    int* cout = ws->counts + 2 * (s + 1);
+    RowSrc src{};
+    src.st = ws->st; src.dir = ws->dir; src.cams = ws->cams;
+    if (p->precision == DIST_PREC_BF16) {
+      src.count = cin + 0;
+      src.idx = ws->act[par][0];
+      DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, ws->fbuf[0], st));
+    }
+    src.count = cin + 1;
+    src.idx = ws->act[par][1];
+    DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->fbuf[1], st));
+    StepLists L;
+    L.cnt_in = cin; L.cnt_out = cout;
+    L.in[0] = ws->act[par][0]; L.in[1] = ws->act[par][1];
+    L.f[0] = ws->fbuf[0]; L.f[1] = ws->fbuf[1];
+    L.out[0] = ws->act[par ^ 1][0]; L.out[1] = ws->act[par ^ 1][1];
+    step_kernel<<<step_grid, 256, 0, st>>>(a, L, o->queries);
+    DIST_CUDA_TRY(cudaGetLastError());
+  }
+  if (o->normal) return normals_impl(dec, p, o, o->normal, ws, n_cams, n_pix, st);
+  return DIST_OK;
+}
+
+dist_status dist_render_normals(const dist_decoder* dec, const float* z, int n_shapes,
+                                const dist_camera* cams, int n_cams, const dist_trace_params* p,
+                                const dist_trace_out* fwd, float* normal, dist_workspace* ws,
+                                void* stream) {
+  DIST_CHECK(normal, DIST_E_INVALID, "dist_render_normals: NULL normal");
+  Prepared pr;
+  dist_status s = validate_and_upload(dec, z, n_shapes, cams, n_cams, p, fwd, ws, stream, &pr);
+  if (s != DIST_OK) return s;
+  return normals_impl(dec, p, fwd, normal, ws, n_cams, pr.n_pix, pr.st);
+}
+
+dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes,
+                           const dist_camera* cams, int n_cams, const dist_trace_params* p,
+                           const dist_trace_out* fwd, const float* g_depth,
+                           const float* g_normal, const float* g_sil, float* dz,
+                           dist_workspace* ws, void* stream) {
+  DIST_CHECK(dz, DIST_E_INVALID, "dist_trace_bwd: NULL dz");
+  DIST_CHECK(!g_normal || p == nullptr || p->normal_delta > 0.f, DIST_E_INVALID,
+             "dist_trace_bwd: a normal gradient needs normal_delta > 0 (the analytic normal of a "
+             "ReLU decoder has zero latent gradient almost everywhere)");
+  Prepared pr;
+  dist_status s = validate_and_upload(dec, z, n_shapes, cams, n_cams, p, fwd, ws, stream, &pr);
+  if (s != DIST_OK) return s;
+  cudaStream_t st = pr.st;
+  const long long n_pix = pr.n_pix;
+  const DecoderF32& d = dec->f32;
+  const float* b0 = ws->bfold;
+  const float* bs = ws->bfold + kMaxShapes * 512;
+  double* G0 = ws->gacc;
+  double* Gs = ws->gacc + kMaxShapes * 512;
+  DIST_CUDA_TRY(cudaMemsetAsync(G0, 0, (size_t)n_shapes * d.width * sizeof(double), st));
+  DIST_CUDA_TRY(cudaMemsetAsync(Gs, 0, (size_t)n_shapes * d.width * sizeof(double), st));
+  DIST_CUDA_TRY(cudaMemsetAsync(ws->probe_count, 0, 8 * sizeof(int), st));
+  const int g = grid_for(n_pix, 256);
+  if (g_depth || g_sil) {
+    ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, 0, 0);
+    probes_bwd_kernel<<<g, 256, 0, st>>>(a, g_depth, g_sil, p->grad_mode == DIST_GRAD_PAPER,
+                                         p->alpha);
+    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p, ws->probe_q, ws->probe_count, b0, bs, nullptr,
+                                   G0, Gs, 1, st));
+  }
+  if (g_normal) {
+    const long long off = 4 * (long long)ws->max_rays;
+    ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, off, 1);
+    probes_fd_kernel<<<g, 256, 0, st>>>(a, p->normal_delta, g_normal);
+    DIST_CUDA_TRY(cudaGetLastError());
+    RowSrc src{};
+    src.count = ws->probe_count + 1;
+    src.pts = ws->probe_p + off;
+    float* f6 = ws->probe_out + off * 4;
+    DIST_CUDA_TRY(mlp_fp32_forward(d, src, b0, bs, f6, st));
+    fd_coef_kernel<<<g, 256, 0, st>>>(f6, ws->probe_pix + off, ws->probe_count + 1,
+                                      p->normal_delta, g_normal, ws->probe_q + off);
+    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p + off, ws->probe_q + off, ws->probe_count + 1,
+                                   b0, bs, nullptr, G0, Gs, 1, st));
+  }
+  dim3 fg((d.latent + 127) / 128, n_shapes);
+  latent_finalize_kernel<<<fg, 128, 0, st>>>(d, G0, Gs, n_shapes, dz);
+  DIST_CUDA_TRY(cudaGetLastError());
+  return DIST_OK;
+}
+
+dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
+                          const float* pts, const int32_t* shape, int64_t n, int precision,
+                          float* f, float* grad, dist_workspace* ws, void* stream) {
+  DIST_CHECK(dec && z && pts && shape && f && ws, DIST_E_INVALID, "dist_sdf_eval: NULL argument");
+  DIST_CHECK(n >= 1 && n <= ws->max_rays * kProbesPerRay, DIST_E_INVALID,
+             "dist_sdf_eval: n must be 1..10 * workspace max_rays");
+  DIST_CHECK(n_shapes >= 1 && n_shapes <= kMaxShapes, DIST_E_INVALID, "n_shapes out of range");
+  DIST_CHECK(precision == DIST_PREC_FP32 || (precision == DIST_PREC_BF16 && !grad),
+             DIST_E_INVALID, "dist_sdf_eval: bad precision (BF16 has no gradient)");
+  DIST_CHECK(precision != DIST_PREC_BF16 || dec->tc.ok, DIST_E_UNSUPPORTED,
+             "BF16 tensor-core MLP covers only the DeepSDF decoder shape");
+  cudaStream_t st = (cudaStream_t)stream;
+  const DecoderF32& d = dec->f32;
+  dim3 fg(n_shapes, 2, (d.width + 63) / 64);
+  fold_bias_kernel<<<fg, 256, 0, st>>>(d, z, n_shapes, ws->bfold, ws->bfold + kMaxShapes * 512);
+  DIST_CUDA_TRY(cudaGetLastError());
+  const float* b0 = ws->bfold;
+  const float* bs = ws->bfold + kMaxShapes * 512;
+  const int g = grid_for(n, 256);
+  pack_points_kernel<<<g, 256, 0, st>>>(pts, shape, n, n_shapes, ws->probe_p, ws->probe_count);
+  DIST_CUDA_TRY(cudaGetLastError());
+  RowSrc src{};
+  src.count = ws->probe_count;
+  src.pts = ws->probe_p;
+  if (precision == DIST_PREC_BF16) {
+    DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, f, st));
+  } else if (!grad) {
+    DIST_CUDA_TRY(mlp_fp32_forward(d, src, b0, bs, f, st));
+  } else {
+    DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p, nullptr, ws->probe_count, b0, bs,
+                                   ws->probe_out, nullptr, nullptr, 0, st));
+    unpack_grad_kernel<<<g, 256, 0, st>>>(ws->probe_out, n, f, grad);
+    DIST_CUDA_TRY(cudaGetLastError());
+  }
+  return DIST_OK;
+}
+
+dist_status dist_loss(int64_t n, const float* depth, const uint8_t* mask, const float* sil,
+                      const float* normal, const float* tgt_depth, const float* tgt_normal,
+                      const float* tgt_sil, const float* z, int n_shapes, int latent_dim,
+                      const dist_loss_weights* w, double* loss, float* g_depth, float* g_normal,
+                      float* g_sil, float* dz, dist_workspace* ws, void* stream) {
+  DIST_CHECK(n >= 1 && depth && mask && tgt_depth && w && loss && ws, DIST_E_INVALID,
+             "dist_loss: NULL argument or empty batch");
+  DIST_CHECK(w->w_depth == 0.f || g_depth, DIST_E_INVALID, "dist_loss: g_depth required");
+  DIST_CHECK(w->w_normal == 0.f || (normal && tgt_normal && g_normal), DIST_E_INVALID,
+             "dist_loss: normal terms need normal, tgt_normal and g_normal");
+  DIST_CHECK(w->w_sil == 0.f || (sil && tgt_sil && g_sil), DIST_E_INVALID,
+             "dist_loss: silhouette terms need sil, tgt_sil and g_sil");
+  DIST_CHECK(w->w_reg == 0.f || (z && n_shapes > 0 && latent_dim > 0), DIST_E_INVALID,
+             "dist_loss: regulariser needs z");
+  cudaStream_t st = (cudaStream_t)stream;
+  DIST_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(double), st));
+  DIST_CUDA_TRY(cudaMemsetAsync(ws->ired, 0, sizeof(int), st));
+  const int g = grid_for(n, 256);
+  loss_count_kernel<<<g, 256, 0, st>>>(n, mask, tgt_depth, ws->ired);
+  DIST_CUDA_TRY(cudaGetLastError());
+  LossArgs a;
+  a.n = n; a.depth = depth; a.sil = sil; a.normal = normal; a.tgt_depth = tgt_depth;
+  a.tgt_normal = tgt_normal; a.tgt_sil = tgt_sil; a.mask = mask; a.w = *w; a.cnt = ws->ired;
+  a.loss = loss; a.g_depth = g_depth; a.g_normal = g_normal; a.g_sil = g_sil;
+  loss_terms_kernel<<<g, 256, 0, st>>>(a);
+  DIST_CUDA_TRY(cudaGetLastError());
+  if (dz && z && n_shapes > 0 && latent_dim > 0) {
+    const long long nz = (long long)n_shapes * latent_dim;
+    loss_reg_kernel<<<grid_for(nz, 256), 256, 0, st>>>(z, nz, w->w_reg, loss, dz);
+    DIST_CUDA_TRY(cudaGetLastError());
+  }
+  return DIST_OK;
+}
+
+}  // extern "C"

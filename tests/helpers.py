@@ -1,0 +1,62 @@
+"""Shared helpers for the GPU parity tests: seeded workloads and the
+classification of rays whose discrete decisions are within rounding of a
+threshold (so FP32 and FP64 may legitimately take different branches)."""
+
+from __future__ import annotations
+
+import numpy as np
+
+import synth
+from oracle import tracer
+from oracle.mlp import from_synth
+from oracle.sdf import MLPSDF
+
+
+def workload(spec, seed=0, n_shapes=1, latent_seed=0):
+    Ws, bs = synth.make_decoder(spec, seed=seed)
+    Z = synth.make_latents(spec, n_shapes, seed=latent_seed)
+    return Ws, bs, Z
+
+
+def oracle_sdf(spec, Ws, bs, Z):
+    return MLPSDF(from_synth(Ws, bs, spec), Z.astype(np.float64))
+
+
+def gpu_decoder(spec, Ws, bs):
+    from paper_1911_13225_b300 import api
+    return api.Decoder.from_spec(spec, Ws, bs)
+
+
+def to_np(t):
+    return t.detach().cpu().numpy()
+
+
+def ambiguous_rays(orc, tol_f, tol_d=1e-5, max_steps=50, grazing=0.05, near_miss=0.0,
+                   normals=None):
+    """Rays whose FP32 trace may take a different branch than FP64.
+
+    * some sample has | |f| - eps | < tol_f  (convergence test);
+    * some stepped distance lands within tol_d of t_in / t_out (exit test);
+    * the ray used (almost) its whole step budget;
+    * hits at grazing incidence (|n . v| < grazing) -- the silhouette;
+    * misses whose min |f| < near_miss.
+    """
+    eps, alpha = orc["eps"], orc["alpha"]
+    rf, rd = orc["rec_f"], orc["rec_d"]
+    with np.errstate(invalid="ignore"):
+        a = np.abs(np.abs(rf) - eps) < tol_f
+        stepped = rd + alpha * rf
+        ex = (np.abs(stepped - orc["t_out"][:, None]) < tol_d) | \
+             (np.abs(stepped - orc["t_in"][:, None]) < tol_d)
+    amb = np.any(a, axis=1) | np.any(ex, axis=1)
+    amb |= orc["steps"] >= max_steps - 2
+    if normals is not None:
+        nv = np.abs(np.einsum("ij,ij->i", normals, orc["v"]))
+        amb |= orc["mask"] & (nv < grazing)
+    if near_miss > 0:
+        amb |= orc["enters"] & ~orc["mask"] & (orc["min_abs_f"] < near_miss)
+    # rays grazing the bounding sphere: FP32 and FP64 may disagree on entry
+    b = np.einsum("ij,ij->i", orc["v"], orc["c"])
+    qq = np.einsum("ij,ij->i", orc["c"], orc["c"]) - b * b
+    amb |= np.abs(qq - 1.0) < 1e-5
+    return amb

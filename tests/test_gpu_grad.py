@@ -1,0 +1,180 @@
+"""Loss and latent-gradient parity of the CUDA path (dist_loss,
+dist_trace_bwd, the autograd wrapper) against the FP64 oracle.
+
+The upstream per-pixel gradients are taken from the GPU render and zeroed on
+decision-ambiguous rays; the same gradients go to dist_trace_bwd and to the
+oracle's latent_vjp (evaluated on the oracle's own trace), so the comparison
+isolates the backward pass.  Tolerance: relative l2 error 1e-3 (FP32)."""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import tracer
+from oracle.grad import latent_vjp
+from oracle.loss import loss_terms
+from tests.helpers import ambiguous_rays, gpu_decoder, oracle_sdf, to_np, workload
+
+pytestmark = pytest.mark.gpu
+
+GRAD_TOL = 1e-3
+
+
+def _setup(cuda_device, spec, size=48, k_min=1, delta=0.0, n_views=1):
+    from paper_1911_13225_b300 import api
+    Ws, bs, Z = workload(spec, seed=7, n_shapes=2)
+    dec = gpu_decoder(spec, Ws, bs)
+    vps = synth.random_viewpoints(n_views, seed=11)
+    cams = [synth.look_at_camera(vps[i], size, size, shape=0) for i in range(n_views)]
+    tcams = [dict(c, shape=1) for c in cams]
+    n = api.n_pixels(cams)
+    ws = api.Workspace(n, 60)
+    z = torch.from_numpy(Z).to(cuda_device)
+    params = api.TraceParams(max_steps=60, k_min=k_min, normal_delta=delta)
+    res = api.trace(dec, z, cams, params, ws, normals=True)
+    tgt = api.trace(dec, z, tcams, params, ws, normals=True)
+    torch.cuda.synchronize()
+    sdf = oracle_sdf(spec, Ws, bs, Z)
+    orc = tracer.render(sdf, cams, max_steps=60, k_min=k_min, normal_delta=delta, record=True)
+    amb = ambiguous_rays(orc, tol_f=1e-5, max_steps=60, normals=orc["normal"], near_miss=1e-3)
+    return api, dec, ws, z, params, cams, res, tgt, sdf, orc, amb
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
+
+
+def test_loss_terms_match_oracle_on_gpu_render(cuda_device):
+    api, dec, ws, z, params, cams, res, tgt, sdf, orc, amb = _setup(cuda_device, synth.SMALL_SPEC,
+                                                                    delta=1e-3)
+    rng = np.random.default_rng(0)
+    sil_gt = (to_np(tgt.mask) > 0).astype(np.float32)
+    target = {"depth": tgt.depth, "normal": tgt.normal, "sil": torch.from_numpy(sil_gt).to(z.device)}
+    L, gd, gn, gs, dz = api.loss(res, target, z, ws, w_depth=10.0, w_normal=1.0, w_sil=1.0,
+                                 w_reg=0.5)
+    torch.cuda.synchronize()
+    out_np = {"depth": to_np(res.depth).astype(np.float64), "mask": to_np(res.mask).astype(bool),
+              "sil": to_np(res.sil).astype(np.float64), "normal": to_np(res.normal).astype(np.float64)}
+    tgt_np = {"depth": to_np(tgt.depth).astype(np.float64),
+              "normal": to_np(tgt.normal).astype(np.float64), "sil": sil_gt.astype(np.float64)}
+    Lo, gdo, gno, gso = loss_terms(out_np, tgt_np, w_depth=10.0, w_normal=1.0, w_sil=1.0)
+    Lo += 0.5 * float((z.double().cpu().numpy() ** 2).sum())
+    assert abs(float(L.item()) - Lo) <= 1e-9 * abs(Lo)
+    np.testing.assert_allclose(to_np(gd), gdo, rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(to_np(gn), gno, rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(to_np(gs), gso, rtol=1e-6, atol=1e-12)
+    np.testing.assert_allclose(to_np(dz), 1.0 * to_np(z), rtol=1e-6)
+
+
+@pytest.mark.parametrize("spec", [synth.SMALL_SPEC, synth.DEEPSDF_SPEC])
+def test_exact_depth_gradient(cuda_device, spec):
+    api, dec, ws, z, params, cams, res, tgt, sdf, orc, amb = _setup(cuda_device, spec)
+    _, gd, _, _, _ = api.loss(res, {"depth": tgt.depth}, z, ws, w_depth=1.0)
+    g = to_np(gd).astype(np.float64)
+    g[amb] = 0.0
+    gt = torch.from_numpy(g.astype(np.float32)).to(z.device)
+    dz = api.backward(dec, z, cams, params, ws, res, g_depth=gt)
+    torch.cuda.synchronize()
+    G = latent_vjp(sdf, orc, 2, spec.latent_dim, g_depth=g.astype(np.float32).astype(np.float64))
+    assert np.abs(G).max() > 0
+    assert _rel(to_np(dz).astype(np.float64), G) < GRAD_TOL
+
+
+@pytest.mark.parametrize("k_min", [1, 3])
+def test_paper_first_term_gradient(cuda_device, k_min):
+    spec = synth.SMALL_SPEC
+    api, dec, ws, z, params, cams, res, tgt, sdf, orc, amb = _setup(cuda_device, spec, k_min=k_min)
+    params.grad_mode = "paper"
+    _, gd, _, _, _ = api.loss(res, {"depth": tgt.depth}, z, ws, w_depth=1.0)
+    g = to_np(gd).astype(np.float64)
+    g[amb] = 0.0
+    dz = api.backward(dec, z, cams, params, ws, res,
+                      g_depth=torch.from_numpy(g.astype(np.float32)).to(z.device))
+    torch.cuda.synchronize()
+    G = latent_vjp(sdf, orc, 2, spec.latent_dim, g_depth=g.astype(np.float32).astype(np.float64),
+                   mode="paper")
+    assert _rel(to_np(dz).astype(np.float64), G) < GRAD_TOL
+
+
+def test_silhouette_gradient(cuda_device):
+    spec = synth.SMALL_SPEC
+    api, dec, ws, z, params, cams, res, tgt, sdf, orc, amb = _setup(cuda_device, spec)
+    sil_gt = torch.from_numpy((to_np(tgt.mask) > 0).astype(np.float32)).to(z.device)
+    _, _, _, gs, _ = api.loss(res, {"depth": tgt.depth, "sil": sil_gt}, z, ws, w_depth=0.0,
+                              w_sil=1.0)
+    g = to_np(gs).astype(np.float64)
+    g[amb] = 0.0
+    dz = api.backward(dec, z, cams, params, ws, res,
+                      g_sil=torch.from_numpy(g.astype(np.float32)).to(z.device))
+    torch.cuda.synchronize()
+    G = latent_vjp(sdf, orc, 2, spec.latent_dim, g_sil=g.astype(np.float32).astype(np.float64))
+    assert np.abs(G).max() > 0
+    assert _rel(to_np(dz).astype(np.float64), G) < GRAD_TOL
+
+
+def test_fd_normal_gradient(cuda_device):
+    spec = synth.SMALL_SPEC
+    delta = 1e-3
+    api, dec, ws, z, params, cams, res, tgt, sdf, orc, amb = _setup(cuda_device, spec, delta=delta)
+    _, _, gn, _, _ = api.loss(res, {"depth": tgt.depth, "normal": tgt.normal}, z, ws,
+                              w_depth=0.0, w_normal=1.0)
+    g = to_np(gn).astype(np.float64)
+    g[amb] = 0.0
+    dz = api.backward(dec, z, cams, params, ws, res,
+                      g_normal=torch.from_numpy(g.astype(np.float32)).to(z.device))
+    torch.cuda.synchronize()
+    G = latent_vjp(sdf, orc, 2, spec.latent_dim, g_normal=g.astype(np.float32).astype(np.float64),
+                   normal_delta=delta)
+    assert np.abs(G).max() > 0
+    # FD normals divide FP32 differences by 2 delta: looser than the depth bar
+    assert _rel(to_np(dz).astype(np.float64), G) < 2e-2
+
+
+def test_autograd_function_and_finite_differences(cuda_device):
+    from paper_1911_13225_b300 import api
+    spec = synth.SMALL_SPEC
+    Ws, bs, Z = workload(spec, seed=7, n_shapes=2)
+    dec = gpu_decoder(spec, Ws, bs)
+    cam = synth.look_at_camera(synth.random_viewpoints(1, seed=11)[0], 40, 40)
+    ws = api.Workspace(1600, 200)
+    params = api.TraceParams(max_steps=200, eps=1e-6)
+    z_all = torch.from_numpy(Z).to(cuda_device)
+    tgt = api.trace(dec, z_all, [dict(cam, shape=1)], params, ws)
+    z = z_all.clone().requires_grad_(True)
+    depth, sil, mask = api.render(z, dec, [cam], params, ws)
+    m = (mask > 0) & torch.isfinite(tgt.depth)
+    loss = (depth[m] - tgt.depth[m]).abs().mean()
+    (gz,) = torch.autograd.grad(loss, z)
+    gz = to_np(gz)
+    dz_direct = api.backward(dec, z_all, [cam], params, ws,
+                             api.trace(dec, z_all, [cam], params, ws),
+                             g_depth=torch.where(m, torch.sign(depth - tgt.depth) / m.sum(),
+                                                 torch.zeros_like(depth)).detach())
+    np.testing.assert_allclose(gz, to_np(dz_direct), rtol=1e-5, atol=1e-9)
+    # central differences (h = 1e-3, 16 latent dims) of a smooth depth loss
+    # over an eroded foreground, so that no pixel crosses the silhouette or
+    # an L1 kink: this checks the depth Jacobian the backward pass applies.
+    mm = m.reshape(40, 40)
+    er = mm.clone()
+    er[1:, :] &= mm[:-1, :]; er[:-1, :] &= mm[1:, :]; er[:, 1:] &= mm[:, :-1]; er[:, :-1] &= mm[:, 1:]
+    er = er.reshape(-1)
+    z = z_all.clone().requires_grad_(True)
+    depth, _, _ = api.render(z, dec, [cam], params, ws)
+    loss = ((depth[er] - tgt.depth[er]) ** 2).sum()
+    (gz,) = torch.autograd.grad(loss, z)
+    gz = to_np(gz)
+    h = 1e-3
+    dims = np.random.default_rng(1).choice(spec.latent_dim, 16, replace=False)
+    fd = []
+    for j in dims:
+        vals = []
+        for sgn in (1, -1):
+            zp = z_all.clone()
+            zp[0, j] += sgn * h
+            r = api.trace(dec, zp, [cam], params, ws)
+            assert bool((r.mask[er] > 0).all())
+            vals.append(float(((r.depth[er].double() - tgt.depth[er].double()) ** 2).sum()))
+        fd.append((vals[0] - vals[1]) / (2 * h))
+    fd = np.array(fd)
+    assert _rel(gz[0, dims], fd) < 5e-2

@@ -1,0 +1,141 @@
+"""FP32 CUDA sphere tracer vs the FP64 oracle, element by element
+(dist_trace_fwd / dist_render_normals through the C ABI).
+
+Away from rays whose discrete decisions sit within rounding of a threshold
+(tests/helpers.ambiguous_rays), masks, step counts and outcome codes must be
+identical and depth / silhouette within 1e-5 in scene units."""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import tracer
+from tests.helpers import ambiguous_rays, gpu_decoder, oracle_sdf, to_np, workload
+
+pytestmark = pytest.mark.gpu
+
+DEPTH_TOL = 1e-5
+
+
+def _run(cuda_device, spec, cams, n_shapes=1, alpha=1.5, max_steps=50, k_min=1, seed=0,
+         normals=False, delta=0.0):
+    from paper_1911_13225_b300 import api
+    Ws, bs, Z = workload(spec, seed=seed, n_shapes=n_shapes)
+    dec = gpu_decoder(spec, Ws, bs)
+    n = api.n_pixels(cams)
+    ws = api.Workspace(n, max_steps)
+    params = api.TraceParams(max_steps=max_steps, alpha=alpha, k_min=k_min, normal_delta=delta)
+    res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), cams, params, ws, normals=normals)
+    torch.cuda.synchronize()
+    sdf = oracle_sdf(spec, Ws, bs, Z)
+    orc = tracer.render(sdf, cams, max_steps=max_steps, alpha=alpha, k_min=k_min,
+                        with_normals=True, record=True)
+    return res, orc, sdf
+
+
+def _compare(res, orc, max_steps, tol_f):
+    amb = ambiguous_rays(orc, tol_f=tol_f, max_steps=max_steps, normals=orc["normal"])
+    ok = ~amb
+    assert ok.mean() > 0.9, f"too many ambiguous rays: {amb.mean():.3f}"
+    mask = to_np(res.mask).astype(bool)
+    assert np.array_equal(mask[ok], orc["mask"][ok])
+    assert np.array_equal(to_np(res.steps)[ok], orc["steps"][ok])
+    assert np.array_equal(to_np(res.status)[ok], orc["status"][ok])
+    hit = ok & orc["mask"]
+    assert hit.sum() > 0
+    assert np.max(np.abs(to_np(res.depth)[hit] - orc["depth"][hit])) < DEPTH_TOL
+    assert np.all(np.isinf(to_np(res.depth)[ok & ~orc["mask"]]))
+    assert np.max(np.abs(to_np(res.sil)[ok] - orc["sil"][ok])) < DEPTH_TOL
+    # invariant on every ray: S < 0 <=> hit
+    assert np.array_equal(to_np(res.sil) < 0, mask)
+    return ok
+
+
+@pytest.mark.parametrize("alpha", [1.5, 1.0])
+def test_small_decoder_32x32(cuda_device, alpha):
+    cam = synth.look_at_camera((0, 0, 2.5), 32, 32)
+    res, orc, _ = _run(cuda_device, synth.SMALL_SPEC, [cam], alpha=alpha)
+    _compare(res, orc, 50, tol_f=4e-6)
+
+
+def test_deepsdf_decoder_ragged_tiles(cuda_device):
+    cam = synth.look_at_camera(synth.random_viewpoints(1, seed=3)[0], 45, 37)
+    res, orc, _ = _run(cuda_device, synth.DEEPSDF_SPEC, [cam])
+    _compare(res, orc, 50, tol_f=1e-5)
+
+
+def test_multi_camera_multi_shape_topk(cuda_device):
+    vps = synth.random_viewpoints(3, seed=5)
+    cams = [synth.look_at_camera(vps[0], 24, 20, shape=1),
+            synth.look_at_camera(vps[1], 16, 16, shape=0),
+            synth.look_at_camera(vps[2], 9, 31, shape=1)]
+    res, orc, _ = _run(cuda_device, synth.SMALL_SPEC, cams, n_shapes=2, k_min=3)
+    ok = _compare(res, orc, 50, tol_f=4e-6)
+    dmin, fmin = to_np(res.d_min), to_np(res.f_min)
+    ent = ok & orc["enters"]
+    have = np.isfinite(orc["topk_d"][ent])
+    np.testing.assert_array_equal(np.isfinite(dmin[ent]), have)
+    assert np.max(np.abs(dmin[ent][have] - orc["topk_d"][ent][have])) < DEPTH_TOL
+    assert np.max(np.abs(fmin[ent][have] - orc["topk_s"][ent][have])) < DEPTH_TOL
+
+
+@pytest.mark.parametrize("delta", [0.0, 1e-3])
+def test_normals_at_gpu_hits(cuda_device, delta):
+    cam = synth.look_at_camera((0.4, 0.7, 2.3), 40, 40)
+    spec = synth.DEEPSDF_SPEC
+    res, orc, sdf = _run(cuda_device, spec, [cam], normals=True, delta=delta)
+    m = to_np(res.mask).astype(bool)
+    c, v = orc["c"], orc["v"]
+    p = c[m] + to_np(res.d_hit)[m].astype(np.float64)[:, None] * v[m]
+    n_ref = tracer.normals(sdf, p, orc["shape"][m], np.ones(m.sum(), bool), delta)
+    err = np.linalg.norm(to_np(res.normal)[m] - n_ref, axis=1)
+    tol = 1e-4 if delta == 0.0 else 3e-3
+    assert np.quantile(err, 0.99) < tol and np.max(err) < 10 * tol
+    assert np.all(to_np(res.normal)[~m] == 0)
+
+
+def test_all_rays_miss_the_sphere(cuda_device):
+    from paper_1911_13225_b300 import api
+    spec = synth.SMALL_SPEC
+    Ws, bs, Z = workload(spec)
+    dec = gpu_decoder(spec, Ws, bs)
+    cam = synth.look_at_camera((0, 0, 2.5), 8, 8)
+    cam["R"] = -cam["R"]            # looking away from the origin
+    cam["R"][:, 0] *= -1            # keep a proper rotation
+    ws = api.Workspace(64)
+    res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), [cam], api.TraceParams(), ws)
+    torch.cuda.synchronize()
+    assert not to_np(res.mask).any()
+    assert np.all(np.isinf(to_np(res.depth)))
+    assert np.all(to_np(res.sil) > 0)
+    assert np.all(to_np(res.steps) == 0)
+    assert int(res.queries.sum()) == 0
+
+
+def test_one_pixel_and_invalid_arguments(cuda_device):
+    from paper_1911_13225_b300 import api
+    from paper_1911_13225_b300._abi import DistError, DIST_E_INVALID
+    spec = synth.SMALL_SPEC
+    Ws, bs, Z = workload(spec)
+    dec = gpu_decoder(spec, Ws, bs)
+    ws = api.Workspace(16, 50)
+    z = torch.from_numpy(Z).to(cuda_device)
+    cam = synth.look_at_camera((0, 0, 2.5), 1, 1)
+    res = api.trace(dec, z, [cam], api.TraceParams(), ws)
+    torch.cuda.synchronize()
+    orc = tracer.render(oracle_sdf(spec, Ws, bs, Z), [cam], with_normals=False)
+    assert bool(to_np(res.mask)[0]) == bool(orc["mask"][0])
+    inside = synth.look_at_camera((0, 0, 0.5), 4, 4)
+    with pytest.raises(DistError) as e:
+        api.trace(dec, z, [inside], api.TraceParams(), ws)
+    assert e.value.status == DIST_E_INVALID
+    with pytest.raises(DistError):
+        api.trace(dec, z, [cam], api.TraceParams(k_min=4), ws)
+    with pytest.raises(DistError):
+        api.trace(dec, z, [synth.look_at_camera((0, 0, 2.5), 5, 5)], api.TraceParams(), ws)
+    with pytest.raises(DistError):
+        api.trace(dec, z, [cam], api.TraceParams(max_steps=51), ws)
+    bad_shape = dict(cam, shape=3)
+    with pytest.raises(DistError):
+        api.trace(dec, z, [bad_shape], api.TraceParams(), ws)
