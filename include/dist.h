@@ -80,6 +80,12 @@ dist_status dist_decoder_create(const dist_decoder_desc* desc,
 dist_status dist_decoder_destroy(dist_decoder* dec);
 /* 1 if the BF16 tensor-core MLP covers this decoder, else 0. */
 int dist_decoder_has_bf16(const dist_decoder* dec);
+/* Not from the paper: every device-side wait of the tensor-core kernel is
+ * bounded (1 s).  A launch that gives up sets bits in a device error word of
+ * the decoder and returns early (its outputs are then invalid).  This call
+ * synchronises the device, returns the word in *code (0 = no timeout since
+ * the last call) and clears it. */
+dist_status dist_decoder_device_error(const dist_decoder* dec, int32_t* code);
 
 /* ----------------------------------------------------------------- camera */
 
@@ -271,6 +277,22 @@ dist_status dist_serve_submit(dist_server* s, const dist_request* req, uint64_t*
 dist_status dist_serve_poll(dist_server* s, uint64_t ticket, int* done);
 /* Stops the server thread (bounded wait) and frees its memory. */
 dist_status dist_serve_destroy(dist_server* s);
+
+/* ------------------------------------------------------------ measurement */
+
+/* Not from the paper: instrumentation used to measure the kernels against
+ * their roofline.  While enabled, every decoder-MLP launch of the march in
+ * dist_trace_fwd (the dominant kernels) is bracketed by CUDA events recorded
+ * on the stream it is launched on, and every kernel launch of the library is
+ * counted.  enable = 1 resets the counters and starts recording (host-side
+ * state, not thread-safe); 0 stops.  dist_profile_read synchronises the
+ * recorded events and returns, per kernel kind ([0] BF16 tensor-core MLP,
+ * [1] FP32 SIMT MLP), the summed kernel time in ms and the number of timed
+ * launches, plus the count of all library kernel launches.  Each array
+ * argument points to 2 host values; any pointer may be NULL.  At most 65536
+ * launches are timed per enable. */
+dist_status dist_profile_enable(int enable);
+dist_status dist_profile_read(double* mlp_ms, int64_t* mlp_launches, int64_t* all_launches);
 
 /* ------------------------------------------------------------------- misc */
 

@@ -93,6 +93,12 @@ class Decoder:
     def has_bf16(self) -> bool:
         return bool(lib().dist_decoder_has_bf16(self.handle))
 
+    def device_error(self) -> int:
+        """Synchronise and return (then clear) the tensor-core kernel's timeout word."""
+        code = ctypes.c_int32(0)
+        check(lib().dist_decoder_device_error(self.handle, byref(code)), "dist_decoder_device_error")
+        return int(code.value)
+
     def close(self):
         if self.handle:
             lib().dist_decoder_destroy(self.handle)

@@ -150,6 +150,18 @@ dist_status dist_decoder_destroy(dist_decoder* d) {
 
 int dist_decoder_has_bf16(const dist_decoder* d) { return d && d->tc.ok ? 1 : 0; }
 
+dist_status dist_decoder_device_error(const dist_decoder* d, int32_t* code) {
+  DIST_CHECK(d && code, DIST_E_INVALID, "dist_decoder_device_error: NULL argument");
+  *code = 0;
+  if (!d->tc.ok) return DIST_OK;
+  DIST_CUDA_TRY(cudaDeviceSynchronize());
+  int v = 0;
+  DIST_CUDA_TRY(cudaMemcpy(&v, d->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
+  DIST_CUDA_TRY(cudaMemset(d->tc.err, 0, sizeof(int)));
+  *code = v;
+  return DIST_OK;
+}
+
 dist_status dist_workspace_create(int64_t max_rays, int max_steps, dist_workspace** out) {
   DIST_CHECK(out && max_rays > 0 && max_rays <= (int64_t)1 << 28 && max_steps > 0 &&
                  max_steps <= 100000,

@@ -1,6 +1,7 @@
 // Internal definitions shared by the libdist translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -23,6 +24,17 @@ void set_error(const std::string& msg);
       ::dist::set_error(std::string(#call) + ": " + cudaGetErrorString(e_));  \
       return DIST_E_CUDA;                                                     \
     }                                                                         \
+  } while (0)
+
+void count_launch(int n = 1);
+void prof_mlp_begin(cudaStream_t st, int kind);   // kind 0: BF16 tensor core, 1: FP32 SIMT
+void prof_mlp_end(cudaStream_t st);
+
+// After a kernel launch: count it (measurement) and check the launch error.
+#define DIST_LAUNCH_CHECK()                                                   \
+  do {                                                                        \
+    ::dist::count_launch(1);                                                  \
+    DIST_CUDA_TRY(cudaGetLastError());                                        \
   } while (0)
 
 #define DIST_CHECK(cond, code, msg)                                           \
@@ -71,11 +83,17 @@ struct DecoderF32 {
   float b_head;
 };
 
-// BF16 tensor-core packing of the DeepSDF shape (width 512, 8 hidden, skip 4).
+// BF16 tensor-core packing of the DeepSDF shape (width 512, 8 hidden, skip 4):
+// GEMM layers 1..7 as bf16 [N rows][K cols] (K contiguous) with one TMA
+// tensor map each (box 64 K x 256 N, 128-byte swizzle).
+struct TCMaps {
+  CUtensorMap m[7];
+};
 struct DecoderTC {
   bool ok;
-  const __nv_bfloat16* W[8];     // GEMM layers 1..7: [N rows][K cols] K-major bf16
-  int n_rows[8], k_cols[8];
+  const __nv_bfloat16* W[7];
+  TCMaps maps;
+  int* err;                      // device error word of the bounded waits
 };
 
 }  // namespace dist

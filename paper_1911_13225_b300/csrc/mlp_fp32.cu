@@ -400,6 +400,7 @@ cudaError_t launch_fwd(const DecoderF32& d, const RowSrc& src, const float* b0, 
     configured = true;
   }
   mlp_fp32_fwd_kernel<WIDTH><<<num_sms(), kFwdRows * 8, sm, st>>>(d, src, b0, bs, fout);
+  count_launch(1);
   return cudaGetLastError();
 }
 
@@ -417,6 +418,7 @@ cudaError_t launch_adj(const DecoderF32& d, const float4* pp, const float4* pq, 
   }
   mlp_fp32_adj_kernel<WIDTH><<<num_sms(), kAdjRows * 8, sm, st>>>(d, pp, pq, count, b0, bs, out4,
                                                                     g0, gs, acc);
+  count_launch(1);
   return cudaGetLastError();
 }
 

@@ -1,18 +1,502 @@
-// BF16 tcgen05 decoder forward (DeepSDF shape).  Placeholder until the
-// tensor-core kernel lands: the decoder reports no BF16 support.
+// BF16 tcgen05 decoder forward for the DeepSDF shape: 8 hidden layers of
+// 512, latent 256 folded into per-shape biases of layer 0 and the skip
+// layer 4, ReLU, tanh head (Sec. B.1).  GEMM layers 1..7 run on the 5th
+// generation tensor cores with FP32 accumulation in tensor memory; layer 0
+// (3 inputs), the xyz columns of layer 4 and the 512 -> 1 head run on CUDA
+// cores in FP32 inside the epilogue.
+//
+// One persistent CTA per SM, 128-row tiles (one row per TMEM lane):
+//   warp 0     TMA producer: weight slices [256 N x 64 K] bf16 (128B swizzle)
+//              into a 3-stage ring;
+//   warp 1     TMEM owner and single-thread MMA issuer
+//              (M = 128, N = 256, K = 16 per instruction);
+//   warps 2-9  epilogue: two warps per TMEM lane quadrant split the columns;
+//              tcgen05.ld the accumulator, add bias (+ xyz term), ReLU,
+//              round to bf16 and write the next layer's A operand into the
+//              shared activation tile in the same 128B-swizzled K-major
+//              layout the MMA descriptors describe.
+// Activations never leave the SM.  Every wait is bounded (1 s): on timeout
+// the CTA raises an error word, drains its MMAs and frees its TMEM.
+#include <cudaTypedefs.h>
+
+#include <vector>
+
 #include "common.cuh"
 
 namespace dist {
 
+namespace {
+
+constexpr int BM = 128;                       // rows per tile == TMEM lanes
+constexpr int BN = 256;                       // N per stage and per MMA
+constexpr int BK = 64;                        // K per stage: one 128-byte bf16 row
+constexpr int STAGES = 3;
+constexpr int NUM_EPI = 8;                    // epilogue warps
+constexpr int THREADS = 64 + NUM_EPI * 32;
+constexpr int ACT_BYTES = BM * 512 * 2;       // 8 K-chunks of [128 x 64] bf16
+constexpr int CHUNK_BYTES = BM * BK * 2;      // 16 KB
+constexpr int STAGE_BYTES = BN * BK * 2;      // 32 KB
+constexpr int NUM_GEMM = 7;                   // layers 1..7
+constexpr int BAR_BYTES = 256;
+constexpr int SMEM_BYTES = 1024 + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES + BM * 4;
+constexpr unsigned long long kTimeoutNs = 1000000000ull;
+
+// Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
+// B bf16 (10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
+                            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__host__ __device__ constexpr int gemm_k(int g) { return g == 3 ? 256 : 512; }
+__host__ __device__ constexpr int gemm_n(int g) { return g == 2 ? 256 : 512; }
+
+// ------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with `parity` to complete; false on timeout or
+// when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (uint32_t it = 1;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0) {
+      if (*abort_flag) return false;
+      if (globaltimer() - t0 > kTimeoutNs) return false;
+    }
+  }
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                   smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_async_shared() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// This warp's 32 TMEM lanes x 32 consecutive fp32 columns.
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (SBO), version 1 (bit 46), swizzle mode 2 (bits 61-63).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Byte offset of bf16 column group u (8 columns = 16 bytes) of row r inside a
+// 128B-swizzled [128 x 64] chunk.
+__device__ __forceinline__ uint32_t swz(int r, int u) {
+  return (uint32_t)(r * 128 + ((u ^ (r & 7)) << 4));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// Store 32 consecutive activations (columns c..c+31, c % 32 == 0) of row r.
+__device__ __forceinline__ void store_act32(uint8_t* act, int r, int c, const float (&v)[32]) {
+  uint8_t* chunk = act + (c >> 6) * CHUNK_BYTES;
+  const int u0 = (c & 63) >> 3;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const uint32_t off = swz(r, u0 + q);
+    const uint32_t a = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
+    const uint32_t b = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
+    const uint32_t cc = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
+    const uint32_t d = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(chunk + off)), "r"(a),
+                 "r"(b), "r"(cc), "r"(d)
+                 : "memory");
+  }
+}
+
+struct TCArgs {
+  const float* bias[NUM_GEMM];   // layers 1..7, padded to 512 (layer 4 entry unused)
+  const float* Wx0;              // [512][4]
+  const float* Wx4;              // [512][4]
+  const float* w_head;           // [512]
+  float b_head;
+  const float* bfold0;           // [shape][512]
+  const float* bfold4;           // [shape][512]
+  RowSrc src;
+  float* fout;
+  int* err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* act = smem;
+  uint8_t* wst = smem + ACT_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wst + STAGES * STAGE_BYTES);
+  uint64_t* full = bars;                     // [STAGES]
+  uint64_t* empty = bars + STAGES;           // [STAGES]
+  uint64_t* acc_full = bars + 2 * STAGES;    // MMA -> epilogue, once per layer
+  uint64_t* act_full = bars + 2 * STAGES + 1;  // epilogue -> MMA, once per layer
+  uint64_t* drain = bars + 2 * STAGES + 2;   // final MMA completion
+  uint64_t* head_bar = bars + 2 * STAGES + 3;  // column half 1 -> half 0, once per tile
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* head_part = reinterpret_cast<float*>(smem + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n = rowsrc_count(a.src);
+  const int n_tiles = (n + BM - 1) / BM;
+  if ((int)blockIdx.x >= n_tiles) return;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(act_full, NUM_EPI * 32);
+    mbar_init(drain, 1);
+    mbar_init(head_bar, NUM_EPI * 16);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_parity[STAGES];
+      bool issued[STAGES];
+      for (int s = 0; s < STAGES; ++s) issued[s] = false;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+        for (int g = 0; ok && g < NUM_GEMM; ++g) {
+          for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
+            for (int kc = 0; kc < gemm_k(g) / BK; ++kc) {
+              if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) { ok = false; break; }
+              mbar_expect_tx(full + stage, STAGE_BYTES);
+              tma_load_2d(wst + stage * STAGE_BYTES, &maps.m[g], full + stage, kc * BK, nh * BN);
+              issued[stage] = true;
+              issued_parity[stage] = phase;
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.err, 1);
+      }
+      // every issued copy must land before the CTA exits
+      for (int s = 0; s < STAGES; ++s) {
+        if (!issued[s]) continue;
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(full + s, issued_parity[s]) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, act_phase = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+        for (int g = 0; ok && g < NUM_GEMM; ++g) {
+          if (!mbar_wait(act_full, act_phase, abort_flag)) { ok = false; break; }
+          act_phase ^= 1u;
+          tc_fence_after();
+          for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
+            for (int kc = 0; kc < gemm_k(g) / BK; ++kc) {
+              if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t a_base = smem_u32(act + kc * CHUNK_BYTES);
+              const uint32_t b_base = smem_u32(wst + stage * STAGE_BYTES);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k)
+                mma_bf16(tmem + (uint32_t)(nh * BN), sw128_desc(a_base + 32 * k),
+                         sw128_desc(b_base + 32 * k), kIdesc, (kc | k) != 0);
+              mma_commit(empty + stage);
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+          }
+          if (ok) mma_commit(acc_full);
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.err, 2);
+      }
+      // all issued MMAs complete before TMEM is released
+      mma_commit(drain);
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+      }
+    }
+  } else {
+    // --------------------------------------------------------- epilogue
+    const int ew = warp - 2;                 // 0..7
+    const int quad = warp & 3;               // TMEM lane quadrant of this warp
+    const int half = ew >> 2;                // column half
+    const int row = quad * 32 + lane;        // tile row == TMEM lane
+    const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
+    uint32_t acc_phase = 0, head_phase = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+      const int j = tile * BM + row;
+      const bool valid = j < n;
+      float3 p = make_float3(0.f, 0.f, 0.f);
+      int shape = 0;
+      if (valid) rowsrc_load(a.src, j, p, shape);
+      // layer 0 on CUDA cores: h0 = relu(Wx0 p + b0'[shape])
+      {
+        const float* bf = a.bfold0 + (size_t)shape * 512;
+        for (int c = half * 256; c < half * 256 + 256; c += 32) {
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float4 w = __ldg(reinterpret_cast<const float4*>(a.Wx0) + c + i);
+            const float t = fmaf(w.x, p.x, fmaf(w.y, p.y, fmaf(w.z, p.z, __ldg(bf + c + i))));
+            v[i] = fmaxf(t, 0.f);
+          }
+          store_act32(act, row, c, v);
+        }
+        fence_async_shared();
+        mbar_arrive(act_full);
+      }
+      float head = 0.f;
+      for (int g = 0; g < NUM_GEMM; ++g) {
+        if (!mbar_wait(acc_full, acc_phase, abort_flag)) { ok = false; break; }
+        acc_phase ^= 1u;
+        tc_fence_after();
+        const int ncol = gemm_n(g) / 2;
+        const int c0 = half * ncol;
+        const bool skip_layer = (g == 3);
+        const float* bias = skip_layer ? a.bfold4 + (size_t)shape * 512 : a.bias[g];
+        for (int c = c0; c < c0 + ncol; c += 32) {
+          uint32_t r[32];
+          tmem_ld32(t_row + (uint32_t)c, r);
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + c + i));
+            v[i + 0] = __uint_as_float(r[i + 0]) + b4.x;
+            v[i + 1] = __uint_as_float(r[i + 1]) + b4.y;
+            v[i + 2] = __uint_as_float(r[i + 2]) + b4.z;
+            v[i + 3] = __uint_as_float(r[i + 3]) + b4.w;
+          }
+          if (skip_layer) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const float4 w = __ldg(reinterpret_cast<const float4*>(a.Wx4) + c + i);
+              v[i] = fmaf(w.x, p.x, fmaf(w.y, p.y, fmaf(w.z, p.z, v[i])));
+            }
+          }
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+          if (g < NUM_GEMM - 1) {
+            store_act32(act, row, c, v);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+              const float4 w = __ldg(reinterpret_cast<const float4*>(a.w_head + c + i));
+              head = fmaf(v[i], w.x, fmaf(v[i + 1], w.y, fmaf(v[i + 2], w.z, fmaf(v[i + 3], w.w, head))));
+            }
+          }
+        }
+        tc_fence_before();
+        if (g < NUM_GEMM - 1) {
+          fence_async_shared();
+          mbar_arrive(act_full);
+        }
+      }
+      if (!ok) break;
+      // head: f = tanh(w . h7 + b); half 1 hands its partial sums to half 0
+      // (head_part is rewritten only after the next tile's seven layers,
+      // which half 0 takes part in, so one barrier phase per tile suffices)
+      if (half == 1) {
+        head_part[row] = head;
+        mbar_arrive(head_bar);
+      } else {
+        if (!mbar_wait(head_bar, head_phase, abort_flag)) { ok = false; break; }
+        if (valid) a.fout[j] = tanhf(head + head_part[row] + a.b_head);
+      }
+      head_phase ^= 1u;
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      atomicOr(a.err, 4);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
 dist_status pack_tc(dist_decoder* d, const float* const* W) {
-  (void)W;
   d->tc.ok = false;
+  auto enc = tensor_map_encoder();
+  DIST_CHECK(enc != nullptr, DIST_E_CUDA, "cuTensorMapEncodeTiled entry point not available");
+  const int L = 256, Hh = 253;   // latent, h-part of the skip input
+  for (int g = 0; g < NUM_GEMM; ++g) {
+    const int l = g + 1;
+    const int N = gemm_n(g), K = gemm_k(g);
+    std::vector<__nv_bfloat16> h((size_t)N * K, __float2bfloat16_rn(0.f));
+    const int n_real = (l == 3) ? Hh : 512;
+    const int k_real = (l == 4) ? Hh : 512;
+    const int in_dim = (l == 4) ? Hh + L + 3 : 512;
+    for (int n = 0; n < n_real; ++n)
+      for (int k = 0; k < k_real; ++k)
+        h[(size_t)n * K + k] = __float2bfloat16_rn(W[l][(size_t)n * in_dim + k]);
+    void* p = nullptr;
+    DIST_CUDA_TRY(cudaMalloc(&p, h.size() * sizeof(__nv_bfloat16)));
+    d->allocations.push_back(p);
+    DIST_CUDA_TRY(cudaMemcpy(p, h.data(), h.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
+    d->tc.W[g] = static_cast<const __nv_bfloat16*>(p);
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
+    cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(__nv_bfloat16)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BN};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&d->tc.maps.m[g], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p, dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed");
+  }
+  void* e = nullptr;
+  DIST_CUDA_TRY(cudaMalloc(&e, sizeof(int)));
+  d->allocations.push_back(e);
+  DIST_CUDA_TRY(cudaMemset(e, 0, sizeof(int)));
+  d->tc.err = static_cast<int*>(e);
+  d->tc.ok = true;
   return DIST_OK;
 }
 
-cudaError_t mlp_tc_forward(const dist_decoder*, const RowSrc&, const float*, const float*, float*,
-                           cudaStream_t) {
-  return cudaErrorNotSupported;
+cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
+                           const float* bfolds, float* fout, cudaStream_t st) {
+  if (!dec->tc.ok) return cudaErrorNotSupported;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const DecoderF32& f = dec->f32;
+  TCArgs a;
+  for (int g = 0; g < NUM_GEMM; ++g) a.bias[g] = f.b[g + 1];
+  a.Wx0 = f.Wx0;
+  a.Wx4 = f.Wxs;
+  a.w_head = f.w_head;
+  a.b_head = f.b_head;
+  a.bfold0 = bfold0;
+  a.bfold4 = bfolds;
+  a.src = src;
+  a.fout = fout;
+  a.err = dec->tc.err;
+  mlp_tc_kernel<<<num_sms(), THREADS, SMEM_BYTES, st>>>(dec->tc.maps, a);
+  count_launch(1);
+  return cudaGetLastError();
 }
 
 }  // namespace dist

@@ -605,14 +605,14 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
       ch.n = c % kCamChunk + 1;
       ch.first = c - (c % kCamChunk);
       write_cams_kernel<<<1, 64, 0, st>>>(ch, ws->cams);
-      DIST_CUDA_TRY(cudaGetLastError());
+      DIST_LAUNCH_CHECK();
     }
   }
   DIST_CHECK(n_pix <= ws->max_rays, DIST_E_INVALID, "more pixels than the workspace holds");
   const DecoderF32& d = dec->f32;
   dim3 g(n_shapes, 2, (d.width + 63) / 64);
   fold_bias_kernel<<<g, 256, 0, st>>>(d, z, n_shapes, ws->bfold, ws->bfold + kMaxShapes * 512);
-  DIST_CUDA_TRY(cudaGetLastError());
+  DIST_LAUNCH_CHECK();
   out->n_pix = n_pix;
   out->st = st;
   return DIST_OK;
@@ -648,23 +648,23 @@ dist_status normals_impl(const dist_decoder* dec, const dist_trace_params* p,
   if (p->normal_delta == 0.f) {
     ProbeArgs a = make_probe_args(p, o, ws, n_cams, n_pix, 0, 0);
     probes_hits_kernel<<<g, 256, 0, st>>>(a);
-    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_LAUNCH_CHECK();
     DIST_CUDA_TRY(mlp_fp32_adjoint(dec->f32, ws->probe_p, nullptr, ws->probe_count, b0, bs,
                                    ws->probe_out, nullptr, nullptr, 0, st));
     normals_from_grad_kernel<<<g, 256, 0, st>>>(ws->probe_out, ws->probe_pix, ws->probe_count,
                                                  normal);
-    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_LAUNCH_CHECK();
   } else {
     ProbeArgs a = make_probe_args(p, o, ws, n_cams, n_pix, 0, 0);
     probes_fd_kernel<<<g, 256, 0, st>>>(a, p->normal_delta, nullptr);
-    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_LAUNCH_CHECK();
     RowSrc src{};
     src.count = ws->probe_count;
     src.pts = ws->probe_p;
     DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->probe_out, st));
     normals_from_fd_kernel<<<g, 256, 0, st>>>(ws->probe_out, ws->probe_pix, ws->probe_count,
                                                p->normal_delta, normal);
-    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_LAUNCH_CHECK();
   }
   return DIST_OK;
 }
@@ -688,7 +688,7 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
   DIST_CUDA_TRY(cudaMemsetAsync(ws->counts, 0, (size_t)(p->max_steps + 2) * 2 * sizeof(int), st));
   const int first = p->precision == DIST_PREC_BF16 ? 0 : 1;
   raygen_kernel<<<grid_for(n_pix, 256), 256, 0, st>>>(a, ws->act[0][first], ws->counts + first);
-  DIST_CUDA_TRY(cudaGetLastError());
+  DIST_LAUNCH_CHECK();
   const float* b0 = ws->bfold;
   const float* bs = ws->bfold + kMaxShapes * 512;
   const int step_grid = num_sms() * 4;
@@ -701,18 +701,22 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
     if (p->precision == DIST_PREC_BF16) {
       src.count = cin + 0;
       src.idx = ws->act[par][0];
+      prof_mlp_begin(st, 0);
       DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, ws->fbuf[0], st));
+      prof_mlp_end(st);
     }
     src.count = cin + 1;
     src.idx = ws->act[par][1];
+    prof_mlp_begin(st, 1);
     DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->fbuf[1], st));
+    prof_mlp_end(st);
     StepLists L;
     L.cnt_in = cin; L.cnt_out = cout;
     L.in[0] = ws->act[par][0]; L.in[1] = ws->act[par][1];
     L.f[0] = ws->fbuf[0]; L.f[1] = ws->fbuf[1];
     L.out[0] = ws->act[par ^ 1][0]; L.out[1] = ws->act[par ^ 1][1];
     step_kernel<<<step_grid, 256, 0, st>>>(a, L, o->queries);
-    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_LAUNCH_CHECK();
   }
   if (o->normal) return normals_impl(dec, p, o, o->normal, ws, n_cams, n_pix, st);
   return DIST_OK;
@@ -756,7 +760,7 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
     ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, 0, 0);
     probes_bwd_kernel<<<g, 256, 0, st>>>(a, g_depth, g_sil, p->grad_mode == DIST_GRAD_PAPER,
                                          p->alpha);
-    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_LAUNCH_CHECK();
     DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p, ws->probe_q, ws->probe_count, b0, bs, nullptr,
                                    G0, Gs, 1, st));
   }
@@ -764,7 +768,7 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
     const long long off = 4 * (long long)ws->max_rays;
     ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, off, 1);
     probes_fd_kernel<<<g, 256, 0, st>>>(a, p->normal_delta, g_normal);
-    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_LAUNCH_CHECK();
     RowSrc src{};
     src.count = ws->probe_count + 1;
     src.pts = ws->probe_p + off;
@@ -772,13 +776,13 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
     DIST_CUDA_TRY(mlp_fp32_forward(d, src, b0, bs, f6, st));
     fd_coef_kernel<<<g, 256, 0, st>>>(f6, ws->probe_pix + off, ws->probe_count + 1,
                                       p->normal_delta, g_normal, ws->probe_q + off);
-    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_LAUNCH_CHECK();
     DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p + off, ws->probe_q + off, ws->probe_count + 1,
                                    b0, bs, nullptr, G0, Gs, 1, st));
   }
   dim3 fg((d.latent + 127) / 128, n_shapes);
   latent_finalize_kernel<<<fg, 128, 0, st>>>(d, G0, Gs, n_shapes, dz);
-  DIST_CUDA_TRY(cudaGetLastError());
+  DIST_LAUNCH_CHECK();
   return DIST_OK;
 }
 
@@ -797,12 +801,12 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
   const DecoderF32& d = dec->f32;
   dim3 fg(n_shapes, 2, (d.width + 63) / 64);
   fold_bias_kernel<<<fg, 256, 0, st>>>(d, z, n_shapes, ws->bfold, ws->bfold + kMaxShapes * 512);
-  DIST_CUDA_TRY(cudaGetLastError());
+  DIST_LAUNCH_CHECK();
   const float* b0 = ws->bfold;
   const float* bs = ws->bfold + kMaxShapes * 512;
   const int g = grid_for(n, 256);
   pack_points_kernel<<<g, 256, 0, st>>>(pts, shape, n, n_shapes, ws->probe_p, ws->probe_count);
-  DIST_CUDA_TRY(cudaGetLastError());
+  DIST_LAUNCH_CHECK();
   RowSrc src{};
   src.count = ws->probe_count;
   src.pts = ws->probe_p;
@@ -814,7 +818,7 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
     DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p, nullptr, ws->probe_count, b0, bs,
                                    ws->probe_out, nullptr, nullptr, 0, st));
     unpack_grad_kernel<<<g, 256, 0, st>>>(ws->probe_out, n, f, grad);
-    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_LAUNCH_CHECK();
   }
   return DIST_OK;
 }
@@ -838,17 +842,17 @@ dist_status dist_loss(int64_t n, const float* depth, const uint8_t* mask, const 
   DIST_CUDA_TRY(cudaMemsetAsync(ws->ired, 0, sizeof(int), st));
   const int g = grid_for(n, 256);
   loss_count_kernel<<<g, 256, 0, st>>>(n, mask, tgt_depth, ws->ired);
-  DIST_CUDA_TRY(cudaGetLastError());
+  DIST_LAUNCH_CHECK();
   LossArgs a;
   a.n = n; a.depth = depth; a.sil = sil; a.normal = normal; a.tgt_depth = tgt_depth;
   a.tgt_normal = tgt_normal; a.tgt_sil = tgt_sil; a.mask = mask; a.w = *w; a.cnt = ws->ired;
   a.loss = loss; a.g_depth = g_depth; a.g_normal = g_normal; a.g_sil = g_sil;
   loss_terms_kernel<<<g, 256, 0, st>>>(a);
-  DIST_CUDA_TRY(cudaGetLastError());
+  DIST_LAUNCH_CHECK();
   if (dz && z && n_shapes > 0 && latent_dim > 0) {
     const long long nz = (long long)n_shapes * latent_dim;
     loss_reg_kernel<<<grid_for(nz, 256), 256, 0, st>>>(z, nz, w->w_reg, loss, dz);
-    DIST_CUDA_TRY(cudaGetLastError());
+    DIST_LAUNCH_CHECK();
   }
   return DIST_OK;
 }

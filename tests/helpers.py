@@ -31,6 +31,36 @@ def to_np(t):
     return t.detach().cpu().numpy()
 
 
+def bf16_round(x):
+    """Round to the nearest bfloat16 (ties to even), returned as float64."""
+    a = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    a = ((a + 0x7FFF + ((a >> 16) & 1)) >> 16) << 16
+    return a.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def bf16_decoder_reference(Ws, bs, Z, pts, shape, latent=256, skip=4):
+    """The DeepSDF decoder evaluated the way the BF16 tensor-core kernel does:
+    GEMM layers 1..7 with bf16-rounded weights and bf16-rounded input
+    activations (fp64 accumulation), layer 0, the skip layer's xyz columns,
+    the folded latent biases and the head in full precision."""
+    W = [np.asarray(w, dtype=np.float64) for w in Ws]
+    b = [np.asarray(v, dtype=np.float64) for v in bs]
+    z = np.asarray(Z, dtype=np.float64)[shape]
+    p = np.asarray(pts, dtype=np.float64)
+    hk = W[skip].shape[1] - latent - 3
+    b0 = (z @ W[0][:, :latent].T + b[0]).astype(np.float32).astype(np.float64)
+    bs_ = (z @ W[skip][:, hk:hk + latent].T + b[skip]).astype(np.float32).astype(np.float64)
+    h = np.maximum(p @ W[0][:, latent:].T + b0, 0.0)
+    for l in range(1, len(W) - 1):
+        hb = bf16_round(h)
+        if l == skip:
+            a = hb @ bf16_round(W[l][:, :hk]).T + p @ W[l][:, hk + latent:].T + bs_
+        else:
+            a = hb @ bf16_round(W[l]).T + b[l]
+        h = np.maximum(a, 0.0)
+    return np.tanh(h @ W[-1].T + b[-1])[:, 0]
+
+
 def ambiguous_rays(orc, tol_f, tol_d=1e-5, max_steps=50, grazing=0.05, near_miss=0.0,
                    normals=None):
     """Rays whose FP32 trace may take a different branch than FP64.
