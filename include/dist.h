@@ -189,6 +189,27 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
                           const float* pts, const int32_t* shape, int64_t n, int precision,
                           float* f, float* grad, dist_workspace* ws, void* stream);
 
+/* dist_sdf_eval without a workspace and without allocating (the paper has
+ * no counterpart: this is a convenience of this library).  Meant for callers
+ * that cannot call cudaMalloc: a plugin that must live inside a host
+ * application's fixed GPU memory budget, a framework whose pool owns all
+ * device memory, or a latency-critical thread that must not take the device
+ * synchronisation an allocation can imply.  The scratch (folded latent
+ * biases, packed points, gradient staging) is a built-in device array of
+ * 2,359,552 bytes that every GPU which loads the library keeps until the
+ * process exits.  Limits: 1 <= n <= 65536 points and 1 <= n_shapes <= 64;
+ * larger sizes return DIST_E_INVALID.  Arguments and results are those of
+ * dist_sdf_eval (no workspace).  The first call on a device, made with that
+ * device current, looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one
+ * array, so calls whose work overlaps on the GPU (different streams, or
+ * threads without ordering) race and corrupt each other's results; a call
+ * rewrites every scratch entry it reads, so nothing carries over between
+ * ordered calls.  Allocates nothing and frees nothing. */
+dist_status dist_sdf_eval_static(const dist_decoder* dec, const float* z, int n_shapes,
+                                 const float* pts, const int32_t* shape, int64_t n,
+                                 int precision, float* f, float* grad, void* stream);
+
 /* ------------------------------------------------------------------- loss */
 
 typedef struct {

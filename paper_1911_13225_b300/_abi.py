@@ -30,7 +30,7 @@ EXPORTS = [
     "dist_trace_params_default", "dist_workspace_create", "dist_workspace_destroy",
     "dist_trace_fwd", "dist_render_normals", "dist_sdf_eval", "dist_loss", "dist_trace_bwd",
     "dist_serve_create", "dist_serve_submit", "dist_serve_poll", "dist_serve_destroy",
-    "dist_last_error", "dist_version",
+    "dist_last_error", "dist_version", "dist_sdf_eval_static",
 ]
 
 
@@ -113,6 +113,8 @@ def lib():
         "dist_serve_destroy": (c_int, [c_void_p]),
         "dist_last_error": (c_char_p, []),
         "dist_version": (c_char_p, []),
+        "dist_sdf_eval_static": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int64,
+                                         c_int, c_void_p, c_void_p, c_void_p]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(L, name):

@@ -182,6 +182,14 @@ cudaError_t mlp_fp32_adjoint(const DecoderF32& d, const float4* pp, const float4
                              float* out4, double* gacc0, double* gaccs, int accumulate,
                              cudaStream_t st);
 
+// Point-evaluation helpers (trace.cu) for callers with their own scratch.
+cudaError_t launch_fold_bias(const DecoderF32& d, const float* z, int n_shapes, float* bfold0,
+                             float* bfolds, cudaStream_t st);
+cudaError_t launch_pack_points(const float* pts, const int* shape, long long n, int n_shapes,
+                               float4* out, int* count, cudaStream_t st);
+cudaError_t launch_unpack_grad(const float* out4, long long n, float* f, float* grad,
+                               cudaStream_t st);
+
 // BF16 tcgen05 decoder forward (DeepSDF shape only).
 cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
                            const float* bfolds, float* fout, cudaStream_t st);

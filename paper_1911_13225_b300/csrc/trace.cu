@@ -670,6 +670,31 @@ dist_status normals_impl(const dist_decoder* dec, const dist_trace_params* p,
 }
 
 }  // namespace
+
+// Launchers of the point-evaluation kernels for callers that bring their own
+// scratch memory instead of a workspace.
+cudaError_t launch_fold_bias(const DecoderF32& d, const float* z, int n_shapes, float* bfold0,
+                             float* bfolds, cudaStream_t st) {
+  dim3 g(n_shapes, 2, (d.width + 63) / 64);
+  fold_bias_kernel<<<g, 256, 0, st>>>(d, z, n_shapes, bfold0, bfolds);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_points(const float* pts, const int* shape, long long n, int n_shapes,
+                               float4* out, int* count, cudaStream_t st) {
+  pack_points_kernel<<<grid_for(n, 256), 256, 0, st>>>(pts, shape, n, n_shapes, out, count);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_grad(const float* out4, long long n, float* f, float* grad,
+                               cudaStream_t st) {
+  unpack_grad_kernel<<<grid_for(n, 256), 256, 0, st>>>(out4, n, f, grad);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
 }  // namespace dist
 
 using namespace dist;
