@@ -190,6 +190,30 @@ cudaError_t launch_pack_points(const float* pts, const int* shape, long long n, 
 cudaError_t launch_unpack_grad(const float* out4, long long n, float* f, float* grad,
                                cudaStream_t st);
 
+// A pool of rays driven one march step at a time (serving).  Pixel indices
+// are pool indices; camera index == request slot == latent index.
+struct RayPool {
+  const CamDev* cams;
+  float4* st;
+  float4* dir;
+  dist_trace_out o;
+  int K;
+  float eps, alpha, eps_bf16, radius;
+  int max_steps;
+};
+cudaError_t pool_write_cam(const CamDev& c, int slot, CamDev* dst, cudaStream_t st);
+cudaError_t pool_raygen(const RayPool& P, int cam, long long pix0, long long n, int* list0,
+                        int* count0, cudaStream_t st);
+cudaError_t pool_step(const RayPool& P, const int* cnt_in, int* cnt_out, int* const in[2],
+                      const float* const f[2], int* const out[2], cudaStream_t st);
+cudaError_t pool_probes_depth(const RayPool& P, int cam, long long pix0, long long n,
+                              const float* g_depth, float4* pp, float4* pq, int* pix, int* count,
+                              cudaStream_t st);
+cudaError_t pool_loss_depth(long long n, const float* depth, const uint8_t* mask, const float* tgt,
+                            double* loss, float* g_depth, int* cnt, cudaStream_t st);
+cudaError_t pool_latent_finalize(const DecoderF32& d, const double* G0, const double* Gs,
+                                 float* dz, cudaStream_t st);
+
 // BF16 tcgen05 decoder forward (DeepSDF shape only).
 cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
                            const float* bfolds, float* fout, cudaStream_t st);

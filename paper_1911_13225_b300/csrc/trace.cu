@@ -95,6 +95,8 @@ struct TraceArgs {
   const CamDev* cams;
   int n_cams;
   long long n_pix;
+  long long pix0;       // first pixel index handled (0 for a whole batch)
+  int cam_fixed;        // >= 0: every pixel belongs to this camera
   float radius;
   int K;
   float eps, alpha, eps_bf16;
@@ -112,10 +114,10 @@ __global__ void raygen_kernel(TraceArgs a, int* list0, int* count0) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
        base < a.n_pix; base += stride) {
-    const long long i = base + lane_id();
+    const long long i = a.pix0 + base + lane_id();
     bool enters = false;
-    if (i < a.n_pix) {
-      const int ci = find_cam(a.cams, a.n_cams, i);
+    if (base + lane_id() < a.n_pix) {
+      const int ci = a.cam_fixed >= 0 ? a.cam_fixed : find_cam(a.cams, a.n_cams, i);
       const CamDev& c = a.cams[ci];
       const long long li = i - c.offset;
       const int x = (int)(li % c.W), y = (int)(li / c.W);
@@ -260,6 +262,8 @@ struct ProbeArgs {
   const float4* st;       // unused after the trace except for the camera id
   const float4* dir;
   long long n_pix;
+  long long pix0;         // first pixel handled (probes_bwd_kernel)
+  int cam_fixed;          // >= 0: all pixels belong to this camera (probes_bwd_kernel)
   int n_cams;
   int K;
   dist_trace_out o;
@@ -355,10 +359,10 @@ __global__ void probes_bwd_kernel(ProbeArgs a, const float* g_depth, const float
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
        base < a.n_pix; base += stride) {
-    const long long i = base + lane_id();
+    const long long i = a.pix0 + base + lane_id();
     int nd = 0, ns = 0;
     float gd = 0.f, gs = 0.f;
-    if (i < a.n_pix) {
+    if (base + lane_id() < a.n_pix) {
       gd = g_depth ? g_depth[i] : 0.f;
       gs = g_sil ? g_sil[i] : 0.f;
       if (a.o.mask[i] && gd != 0.f) {
@@ -371,7 +375,7 @@ __global__ void probes_bwd_kernel(ProbeArgs a, const float* g_depth, const float
     }
     int slot = warp_append_n(nd + ns, a.count);
     if (nd + ns > 0) {
-      const CamDev& c = a.cams[find_cam(a.cams, a.n_cams, i)];
+      const CamDev& c = a.cams[a.cam_fixed >= 0 ? a.cam_fixed : find_cam(a.cams, a.n_cams, i)];
       const float4 v = a.dir[i];
       if (nd > 0 && !paper) {
         a.pp[slot] = ray_point(c, v, a.o.d_hit[i], c.shape);
@@ -622,6 +626,7 @@ TraceArgs make_args(const dist_trace_params* p, const dist_trace_out* o, dist_wo
                     int n_cams, long long n_pix) {
   TraceArgs a;
   a.cams = ws->cams; a.n_cams = n_cams; a.n_pix = n_pix; a.radius = p->radius; a.K = p->k_min;
+  a.pix0 = 0; a.cam_fixed = -1;
   a.eps = p->eps; a.alpha = p->alpha; a.eps_bf16 = p->eps_bf16; a.max_steps = p->max_steps;
   a.o = *o; a.st = ws->st; a.dir = ws->dir;
   return a;
@@ -631,6 +636,7 @@ ProbeArgs make_probe_args(const dist_trace_params* p, const dist_trace_out* o, d
                           int n_cams, long long n_pix, long long offset, int count_slot) {
   ProbeArgs a;
   a.cams = ws->cams; a.st = ws->st; a.dir = ws->dir; a.n_pix = n_pix; a.n_cams = n_cams;
+  a.pix0 = 0; a.cam_fixed = -1;
   a.K = p->k_min; a.o = *o;
   a.pp = ws->probe_p + offset; a.pq = ws->probe_q + offset; a.pix = ws->probe_pix + offset;
   a.count = ws->probe_count + count_slot;
@@ -691,6 +697,82 @@ cudaError_t launch_pack_points(const float* pts, const int* shape, long long n, 
 cudaError_t launch_unpack_grad(const float* out4, long long n, float* f, float* grad,
                                cudaStream_t st) {
   unpack_grad_kernel<<<grid_for(n, 256), 256, 0, st>>>(out4, n, f, grad);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+// ---- serving: the server drives the same kernels one step at a time over a
+// pool of rays that belong to many requests (one camera slot per request).
+
+static TraceArgs pool_args(const RayPool& P) {
+  TraceArgs a;
+  a.cams = P.cams; a.n_cams = 0; a.n_pix = 0; a.pix0 = 0; a.cam_fixed = -1;
+  a.radius = P.radius; a.K = P.K; a.eps = P.eps; a.alpha = P.alpha; a.eps_bf16 = P.eps_bf16;
+  a.max_steps = P.max_steps; a.o = P.o; a.st = P.st; a.dir = P.dir;
+  return a;
+}
+
+cudaError_t pool_write_cam(const CamDev& c, int slot, CamDev* dst, cudaStream_t st) {
+  CamChunk ch;
+  std::memset(&ch, 0, sizeof(ch));
+  ch.c[0] = c;
+  ch.n = 1;
+  ch.first = slot;
+  write_cams_kernel<<<1, 64, 0, st>>>(ch, dst);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t pool_raygen(const RayPool& P, int cam, long long pix0, long long n, int* list0,
+                        int* count0, cudaStream_t st) {
+  TraceArgs a = pool_args(P);
+  a.n_pix = n; a.pix0 = pix0; a.cam_fixed = cam;
+  raygen_kernel<<<grid_for(n, 256), 256, 0, st>>>(a, list0, count0);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t pool_step(const RayPool& P, const int* cnt_in, int* cnt_out, int* const in[2],
+                      const float* const f[2], int* const out[2], cudaStream_t st) {
+  StepLists L;
+  L.cnt_in = cnt_in; L.cnt_out = cnt_out;
+  for (int k = 0; k < 2; ++k) { L.in[k] = in[k]; L.f[k] = f[k]; L.out[k] = out[k]; }
+  step_kernel<<<num_sms() * 4, 256, 0, st>>>(pool_args(P), L, P.o.queries);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t pool_probes_depth(const RayPool& P, int cam, long long pix0, long long n,
+                              const float* g_depth, float4* pp, float4* pq, int* pix, int* count,
+                              cudaStream_t st) {
+  ProbeArgs a;
+  a.cams = P.cams; a.st = P.st; a.dir = P.dir; a.n_pix = n; a.pix0 = pix0; a.cam_fixed = cam;
+  a.n_cams = 0; a.K = P.K; a.o = P.o; a.pp = pp; a.pq = pq; a.pix = pix; a.count = count;
+  probes_bwd_kernel<<<grid_for(n, 256), 256, 0, st>>>(a, g_depth, nullptr, 0, P.alpha);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t pool_loss_depth(long long n, const float* depth, const uint8_t* mask, const float* tgt,
+                            double* loss, float* g_depth, int* cnt, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(cnt, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  loss_count_kernel<<<grid_for(n, 256), 256, 0, st>>>(n, mask, tgt, cnt);
+  LossArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.n = n; a.depth = depth; a.tgt_depth = tgt; a.mask = mask; a.cnt = cnt; a.loss = loss;
+  a.g_depth = g_depth;
+  a.w.w_depth = 1.f;
+  loss_terms_kernel<<<grid_for(n, 256), 256, 0, st>>>(a);
+  count_launch(2);
+  return cudaGetLastError();
+}
+
+cudaError_t pool_latent_finalize(const DecoderF32& d, const double* G0, const double* Gs,
+                                 float* dz, cudaStream_t st) {
+  dim3 fg((d.latent + 127) / 128, 1);
+  latent_finalize_kernel<<<fg, 128, 0, st>>>(d, G0, Gs, 1, dz);
   count_launch(1);
   return cudaGetLastError();
 }
