@@ -159,7 +159,8 @@ def run_ours(args, rank, world, local_rank):
     precision = args.precision
     if precision == "auto":
         precision = "bf16" if dec.has_bf16 else "fp32"
-    params = api.TraceParams(max_steps=MAX_STEPS, precision=precision)
+    params = api.TraceParams(max_steps=MAX_STEPS, precision=precision, eps_bf16=args.eps_lo,
+                             refine_steps=args.refine)
     ws = api.Workspace(SIZE * SIZE, MAX_STEPS)
     z = torch.from_numpy(Z).to(dev)
     # target: depth of the second latent (untimed setup)
@@ -199,8 +200,8 @@ def run_ours(args, rank, world, local_rank):
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in evs]
     total_ms = float(sum(step_ms))
-    ms_arr = (c_double * 2)()
-    cnt_arr = (c_int64 * 2)()
+    ms_arr = (c_double * 3)()
+    cnt_arr = (c_int64 * 3)()
     all_launches = c_int64()
     _abi.check(L.dist_profile_read(ms_arr, cnt_arr, byref(all_launches)), "dist_profile_read")
     queries = step.res.queries.cpu().numpy().astype(np.int64)
@@ -234,11 +235,13 @@ def run_ours(args, rank, world, local_rank):
     rays = SIZE * SIZE
     value = rays * world * args.steps / (total_ms * 1e-3)
     peaks, peak_src = load_peaks()
-    if precision == "bf16":
+    if precision in ("bf16", "fp16"):
         k_ms, k_q, k_n = ms_arr[0], queries[0], cnt_arr[0]
         achieved = k_q * FLOP_PER_QUERY / (k_ms * 1e-3) / 1e12 if k_ms > 0 else 0.0
         peak = peaks["bf16_tflops"]
-        roof = {"bound": "tensor", "kernel": "mlp_tc_kernel (BF16 tcgen05 decoder)",
+        roof = {"bound": "tensor",
+                "kernel": f"mlp_tc_kernel ({precision.upper()} tcgen05 decoder; fp16 and "
+                          f"bf16 share the dense tensor rate)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "peak_source": f"{peak_src} bf16 burst",
                 "traffic": None}
@@ -254,15 +257,21 @@ def run_ours(args, rank, world, local_rank):
     roof["mlp_ms_per_step"] = k_ms / args.steps
     roof["mlp_launches_per_step"] = k_n / args.steps
     roof["queries_per_step"] = float(k_q) / args.steps
+    breakdown = {"march_bf16_tc_ms": ms_arr[0] / args.steps,
+                 "march_fp32_simt_ms": ms_arr[1] / args.steps,
+                 "adjoint_ms": ms_arr[2] / args.steps,
+                 "other_ms": ms_per_step - (ms_arr[0] + ms_arr[1] + ms_arr[2]) / args.steps}
     bi = z_host.numel() * 4 + tgt_host.numel() * 4
     bo = 8 + dz_host.numel() * 4
     line = {
         "metric": "rays/s (pixels traced per second, forward+backward)",
         "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if precision == "bf16" else "f32",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16": "bf16", "fp16": "f16", "fp32": "f32"}[precision],
         "data": "synthetic (seeded decoder, latents and camera; no DeepSDF weights)",
         "config": {"workload": WORKLOAD, "rays_per_step": rays, "precision": precision,
+                   "eps_lo": args.eps_lo, "refine_steps": args.refine,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MB write, untimed)"},
         "sdf_queries_per_s": float(queries.sum()) * world / (total_ms * 1e-3),
@@ -272,6 +281,7 @@ def run_ours(args, rank, world, local_rank):
         "e2e": {"value": rays * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo},
         "gpu_launches": int(all_launches.value),
+        "step_breakdown_ms": breakdown,
         "roofline": roof,
         "clocks": clk,
     }
@@ -360,7 +370,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp32"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp16", "fp32"])
+    ap.add_argument("--eps-lo", type=float, default=1e-3,
+                    help="|f| below which a BF16/FP16 ray switches to FP32 queries")
+    ap.add_argument("--refine", type=int, default=0,
+                    help="0: FP32 convergence to eps; n: accept after n FP32 queries")
     ap.add_argument("--cpu-crop", type=int, default=96)
     ap.add_argument("--ref-crop", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")

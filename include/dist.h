@@ -46,7 +46,10 @@ typedef enum {
                              shape it does not cover                      */
 } dist_status;
 
-typedef enum { DIST_PREC_FP32 = 0, DIST_PREC_BF16 = 1 } dist_precision;
+/* Precision of the marching decoder queries.  BF16 and FP16 run the GEMM
+ * layers on the tensor cores (16-bit operands, FP32 accumulation) and hand a
+ * ray to FP32 queries once |f| < eps_bf16; FP32 runs every query in FP32. */
+typedef enum { DIST_PREC_FP32 = 0, DIST_PREC_BF16 = 1, DIST_PREC_FP16 = 2 } dist_precision;
 typedef enum { DIST_GRAD_EXACT = 0, DIST_GRAD_PAPER = 1 } dist_grad_mode;
 
 /* Ray outcome codes written to dist_trace_out.status. */
@@ -110,13 +113,19 @@ typedef struct {
                           with this step (Sec. 3.3)                         */
   int grad_mode;       /* dist_grad_mode for the depth term                */
   int precision;       /* dist_precision of the marching queries           */
-  float eps_bf16;      /* BF16 path: |f_bf16| below which a ray switches
-                          to FP32 queries (then converges on eps)          */
+  float eps_bf16;      /* BF16/FP16 path: |f| below which a ray switches
+                          to FP32 queries at the same point                 */
   float radius;        /* bounding sphere radius (Sec. 3.2: unit sphere)   */
+  int refine_steps;    /* BF16/FP16 path: 0 = FP32 queries continue until
+                          |f| < eps; n > 0 = after n FP32 queries a ray with
+                          |f| < 4 eps_bf16 is also accepted as a hit (unit
+                          final step, Eq. 1), its silhouette then reported
+                          as |f| - 4 eps_bf16.  Ignored for FP32.          */
 } dist_trace_params;
 
 /* Fill `p` with the paper's defaults: max_steps 50, eps 5e-5, alpha 1.5,
- * k_min 1, normal_delta 0, exact gradients, FP32, eps_bf16 1e-3, radius 1. */
+ * k_min 1, normal_delta 0, exact gradients, FP32, eps_bf16 1e-3, radius 1,
+ * refine_steps 0. */
 void dist_trace_params_default(dist_trace_params* p);
 
 /* -------------------------------------------------------------- workspace */
@@ -305,13 +314,14 @@ dist_status dist_serve_destroy(dist_server* s);
  * their roofline.  While enabled, every decoder-MLP launch of the march in
  * dist_trace_fwd (the dominant kernels) is bracketed by CUDA events recorded
  * on the stream it is launched on, and every kernel launch of the library is
- * counted.  enable = 1 resets the counters and starts recording (host-side
- * state, not thread-safe); 0 stops.  dist_profile_read synchronises the
- * recorded events and returns, per kernel kind ([0] BF16 tensor-core MLP,
- * [1] FP32 SIMT MLP), the summed kernel time in ms and the number of timed
- * launches, plus the count of all library kernel launches.  Each array
- * argument points to 2 host values; any pointer may be NULL.  At most 65536
- * launches are timed per enable. */
+ * counted, as is every decoder adjoint launch (normals and backward).
+ * enable = 1 resets the counters and starts recording (host-side state, not
+ * thread-safe); 0 stops.  dist_profile_read synchronises the recorded events
+ * and returns, per kernel kind ([0] BF16 tensor-core MLP of the march,
+ * [1] FP32 SIMT MLP of the march, [2] decoder adjoint), the summed kernel
+ * time in ms and the number of timed launches, plus the count of all library
+ * kernel launches.  Each array argument points to 3 host values; any pointer
+ * may be NULL.  At most 65536 launches are timed per enable. */
 dist_status dist_profile_enable(int enable);
 dist_status dist_profile_read(double* mlp_ms, int64_t* mlp_launches, int64_t* all_launches);
 

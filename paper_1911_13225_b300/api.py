@@ -38,17 +38,18 @@ class TraceParams:
     k_min: int = 1
     normal_delta: float = 0.0
     grad_mode: str = "exact"      # "exact" | "paper"
-    precision: str = "fp32"       # "fp32" | "bf16"
-    eps_bf16: float = 1e-3
+    precision: str = "fp32"       # "fp32" | "bf16" | "fp16"
+    eps_bf16: float = 1e-3        # low-precision phase threshold (BF16 / FP16)
     radius: float = 1.0
+    refine_steps: int = 0         # 0: FP32 convergence; n: accept after n FP32 queries
 
     def c(self) -> _abi.TraceParams:
         return _abi.TraceParams(
             int(self.max_steps), float(self.eps), float(self.alpha), int(self.k_min),
             float(self.normal_delta),
             _abi.GRAD_EXACT if self.grad_mode == "exact" else _abi.GRAD_PAPER,
-            _abi.PREC_FP32 if self.precision == "fp32" else _abi.PREC_BF16,
-            float(self.eps_bf16), float(self.radius))
+            _abi.PRECISIONS[self.precision], float(self.eps_bf16), float(self.radius),
+            int(self.refine_steps))
 
 
 def camera_struct(cam) -> _abi.Camera:
@@ -197,7 +198,7 @@ def sdf_eval(dec: Decoder, z: torch.Tensor, pts: torch.Tensor, shape: torch.Tens
     n = pts.shape[0]
     f = torch.empty(n, device=pts.device, dtype=torch.float32)
     g = torch.empty(n, 3, device=pts.device, dtype=torch.float32) if grad else None
-    prec = _abi.PREC_FP32 if precision == "fp32" else _abi.PREC_BF16
+    prec = _abi.PRECISIONS[precision]
     check(lib().dist_sdf_eval(dec.handle, _ptr(z.contiguous()), int(z.shape[0]), _ptr(pts),
                               _ptr(shape), n, prec, _ptr(f), _ptr(g), ws.handle, _stream(stream)),
           "dist_sdf_eval")

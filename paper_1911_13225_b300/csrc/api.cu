@@ -68,6 +68,7 @@ void dist_trace_params_default(dist_trace_params* p) {
   p->precision = DIST_PREC_FP32;
   p->eps_bf16 = 1e-3f;
   p->radius = 1.f;
+  p->refine_steps = 0;
 }
 
 dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* const* W,
@@ -182,6 +183,8 @@ dist_status dist_workspace_create(int64_t max_rays, int max_steps, dist_workspac
   }
   WS_ALLOC(dir, n * sizeof(float4));
   WS_ALLOC(st, n * sizeof(float4));
+  WS_ALLOC(fq, n * sizeof(int));
+  WS_ALLOC(fprev, n * sizeof(float));
   WS_ALLOC(act[0][0], n * sizeof(int));
   WS_ALLOC(act[0][1], n * sizeof(int));
   WS_ALLOC(act[1][0], n * sizeof(int));

@@ -45,6 +45,11 @@ void prof_mlp_end(cudaStream_t st);
     }                                                                         \
   } while (0)
 
+// Precisions whose march runs on the tensor cores.
+inline bool is_tc(int precision) {
+  return precision == DIST_PREC_BF16 || precision == DIST_PREC_FP16;
+}
+
 constexpr int kMaxShapes = 1024;    // folded-bias capacity of a workspace
 constexpr int kMaxK = 3;            // k_min upper bound (Sec. B.4 uses 1 or 3)
 constexpr int kProbesPerRay = 10;   // probe capacity per pixel in a workspace:
@@ -91,8 +96,8 @@ struct TCMaps {
 };
 struct DecoderTC {
   bool ok;
-  const __nv_bfloat16* W[7];
-  TCMaps maps;
+  TCMaps maps;                   // bf16 operands
+  TCMaps maps16;                 // fp16 operands (same layout)
   int* err;                      // device error word of the bounded waits
 };
 
@@ -111,6 +116,8 @@ struct dist_workspace {
   // ray state
   float4* dir;        // (vx, vy, vz, 1/sqrt(x~^2+y~^2+1))
   float4* st;         // (d, t_in, t_out, camera index as int bits)
+  int* fq;            // FP32 queries a ray made after its low-precision phase
+  float* fprev;       // previous low-precision sample of each ray
   int* act[2][2];     // [parity][0 = BF16 list, 1 = FP32 list] active ray ids
   float* fbuf[2];     // MLP outputs for the two lists
   int* counts;        // [(max_steps + 2) * 2] list lengths per step
@@ -171,8 +178,10 @@ __device__ __forceinline__ void rowsrc_load(const RowSrc& s, int j, float3& p, i
 int num_sms();
 
 // FP32 SIMT decoder forward over `src` rows: fout[j] = f(p_j, z_shape_j).
+// small_tiles: 16-row tiles (for short, latency-bound row lists).
 cudaError_t mlp_fp32_forward(const DecoderF32& d, const RowSrc& src, const float* bfold0,
-                             const float* bfolds, float* fout, cudaStream_t st);
+                             const float* bfolds, float* fout, cudaStream_t st,
+                             bool small_tiles = false);
 
 // FP32 SIMT adjoint over probes: f and grad_p f per probe (out4, optional) and
 // FP64 accumulation of coef * (pre-activation gradients at layer 0 and the
@@ -196,6 +205,9 @@ struct RayPool {
   const CamDev* cams;
   float4* st;
   float4* dir;
+  int* fq;
+  float* fprev;
+  int refine;
   dist_trace_out o;
   int K;
   float eps, alpha, eps_bf16, radius;
@@ -214,8 +226,9 @@ cudaError_t pool_loss_depth(long long n, const float* depth, const uint8_t* mask
 cudaError_t pool_latent_finalize(const DecoderF32& d, const double* G0, const double* Gs,
                                  float* dz, cudaStream_t st);
 
-// BF16 tcgen05 decoder forward (DeepSDF shape only).
+// tcgen05 decoder forward with BF16 (f16 = false) or FP16 operands
+// (DeepSDF shape only).
 cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
-                           const float* bfolds, float* fout, cudaStream_t st);
+                           const float* bfolds, float* fout, cudaStream_t st, bool f16);
 
 }  // namespace dist

@@ -139,11 +139,10 @@ __device__ __forceinline__ void relu_rows(float4 (&acc)[4][WIDTH / 128]) {
 
 // ---------------------------------------------------------------- forward
 
-template <int WIDTH>
-__global__ void __launch_bounds__(kFwdRows * 8, 1)
+template <int WIDTH, int TM>
+__global__ void __launch_bounds__(TM * 8, TM >= 64 ? 1 : 4)
 mlp_fp32_fwd_kernel(DecoderF32 d, RowSrc src, const float* bfold0, const float* bfolds,
                     float* __restrict__ fout) {
-  constexpr int TM = kFwdRows;
   extern __shared__ __align__(16) float smem[];
   float* A = smem;                                         // [TM][WIDTH]
   float4* pos = reinterpret_cast<float4*>(A + TM * WIDTH);   // [TM]
@@ -379,8 +378,8 @@ mlp_fp32_adj_kernel(DecoderF32 d, const float4* __restrict__ pp, const float4* _
   }
 }
 
-template <int WIDTH>
-size_t fwd_smem() { return (size_t)kFwdRows * WIDTH * 4 + kFwdRows * 16; }
+template <int WIDTH, int TM>
+size_t fwd_smem() { return (size_t)TM * WIDTH * 4 + TM * 16; }
 
 template <int WIDTH>
 size_t adj_smem() {
@@ -388,18 +387,22 @@ size_t adj_smem() {
          kAdjRows * 16 + kAdjRows * 4 + (size_t)(kAdjRows / 4) * WIDTH * 8;
 }
 
-template <int WIDTH>
+// TM = 64 rows per CTA (one CTA per SM) for large batches; TM = 16 (four
+// CTAs per SM) for the sparse lists of the march, where the latency of one
+// tile, not throughput, sets the launch time.
+template <int WIDTH, int TM>
 cudaError_t launch_fwd(const DecoderF32& d, const RowSrc& src, const float* b0, const float* bs,
                        float* fout, cudaStream_t st) {
-  const size_t sm = fwd_smem<WIDTH>();
+  const size_t sm = fwd_smem<WIDTH, TM>();
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_fp32_fwd_kernel<WIDTH>,
+    cudaError_t e = cudaFuncSetAttribute(mlp_fp32_fwd_kernel<WIDTH, TM>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  mlp_fp32_fwd_kernel<WIDTH><<<num_sms(), kFwdRows * 8, sm, st>>>(d, src, b0, bs, fout);
+  const int grid = num_sms() * (TM >= 64 ? 1 : 4);
+  mlp_fp32_fwd_kernel<WIDTH, TM><<<grid, TM * 8, sm, st>>>(d, src, b0, bs, fout);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -416,8 +419,10 @@ cudaError_t launch_adj(const DecoderF32& d, const float4* pp, const float4* pq, 
     if (e != cudaSuccess) return e;
     configured = true;
   }
+  prof_mlp_begin(st, 2);
   mlp_fp32_adj_kernel<WIDTH><<<num_sms(), kAdjRows * 8, sm, st>>>(d, pp, pq, count, b0, bs, out4,
                                                                     g0, gs, acc);
+  prof_mlp_end(st);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -425,12 +430,21 @@ cudaError_t launch_adj(const DecoderF32& d, const float4* pp, const float4* pq, 
 }  // namespace
 
 cudaError_t mlp_fp32_forward(const DecoderF32& d, const RowSrc& src, const float* bfold0,
-                             const float* bfolds, float* fout, cudaStream_t st) {
-  switch (d.width) {
-    case 128: return launch_fwd<128>(d, src, bfold0, bfolds, fout, st);
-    case 256: return launch_fwd<256>(d, src, bfold0, bfolds, fout, st);
-    case 384: return launch_fwd<384>(d, src, bfold0, bfolds, fout, st);
-    case 512: return launch_fwd<512>(d, src, bfold0, bfolds, fout, st);
+                             const float* bfolds, float* fout, cudaStream_t st, bool small_tiles) {
+  if (small_tiles) {
+    switch (d.width) {
+      case 128: return launch_fwd<128, 16>(d, src, bfold0, bfolds, fout, st);
+      case 256: return launch_fwd<256, 16>(d, src, bfold0, bfolds, fout, st);
+      case 384: return launch_fwd<384, 16>(d, src, bfold0, bfolds, fout, st);
+      case 512: return launch_fwd<512, 16>(d, src, bfold0, bfolds, fout, st);
+    }
+  } else {
+    switch (d.width) {
+      case 128: return launch_fwd<128, kFwdRows>(d, src, bfold0, bfolds, fout, st);
+      case 256: return launch_fwd<256, kFwdRows>(d, src, bfold0, bfolds, fout, st);
+      case 384: return launch_fwd<384, kFwdRows>(d, src, bfold0, bfolds, fout, st);
+      case 512: return launch_fwd<512, kFwdRows>(d, src, bfold0, bfolds, fout, st);
+    }
   }
   return cudaErrorInvalidValue;
 }

@@ -44,8 +44,12 @@ constexpr unsigned long long kTimeoutNs = 1000000000ull;
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
 // B bf16 (10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
 // M >> 4 at bits 24-28.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) |
-                            ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// With F16 the operand formats (bits 7-9, 10-12) are 0 = fp16 instead of bf16.
+template <bool F16>
+__host__ __device__ constexpr uint32_t instr_desc() {
+  return (1u << 4) | ((F16 ? 0u : 1u) << 7) | ((F16 ? 0u : 1u) << 10) |
+         ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
 __host__ __device__ constexpr int gemm_k(int g) { return g == 3 ? 256 : 512; }
 __host__ __device__ constexpr int gemm_n(int g) { return g == 2 ? 256 : 512; }
@@ -166,22 +170,30 @@ __device__ __forceinline__ uint32_t swz(int r, int u) {
   return (uint32_t)(r * 128 + ((u ^ (r & 7)) << 4));
 }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
-  return *reinterpret_cast<uint32_t*>(&h);
+// Two floats rounded to the operand type (nearest even), packed.
+template <bool F16>
+__device__ __forceinline__ uint32_t pack16(float a, float b) {
+  if constexpr (F16) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
 }
 
 // Store 32 consecutive activations (columns c..c+31, c % 32 == 0) of row r.
+template <bool F16>
 __device__ __forceinline__ void store_act32(uint8_t* act, int r, int c, const float (&v)[32]) {
   uint8_t* chunk = act + (c >> 6) * CHUNK_BYTES;
   const int u0 = (c & 63) >> 3;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const uint32_t off = swz(r, u0 + q);
-    const uint32_t a = pack_bf16(v[8 * q + 0], v[8 * q + 1]);
-    const uint32_t b = pack_bf16(v[8 * q + 2], v[8 * q + 3]);
-    const uint32_t cc = pack_bf16(v[8 * q + 4], v[8 * q + 5]);
-    const uint32_t d = pack_bf16(v[8 * q + 6], v[8 * q + 7]);
+    const uint32_t a = pack16<F16>(v[8 * q + 0], v[8 * q + 1]);
+    const uint32_t b = pack16<F16>(v[8 * q + 2], v[8 * q + 3]);
+    const uint32_t cc = pack16<F16>(v[8 * q + 4], v[8 * q + 5]);
+    const uint32_t d = pack16<F16>(v[8 * q + 6], v[8 * q + 7]);
     asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(chunk + off)), "r"(a),
                  "r"(b), "r"(cc), "r"(d)
                  : "memory");
@@ -201,8 +213,10 @@ struct TCArgs {
   int* err;
 };
 
+template <bool F16>
 __global__ void __launch_bounds__(THREADS, 1)
 mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
+  constexpr uint32_t kIdesc = instr_desc<F16>();
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -342,7 +356,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
             const float t = fmaf(w.x, p.x, fmaf(w.y, p.y, fmaf(w.z, p.z, __ldg(bf + c + i))));
             v[i] = fmaxf(t, 0.f);
           }
-          store_act32(act, row, c, v);
+          store_act32<F16>(act, row, c, v);
         }
         fence_async_shared();
         mbar_arrive(act_full);
@@ -378,7 +392,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
           if (g < NUM_GEMM - 1) {
-            store_act32(act, row, c, v);
+            store_act32<F16>(act, row, c, v);
           } else {
 #pragma unroll
             for (int i = 0; i < 32; i += 4) {
@@ -439,29 +453,40 @@ dist_status pack_tc(dist_decoder* d, const float* const* W) {
   auto enc = tensor_map_encoder();
   DIST_CHECK(enc != nullptr, DIST_E_CUDA, "cuTensorMapEncodeTiled entry point not available");
   const int L = 256, Hh = 253;   // latent, h-part of the skip input
-  for (int g = 0; g < NUM_GEMM; ++g) {
-    const int l = g + 1;
-    const int N = gemm_n(g), K = gemm_k(g);
-    std::vector<__nv_bfloat16> h((size_t)N * K, __float2bfloat16_rn(0.f));
-    const int n_real = (l == 3) ? Hh : 512;
-    const int k_real = (l == 4) ? Hh : 512;
-    const int in_dim = (l == 4) ? Hh + L + 3 : 512;
-    for (int n = 0; n < n_real; ++n)
-      for (int k = 0; k < k_real; ++k)
-        h[(size_t)n * K + k] = __float2bfloat16_rn(W[l][(size_t)n * in_dim + k]);
-    void* p = nullptr;
-    DIST_CUDA_TRY(cudaMalloc(&p, h.size() * sizeof(__nv_bfloat16)));
-    d->allocations.push_back(p);
-    DIST_CUDA_TRY(cudaMemcpy(p, h.data(), h.size() * sizeof(__nv_bfloat16), cudaMemcpyHostToDevice));
-    d->tc.W[g] = static_cast<const __nv_bfloat16*>(p);
-    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
-    cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(__nv_bfloat16)};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BN};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(&d->tc.maps.m[g], CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p, dims, strides, box,
-                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed");
+  for (int f16 = 0; f16 < 2; ++f16) {
+    for (int g = 0; g < NUM_GEMM; ++g) {
+      const int l = g + 1;
+      const int N = gemm_n(g), K = gemm_k(g);
+      std::vector<uint16_t> h((size_t)N * K, 0);   // +0 in both formats
+      const int n_real = (l == 3) ? Hh : 512;
+      const int k_real = (l == 4) ? Hh : 512;
+      const int in_dim = (l == 4) ? Hh + L + 3 : 512;
+      for (int n = 0; n < n_real; ++n)
+        for (int k = 0; k < k_real; ++k) {
+          const float w = W[l][(size_t)n * in_dim + k];
+          if (f16) {
+            __half v = __float2half_rn(w);
+            h[(size_t)n * K + k] = *reinterpret_cast<uint16_t*>(&v);
+          } else {
+            __nv_bfloat16 v = __float2bfloat16_rn(w);
+            h[(size_t)n * K + k] = *reinterpret_cast<uint16_t*>(&v);
+          }
+        }
+      void* p = nullptr;
+      DIST_CUDA_TRY(cudaMalloc(&p, h.size() * sizeof(uint16_t)));
+      d->allocations.push_back(p);
+      DIST_CUDA_TRY(cudaMemcpy(p, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+      cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
+      cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(uint16_t)};
+      cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BN};
+      cuuint32_t estr[2] = {1, 1};
+      CUtensorMap* m = f16 ? &d->tc.maps16.m[g] : &d->tc.maps.m[g];
+      CUresult r = enc(m, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                       2, p, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                       CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                       CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed");
+    }
   }
   void* e = nullptr;
   DIST_CUDA_TRY(cudaMalloc(&e, sizeof(int)));
@@ -473,12 +498,15 @@ dist_status pack_tc(dist_decoder* d, const float* const* W) {
 }
 
 cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
-                           const float* bfolds, float* fout, cudaStream_t st) {
+                           const float* bfolds, float* fout, cudaStream_t st, bool f16) {
   if (!dec->tc.ok) return cudaErrorNotSupported;
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         SMEM_BYTES);
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mlp_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               SMEM_BYTES);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -494,7 +522,10 @@ cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const flo
   a.src = src;
   a.fout = fout;
   a.err = dec->tc.err;
-  mlp_tc_kernel<<<num_sms(), THREADS, SMEM_BYTES, st>>>(dec->tc.maps, a);
+  if (f16)
+    mlp_tc_kernel<true><<<num_sms(), THREADS, SMEM_BYTES, st>>>(dec->tc.maps16, a);
+  else
+    mlp_tc_kernel<false><<<num_sms(), THREADS, SMEM_BYTES, st>>>(dec->tc.maps, a);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -60,8 +60,8 @@ dist_status dist_profile_enable(int enable) {
 }
 
 dist_status dist_profile_read(double* mlp_ms, int64_t* mlp_launches, int64_t* all_launches) {
-  double ms[2] = {0.0, 0.0};
-  int64_t cnt[2] = {0, 0};
+  double ms[3] = {0.0, 0.0, 0.0};
+  int64_t cnt[3] = {0, 0, 0};
   for (int i = 0; i + 1 < g_prof.used; i += 2) {
     DIST_CUDA_TRY(cudaEventSynchronize(g_prof.ev[i + 1]));
     float t = 0.f;
@@ -70,8 +70,10 @@ dist_status dist_profile_read(double* mlp_ms, int64_t* mlp_launches, int64_t* al
     ms[k] += t;
     cnt[k] += 1;
   }
-  if (mlp_ms) { mlp_ms[0] = ms[0]; mlp_ms[1] = ms[1]; }
-  if (mlp_launches) { mlp_launches[0] = cnt[0]; mlp_launches[1] = cnt[1]; }
+  for (int k = 0; k < 3; ++k) {
+    if (mlp_ms) mlp_ms[k] = ms[k];
+    if (mlp_launches) mlp_launches[k] = cnt[k];
+  }
   if (all_launches) *all_launches = g_prof.launches;
   return DIST_OK;
 }

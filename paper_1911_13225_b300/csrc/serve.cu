@@ -61,7 +61,7 @@ __global__ void count_slots_kernel(const int* l0, const int* c0, const int* l1, 
 size_t bytes_per_pixel(int K) {
   // ray state, lists, MLP outputs, per-pixel outputs, target, upstream
   // gradient and backward probes
-  return 16 + 16 + 16 + 8 + (4 + 4 + 1 + 4 + 4 + 4 + 8 * K) + 4 + 4 + (16 + 16 + 4);
+  return 16 + 16 + 8 + 16 + 8 + (4 + 4 + 1 + 4 + 4 + 4 + 8 * K) + 4 + 4 + (16 + 16 + 4);
 }
 
 }  // namespace
@@ -80,6 +80,8 @@ struct dist_server {
   // device pool
   float4* dir = nullptr;
   float4* stt = nullptr;
+  int* fq = nullptr;
+  float* fprev = nullptr;
   int* act[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   float* fbuf[2] = {nullptr, nullptr};
   int* cnt = nullptr;             // [parity][list]
@@ -115,7 +117,8 @@ struct dist_server {
 
   RayPool pool() const {
     RayPool P;
-    P.cams = cams; P.st = stt; P.dir = dir;
+    P.cams = cams; P.st = stt; P.dir = dir; P.fq = fq; P.fprev = fprev;
+    P.refine = is_tc(p.precision) ? p.refine_steps : 0;
     std::memset(&P.o, 0, sizeof(P.o));
     P.o.depth = depth; P.o.sil = sil; P.o.mask = mask; P.o.steps = steps; P.o.status = status;
     P.o.d_hit = d_hit; P.o.d_min = d_min; P.o.f_min = f_min; P.o.queries = queries;
@@ -174,7 +177,7 @@ struct dist_server {
       }
     }
     *any = !now.empty();
-    const int first = p.precision == DIST_PREC_BF16 ? 0 : 1;
+    const int first = is_tc(p.precision) ? 0 : 1;
     const RayPool P = pool();
     for (Req* R : now) {
       CamDev c;
@@ -203,14 +206,14 @@ struct dist_server {
     const float* bs = bfold + (size_t)max_req * 512;
     RowSrc src{};
     src.st = stt; src.dir = dir; src.cams = cams;
-    if (p.precision == DIST_PREC_BF16) {
+    if (is_tc(p.precision)) {
       src.count = cnt + 2 * par;
       src.idx = act[par][0];
-      DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, fbuf[0], st));
+      DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, fbuf[0], st, p.precision == DIST_PREC_FP16));
     }
     src.count = cnt + 2 * par + 1;
     src.idx = act[par][1];
-    DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, fbuf[1], st));
+    DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, fbuf[1], st, is_tc(p.precision)));
     DIST_CUDA_TRY(cudaMemsetAsync(cnt + 2 * (par ^ 1), 0, 2 * sizeof(int), st));
     int* in[2] = {act[par][0], act[par][1]};
     const float* f[2] = {fbuf[0], fbuf[1]};
@@ -356,7 +359,9 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
   DIST_CHECK(p->max_steps >= 1 && p->k_min >= 1 && p->k_min <= kMaxK && p->eps > 0.f &&
                  p->alpha > 0.f && p->radius > 0.f,
              DIST_E_INVALID, "dist_serve_create: bad trace parameters");
-  DIST_CHECK(p->precision != DIST_PREC_BF16 || dec->tc.ok, DIST_E_UNSUPPORTED,
+  DIST_CHECK(p->precision == DIST_PREC_FP32 || is_tc(p->precision), DIST_E_INVALID,
+             "dist_serve_create: bad precision");
+  DIST_CHECK(!is_tc(p->precision) || dec->tc.ok, DIST_E_UNSUPPORTED,
              "BF16 tensor-core MLP covers only the DeepSDF decoder shape");
   dist_server* S = new dist_server();
   S->dec = dec;
@@ -377,6 +382,8 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
   }
   SV_ALLOC(dir, n * sizeof(float4));
   SV_ALLOC(stt, n * sizeof(float4));
+  SV_ALLOC(fq, n * sizeof(int));
+  SV_ALLOC(fprev, n * sizeof(float));
   SV_ALLOC(act[0][0], n * sizeof(int));
   SV_ALLOC(act[0][1], n * sizeof(int));
   SV_ALLOC(act[1][0], n * sizeof(int));

@@ -101,9 +101,12 @@ struct TraceArgs {
   int K;
   float eps, alpha, eps_bf16;
   int max_steps;
+  int refine;           // refine_steps for a tensor-core march, else 0
   dist_trace_out o;
   float4* st;
   float4* dir;
+  int* fq;              // FP32 queries per ray after the low-precision phase
+  float* fprev;         // previous low-precision sample of each ray
 };
 
 // One thread per pixel (Sec. 3.2 "Initialization"): the ray through the
@@ -146,6 +149,8 @@ __global__ void raygen_kernel(TraceArgs a, int* list0, int* count0) {
       }
       if (enters) {
         a.st[i] = make_float4(t_in, t_in, t_out, __int_as_float(ci));
+        a.fq[i] = 0;
+        a.fprev[i] = 0.f;
       } else {
         const float cc = c.c[0] * c.c[0] + c.c[1] * c.c[1] + c.c[2] * c.c[2];
         const float dist = b < 0.f ? sqrtf(qq) : sqrtf(cc);
@@ -164,8 +169,8 @@ __global__ void raygen_kernel(TraceArgs a, int* list0, int* count0) {
 // ------------------------------------------------------------- march step
 
 struct StepLists {
-  const int* cnt_in;      // [2]: BF16 list, FP32 list
-  int* cnt_out;           // [2]
+  const int* cnt_in[2];   // list lengths: [0] low-precision list, [1] FP32 list
+  int* cnt_out[2];        // append counters of the output lists
   const int* in[2];
   const float* f[2];
   int* out[2];
@@ -183,7 +188,7 @@ struct StepLists {
 // same point; their samples enter the |f| tracking as max(|f|, eps) so that
 // only FP32 samples can make the silhouette negative.
 __global__ void step_kernel(TraceArgs a, StepLists L, unsigned long long* queries) {
-  const int n0 = L.cnt_in[0], n1 = L.cnt_in[1];
+  const int n0 = *L.cnt_in[0], n1 = *L.cnt_in[1];
   const int n = n0 + n1;
   if (queries && blockIdx.x == 0 && threadIdx.x == 0) {
     atomicAdd(queries + 0, (unsigned long long)n0);
@@ -221,9 +226,25 @@ __global__ void step_kernel(TraceArgs a, StepLists L, unsigned long long* querie
       }
       int outcome = -1;   // -1 keep marching
       float dn = d;
-      if (list == 1 && af < a.eps) {
+      bool accepted = false;
+      if (list == 1 && a.refine > 0) {
+        // FP32 refinement after a tensor-core march: after `refine` FP32
+        // queries a ray within 4 eps_bf16 of the surface is accepted
+        const int q = a.fq[i] + 1;
+        a.fq[i] = q;
+        accepted = q >= a.refine && af >= a.eps && af < 4.f * a.eps_bf16;
+      }
+      bool crossed = false;
+      if (list == 0) {
+        // a low-precision march that steps across the surface close to it
+        // hands over to FP32 even if its noisy |f| never drops below eps_bf16
+        const float fp = a.fprev[i];
+        a.fprev[i] = f;
+        crossed = fp != 0.f && ((fp > 0.f) != (f > 0.f)) && af < 16.f * a.eps_bf16;
+      }
+      if (list == 1 && (af < a.eps || accepted)) {
         outcome = DIST_RAY_HIT;
-      } else if (list == 0 && af < a.eps_bf16) {
+      } else if (list == 0 && (af < a.eps_bf16 || crossed)) {
         keep = 1;       // switch to FP32 queries at the same point
       } else {
         dn = fmaf(a.alpha, f, d);
@@ -236,7 +257,7 @@ __global__ void step_kernel(TraceArgs a, StepLists L, unsigned long long* querie
         a.o.d_hit[i] = dh;
         a.o.depth[i] = dh * a.dir[i].w;
         a.o.mask[i] = 1;
-        a.o.sil[i] = fabsf(fm[0]) - a.eps;
+        a.o.sil[i] = accepted ? af - 4.f * a.eps_bf16 : fabsf(fm[0]) - a.eps;
       } else if (outcome >= 0) {
         a.o.d_hit[i] = kInf;
         a.o.depth[i] = kInf;
@@ -248,9 +269,9 @@ __global__ void step_kernel(TraceArgs a, StepLists L, unsigned long long* querie
       }
       if (outcome >= 0 && a.o.status) a.o.status[i] = outcome;
     }
-    const int s0 = warp_append(keep == 0, L.cnt_out + 0);
+    const int s0 = warp_append(keep == 0, L.cnt_out[0]);
     if (s0 >= 0) L.out[0][s0] = ray;
-    const int s1 = warp_append(keep == 1, L.cnt_out + 1);
+    const int s1 = warp_append(keep == 1, L.cnt_out[1]);
     if (s1 >= 0) L.out[1][s1] = ray;
   }
 }
@@ -577,11 +598,12 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
   DIST_CHECK(p->k_min >= 1 && p->k_min <= kMaxK, DIST_E_INVALID, "k_min must be 1..3");
   DIST_CHECK(p->eps > 0.f && p->alpha > 0.f && p->radius > 0.f && p->normal_delta >= 0.f,
              DIST_E_INVALID, "eps, alpha, radius must be > 0 and normal_delta >= 0");
-  DIST_CHECK(p->precision == DIST_PREC_FP32 || p->precision == DIST_PREC_BF16, DIST_E_INVALID,
+  DIST_CHECK(p->precision == DIST_PREC_FP32 || is_tc(p->precision), DIST_E_INVALID,
              "bad precision");
+  DIST_CHECK(p->refine_steps >= 0, DIST_E_INVALID, "refine_steps must be >= 0");
   DIST_CHECK(p->grad_mode == DIST_GRAD_EXACT || p->grad_mode == DIST_GRAD_PAPER, DIST_E_INVALID,
              "bad grad_mode");
-  DIST_CHECK(p->precision != DIST_PREC_BF16 || dec->tc.ok, DIST_E_UNSUPPORTED,
+  DIST_CHECK(!is_tc(p->precision) || dec->tc.ok, DIST_E_UNSUPPORTED,
              "BF16 tensor-core MLP covers only the DeepSDF decoder shape (512 x 8, skip 4, latent 256)");
   DIST_CHECK(o->depth && o->sil && o->mask && o->steps && o->d_hit && o->d_min && o->f_min,
              DIST_E_INVALID, "dist_trace_out: NULL required buffer");
@@ -628,7 +650,8 @@ TraceArgs make_args(const dist_trace_params* p, const dist_trace_out* o, dist_wo
   a.cams = ws->cams; a.n_cams = n_cams; a.n_pix = n_pix; a.radius = p->radius; a.K = p->k_min;
   a.pix0 = 0; a.cam_fixed = -1;
   a.eps = p->eps; a.alpha = p->alpha; a.eps_bf16 = p->eps_bf16; a.max_steps = p->max_steps;
-  a.o = *o; a.st = ws->st; a.dir = ws->dir;
+  a.refine = is_tc(p->precision) ? p->refine_steps : 0;
+  a.o = *o; a.st = ws->st; a.dir = ws->dir; a.fq = ws->fq; a.fprev = ws->fprev;
   return a;
 }
 
@@ -709,6 +732,7 @@ static TraceArgs pool_args(const RayPool& P) {
   a.cams = P.cams; a.n_cams = 0; a.n_pix = 0; a.pix0 = 0; a.cam_fixed = -1;
   a.radius = P.radius; a.K = P.K; a.eps = P.eps; a.alpha = P.alpha; a.eps_bf16 = P.eps_bf16;
   a.max_steps = P.max_steps; a.o = P.o; a.st = P.st; a.dir = P.dir;
+  a.fq = P.fq; a.fprev = P.fprev; a.refine = P.refine;
   return a;
 }
 
@@ -735,7 +759,8 @@ cudaError_t pool_raygen(const RayPool& P, int cam, long long pix0, long long n, 
 cudaError_t pool_step(const RayPool& P, const int* cnt_in, int* cnt_out, int* const in[2],
                       const float* const f[2], int* const out[2], cudaStream_t st) {
   StepLists L;
-  L.cnt_in = cnt_in; L.cnt_out = cnt_out;
+  L.cnt_in[0] = cnt_in; L.cnt_in[1] = cnt_in + 1;
+  L.cnt_out[0] = cnt_out; L.cnt_out[1] = cnt_out + 1;
   for (int k = 0; k < 2; ++k) { L.in[k] = in[k]; L.f[k] = f[k]; L.out[k] = out[k]; }
   step_kernel<<<num_sms() * 4, 256, 0, st>>>(pool_args(P), L, P.o.queries);
   count_launch(1);
@@ -792,36 +817,64 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
   cudaStream_t st = pr.st;
   const long long n_pix = pr.n_pix;
   TraceArgs a = make_args(p, o, ws, n_cams, n_pix);
-  DIST_CUDA_TRY(cudaMemsetAsync(ws->counts, 0, (size_t)(p->max_steps + 2) * 2 * sizeof(int), st));
-  const int first = p->precision == DIST_PREC_BF16 ? 0 : 1;
-  raygen_kernel<<<grid_for(n_pix, 256), 256, 0, st>>>(a, ws->act[0][first], ws->counts + first);
+  // list lengths: cA[s] low-precision list at step s, cB[t] FP32 list at
+  // FP32 step t, and a constant zero for a list that is not used
+  const int M = p->max_steps;
+  int* cA = ws->counts;
+  int* cB = ws->counts + (M + 1);
+  int* zero = ws->counts + 2 * (M + 1);
+  DIST_CUDA_TRY(cudaMemsetAsync(ws->counts, 0, (size_t)(2 * (M + 1) + 1) * sizeof(int), st));
+  const bool tc = is_tc(p->precision);
+  if (tc)
+    raygen_kernel<<<grid_for(n_pix, 256), 256, 0, st>>>(a, ws->act[0][0], cA);
+  else
+    raygen_kernel<<<grid_for(n_pix, 256), 256, 0, st>>>(a, ws->act[0][1], cB);
   DIST_LAUNCH_CHECK();
   const float* b0 = ws->bfold;
   const float* bs = ws->bfold + kMaxShapes * 512;
   const int step_grid = num_sms() * 4;
-  for (int s = 0; s < p->max_steps; ++s) {
-    const int par = s & 1;
-    int* cin = ws->counts + 2 * s;
-    int* cout = ws->counts + 2 * (s + 1);
-    RowSrc src{};
-    src.st = ws->st; src.dir = ws->dir; src.cams = ws->cams;
-    if (p->precision == DIST_PREC_BF16) {
-      src.count = cin + 0;
+  RowSrc src{};
+  src.st = ws->st; src.dir = ws->dir; src.cams = ws->cams;
+  if (tc) {
+    // Tensor-core march.  Rays whose low-precision |f| is small enough move
+    // to one FP32 list that grows over all steps: their FP32 queries run
+    // together afterwards instead of as a small launch every step.  A ray's
+    // result does not depend on when its queries run.
+    for (int s = 0; s < M; ++s) {
+      const int par = s & 1;
+      src.count = cA + s;
       src.idx = ws->act[par][0];
       prof_mlp_begin(st, 0);
-      DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, ws->fbuf[0], st));
+      DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, ws->fbuf[0], st,
+                                   p->precision == DIST_PREC_FP16));
       prof_mlp_end(st);
+      StepLists L;
+      L.cnt_in[0] = cA + s; L.cnt_in[1] = zero;
+      L.cnt_out[0] = cA + s + 1; L.cnt_out[1] = cB;
+      L.in[0] = ws->act[par][0]; L.in[1] = ws->act[0][1];
+      L.f[0] = ws->fbuf[0]; L.f[1] = ws->fbuf[1];
+      L.out[0] = ws->act[par ^ 1][0]; L.out[1] = ws->act[0][1];
+      step_kernel<<<step_grid, 256, 0, st>>>(a, L, o->queries);
+      DIST_LAUNCH_CHECK();
     }
-    src.count = cin + 1;
+  }
+  // FP32 march (all rays for FP32 precision; the handed-over rays otherwise).
+  // After the tensor-core march the first FP32 launch holds every handed-over
+  // ray (64-row tiles for throughput); the shrinking tail after it runs in
+  // 16-row tiles, whose launch latency is a quarter of a 64-row tile's.
+  for (int t = 0; t < M; ++t) {
+    const int par = t & 1;
+    src.count = cB + t;
     src.idx = ws->act[par][1];
     prof_mlp_begin(st, 1);
-    DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->fbuf[1], st));
+    DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->fbuf[1], st, tc && t > 0));
     prof_mlp_end(st);
     StepLists L;
-    L.cnt_in = cin; L.cnt_out = cout;
-    L.in[0] = ws->act[par][0]; L.in[1] = ws->act[par][1];
+    L.cnt_in[0] = zero; L.cnt_in[1] = cB + t;
+    L.cnt_out[0] = zero; L.cnt_out[1] = cB + t + 1;
+    L.in[0] = ws->act[0][0]; L.in[1] = ws->act[par][1];
     L.f[0] = ws->fbuf[0]; L.f[1] = ws->fbuf[1];
-    L.out[0] = ws->act[par ^ 1][0]; L.out[1] = ws->act[par ^ 1][1];
+    L.out[0] = ws->act[0][0]; L.out[1] = ws->act[par ^ 1][1];
     step_kernel<<<step_grid, 256, 0, st>>>(a, L, o->queries);
     DIST_LAUNCH_CHECK();
   }
@@ -900,9 +953,9 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
   DIST_CHECK(n >= 1 && n <= ws->max_rays * kProbesPerRay, DIST_E_INVALID,
              "dist_sdf_eval: n must be 1..10 * workspace max_rays");
   DIST_CHECK(n_shapes >= 1 && n_shapes <= kMaxShapes, DIST_E_INVALID, "n_shapes out of range");
-  DIST_CHECK(precision == DIST_PREC_FP32 || (precision == DIST_PREC_BF16 && !grad),
-             DIST_E_INVALID, "dist_sdf_eval: bad precision (BF16 has no gradient)");
-  DIST_CHECK(precision != DIST_PREC_BF16 || dec->tc.ok, DIST_E_UNSUPPORTED,
+  DIST_CHECK(precision == DIST_PREC_FP32 || (is_tc(precision) && !grad),
+             DIST_E_INVALID, "dist_sdf_eval: bad precision (BF16/FP16 have no gradient)");
+  DIST_CHECK(!is_tc(precision) || dec->tc.ok, DIST_E_UNSUPPORTED,
              "BF16 tensor-core MLP covers only the DeepSDF decoder shape");
   cudaStream_t st = (cudaStream_t)stream;
   const DecoderF32& d = dec->f32;
@@ -917,8 +970,8 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
   RowSrc src{};
   src.count = ws->probe_count;
   src.pts = ws->probe_p;
-  if (precision == DIST_PREC_BF16) {
-    DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, f, st));
+  if (is_tc(precision)) {
+    DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, f, st, precision == DIST_PREC_FP16));
   } else if (!grad) {
     DIST_CUDA_TRY(mlp_fp32_forward(d, src, b0, bs, f, st));
   } else {

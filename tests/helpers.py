@@ -38,11 +38,23 @@ def bf16_round(x):
     return a.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-def bf16_decoder_reference(Ws, bs, Z, pts, shape, latent=256, skip=4):
+def fp16_round(x):
+    """Round to the nearest IEEE half (ties to even), returned as float64."""
+    return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float64)
+
+
+def lowp_decoder_reference(Ws, bs, Z, pts, shape, precision, latent=256, skip=4):
+    rnd = bf16_round if precision == "bf16" else fp16_round
+    return bf16_decoder_reference(Ws, bs, Z, pts, shape, latent, skip, rnd=rnd)
+
+
+def bf16_decoder_reference(Ws, bs, Z, pts, shape, latent=256, skip=4, rnd=None):
     """The DeepSDF decoder evaluated the way the BF16 tensor-core kernel does:
     GEMM layers 1..7 with bf16-rounded weights and bf16-rounded input
     activations (fp64 accumulation), layer 0, the skip layer's xyz columns,
-    the folded latent biases and the head in full precision."""
+    the folded latent biases and the head in full precision.  ``rnd``
+    replaces the bf16 rounding (e.g. by fp16)."""
+    bf16_round_ = rnd or bf16_round
     W = [np.asarray(w, dtype=np.float64) for w in Ws]
     b = [np.asarray(v, dtype=np.float64) for v in bs]
     z = np.asarray(Z, dtype=np.float64)[shape]
@@ -52,11 +64,11 @@ def bf16_decoder_reference(Ws, bs, Z, pts, shape, latent=256, skip=4):
     bs_ = (z @ W[skip][:, hk:hk + latent].T + b[skip]).astype(np.float32).astype(np.float64)
     h = np.maximum(p @ W[0][:, latent:].T + b0, 0.0)
     for l in range(1, len(W) - 1):
-        hb = bf16_round(h)
+        hb = bf16_round_(h)
         if l == skip:
-            a = hb @ bf16_round(W[l][:, :hk]).T + p @ W[l][:, hk + latent:].T + bs_
+            a = hb @ bf16_round_(W[l][:, :hk]).T + p @ W[l][:, hk + latent:].T + bs_
         else:
-            a = hb @ bf16_round(W[l]).T + b[l]
+            a = hb @ bf16_round_(W[l]).T + b[l]
         h = np.maximum(a, 0.0)
     return np.tanh(h @ W[-1].T + b[-1])[:, 0]
 

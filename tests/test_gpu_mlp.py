@@ -7,16 +7,17 @@ import pytest
 import torch
 
 import synth
-from tests.helpers import bf16_decoder_reference, gpu_decoder, oracle_sdf, to_np, workload
+from tests.helpers import gpu_decoder, lowp_decoder_reference, oracle_sdf, to_np, workload
 
 pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("n", [1, 127, 128 * 3 + 5, 148 * 128 + 77])
-def test_bf16_tensor_core_decoder(cuda_device, n):
-    """tcgen05 BF16 decoder (dist_sdf_eval, precision BF16): against the same
-    arithmetic emulated in fp64 (bf16-rounded weights and activations) and
-    against the FP64 oracle."""
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_tensor_core_decoder(cuda_device, n, precision):
+    """tcgen05 decoder (dist_sdf_eval, precision BF16 or FP16): against the
+    same arithmetic emulated in fp64 (16-bit-rounded weights and activations)
+    and against the FP64 oracle."""
     from paper_1911_13225_b300 import api
     spec = synth.DEEPSDF_SPEC
     Ws, bs, Z = workload(spec, seed=4, n_shapes=3)
@@ -27,19 +28,21 @@ def test_bf16_tensor_core_decoder(cuda_device, n):
     pts = rng.uniform(-0.9, 0.9, (n, 3)).astype(np.float32)
     shp = rng.integers(0, 3, n).astype(np.int32)
     f = api.sdf_eval(dec, torch.from_numpy(Z).to(cuda_device), torch.from_numpy(pts).to(cuda_device),
-                     torch.from_numpy(shp).to(cuda_device), ws, precision="bf16")
+                     torch.from_numpy(shp).to(cuda_device), ws, precision=precision)
     f = to_np(f).astype(np.float64)
     assert dec.device_error() == 0
-    emu = bf16_decoder_reference(Ws, bs, Z, pts, shp)
+    emu = lowp_decoder_reference(Ws, bs, Z, pts, shp, precision)
     d_emu = np.abs(f - emu)
     # identical arithmetic up to FP32 summation order; an activation whose
-    # FP32 value sits at a bf16 rounding midpoint may round the other way
-    # and move f by ~1e-3, so the bound is on the typical point
-    assert np.median(d_emu) < 1e-5
-    assert np.quantile(d_emu, 0.99) < 1e-3 and np.max(d_emu) < 5e-3
+    # FP32 value sits at a rounding midpoint may round the other way and move
+    # f by up to ~1e-3 (bf16), so the bound is on the typical point
+    scale = 1.0 if precision == "bf16" else 0.125
+    # fp16's 8x finer grid puts more activations near a rounding midpoint
+    assert np.median(d_emu) < (1e-5 if precision == "bf16" else 5e-5)
+    assert np.quantile(d_emu, 0.99) < 1e-3 * scale and np.max(d_emu) < 5e-3 * scale
     fo = oracle_sdf(spec, Ws, bs, Z)(pts.astype(np.float64), shp)
     d_or = np.abs(f - fo)
-    assert np.max(d_or) < 5e-3 and np.mean(d_or) < 1e-3
+    assert np.max(d_or) < 5e-3 * scale and np.mean(d_or) < 1e-3 * scale
 
 
 @pytest.mark.parametrize("spec,tol_f,tol_g", [(synth.SMALL_SPEC, 2e-6, 1e-5),

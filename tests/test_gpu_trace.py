@@ -95,18 +95,22 @@ def test_normals_at_gpu_hits(cuda_device, delta):
     assert np.all(to_np(res.normal)[~m] == 0)
 
 
+@pytest.mark.parametrize("precision,eps_lo,refine", [("bf16", 1e-3, 0), ("fp16", 1e-3, 0),
+                                                     ("fp16", 1e-4, 1), ("fp16", 2e-4, 1)])
 @pytest.mark.parametrize("size,vp_seed", [(64, 3), (96, 8)])
-def test_bf16_trace_depth_within_2e3(cuda_device, size, vp_seed):
-    """BF16 tensor-core marching with FP32 convergence (eps_bf16 = 1e-3 then
-    eps = 5e-5, unit final step): depth within 2e-3 of the FP64 oracle on
-    hits away from the silhouette; masks agree except near-silhouette rays."""
+def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precision, eps_lo, refine):
+    """Tensor-core marching (BF16 or FP16 operands) until |f| < eps_lo, then
+    FP32 queries: converge to eps = 5e-5 (refine = 0) or accept after
+    `refine` FP32 queries within 4 eps_lo (unit final step).  Depth within
+    2e-3 of the FP64 oracle on hits away from the silhouette; masks agree
+    except near-silhouette rays."""
     from paper_1911_13225_b300 import api
     spec = synth.DEEPSDF_SPEC
     Ws, bs, Z = workload(spec, seed=0, n_shapes=1)
     dec = gpu_decoder(spec, Ws, bs)
     cam = synth.look_at_camera(synth.random_viewpoints(1, seed=vp_seed)[0], size, size)
     ws = api.Workspace(size * size, 50)
-    params = api.TraceParams(precision="bf16")
+    params = api.TraceParams(precision=precision, eps_bf16=eps_lo, refine_steps=refine)
     res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), [cam], params, ws)
     assert dec.device_error() == 0
     orc = tracer.render(oracle_sdf(spec, Ws, bs, Z), [cam], record=True)
