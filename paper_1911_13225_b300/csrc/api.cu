@@ -202,6 +202,7 @@ dist_status dist_workspace_create(int64_t max_rays, int max_steps, dist_workspac
   WS_ALLOC(probe_count, 8 * sizeof(int));
   WS_ALLOC(red, 8 * sizeof(double));
   WS_ALLOC(ired, 8 * sizeof(int));
+  WS_ALLOC(tc_scratch, (size_t)num_sms() * kTcAdjScratchPerCta);
 #undef WS_ALLOC
   if (s != DIST_OK) {
     dist_workspace_destroy(w);

@@ -98,8 +98,14 @@ struct DecoderTC {
   bool ok;
   TCMaps maps;                   // bf16 operands
   TCMaps maps16;                 // fp16 operands (same layout)
+  TCMaps bmaps;                  // W_l^T for the adjoint's backward GEMMs (bf16)
+  TCMaps bmaps16;                // same, fp16
   int* err;                      // device error word of the bounded waits
 };
+
+// Per-CTA global scratch of the tensor-core adjoint: ReLU masks and the
+// skip layer's pre-activation gradient of one 128-row tile.
+constexpr size_t kTcAdjScratchPerCta = (size_t)8 * 128 * 2 * 8 * 4 + (size_t)128 * 512 * 4;
 
 }  // namespace dist
 
@@ -132,6 +138,7 @@ struct dist_workspace {
   int* probe_count;   // [4]
   double* red;        // [8] small FP64 reduction scratch
   int* ired;          // [8] small integer scratch
+  void* tc_scratch;   // num_sms() * kTcAdjScratchPerCta bytes (tensor-core adjoint)
   std::vector<void*> allocations;
 };
 
@@ -230,5 +237,12 @@ cudaError_t pool_latent_finalize(const DecoderF32& d, const double* G0, const do
 // (DeepSDF shape only).
 cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
                            const float* bfolds, float* fout, cudaStream_t st, bool f16);
+
+// tcgen05 decoder adjoint over probes (same contract as mlp_fp32_adjoint;
+// `scratch` holds num_sms() * kTcAdjScratchPerCta bytes).
+cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const float4* pq,
+                           const int* count, const float* bfold0, const float* bfolds,
+                           float* out4, double* gacc0, double* gaccs, int accumulate,
+                           void* scratch, cudaStream_t st, bool f16);
 
 }  // namespace dist

@@ -433,6 +433,439 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- adjoint
+//
+// The same pipeline runs 14 GEMMs per 128-probe tile: the 7 forward layers
+// again (recording ReLU masks), then, from g_7 = (1 - f^2) w_head * 1[a_7 > 0],
+// the 7 backward GEMMs g_{l-1} = (W_l^T g_l) * 1[a_{l-1} > 0] with W_l^T tiles
+// (TMA maps over the transposed weights).  The skip layer's gradient g_4 and
+// layer 0's g_0 give grad_p f = Wx0^T g_0 + Wx4^T g_4 and the latent
+// gradient W_z0^T g_0 + W_z4^T g_4; per probe coefficients c (the paper's
+// first-term weight, or -w / (grad f . v) for the exact depth gradient) scale
+// g_0 and g_4, which are summed over rays into FP64 per-shape accumulators
+// (a warp transpose-reduction over 32 rays in FP32, then FP64 atomics).
+//
+// The two column halves of a row meet through a small exchange buffer and
+// two mbarriers (half 1 -> half 0: head and gradient partial sums; half 0 ->
+// half 1: 1 - f^2 and the coefficient).
+
+constexpr int XFER_BYTES = 3 * BM * 4;
+constexpr int ADJ_SMEM_BYTES = 1024 + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES + XFER_BYTES;
+constexpr int NUM_ADJ_GEMM = 14;
+constexpr size_t kMaskWordsPerCta = (size_t)8 * 128 * 2 * 8;
+
+// GEMM e of a tile: forward layers 1..7 (e < 7), then backward layers 7..1.
+__device__ __forceinline__ int adj_n(int e) { return e < 7 ? gemm_n(e) : gemm_k(13 - e); }
+__device__ __forceinline__ int adj_k(int e) { return e < 7 ? gemm_k(e) : gemm_n(13 - e); }
+
+struct TCAdjArgs {
+  const float* bias[NUM_GEMM];
+  const float* Wx0;
+  const float* Wx4;
+  const float* w_head;
+  float b_head;
+  const float* bfold0;
+  const float* bfold4;
+  const float4* pp;
+  const float4* pq;
+  const int* count;
+  float* out4;
+  double* gacc0;
+  double* gacc4;
+  int accumulate;
+  uint8_t* scratch;   // gridDim.x * kTcAdjScratchPerCta bytes
+  int* err;
+};
+
+// Sum of v[0..31] over the 32 lanes of the warp, column by column: lane L
+// returns the column-L total (recursive halving, 31 shuffles).
+__device__ __forceinline__ float warp_column_sum(float (&v)[32], int lane) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    const bool upper = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < o; ++i) {
+      const float send = upper ? v[i] : v[i + o];
+      const float recv = __shfl_xor_sync(0xffffffffu, send, o);
+      v[i] = (upper ? v[i + o] : v[i]) + recv;
+    }
+  }
+  return v[0];
+}
+
+template <bool F16>
+__global__ void __launch_bounds__(THREADS, 1)
+mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ TCMaps bmaps,
+                  const TCAdjArgs a) {
+  constexpr uint32_t kIdesc = instr_desc<F16>();
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* act = smem;
+  uint8_t* wst = smem + ACT_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wst + STAGES * STAGE_BYTES);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* acc_full = bars + 2 * STAGES;
+  uint64_t* act_full = bars + 2 * STAGES + 1;
+  uint64_t* drain = bars + 2 * STAGES + 2;
+  uint64_t* h2l = bars + 2 * STAGES + 3;      // half 1 -> half 0
+  uint64_t* l2h = bars + 2 * STAGES + 4;      // half 0 -> half 1
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* xfer = reinterpret_cast<float*>(smem + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n = *a.count;
+  const int n_tiles = (n + BM - 1) / BM;
+  if ((int)blockIdx.x >= n_tiles) return;
+  uint32_t* masks = reinterpret_cast<uint32_t*>(a.scratch + (size_t)blockIdx.x * kTcAdjScratchPerCta);
+  float* g4s = reinterpret_cast<float*>(masks + kMaskWordsPerCta);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(act_full, NUM_EPI * 32);
+    mbar_init(drain, 1);
+    mbar_init(h2l, NUM_EPI * 16);
+    mbar_init(l2h, NUM_EPI * 16);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_parity[STAGES];
+      bool issued[STAGES];
+      for (int s = 0; s < STAGES; ++s) issued[s] = false;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+        for (int e = 0; ok && e < NUM_ADJ_GEMM; ++e) {
+          const CUtensorMap* map = e < 7 ? &fmaps.m[e] : &bmaps.m[13 - e];
+          for (int nh = 0; ok && nh < adj_n(e) / BN; ++nh) {
+            for (int kc = 0; kc < adj_k(e) / BK; ++kc) {
+              if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) { ok = false; break; }
+              mbar_expect_tx(full + stage, STAGE_BYTES);
+              tma_load_2d(wst + stage * STAGE_BYTES, map, full + stage, kc * BK, nh * BN);
+              issued[stage] = true;
+              issued_parity[stage] = phase;
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.err, 8);
+      }
+      for (int s = 0; s < STAGES; ++s) {
+        if (!issued[s]) continue;
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(full + s, issued_parity[s]) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0, act_phase = 0;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+        for (int e = 0; ok && e < NUM_ADJ_GEMM; ++e) {
+          if (!mbar_wait(act_full, act_phase, abort_flag)) { ok = false; break; }
+          act_phase ^= 1u;
+          tc_fence_after();
+          for (int nh = 0; ok && nh < adj_n(e) / BN; ++nh) {
+            for (int kc = 0; kc < adj_k(e) / BK; ++kc) {
+              if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
+              tc_fence_after();
+              const uint32_t a_base = smem_u32(act + kc * CHUNK_BYTES);
+              const uint32_t b_base = smem_u32(wst + stage * STAGE_BYTES);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k)
+                mma_bf16(tmem + (uint32_t)(nh * BN), sw128_desc(a_base + 32 * k),
+                         sw128_desc(b_base + 32 * k), kIdesc, (kc | k) != 0);
+              mma_commit(empty + stage);
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+          }
+          if (ok) mma_commit(acc_full);
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.err, 16);
+      }
+      mma_commit(drain);
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+      }
+    }
+  } else {
+    // --------------------------------------------------------- epilogue
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int half = ew >> 2;
+    const int row = quad * 32 + lane;
+    const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
+    uint32_t acc_phase = 0, h2l_phase = 0, l2h_phase = 0;
+    bool ok = true;
+    // mask words of (layer, row, half): 8 words cover this thread's columns
+    auto mask_ptr = [&](int layer) { return masks + ((size_t)(layer * BM + row) * 2 + half) * 8; };
+    for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+      const int j = tile * BM + row;
+      const bool valid = j < n;
+      float4 pv = valid ? a.pp[j] : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+      const float3 p = make_float3(pv.x, pv.y, pv.z);
+      const int shape = __float_as_int(pv.w);
+      // ---- forward recompute with ReLU masks
+      {
+        const float* bf = a.bfold0 + (size_t)shape * 512;
+        uint32_t mw[8];
+        for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+          float v[32];
+          uint32_t bits = 0;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            const float4 wx = __ldg(reinterpret_cast<const float4*>(a.Wx0) + c + i);
+            const float t = fmaf(wx.x, p.x, fmaf(wx.y, p.y, fmaf(wx.z, p.z, __ldg(bf + c + i))));
+            bits |= (t > 0.f ? 1u : 0u) << i;
+            v[i] = fmaxf(t, 0.f);
+          }
+          mw[w] = bits;
+          store_act32<F16>(act, row, c, v);
+        }
+        uint4* mp = reinterpret_cast<uint4*>(mask_ptr(0));
+        mp[0] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+        mp[1] = make_uint4(mw[4], mw[5], mw[6], mw[7]);
+        fence_async_shared();
+        mbar_arrive(act_full);
+      }
+      float head = 0.f;
+      for (int g = 0; g < NUM_GEMM; ++g) {
+        if (!mbar_wait(acc_full, acc_phase, abort_flag)) { ok = false; break; }
+        acc_phase ^= 1u;
+        tc_fence_after();
+        const int ncol = gemm_n(g) / 2;
+        const int c0 = half * ncol;
+        const bool skip_layer = (g == 3);
+        const float* bias = skip_layer ? a.bfold4 + (size_t)shape * 512 : a.bias[g];
+        uint32_t mw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int c = c0, w = 0; c < c0 + ncol; c += 32, ++w) {
+          uint32_t r[32];
+          tmem_ld32(t_row + (uint32_t)c, r);
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + c + i));
+            v[i + 0] = __uint_as_float(r[i + 0]) + b4.x;
+            v[i + 1] = __uint_as_float(r[i + 1]) + b4.y;
+            v[i + 2] = __uint_as_float(r[i + 2]) + b4.z;
+            v[i + 3] = __uint_as_float(r[i + 3]) + b4.w;
+          }
+          if (skip_layer) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const float4 wx = __ldg(reinterpret_cast<const float4*>(a.Wx4) + c + i);
+              v[i] = fmaf(wx.x, p.x, fmaf(wx.y, p.y, fmaf(wx.z, p.z, v[i])));
+            }
+          }
+          uint32_t bits = 0;
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            bits |= (v[i] > 0.f ? 1u : 0u) << i;
+            v[i] = fmaxf(v[i], 0.f);
+          }
+          mw[w] = bits;
+          if (g < NUM_GEMM - 1) {
+            store_act32<F16>(act, row, c, v);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+              const float4 wh = __ldg(reinterpret_cast<const float4*>(a.w_head + c + i));
+              head = fmaf(v[i], wh.x, fmaf(v[i + 1], wh.y, fmaf(v[i + 2], wh.z, fmaf(v[i + 3], wh.w, head))));
+            }
+          }
+        }
+        uint4* mp = reinterpret_cast<uint4*>(mask_ptr(g + 1));
+        mp[0] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+        mp[1] = make_uint4(mw[4], mw[5], mw[6], mw[7]);
+        tc_fence_before();
+        if (g < NUM_GEMM - 1) {
+          fence_async_shared();
+          mbar_arrive(act_full);
+        }
+      }
+      if (!ok) break;
+      // ---- head: f, then 1 - f^2 to both halves
+      float fval = 0.f, dfs = 0.f;
+      if (half == 1) {
+        xfer[row] = head;
+        mbar_arrive(h2l);
+        if (!mbar_wait(l2h, l2h_phase, abort_flag)) { ok = false; break; }
+        dfs = xfer[row];
+      } else {
+        if (!mbar_wait(h2l, h2l_phase, abort_flag)) { ok = false; break; }
+        fval = tanhf(head + xfer[row] + a.b_head);
+        dfs = 1.f - fval * fval;
+        xfer[row] = dfs;
+        mbar_arrive(l2h);
+      }
+      h2l_phase ^= 1u;
+      l2h_phase ^= 1u;
+      // ---- g_7 = (1 - f^2) w_head * mask_7 into the A tile
+      {
+        const uint32_t* mw = mask_ptr(7);
+        for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+          const uint32_t bits = mw[w];
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; i += 4) {
+            const float4 wh = __ldg(reinterpret_cast<const float4*>(a.w_head + c + i));
+            v[i + 0] = ((bits >> (i + 0)) & 1u) ? dfs * wh.x : 0.f;
+            v[i + 1] = ((bits >> (i + 1)) & 1u) ? dfs * wh.y : 0.f;
+            v[i + 2] = ((bits >> (i + 2)) & 1u) ? dfs * wh.z : 0.f;
+            v[i + 3] = ((bits >> (i + 3)) & 1u) ? dfs * wh.w : 0.f;
+          }
+          store_act32<F16>(act, row, c, v);
+        }
+        fence_async_shared();
+        mbar_arrive(act_full);
+      }
+      // ---- backward GEMMs for layers 7..1: g_{l-1} = acc * mask_{l-1}
+      float gx = 0.f, gy = 0.f, gz = 0.f;
+      for (int l = 7; l >= 1; --l) {
+        if (!mbar_wait(acc_full, acc_phase, abort_flag)) { ok = false; break; }
+        acc_phase ^= 1u;
+        tc_fence_after();
+        const int nout = gemm_k(l - 1);   // width of layer l's h-input
+        const int ncol = nout / 2;
+        const int c0 = half * ncol;
+        const uint32_t* mw = mask_ptr(l - 1);
+        for (int c = c0, w = 0; c < c0 + ncol; c += 32, ++w) {
+          uint32_t r[32];
+          tmem_ld32(t_row + (uint32_t)c, r);
+          const uint32_t bits = mw[w];
+          float v[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] = ((bits >> i) & 1u) ? __uint_as_float(r[i]) : 0.f;
+          if (l == 5 || l == 1) {
+            // g_4 or g_0: the xyz columns of that layer give grad_p f
+            const float* Wx = l == 5 ? a.Wx4 : a.Wx0;
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const float4 wx = __ldg(reinterpret_cast<const float4*>(Wx) + c + i);
+              gx = fmaf(v[i], wx.x, gx);
+              gy = fmaf(v[i], wx.y, gy);
+              gz = fmaf(v[i], wx.z, gz);
+            }
+            if (l == 5) {
+              float4* dst = reinterpret_cast<float4*>(g4s + (size_t)row * 512 + c);
+#pragma unroll
+              for (int i = 0; i < 32; i += 4) dst[i / 4] = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            }
+          }
+          if (l > 1) store_act32<F16>(act, row, c, v);
+        }
+        tc_fence_before();
+        if (l > 1) {
+          fence_async_shared();
+          mbar_arrive(act_full);
+        }
+      }
+      if (!ok) break;
+      // ---- grad_p f and the probe coefficient
+      float coef = 0.f;
+      if (half == 1) {
+        xfer[row] = gx;
+        xfer[BM + row] = gy;
+        xfer[2 * BM + row] = gz;
+        mbar_arrive(h2l);
+        if (!mbar_wait(l2h, l2h_phase, abort_flag)) { ok = false; break; }
+        coef = xfer[row];
+      } else {
+        if (!mbar_wait(h2l, h2l_phase, abort_flag)) { ok = false; break; }
+        gx += xfer[row];
+        gy += xfer[BM + row];
+        gz += xfer[2 * BM + row];
+        if (valid) {
+          if (a.out4) reinterpret_cast<float4*>(a.out4)[j] = make_float4(fval, gx, gy, gz);
+          const float4 q4 = a.pq ? a.pq[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          coef = q4.w;
+          if (q4.x != 0.f || q4.y != 0.f || q4.z != 0.f) {
+            const float gv = gx * q4.x + gy * q4.y + gz * q4.z;
+            const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
+            coef = (fabsf(gv) >= 1e-3f * gn && gv != 0.f) ? -q4.w / gv : 0.f;
+          }
+        }
+        xfer[row] = coef;
+        mbar_arrive(l2h);
+      }
+      h2l_phase ^= 1u;
+      l2h_phase ^= 1u;
+      // ---- sum coef * g_0 and coef * g_4 over the tile's rays per shape
+      if (a.accumulate) {
+        const uint32_t* m0 = mask_ptr(0);
+        unsigned todo = __ballot_sync(0xffffffffu, valid && coef != 0.f);
+        while (todo) {
+          const int leader = __ffs(todo) - 1;
+          const int s = __shfl_sync(0xffffffffu, shape, leader);
+          const bool mine = valid && coef != 0.f && shape == s;
+          const float cc = mine ? coef : 0.f;
+          for (int which = 0; which < 2; ++which) {
+            double* dst = (which == 0 ? a.gacc0 : a.gacc4) + (size_t)s * 512;
+            for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+              float v[32];
+              if (which == 0) {
+                uint32_t r[32];
+                tmem_ld32(t_row + (uint32_t)c, r);
+                const uint32_t bits = m0[w];
+#pragma unroll
+                for (int i = 0; i < 32; ++i)
+                  v[i] = ((bits >> i) & 1u) ? cc * __uint_as_float(r[i]) : 0.f;
+              } else {
+                const float4* src = reinterpret_cast<const float4*>(g4s + (size_t)row * 512 + c);
+#pragma unroll
+                for (int i = 0; i < 32; i += 4) {
+                  const float4 t = src[i / 4];
+                  v[i] = cc * t.x; v[i + 1] = cc * t.y; v[i + 2] = cc * t.z; v[i + 3] = cc * t.w;
+                }
+              }
+              const float colsum = warp_column_sum(v, lane);
+              if (colsum != 0.f) atomicAdd(dst + c + lane, (double)colsum);
+            }
+          }
+          todo &= ~__ballot_sync(0xffffffffu, mine);
+        }
+      }
+      tc_fence_before();
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      atomicOr(a.err, 32);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -486,6 +919,22 @@ dist_status pack_tc(dist_decoder* d, const float* const* W) {
                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed");
+      // the transpose [K rows][N cols] for the adjoint's backward GEMM
+      std::vector<uint16_t> t((size_t)K * N, 0);
+      for (int nn = 0; nn < N; ++nn)
+        for (int k = 0; k < K; ++k) t[(size_t)k * N + nn] = h[(size_t)nn * K + k];
+      void* q = nullptr;
+      DIST_CUDA_TRY(cudaMalloc(&q, t.size() * sizeof(uint16_t)));
+      d->allocations.push_back(q);
+      DIST_CUDA_TRY(cudaMemcpy(q, t.data(), t.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+      cuuint64_t tdims[2] = {(cuuint64_t)N, (cuuint64_t)K};
+      cuuint64_t tstrides[1] = {(cuuint64_t)N * sizeof(uint16_t)};
+      CUtensorMap* mt = f16 ? &d->tc.bmaps16.m[g] : &d->tc.bmaps.m[g];
+      r = enc(mt, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, q,
+              tdims, tstrides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (transpose)");
     }
   }
   void* e = nullptr;
@@ -526,6 +975,52 @@ cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const flo
     mlp_tc_kernel<true><<<num_sms(), THREADS, SMEM_BYTES, st>>>(dec->tc.maps16, a);
   else
     mlp_tc_kernel<false><<<num_sms(), THREADS, SMEM_BYTES, st>>>(dec->tc.maps, a);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const float4* pq,
+                           const int* count, const float* bfold0, const float* bfolds,
+                           float* out4, double* gacc0, double* gaccs, int accumulate,
+                           void* scratch, cudaStream_t st, bool f16) {
+  if (!dec->tc.ok) return cudaErrorNotSupported;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_adj_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         ADJ_SMEM_BYTES);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mlp_tc_adj_kernel<true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const DecoderF32& f = dec->f32;
+  TCAdjArgs a;
+  for (int g = 0; g < NUM_GEMM; ++g) a.bias[g] = f.b[g + 1];
+  a.Wx0 = f.Wx0;
+  a.Wx4 = f.Wxs;
+  a.w_head = f.w_head;
+  a.b_head = f.b_head;
+  a.bfold0 = bfold0;
+  a.bfold4 = bfolds;
+  a.pp = pp;
+  a.pq = pq;
+  a.count = count;
+  a.out4 = out4;
+  a.gacc0 = gacc0;
+  a.gacc4 = gaccs;
+  a.accumulate = accumulate;
+  a.scratch = static_cast<uint8_t*>(scratch);
+  a.err = dec->tc.err;
+  prof_mlp_begin(st, 2);
+  if (f16)
+    mlp_tc_adj_kernel<true><<<num_sms(), THREADS, ADJ_SMEM_BYTES, st>>>(dec->tc.maps16,
+                                                                        dec->tc.bmaps16, a);
+  else
+    mlp_tc_adj_kernel<false><<<num_sms(), THREADS, ADJ_SMEM_BYTES, st>>>(dec->tc.maps,
+                                                                         dec->tc.bmaps, a);
+  prof_mlp_end(st);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -98,6 +98,7 @@ struct dist_server {
   int* slot_active_host = nullptr;
   double* loss = nullptr;
   unsigned long long* queries = nullptr;
+  void* tc_scratch = nullptr;
   std::vector<void*> allocs;
   // host state
   std::mutex mu;
@@ -252,8 +253,14 @@ struct dist_server {
       DIST_CUDA_TRY(cudaMemsetAsync(Gs + s * w, 0, w * sizeof(double), st));
       DIST_CUDA_TRY(cudaMemsetAsync(pcount, 0, sizeof(int), st));
       DIST_CUDA_TRY(pool_probes_depth(P, s, R->off, R->n, g_depth, pp, pq, pix, pcount, st));
-      DIST_CUDA_TRY(mlp_fp32_adjoint(dec->f32, pp, pq, pcount, bfold, bfold + (size_t)max_req * 512,
-                                     nullptr, G0, Gs, 1, st));
+      // the adjoint in the march's precision, as dist_trace_bwd does
+      if (is_tc(p.precision))
+        DIST_CUDA_TRY(mlp_tc_adjoint(dec, pp, pq, pcount, bfold, bfold + (size_t)max_req * 512,
+                                     nullptr, G0, Gs, 1, tc_scratch, st,
+                                     p.precision == DIST_PREC_FP16));
+      else
+        DIST_CUDA_TRY(mlp_fp32_adjoint(dec->f32, pp, pq, pcount, bfold,
+                                       bfold + (size_t)max_req * 512, nullptr, G0, Gs, 1, st));
       DIST_CUDA_TRY(cudaMemsetAsync(dz + (size_t)s * L, 0, L * sizeof(float), st));
       DIST_CUDA_TRY(pool_latent_finalize(dec->f32, G0 + s * w, Gs + s * w, dz + (size_t)s * L, st));
       DIST_CUDA_TRY(cudaMemcpyAsync(R->r.dz, dz + (size_t)s * L, L * sizeof(float),
@@ -414,6 +421,7 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
   SV_ALLOC(slot_active, max_requests * sizeof(int));
   SV_ALLOC(loss, max_requests * sizeof(double));
   SV_ALLOC(queries, 2 * sizeof(unsigned long long));
+  SV_ALLOC(tc_scratch, (size_t)num_sms() * kTcAdjScratchPerCta);
 #undef SV_ALLOC
   if (s == DIST_OK && cudaMallocHost(&S->slot_active_host, max_requests * sizeof(int)) != cudaSuccess) {
     S->slot_active_host = nullptr;

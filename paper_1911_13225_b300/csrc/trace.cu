@@ -666,6 +666,18 @@ ProbeArgs make_probe_args(const dist_trace_params* p, const dist_trace_out* o, d
   return a;
 }
 
+// The decoder adjoint in the trace's precision: tcgen05 (BF16 / FP16
+// operands) after a tensor-core march, FP32 SIMT otherwise.
+cudaError_t adjoint(const dist_decoder* dec, const dist_trace_params* p, dist_workspace* ws,
+                    const float4* pp, const float4* pq, const int* count, const float* b0,
+                    const float* bs, float* out4, double* G0, double* Gs, int acc,
+                    cudaStream_t st) {
+  if (is_tc(p->precision) && dec->tc.ok)
+    return mlp_tc_adjoint(dec, pp, pq, count, b0, bs, out4, G0, Gs, acc, ws->tc_scratch, st,
+                          p->precision == DIST_PREC_FP16);
+  return mlp_fp32_adjoint(dec->f32, pp, pq, count, b0, bs, out4, G0, Gs, acc, st);
+}
+
 dist_status normals_impl(const dist_decoder* dec, const dist_trace_params* p,
                          const dist_trace_out* o, float* normal, dist_workspace* ws,
                          int n_cams, long long n_pix, cudaStream_t st) {
@@ -678,8 +690,8 @@ dist_status normals_impl(const dist_decoder* dec, const dist_trace_params* p,
     ProbeArgs a = make_probe_args(p, o, ws, n_cams, n_pix, 0, 0);
     probes_hits_kernel<<<g, 256, 0, st>>>(a);
     DIST_LAUNCH_CHECK();
-    DIST_CUDA_TRY(mlp_fp32_adjoint(dec->f32, ws->probe_p, nullptr, ws->probe_count, b0, bs,
-                                   ws->probe_out, nullptr, nullptr, 0, st));
+    DIST_CUDA_TRY(adjoint(dec, p, ws, ws->probe_p, nullptr, ws->probe_count, b0, bs,
+                          ws->probe_out, nullptr, nullptr, 0, st));
     normals_from_grad_kernel<<<g, 256, 0, st>>>(ws->probe_out, ws->probe_pix, ws->probe_count,
                                                  normal);
     DIST_LAUNCH_CHECK();
@@ -916,15 +928,29 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
   DIST_CUDA_TRY(cudaMemsetAsync(Gs, 0, (size_t)n_shapes * d.width * sizeof(double), st));
   DIST_CUDA_TRY(cudaMemsetAsync(ws->probe_count, 0, 8 * sizeof(int), st));
   const int g = grid_for(n_pix, 256);
-  if (g_depth || g_sil) {
+  if (g_depth) {
+    // depth probes (<= k_min per pixel) in [0, 3 max_rays), in the trace's precision
     ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, 0, 0);
-    probes_bwd_kernel<<<g, 256, 0, st>>>(a, g_depth, g_sil, p->grad_mode == DIST_GRAD_PAPER,
+    probes_bwd_kernel<<<g, 256, 0, st>>>(a, g_depth, nullptr, p->grad_mode == DIST_GRAD_PAPER,
                                          p->alpha);
     DIST_LAUNCH_CHECK();
-    DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p, ws->probe_q, ws->probe_count, b0, bs, nullptr,
-                                   G0, Gs, 1, st));
+    DIST_CUDA_TRY(adjoint(dec, p, ws, ws->probe_p, ws->probe_q, ws->probe_count, b0, bs, nullptr,
+                          G0, Gs, 1, st));
+  }
+  if (g_sil) {
+    // silhouette probes (<= 1 per pixel) in [3, 4) max_rays: only rays whose
+    // soft silhouette disagrees with the target contribute, too few for
+    // 16-bit rounding errors to average out, so the FP32 adjoint
+    const long long off = 3 * (long long)ws->max_rays;
+    ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, off, 2);
+    probes_bwd_kernel<<<g, 256, 0, st>>>(a, nullptr, g_sil, 0, p->alpha);
+    DIST_LAUNCH_CHECK();
+    DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p + off, ws->probe_q + off, ws->probe_count + 2,
+                                   b0, bs, nullptr, G0, Gs, 1, st));
   }
   if (g_normal) {
+    // central-difference normals difference nearby values: FP32 queries and
+    // FP32 adjoint whatever the march precision
     const long long off = 4 * (long long)ws->max_rays;
     ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, off, 1);
     probes_fd_kernel<<<g, 256, 0, st>>>(a, p->normal_delta, g_normal);

@@ -45,6 +45,72 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+@pytest.mark.parametrize("mode", ["exact", "paper", "sil"])
+def test_tensor_core_adjoint_gradients(cuda_device, precision, mode):
+    """tcgen05 adjoint (BF16 / FP16 GEMMs, FP32 accumulation, FP64 sums):
+    latent gradient within 2e-2 relative l2 of the FP64 oracle's, with the
+    same upstream gradients on the oracle's trace."""
+    from paper_1911_13225_b300 import api
+    spec = synth.DEEPSDF_SPEC
+    Ws, bs, Z = workload(spec, seed=7, n_shapes=2)
+    dec = gpu_decoder(spec, Ws, bs)
+    cams = [synth.look_at_camera(v, 48, 48, shape=i % 2)
+            for i, v in enumerate(synth.random_viewpoints(2, seed=11))]
+    n = api.n_pixels(cams)
+    ws = api.Workspace(n, 60)
+    z = torch.from_numpy(Z).to(cuda_device)
+    k = 3 if mode == "paper" else 1
+    p32 = api.TraceParams(max_steps=60, k_min=k)
+    res = api.trace(dec, z, cams, p32, ws)
+    tgt = api.trace(dec, z, [dict(c, shape=1 - c["shape"]) for c in cams], p32, ws)
+    sdf = oracle_sdf(spec, Ws, bs, Z)
+    orc = tracer.render(sdf, cams, max_steps=60, k_min=k, record=True)
+    amb = ambiguous_rays(orc, tol_f=1e-5, max_steps=60, normals=orc["normal"], near_miss=1e-3)
+    sil_gt = torch.from_numpy((to_np(tgt.mask) > 0).astype(np.float32)).to(cuda_device)
+    _, gd, _, gs, _ = api.loss(res, {"depth": tgt.depth, "sil": sil_gt}, z, ws, w_depth=1.0,
+                               w_sil=1.0)
+    g = to_np(gs if mode == "sil" else gd).astype(np.float64)
+    g[amb] = 0.0
+    gt = torch.from_numpy(g.astype(np.float32)).to(cuda_device)
+    # backward in the tensor-core precision on the FP32 trace's outputs
+    ptc = api.TraceParams(max_steps=60, k_min=k, precision=precision,
+                          grad_mode="paper" if mode == "paper" else "exact")
+    kw = {"g_sil": gt} if mode == "sil" else {"g_depth": gt}
+    dz = api.backward(dec, z, cams, ptc, ws, res, **kw)
+    torch.cuda.synchronize()
+    assert dec.device_error() == 0
+    okw = {"g_sil": g} if mode == "sil" else {"g_depth": g}
+    G = latent_vjp(sdf, orc, 2, spec.latent_dim, mode="paper" if mode == "paper" else "exact",
+                   **okw)
+    assert np.abs(G).max() > 0
+    assert _rel(to_np(dz).astype(np.float64), G) < 2e-2
+
+
+@pytest.mark.parametrize("precision", ["bf16", "fp16"])
+def test_tensor_core_normals(cuda_device, precision):
+    from paper_1911_13225_b300 import api
+    spec = synth.DEEPSDF_SPEC
+    Ws, bs, Z = workload(spec, seed=0)
+    dec = gpu_decoder(spec, Ws, bs)
+    cam = synth.look_at_camera((0.4, 0.7, 2.3), 64, 64)
+    ws = api.Workspace(64 * 64, 50)
+    z = torch.from_numpy(Z).to(cuda_device)
+    res = api.trace(dec, z, [cam], api.TraceParams(precision=precision), ws, normals=True)
+    torch.cuda.synchronize()
+    assert dec.device_error() == 0
+    m = to_np(res.mask).astype(bool)
+    orc = tracer.render(oracle_sdf(spec, Ws, bs, Z), [cam], with_normals=False)
+    p = orc["c"][m] + to_np(res.d_hit)[m].astype(np.float64)[:, None] * orc["v"][m]
+    n_ref = tracer.normals(oracle_sdf(spec, Ws, bs, Z), p, orc["shape"][m], np.ones(m.sum(), bool))
+    err = np.linalg.norm(to_np(res.normal)[m] - n_ref, axis=1)
+    # 16-bit backward vectors: ~2^-9 (bf16) / 2^-12 (fp16) relative rounding
+    # per layer, plus ReLU masks that flip for near-zero units
+    tol_med, tol_99 = (2e-2, 1e-1) if precision == "bf16" else (5e-3, 5e-2)
+    assert np.median(err) < tol_med and np.quantile(err, 0.99) < tol_99, \
+        (np.median(err), np.quantile(err, 0.99))
+
+
 def test_loss_terms_match_oracle_on_gpu_render(cuda_device):
     api, dec, ws, z, params, cams, res, tgt, sdf, orc, amb = _setup(cuda_device, synth.SMALL_SPEC,
                                                                     delta=1e-3)
