@@ -160,7 +160,7 @@ def run_ours(args, rank, world, local_rank):
     if precision == "auto":
         precision = "bf16" if dec.has_bf16 else "fp32"
     params = api.TraceParams(max_steps=MAX_STEPS, precision=precision, eps_bf16=args.eps_lo,
-                             refine_steps=args.refine)
+                             refine_steps=args.refine, alpha_refine=args.alpha_refine)
     ws = api.Workspace(SIZE * SIZE, MAX_STEPS)
     z = torch.from_numpy(Z).to(dev)
     # target: depth of the second latent (untimed setup)
@@ -270,7 +270,8 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"bf16": "bf16", "fp16": "f16", "fp32": "f32"}[precision],
         "data": "synthetic (seeded decoder, latents and camera; no DeepSDF weights)",
-        "config": {"workload": WORKLOAD, "rays_per_step": rays, "precision": precision,
+        "config": {"workload": WORKLOAD.replace("512x512", f"{SIZE}x{SIZE}"),
+                   "rays_per_step": rays, "precision": precision,
                    "eps_lo": args.eps_lo, "refine_steps": args.refine,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MB write, untimed)"},
@@ -375,10 +376,16 @@ def main():
                     help="|f| below which a BF16/FP16 ray switches to FP32 queries")
     ap.add_argument("--refine", type=int, default=0,
                     help="0: FP32 convergence to eps; n: accept after n FP32 queries")
+    ap.add_argument("--alpha-refine", type=float, default=0.0,
+                    help="step factor of the FP32 phase after a tensor-core march (0: alpha)")
+    ap.add_argument("--size", type=int, default=512,
+                    help="image side (512 is the benchmark workload; smaller for profiling)")
     ap.add_argument("--cpu-crop", type=int, default=96)
     ap.add_argument("--ref-crop", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    global SIZE
+    SIZE = args.size
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))

@@ -121,11 +121,15 @@ typedef struct {
                           |f| < 4 eps_bf16 is also accepted as a hit (unit
                           final step, Eq. 1), its silhouette then reported
                           as |f| - 4 eps_bf16.  Ignored for FP32.          */
+  float alpha_refine;  /* BF16/FP16 path: step factor of the FP32 queries
+                          after the hand-over; 0 = alpha (the paper's
+                          aggressive step), 1 = unit steps.  Ignored for
+                          FP32.                                             */
 } dist_trace_params;
 
 /* Fill `p` with the paper's defaults: max_steps 50, eps 5e-5, alpha 1.5,
  * k_min 1, normal_delta 0, exact gradients, FP32, eps_bf16 1e-3, radius 1,
- * refine_steps 0. */
+ * refine_steps 0, alpha_refine 0. */
 void dist_trace_params_default(dist_trace_params* p);
 
 /* -------------------------------------------------------------- workspace */

@@ -48,7 +48,8 @@ class Camera(Structure):
 class TraceParams(Structure):
     _fields_ = [("max_steps", c_int), ("eps", c_float), ("alpha", c_float), ("k_min", c_int),
                 ("normal_delta", c_float), ("grad_mode", c_int), ("precision", c_int),
-                ("eps_bf16", c_float), ("radius", c_float), ("refine_steps", c_int)]
+                ("eps_bf16", c_float), ("radius", c_float), ("refine_steps", c_int),
+                ("alpha_refine", c_float)]
 
 
 class TraceOut(Structure):

@@ -42,6 +42,7 @@ class TraceParams:
     eps_bf16: float = 1e-3        # low-precision phase threshold (BF16 / FP16)
     radius: float = 1.0
     refine_steps: int = 0         # 0: FP32 convergence; n: accept after n FP32 queries
+    alpha_refine: float = 0.0     # step factor of the FP32 phase (0: alpha)
 
     def c(self) -> _abi.TraceParams:
         return _abi.TraceParams(
@@ -49,7 +50,7 @@ class TraceParams:
             float(self.normal_delta),
             _abi.GRAD_EXACT if self.grad_mode == "exact" else _abi.GRAD_PAPER,
             _abi.PRECISIONS[self.precision], float(self.eps_bf16), float(self.radius),
-            int(self.refine_steps))
+            int(self.refine_steps), float(self.alpha_refine))
 
 
 def camera_struct(cam) -> _abi.Camera:

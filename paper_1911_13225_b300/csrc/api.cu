@@ -69,6 +69,7 @@ void dist_trace_params_default(dist_trace_params* p) {
   p->eps_bf16 = 1e-3f;
   p->radius = 1.f;
   p->refine_steps = 0;
+  p->alpha_refine = 0.f;
 }
 
 dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* const* W,

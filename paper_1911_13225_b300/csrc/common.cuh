@@ -215,6 +215,7 @@ struct RayPool {
   int* fq;
   float* fprev;
   int refine;
+  float alpha_fp32;
   dist_trace_out o;
   int K;
   float eps, alpha, eps_bf16, radius;

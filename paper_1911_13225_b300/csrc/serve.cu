@@ -120,6 +120,7 @@ struct dist_server {
     RayPool P;
     P.cams = cams; P.st = stt; P.dir = dir; P.fq = fq; P.fprev = fprev;
     P.refine = is_tc(p.precision) ? p.refine_steps : 0;
+    P.alpha_fp32 = (is_tc(p.precision) && p.alpha_refine > 0.f) ? p.alpha_refine : p.alpha;
     std::memset(&P.o, 0, sizeof(P.o));
     P.o.depth = depth; P.o.sil = sil; P.o.mask = mask; P.o.steps = steps; P.o.status = status;
     P.o.d_hit = d_hit; P.o.d_min = d_min; P.o.f_min = f_min; P.o.queries = queries;

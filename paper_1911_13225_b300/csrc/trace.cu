@@ -101,6 +101,7 @@ struct TraceArgs {
   int K;
   float eps, alpha, eps_bf16;
   int max_steps;
+  float alpha_fp32;     // step factor of FP32-list rays
   int refine;           // refine_steps for a tensor-core march, else 0
   dist_trace_out o;
   float4* st;
@@ -247,7 +248,7 @@ __global__ void step_kernel(TraceArgs a, StepLists L, unsigned long long* querie
       } else if (list == 0 && (af < a.eps_bf16 || crossed)) {
         keep = 1;       // switch to FP32 queries at the same point
       } else {
-        dn = fmaf(a.alpha, f, d);
+        dn = fmaf(list == 1 ? a.alpha_fp32 : a.alpha, f, d);
         if (dn > s.z || dn < s.y) outcome = DIST_RAY_LEFT;
         else keep = list;
       }
@@ -651,6 +652,7 @@ TraceArgs make_args(const dist_trace_params* p, const dist_trace_out* o, dist_wo
   a.pix0 = 0; a.cam_fixed = -1;
   a.eps = p->eps; a.alpha = p->alpha; a.eps_bf16 = p->eps_bf16; a.max_steps = p->max_steps;
   a.refine = is_tc(p->precision) ? p->refine_steps : 0;
+  a.alpha_fp32 = (is_tc(p->precision) && p->alpha_refine > 0.f) ? p->alpha_refine : p->alpha;
   a.o = *o; a.st = ws->st; a.dir = ws->dir; a.fq = ws->fq; a.fprev = ws->fprev;
   return a;
 }
@@ -744,7 +746,7 @@ static TraceArgs pool_args(const RayPool& P) {
   a.cams = P.cams; a.n_cams = 0; a.n_pix = 0; a.pix0 = 0; a.cam_fixed = -1;
   a.radius = P.radius; a.K = P.K; a.eps = P.eps; a.alpha = P.alpha; a.eps_bf16 = P.eps_bf16;
   a.max_steps = P.max_steps; a.o = P.o; a.st = P.st; a.dir = P.dir;
-  a.fq = P.fq; a.fprev = P.fprev; a.refine = P.refine;
+  a.fq = P.fq; a.fprev = P.fprev; a.refine = P.refine; a.alpha_fp32 = P.alpha_fp32;
   return a;
 }
 

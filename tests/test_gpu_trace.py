@@ -95,10 +95,12 @@ def test_normals_at_gpu_hits(cuda_device, delta):
     assert np.all(to_np(res.normal)[~m] == 0)
 
 
-@pytest.mark.parametrize("precision,eps_lo,refine", [("bf16", 1e-3, 0), ("fp16", 1e-3, 0),
-                                                     ("fp16", 1e-4, 1), ("fp16", 2e-4, 1)])
+@pytest.mark.parametrize("precision,eps_lo,refine,alpha_r", [
+    ("bf16", 1e-3, 0, 0.0), ("fp16", 1e-3, 0, 0.0), ("fp16", 1e-4, 1, 0.0), ("fp16", 2e-4, 1, 0.0),
+    ("bf16", 1e-3, 0, 1.0), ("bf16", 3e-4, 0, 1.0), ("fp16", 1e-4, 1, 1.0)])
 @pytest.mark.parametrize("size,vp_seed", [(64, 3), (96, 8)])
-def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precision, eps_lo, refine):
+def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precision, eps_lo, refine,
+                                            alpha_r):
     """Tensor-core marching (BF16 or FP16 operands) until |f| < eps_lo, then
     FP32 queries: converge to eps = 5e-5 (refine = 0) or accept after
     `refine` FP32 queries within 4 eps_lo (unit final step).  Depth within
@@ -110,7 +112,8 @@ def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precisio
     dec = gpu_decoder(spec, Ws, bs)
     cam = synth.look_at_camera(synth.random_viewpoints(1, seed=vp_seed)[0], size, size)
     ws = api.Workspace(size * size, 50)
-    params = api.TraceParams(precision=precision, eps_bf16=eps_lo, refine_steps=refine)
+    params = api.TraceParams(precision=precision, eps_bf16=eps_lo, refine_steps=refine,
+                             alpha_refine=alpha_r)
     res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), [cam], params, ws)
     assert dec.device_error() == 0
     orc = tracer.render(oracle_sdf(spec, Ws, bs, Z), [cam], record=True)
