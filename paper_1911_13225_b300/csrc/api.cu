@@ -45,7 +45,7 @@ static dist_status upload(std::vector<void*>& list, const T** dst, const std::ve
   return DIST_OK;
 }
 
-dist_status pack_tc(dist_decoder* d, const float* const* W);   // mlp_tc.cu
+dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* b);   // mlp_tc.cu
 
 }  // namespace dist
 
@@ -134,7 +134,7 @@ dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* cons
     f.b_head = b[H][0];
   }
   d->tc.ok = false;
-  if (st == DIST_OK && Wd == 512 && H == 8 && S == 4 && L == 256) st = pack_tc(d, W);
+  if (st == DIST_OK && Wd == 512 && H == 8 && S == 4 && L == 256) st = pack_tc(d, W, b);
   if (st != DIST_OK) {
     dist_decoder_destroy(d);
     return st;

@@ -94,12 +94,22 @@ struct DecoderF32 {
 struct TCMaps {
   CUtensorMap m[7];
 };
+// Per-column constants of the tensor-core epilogues (device copy); the
+// epilogue reads them warp-uniformly as float4 rows.
+struct TCConst {
+  float bias[7][512];            // layers 1..7 (entry 3, the skip layer, unused: folded)
+  float wx0[3][512];             // xyz columns of layer 0, by axis
+  float wx4[3][512];             // xyz columns of the skip layer 4, by axis
+  float w_head[512];
+  float b_head;
+};
 struct DecoderTC {
   bool ok;
   TCMaps maps;                   // bf16 operands
   TCMaps maps16;                 // fp16 operands (same layout)
   TCMaps bmaps;                  // W_l^T for the adjoint's backward GEMMs (bf16)
   TCMaps bmaps16;                // same, fp16
+  const TCConst* cst;            // epilogue constants (device)
   int* err;                      // device error word of the bounded waits
 };
 

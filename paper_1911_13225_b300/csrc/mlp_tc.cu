@@ -38,7 +38,8 @@ constexpr int CHUNK_BYTES = BM * BK * 2;      // 16 KB
 constexpr int STAGE_BYTES = BN * BK * 2;      // 32 KB
 constexpr int NUM_GEMM = 7;                   // layers 1..7
 constexpr int BAR_BYTES = 256;
-constexpr int SMEM_BYTES = 1024 + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES + BM * 4;
+constexpr int SMEM_BYTES =
+    1024 + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES + (NUM_EPI / 4 - 1) * BM * 4;
 constexpr unsigned long long kTimeoutNs = 1000000000ull;
 
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
@@ -142,7 +143,8 @@ __device__ __forceinline__ void tc_fence_after() {
 __device__ __forceinline__ void fence_async_shared() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
-// This warp's 32 TMEM lanes x 32 consecutive fp32 columns.
+// This warp's 32 TMEM lanes x 32 consecutive fp32 columns.  The wait is tied
+// to the destination registers so that no use of them is scheduled before it.
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -154,7 +156,28 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
         "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
         "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
+                 "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
+                 "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
+                 "+r"(r[30]), "+r"(r[31]));
+}
+
+// This warp's 32 TMEM lanes x 16 consecutive fp32 columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
@@ -200,19 +223,125 @@ __device__ __forceinline__ void store_act32(uint8_t* act, int r, int c, const fl
   }
 }
 
+// Store NP packed pairs (columns c..c+2*NP-1, c % 8 == 0) of row r.
+template <int NP>
+__device__ __forceinline__ void store_packed(uint8_t* act, int r, int c, const uint32_t (&h)[NP]) {
+#pragma unroll
+  for (int q = 0; q < NP / 4; ++q) {
+    const int col = c + 8 * q;
+    const uint32_t off = (uint32_t)((col >> 6) * CHUNK_BYTES) + swz(r, (col & 63) >> 3);
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(smem_u32(act + off)),
+                 "r"(h[4 * q]), "r"(h[4 * q + 1]), "r"(h[4 * q + 2]), "r"(h[4 * q + 3])
+                 : "memory");
+  }
+}
+
 struct TCArgs {
-  const float* bias[NUM_GEMM];   // layers 1..7, padded to 512 (layer 4 entry unused)
-  const float* Wx0;              // [512][4]
-  const float* Wx4;              // [512][4]
-  const float* w_head;           // [512]
-  float b_head;
-  const float* bfold0;           // [shape][512]
-  const float* bfold4;           // [shape][512]
+  const TCConst* K;              // epilogue constants (device)
+  const float* bfold0;           // [shape][512] folded bias of layer 0
+  const float* bfold4;           // [shape][512] folded bias of the skip layer 4
   RowSrc src;
   float* fout;
   int* err;
 };
 
+// Epilogue split: EPQ warps share a TMEM lane quadrant; inside each 256-column
+// half of the accumulator a thread owns CPT consecutive columns.
+constexpr int EPQ = NUM_EPI / 4;
+constexpr int CPT = 256 / EPQ;
+
+__device__ __forceinline__ float4 ldg4(const float* p) {
+  return __ldg(reinterpret_cast<const float4*>(p));
+}
+
+// v = relu(Wx0 p + b0'), columns c..c+31 of layer 0
+__device__ __forceinline__ void layer0_32(const TCConst* K, const float* bf, int c, const float3& p,
+                                          float (&v)[32]) {
+#pragma unroll
+  for (int i = 0; i < 32; i += 4) {
+    const float4 b = ldg4(bf + c + i);
+    const float4 x = ldg4(K->wx0[0] + c + i);
+    const float4 y = ldg4(K->wx0[1] + c + i);
+    const float4 z = ldg4(K->wx0[2] + c + i);
+    v[i + 0] = fmaxf(fmaf(x.x, p.x, fmaf(y.x, p.y, fmaf(z.x, p.z, b.x))), 0.f);
+    v[i + 1] = fmaxf(fmaf(x.y, p.x, fmaf(y.y, p.y, fmaf(z.y, p.z, b.y))), 0.f);
+    v[i + 2] = fmaxf(fmaf(x.z, p.x, fmaf(y.z, p.y, fmaf(z.z, p.z, b.z))), 0.f);
+    v[i + 3] = fmaxf(fmaf(x.w, p.x, fmaf(y.w, p.y, fmaf(z.w, p.z, b.w))), 0.f);
+  }
+}
+
+// v = accumulator + bias of GEMM layer g (the skip layer: folded bias +
+// Wx4 p), columns c..c+W-1.
+template <int W>
+__device__ __forceinline__ void bias_cols(const TCConst* K, int g, const float* bf4, int c,
+                                          const float3& p, const uint32_t (&r)[W], float (&v)[W]) {
+  if (g == 3) {
+#pragma unroll
+    for (int i = 0; i < W; i += 4) {
+      const float4 b = ldg4(bf4 + c + i);
+      const float4 x = ldg4(K->wx4[0] + c + i);
+      const float4 y = ldg4(K->wx4[1] + c + i);
+      const float4 z = ldg4(K->wx4[2] + c + i);
+      v[i + 0] = fmaf(x.x, p.x, fmaf(y.x, p.y, fmaf(z.x, p.z, __uint_as_float(r[i + 0]) + b.x)));
+      v[i + 1] = fmaf(x.y, p.x, fmaf(y.y, p.y, fmaf(z.y, p.z, __uint_as_float(r[i + 1]) + b.y)));
+      v[i + 2] = fmaf(x.z, p.x, fmaf(y.z, p.y, fmaf(z.z, p.z, __uint_as_float(r[i + 2]) + b.z)));
+      v[i + 3] = fmaf(x.w, p.x, fmaf(y.w, p.y, fmaf(z.w, p.z, __uint_as_float(r[i + 3]) + b.w)));
+    }
+  } else {
+    const float* bias = K->bias[g];
+#pragma unroll
+    for (int i = 0; i < W; i += 4) {
+      const float4 b = ldg4(bias + c + i);
+      v[i + 0] = __uint_as_float(r[i + 0]) + b.x;
+      v[i + 1] = __uint_as_float(r[i + 1]) + b.y;
+      v[i + 2] = __uint_as_float(r[i + 2]) + b.z;
+      v[i + 3] = __uint_as_float(r[i + 3]) + b.w;
+    }
+  }
+}
+__device__ __forceinline__ void bias32(const TCConst* K, int g, const float* bf4, int c,
+                                       const float3& p, const uint32_t (&r)[32], float (&v)[32]) {
+  bias_cols<32>(K, g, bf4, c, p, r, v);
+}
+__device__ __forceinline__ void bias16(const TCConst* K, int g, const float* bf4, int c,
+                                       const float3& p, const uint32_t (&r)[16], float (&v)[16]) {
+  bias_cols<16>(K, g, bf4, c, p, r, v);
+}
+
+__device__ __forceinline__ float head32(const TCConst* K, int c, const float (&v)[32], float acc) {
+#pragma unroll
+  for (int i = 0; i < 32; i += 4) {
+    const float4 w = ldg4(K->w_head + c + i);
+    acc = fmaf(v[i], w.x, fmaf(v[i + 1], w.y, fmaf(v[i + 2], w.z, fmaf(v[i + 3], w.w, acc))));
+  }
+  return acc;
+}
+
+// Layer 0 for this thread's CPT columns of half h, written as operand.
+template <bool F16>
+__device__ __forceinline__ void layer0_store(const TCConst* K, const float* bf, int c0,
+                                             const float3& p, uint8_t* act, int row) {
+#pragma unroll
+  for (int cc = 0; cc < CPT; cc += 32) {
+    float v[32];
+    layer0_32(K, bf, c0 + cc, p, v);
+    store_act32<F16>(act, row, c0 + cc, v);
+  }
+}
+
+// Forward pipeline.  The accumulator of a 512-wide layer completes in two
+// 256-column halves (acc_full[0], acc_full[1]); the next layer's operand is
+// handed back in two 256-column K halves (act_full[0], act_full[1]).
+//   epilogue: after acc_full[0] it reads half 0 into registers while the
+//     tensor core computes half 1; once acc_full[1] says the layer's MMAs
+//     (which read the operand tile) are done, it writes half 0 of the new
+//     operand, releases act_full[0], then reads, converts and writes half 1
+//     and releases act_full[1].
+//   MMA: the next layer's first output half starts on K half 0 as soon as
+//     act_full[0] arrives, overlapping the epilogue's second half; act_full[1]
+//     also certifies that TMEM columns 256..511 have been read.
+// On the last layer the released operand tile takes the next tile's layer 0,
+// so the next tile's GEMMs overlap this tile's head.
 template <bool F16>
 __global__ void __launch_bounds__(THREADS, 1)
 mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
@@ -223,13 +352,13 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
   uint8_t* act = smem;
   uint8_t* wst = smem + ACT_BYTES;
   uint64_t* bars = reinterpret_cast<uint64_t*>(wst + STAGES * STAGE_BYTES);
-  uint64_t* full = bars;                     // [STAGES]
-  uint64_t* empty = bars + STAGES;           // [STAGES]
-  uint64_t* acc_full = bars + 2 * STAGES;    // MMA -> epilogue, once per layer
-  uint64_t* act_full = bars + 2 * STAGES + 1;  // epilogue -> MMA, once per layer
-  uint64_t* drain = bars + 2 * STAGES + 2;   // final MMA completion
-  uint64_t* head_bar = bars + 2 * STAGES + 3;  // column half 1 -> half 0, once per tile
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 4);
+  uint64_t* full = bars;                       // [STAGES]
+  uint64_t* empty = bars + STAGES;             // [STAGES]
+  uint64_t* acc_full = bars + 2 * STAGES;      // [2] MMA -> epilogue, per N half
+  uint64_t* act_full = bars + 2 * STAGES + 2;  // [2] epilogue -> MMA, per K half
+  uint64_t* drain = bars + 2 * STAGES + 4;     // final MMA completion
+  uint64_t* head_bar = bars + 2 * STAGES + 5;  // head partial sums -> column group 0
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* head_part = reinterpret_cast<float*>(smem + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES);
 
@@ -244,10 +373,12 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
-    mbar_init(acc_full, 1);
-    mbar_init(act_full, NUM_EPI * 32);
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(acc_full + h, 1);
+      mbar_init(act_full + h, NUM_EPI * 32);
+    }
     mbar_init(drain, 1);
-    mbar_init(head_bar, NUM_EPI * 16);
+    mbar_init(head_bar, (NUM_EPI - 4) * 32);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -296,15 +427,19 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
     // ------------------------------------------------------- MMA issuer
     if (lane == 0) {
       int stage = 0;
-      uint32_t phase = 0, act_phase = 0;
+      uint32_t phase = 0;
+      uint32_t act_phase[2] = {0u, 0u};
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
-          if (!mbar_wait(act_full, act_phase, abort_flag)) { ok = false; break; }
-          act_phase ^= 1u;
-          tc_fence_after();
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
             for (int kc = 0; kc < gemm_k(g) / BK; ++kc) {
+              if (nh == 0 && (kc & 3) == 0) {
+                const int h = kc >> 2;
+                if (!mbar_wait(act_full + h, act_phase[h], abort_flag)) { ok = false; break; }
+                act_phase[h] ^= 1u;
+                tc_fence_after();
+              }
               if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
               tc_fence_after();
               const uint32_t a_base = smem_u32(act + kc * CHUNK_BYTES);
@@ -316,8 +451,8 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
               mma_commit(empty + stage);
               if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
+            if (ok) mma_commit(acc_full + nh);
           }
-          if (ok) mma_commit(acc_full);
         }
       }
       if (!ok) {
@@ -332,91 +467,142 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
     }
   } else {
     // --------------------------------------------------------- epilogue
-    const int ew = warp - 2;                 // 0..7
-    const int quad = warp & 3;               // TMEM lane quadrant of this warp
-    const int half = ew >> 2;                // column half
-    const int row = quad * 32 + lane;        // tile row == TMEM lane
+    const int ew = warp - 2;                  // 0..NUM_EPI-1
+    const int quad = warp & 3;                // TMEM lane quadrant of this warp
+    const int grp = ew >> 2;                  // column group inside a half
+    const int row = quad * 32 + lane;         // tile row == TMEM lane
+    const int cq = grp * CPT;                 // first column inside a half
     const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
-    uint32_t acc_phase = 0, head_phase = 0;
+    const TCConst* K = a.K;
+    uint32_t acc_phase[2] = {0u, 0u};
+    uint32_t head_phase = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
-      const int j = tile * BM + row;
-      const bool valid = j < n;
-      float3 p = make_float3(0.f, 0.f, 0.f);
-      int shape = 0;
-      if (valid) rowsrc_load(a.src, j, p, shape);
-      // layer 0 on CUDA cores: h0 = relu(Wx0 p + b0'[shape])
-      {
-        const float* bf = a.bfold0 + (size_t)shape * 512;
-        for (int c = half * 256; c < half * 256 + 256; c += 32) {
-          float v[32];
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            const float4 w = __ldg(reinterpret_cast<const float4*>(a.Wx0) + c + i);
-            const float t = fmaf(w.x, p.x, fmaf(w.y, p.y, fmaf(w.z, p.z, __ldg(bf + c + i))));
-            v[i] = fmaxf(t, 0.f);
-          }
-          store_act32<F16>(act, row, c, v);
-        }
-        fence_async_shared();
-        mbar_arrive(act_full);
-      }
+    int tile = blockIdx.x;
+    int j = tile * BM + row;
+    bool valid = j < n;
+    float3 p = make_float3(0.f, 0.f, 0.f);
+    int shape = 0;
+    if (valid) rowsrc_load(a.src, j, p, shape);
+    for (int h = 0; h < 2; ++h) {
+      layer0_store<F16>(K, a.bfold0 + (size_t)shape * 512, 256 * h + cq, p, act, row);
+      fence_async_shared();
+      mbar_arrive(act_full + h);
+    }
+    auto wait_acc = [&](int h) -> bool {
+      if (!mbar_wait(acc_full + h, acc_phase[h], abort_flag)) return false;
+      acc_phase[h] ^= 1u;
+      tc_fence_after();
+      return true;
+    };
+    auto release = [&](int h) {
+      tc_fence_before();
+      fence_async_shared();
+      mbar_arrive(act_full + h);
+    };
+    for (; tile < n_tiles; tile += gridDim.x) {
+      const float* bf4 = a.bfold4 + (size_t)shape * 512;
+      const int next = tile + (int)gridDim.x;
+      const bool has_next = next < n_tiles;
       float head = 0.f;
-      for (int g = 0; g < NUM_GEMM; ++g) {
-        if (!mbar_wait(acc_full, acc_phase, abort_flag)) { ok = false; break; }
-        acc_phase ^= 1u;
-        tc_fence_after();
-        const int ncol = gemm_n(g) / 2;
-        const int c0 = half * ncol;
-        const bool skip_layer = (g == 3);
-        const float* bias = skip_layer ? a.bfold4 + (size_t)shape * 512 : a.bias[g];
-        for (int c = c0; c < c0 + ncol; c += 32) {
+      for (int g = 0; g < NUM_GEMM - 1; ++g) {
+        if (!wait_acc(0)) { ok = false; break; }
+        if (gemm_n(g) == 256) {
+          // one output half: the layer's MMAs are done, write directly
+#pragma unroll
+          for (int cc = 0; cc < CPT; cc += 32) {
+            uint32_t r[32];
+            tmem_ld32(t_row + (uint32_t)(cq + cc), r);
+            float v[32];
+            bias32(K, g, bf4, cq + cc, p, r, v);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+            store_act32<F16>(act, row, cq + cc, v);
+          }
+          release(0);
+          continue;
+        }
+        uint32_t held[CPT / 2];
+#pragma unroll
+        for (int cc = 0; cc < CPT; cc += 16) {
+          uint32_t r[16];
+          tmem_ld16(t_row + (uint32_t)(cq + cc), r);
+          float v[16];
+          bias16(K, g, bf4, cq + cc, p, r, v);
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            held[cc / 2 + i] = pack16<F16>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+        }
+        if (!wait_acc(1)) { ok = false; break; }
+        store_packed<CPT / 2>(act, row, cq, held);
+        release(0);
+#pragma unroll
+        for (int cc = 0; cc < CPT; cc += 32) {
           uint32_t r[32];
-          tmem_ld32(t_row + (uint32_t)c, r);
+          tmem_ld32(t_row + (uint32_t)(256 + cq + cc), r);
           float v[32];
-#pragma unroll
-          for (int i = 0; i < 32; i += 4) {
-            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + c + i));
-            v[i + 0] = __uint_as_float(r[i + 0]) + b4.x;
-            v[i + 1] = __uint_as_float(r[i + 1]) + b4.y;
-            v[i + 2] = __uint_as_float(r[i + 2]) + b4.z;
-            v[i + 3] = __uint_as_float(r[i + 3]) + b4.w;
-          }
-          if (skip_layer) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float4 w = __ldg(reinterpret_cast<const float4*>(a.Wx4) + c + i);
-              v[i] = fmaf(w.x, p.x, fmaf(w.y, p.y, fmaf(w.z, p.z, v[i])));
-            }
-          }
+          bias32(K, g, bf4, 256 + cq + cc, p, r, v);
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
-          if (g < NUM_GEMM - 1) {
-            store_act32<F16>(act, row, c, v);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 32; i += 4) {
-              const float4 w = __ldg(reinterpret_cast<const float4*>(a.w_head + c + i));
-              head = fmaf(v[i], w.x, fmaf(v[i + 1], w.y, fmaf(v[i + 2], w.z, fmaf(v[i + 3], w.w, head))));
-            }
-          }
+          store_act32<F16>(act, row, 256 + cq + cc, v);
         }
-        tc_fence_before();
-        if (g < NUM_GEMM - 1) {
-          fence_async_shared();
-          mbar_arrive(act_full);
-        }
+        release(1);
       }
       if (!ok) break;
-      // head: f = tanh(w . h7 + b); half 1 hands its partial sums to half 0
-      // (head_part is rewritten only after the next tile's seven layers,
-      // which half 0 takes part in, so one barrier phase per tile suffices)
-      if (half == 1) {
-        head_part[row] = head;
+      // ---- last layer: head partial sums; the operand tile takes the next
+      // tile's layer 0 once this layer's MMAs are done
+      const int cur_j = j;
+      const bool cur_valid = valid;
+      if (has_next) {
+        j = next * BM + row;
+        valid = j < n;
+        p = make_float3(0.f, 0.f, 0.f);
+        shape = 0;
+        if (valid) rowsrc_load(a.src, j, p, shape);
+      }
+      if (!wait_acc(0)) { ok = false; break; }
+#pragma unroll
+      for (int cc = 0; cc < CPT; cc += 32) {
+        uint32_t r[32];
+        tmem_ld32(t_row + (uint32_t)(cq + cc), r);
+        float v[32];
+        bias32(K, NUM_GEMM - 1, bf4, cq + cc, p, r, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+        head = head32(K, cq + cc, v, head);
+      }
+      if (!wait_acc(1)) { ok = false; break; }
+      const float* bf0 = a.bfold0 + (size_t)shape * 512;
+      if (has_next) {
+        layer0_store<F16>(K, bf0, cq, p, act, row);
+        release(0);
+      }
+#pragma unroll
+      for (int cc = 0; cc < CPT; cc += 32) {
+        uint32_t r[32];
+        tmem_ld32(t_row + (uint32_t)(256 + cq + cc), r);
+        float v[32];
+        bias32(K, NUM_GEMM - 1, bf4, 256 + cq + cc, p, r, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+        head = head32(K, 256 + cq + cc, v, head);
+      }
+      if (has_next) {
+        layer0_store<F16>(K, bf0, 256 + cq, p, act, row);
+        release(1);
+      } else {
+        tc_fence_before();
+      }
+      // head: f = tanh(w . h7 + b); column groups 1.. hand their partial sums
+      // to group 0 (head_part is rewritten only after the next tile's layers,
+      // which group 0 takes part in, so one barrier phase per tile suffices)
+      if (grp > 0) {
+        head_part[(grp - 1) * BM + row] = head;
         mbar_arrive(head_bar);
       } else {
         if (!mbar_wait(head_bar, head_phase, abort_flag)) { ok = false; break; }
-        if (valid) a.fout[j] = tanhf(head + head_part[row] + a.b_head);
+#pragma unroll
+        for (int q = 0; q < EPQ - 1; ++q) head += head_part[q * BM + row];
+        if (cur_valid) a.fout[cur_j] = tanhf(head + __ldg(&K->b_head));
       }
       head_phase ^= 1u;
     }
@@ -459,11 +645,7 @@ __device__ __forceinline__ int adj_n(int e) { return e < 7 ? gemm_n(e) : gemm_k(
 __device__ __forceinline__ int adj_k(int e) { return e < 7 ? gemm_k(e) : gemm_n(13 - e); }
 
 struct TCAdjArgs {
-  const float* bias[NUM_GEMM];
-  const float* Wx0;
-  const float* Wx4;
-  const float* w_head;
-  float b_head;
+  const TCConst* K;
   const float* bfold0;
   const float* bfold4;
   const float4* pp;
@@ -637,13 +819,12 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
         uint32_t mw[8];
         for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
           float v[32];
+          layer0_32(a.K, bf, c, p, v);
           uint32_t bits = 0;
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
-            const float4 wx = __ldg(reinterpret_cast<const float4*>(a.Wx0) + c + i);
-            const float t = fmaf(wx.x, p.x, fmaf(wx.y, p.y, fmaf(wx.z, p.z, __ldg(bf + c + i))));
-            bits |= (t > 0.f ? 1u : 0u) << i;
-            v[i] = fmaxf(t, 0.f);
+            bits |= (v[i] > 0.f ? 1u : 0u) << i;
+            v[i] = fmaxf(v[i], 0.f);
           }
           mw[w] = bits;
           store_act32<F16>(act, row, c, v);
@@ -661,28 +842,13 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
         tc_fence_after();
         const int ncol = gemm_n(g) / 2;
         const int c0 = half * ncol;
-        const bool skip_layer = (g == 3);
-        const float* bias = skip_layer ? a.bfold4 + (size_t)shape * 512 : a.bias[g];
+        const float* bf4 = a.bfold4 + (size_t)shape * 512;
         uint32_t mw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int c = c0, w = 0; c < c0 + ncol; c += 32, ++w) {
           uint32_t r[32];
           tmem_ld32(t_row + (uint32_t)c, r);
           float v[32];
-#pragma unroll
-          for (int i = 0; i < 32; i += 4) {
-            const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + c + i));
-            v[i + 0] = __uint_as_float(r[i + 0]) + b4.x;
-            v[i + 1] = __uint_as_float(r[i + 1]) + b4.y;
-            v[i + 2] = __uint_as_float(r[i + 2]) + b4.z;
-            v[i + 3] = __uint_as_float(r[i + 3]) + b4.w;
-          }
-          if (skip_layer) {
-#pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float4 wx = __ldg(reinterpret_cast<const float4*>(a.Wx4) + c + i);
-              v[i] = fmaf(wx.x, p.x, fmaf(wx.y, p.y, fmaf(wx.z, p.z, v[i])));
-            }
-          }
+          bias32(a.K, g, bf4, c, p, r, v);
           uint32_t bits = 0;
 #pragma unroll
           for (int i = 0; i < 32; ++i) {
@@ -693,11 +859,7 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           if (g < NUM_GEMM - 1) {
             store_act32<F16>(act, row, c, v);
           } else {
-#pragma unroll
-            for (int i = 0; i < 32; i += 4) {
-              const float4 wh = __ldg(reinterpret_cast<const float4*>(a.w_head + c + i));
-              head = fmaf(v[i], wh.x, fmaf(v[i + 1], wh.y, fmaf(v[i + 2], wh.z, fmaf(v[i + 3], wh.w, head))));
-            }
+            head = head32(a.K, c, v, head);
           }
         }
         uint4* mp = reinterpret_cast<uint4*>(mask_ptr(g + 1));
@@ -719,7 +881,7 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
         dfs = xfer[row];
       } else {
         if (!mbar_wait(h2l, h2l_phase, abort_flag)) { ok = false; break; }
-        fval = tanhf(head + xfer[row] + a.b_head);
+        fval = tanhf(head + xfer[row] + __ldg(&a.K->b_head));
         dfs = 1.f - fval * fval;
         xfer[row] = dfs;
         mbar_arrive(l2h);
@@ -734,11 +896,11 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           float v[32];
 #pragma unroll
           for (int i = 0; i < 32; i += 4) {
-            const float4 wh = __ldg(reinterpret_cast<const float4*>(a.w_head + c + i));
-            v[i + 0] = ((bits >> (i + 0)) & 1u) ? dfs * wh.x : 0.f;
-            v[i + 1] = ((bits >> (i + 1)) & 1u) ? dfs * wh.y : 0.f;
-            v[i + 2] = ((bits >> (i + 2)) & 1u) ? dfs * wh.z : 0.f;
-            v[i + 3] = ((bits >> (i + 3)) & 1u) ? dfs * wh.w : 0.f;
+            const float4 w = ldg4(a.K->w_head + c + i);
+            v[i + 0] = ((bits >> (i + 0)) & 1u) ? dfs * w.x : 0.f;
+            v[i + 1] = ((bits >> (i + 1)) & 1u) ? dfs * w.y : 0.f;
+            v[i + 2] = ((bits >> (i + 2)) & 1u) ? dfs * w.z : 0.f;
+            v[i + 3] = ((bits >> (i + 3)) & 1u) ? dfs * w.w : 0.f;
           }
           store_act32<F16>(act, row, c, v);
         }
@@ -764,13 +926,13 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           for (int i = 0; i < 32; ++i) v[i] = ((bits >> i) & 1u) ? __uint_as_float(r[i]) : 0.f;
           if (l == 5 || l == 1) {
             // g_4 or g_0: the xyz columns of that layer give grad_p f
-            const float* Wx = l == 5 ? a.Wx4 : a.Wx0;
+            const float(*Wx)[512] = l == 5 ? a.K->wx4 : a.K->wx0;
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const float4 wx = __ldg(reinterpret_cast<const float4*>(Wx) + c + i);
-              gx = fmaf(v[i], wx.x, gx);
-              gy = fmaf(v[i], wx.y, gy);
-              gz = fmaf(v[i], wx.z, gz);
+            for (int i = 0; i < 32; i += 4) {
+              const float4 x = ldg4(Wx[0] + c + i), y = ldg4(Wx[1] + c + i), z = ldg4(Wx[2] + c + i);
+              gx = fmaf(v[i], x.x, fmaf(v[i + 1], x.y, fmaf(v[i + 2], x.z, fmaf(v[i + 3], x.w, gx))));
+              gy = fmaf(v[i], y.x, fmaf(v[i + 1], y.y, fmaf(v[i + 2], y.z, fmaf(v[i + 3], y.w, gy))));
+              gz = fmaf(v[i], z.x, fmaf(v[i + 1], z.y, fmaf(v[i + 2], z.z, fmaf(v[i + 3], z.w, gz))));
             }
             if (l == 5) {
               float4* dst = reinterpret_cast<float4*>(g4s + (size_t)row * 512 + c);
@@ -881,11 +1043,38 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 
 }  // namespace
 
-dist_status pack_tc(dist_decoder* d, const float* const* W) {
+dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* b) {
   d->tc.ok = false;
   auto enc = tensor_map_encoder();
   DIST_CHECK(enc != nullptr, DIST_E_CUDA, "cuTensorMapEncodeTiled entry point not available");
   const int L = 256, Hh = 253;   // latent, h-part of the skip input
+  {
+    // epilogue constants; layer 3 has Hh real outputs, the rest stay 0
+    TCConst* c = new TCConst();
+    for (int g = 0; g < NUM_GEMM; ++g) {
+      const int n_real = (g + 1 == 3) ? Hh : 512;
+      for (int j = 0; j < n_real; ++j) c->bias[g][j] = b[g + 1][j];
+    }
+    for (int j = 0; j < 512; ++j)
+      for (int ax = 0; ax < 3; ++ax) {
+        c->wx0[ax][j] = W[0][(size_t)j * (L + 3) + L + ax];
+        c->wx4[ax][j] = W[4][(size_t)j * 512 + Hh + L + ax];
+      }
+    for (int j = 0; j < 512; ++j) c->w_head[j] = W[8][j];
+    c->b_head = b[8][0];
+    void* q = nullptr;
+    cudaError_t e = cudaMalloc(&q, sizeof(TCConst));
+    if (e == cudaSuccess) {
+      d->allocations.push_back(q);
+      e = cudaMemcpy(q, c, sizeof(TCConst), cudaMemcpyHostToDevice);
+    }
+    delete c;
+    if (e != cudaSuccess) {
+      set_error(std::string("TCConst upload: ") + cudaGetErrorString(e));
+      return DIST_E_CUDA;
+    }
+    d->tc.cst = static_cast<const TCConst*>(q);
+  }
   for (int f16 = 0; f16 < 2; ++f16) {
     for (int g = 0; g < NUM_GEMM; ++g) {
       const int l = g + 1;
@@ -959,13 +1148,8 @@ cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const flo
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const DecoderF32& f = dec->f32;
   TCArgs a;
-  for (int g = 0; g < NUM_GEMM; ++g) a.bias[g] = f.b[g + 1];
-  a.Wx0 = f.Wx0;
-  a.Wx4 = f.Wxs;
-  a.w_head = f.w_head;
-  a.b_head = f.b_head;
+  a.K = dec->tc.cst;
   a.bfold0 = bfold0;
   a.bfold4 = bfolds;
   a.src = src;
@@ -995,13 +1179,8 @@ cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const floa
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  const DecoderF32& f = dec->f32;
   TCAdjArgs a;
-  for (int g = 0; g < NUM_GEMM; ++g) a.bias[g] = f.b[g + 1];
-  a.Wx0 = f.Wx0;
-  a.Wx4 = f.Wxs;
-  a.w_head = f.w_head;
-  a.b_head = f.b_head;
+  a.K = dec->tc.cst;
   a.bfold0 = bfold0;
   a.bfold4 = bfolds;
   a.pp = pp;
@@ -1015,11 +1194,11 @@ cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const floa
   a.err = dec->tc.err;
   prof_mlp_begin(st, 2);
   if (f16)
-    mlp_tc_adj_kernel<true><<<num_sms(), THREADS, ADJ_SMEM_BYTES, st>>>(dec->tc.maps16,
-                                                                        dec->tc.bmaps16, a);
+    mlp_tc_adj_kernel<true><<<num_sms(), THREADS, ADJ_SMEM_BYTES, st>>>(
+        dec->tc.maps16, dec->tc.bmaps16, a);
   else
-    mlp_tc_adj_kernel<false><<<num_sms(), THREADS, ADJ_SMEM_BYTES, st>>>(dec->tc.maps,
-                                                                         dec->tc.bmaps, a);
+    mlp_tc_adj_kernel<false><<<num_sms(), THREADS, ADJ_SMEM_BYTES, st>>>(
+        dec->tc.maps, dec->tc.bmaps, a);
   prof_mlp_end(st);
   count_launch(1);
   return cudaGetLastError();
