@@ -160,7 +160,8 @@ def run_ours(args, rank, world, local_rank):
     if precision == "auto":
         precision = "bf16" if dec.has_bf16 else "fp32"
     params = api.TraceParams(max_steps=MAX_STEPS, precision=precision, eps_bf16=args.eps_lo,
-                             refine_steps=args.refine, alpha_refine=args.alpha_refine)
+                             refine_steps=args.refine, alpha_refine=args.alpha_refine,
+                             refine_engine=args.refine_engine)
     ws = api.Workspace(SIZE * SIZE, MAX_STEPS)
     z = torch.from_numpy(Z).to(dev)
     # target: depth of the second latent (untimed setup)
@@ -245,6 +246,16 @@ def run_ours(args, rank, world, local_rank):
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "peak_source": f"{peak_src} bf16 burst",
                 "traffic": None}
+    elif precision == "fp32_tc":
+        k_ms, k_q, k_n = ms_arr[1], queries[1], cnt_arr[1]
+        achieved = k_q * FLOP_PER_QUERY / (k_ms * 1e-3) / 1e12 if k_ms > 0 else 0.0
+        peak = peaks["bf16_tflops"]
+        roof = {"bound": "tensor",
+                "kernel": "mlp_tcx_kernel (FP32-class tcgen05 decoder: two-term FP16 split, "
+                          "4 tensor FLOP per algorithmic FLOP, so frac <= 0.25)",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "peak_source": f"{peak_src} bf16 burst",
+                "traffic": None}
     else:
         k_ms, k_q, k_n = ms_arr[1], queries[1], cnt_arr[1]
         achieved = k_q * FLOP_PER_QUERY / (k_ms * 1e-3) / 1e12 if k_ms > 0 else 0.0
@@ -257,8 +268,8 @@ def run_ours(args, rank, world, local_rank):
     roof["mlp_ms_per_step"] = k_ms / args.steps
     roof["mlp_launches_per_step"] = k_n / args.steps
     roof["queries_per_step"] = float(k_q) / args.steps
-    breakdown = {"march_bf16_tc_ms": ms_arr[0] / args.steps,
-                 "march_fp32_simt_ms": ms_arr[1] / args.steps,
+    breakdown = {"march_lowp_tc_ms": ms_arr[0] / args.steps,
+                 "march_fp32_class_ms": ms_arr[1] / args.steps,
                  "adjoint_ms": ms_arr[2] / args.steps,
                  "other_ms": ms_per_step - (ms_arr[0] + ms_arr[1] + ms_arr[2]) / args.steps}
     bi = z_host.numel() * 4 + tgt_host.numel() * 4
@@ -268,15 +279,16 @@ def run_ours(args, rank, world, local_rank):
         "value": value, "unit": "rays/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": {"bf16": "bf16", "fp16": "f16", "fp32": "f32"}[precision],
+        "dtype": {"bf16": "bf16", "fp16": "f16", "fp32": "f32", "fp32_tc": "f16x2"}[precision],
         "data": "synthetic (seeded decoder, latents and camera; no DeepSDF weights)",
         "config": {"workload": WORKLOAD.replace("512x512", f"{SIZE}x{SIZE}"),
                    "rays_per_step": rays, "precision": precision,
                    "eps_lo": args.eps_lo, "refine_steps": args.refine,
+                   "refine_engine": args.refine_engine,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MB write, untimed)"},
         "sdf_queries_per_s": float(queries.sum()) * world / (total_ms * 1e-3),
-        "queries_per_step": {"bf16": float(queries[0]) / args.steps,
+        "queries_per_step": {"lowp": float(queries[0]) / args.steps,
                              "fp32": float(queries[1]) / args.steps},
         "hits": hits,
         "e2e": {"value": rays * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": bi,
@@ -371,7 +383,10 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp16", "fp32"])
+    ap.add_argument("--precision", default="auto",
+                    choices=["auto", "bf16", "fp16", "fp32", "fp32_tc"])
+    ap.add_argument("--refine-engine", default="tc", choices=["tc", "simt"],
+                    help="kernel of the FP32-class queries after a BF16/FP16 hand-over")
     ap.add_argument("--eps-lo", type=float, default=1e-3,
                     help="|f| below which a BF16/FP16 ray switches to FP32 queries")
     ap.add_argument("--refine", type=int, default=0,

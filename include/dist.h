@@ -48,8 +48,19 @@ typedef enum {
 
 /* Precision of the marching decoder queries.  BF16 and FP16 run the GEMM
  * layers on the tensor cores (16-bit operands, FP32 accumulation) and hand a
- * ray to FP32 queries once |f| < eps_bf16; FP32 runs every query in FP32. */
-typedef enum { DIST_PREC_FP32 = 0, DIST_PREC_BF16 = 1, DIST_PREC_FP16 = 2 } dist_precision;
+ * ray to FP32-class queries once |f| < eps_bf16; FP32 runs every query in
+ * FP32 on the CUDA cores (the plain FP32 trace); FP32_TC runs every query on
+ * the tensor cores with each operand carried as a sum of two FP16 numbers
+ * (22 significant bits, FP32 accumulation), the DeepSDF shape only. */
+typedef enum {
+  DIST_PREC_FP32 = 0,
+  DIST_PREC_BF16 = 1,
+  DIST_PREC_FP16 = 2,
+  DIST_PREC_FP32_TC = 3
+} dist_precision;
+
+/* Kernel of the FP32-class queries after a BF16/FP16 hand-over. */
+typedef enum { DIST_REFINE_TC = 0, DIST_REFINE_SIMT = 1 } dist_refine_engine;
 typedef enum { DIST_GRAD_EXACT = 0, DIST_GRAD_PAPER = 1 } dist_grad_mode;
 
 /* Ray outcome codes written to dist_trace_out.status. */
@@ -125,11 +136,14 @@ typedef struct {
                           after the hand-over; 0 = alpha (the paper's
                           aggressive step), 1 = unit steps.  Ignored for
                           FP32.                                             */
+  int refine_engine;   /* BF16/FP16 path: dist_refine_engine of the queries
+                          after the hand-over (TC: the FP32_TC kernel,
+                          SIMT: FP32 CUDA-core kernel)                      */
 } dist_trace_params;
 
 /* Fill `p` with the paper's defaults: max_steps 50, eps 5e-5, alpha 1.5,
  * k_min 1, normal_delta 0, exact gradients, FP32, eps_bf16 1e-3, radius 1,
- * refine_steps 0, alpha_refine 0. */
+ * refine_steps 0, alpha_refine 0, refine_engine TC. */
 void dist_trace_params_default(dist_trace_params* p);
 
 /* -------------------------------------------------------------- workspace */
@@ -194,8 +208,9 @@ dist_status dist_render_normals(const dist_decoder* dec, const float* z, int n_s
 /* Evaluate the decoder f(p, z_shape) (Sec. 3.4: f_theta(p, z)) at n points:
  * pts: device float [n][3]; shape: device int32 [n] latent index per point;
  * f: device float [n]; grad: device float [n][3] = grad_p f, or NULL.
- * precision DIST_PREC_FP32 (SIMT kernels; grad allowed) or DIST_PREC_BF16
- * (tensor-core kernel; grad must be NULL).  n <= 10 * workspace max_rays.
+ * precision DIST_PREC_FP32 (SIMT kernels; grad allowed), DIST_PREC_BF16,
+ * DIST_PREC_FP16 or DIST_PREC_FP32_TC (tensor-core kernels; grad must be
+ * NULL).  n <= 10 * workspace max_rays.
  * Shape indices outside [0, n_shapes) are clamped into range.
  * Errors: DIST_E_INVALID, DIST_E_UNSUPPORTED, DIST_E_CUDA. */
 dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,

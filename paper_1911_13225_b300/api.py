@@ -38,11 +38,12 @@ class TraceParams:
     k_min: int = 1
     normal_delta: float = 0.0
     grad_mode: str = "exact"      # "exact" | "paper"
-    precision: str = "fp32"       # "fp32" | "bf16" | "fp16"
+    precision: str = "fp32"       # "fp32" | "bf16" | "fp16" | "fp32_tc"
     eps_bf16: float = 1e-3        # low-precision phase threshold (BF16 / FP16)
     radius: float = 1.0
     refine_steps: int = 0         # 0: FP32 convergence; n: accept after n FP32 queries
     alpha_refine: float = 0.0     # step factor of the FP32 phase (0: alpha)
+    refine_engine: str = "tc"     # FP32-class queries after the hand-over: "tc" | "simt"
 
     def c(self) -> _abi.TraceParams:
         return _abi.TraceParams(
@@ -50,7 +51,8 @@ class TraceParams:
             float(self.normal_delta),
             _abi.GRAD_EXACT if self.grad_mode == "exact" else _abi.GRAD_PAPER,
             _abi.PRECISIONS[self.precision], float(self.eps_bf16), float(self.radius),
-            int(self.refine_steps), float(self.alpha_refine))
+            int(self.refine_steps), float(self.alpha_refine),
+            _abi.REFINE_ENGINES[self.refine_engine])
 
 
 def camera_struct(cam) -> _abi.Camera:

@@ -70,6 +70,7 @@ void dist_trace_params_default(dist_trace_params* p) {
   p->radius = 1.f;
   p->refine_steps = 0;
   p->alpha_refine = 0.f;
+  p->refine_engine = DIST_REFINE_TC;
 }
 
 dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* const* W,

@@ -50,6 +50,17 @@ inline bool is_tc(int precision) {
   return precision == DIST_PREC_BF16 || precision == DIST_PREC_FP16;
 }
 
+// Precisions accepted by the trace and evaluation entry points.
+inline bool valid_precision(int precision) {
+  return precision == DIST_PREC_FP32 || is_tc(precision) || precision == DIST_PREC_FP32_TC;
+}
+
+// The FP32-class queries of a trace (its FP32 list) run on the tensor cores.
+inline bool fp32_on_tc(const dist_trace_params& p) {
+  return p.precision == DIST_PREC_FP32_TC ||
+         (is_tc(p.precision) && p.refine_engine == DIST_REFINE_TC);
+}
+
 constexpr int kMaxShapes = 1024;    // folded-bias capacity of a workspace
 constexpr int kMaxK = 3;            // k_min upper bound (Sec. B.4 uses 1 or 3)
 constexpr int kProbesPerRay = 10;   // probe capacity per pixel in a workspace:
@@ -109,6 +120,8 @@ struct DecoderTC {
   TCMaps maps16;                 // fp16 operands (same layout)
   TCMaps bmaps;                  // W_l^T for the adjoint's backward GEMMs (bf16)
   TCMaps bmaps16;                // same, fp16
+  TCMaps xmaps;                  // [N][2K] fp16 hi | lo split of 2^s_l W_l (FP32-class kernel)
+  float x_inv_scale[7];          // 2^-s_l
   const TCConst* cst;            // epilogue constants (device)
   int* err;                      // device error word of the bounded waits
 };
@@ -248,6 +261,11 @@ cudaError_t pool_latent_finalize(const DecoderF32& d, const double* G0, const do
 // (DeepSDF shape only).
 cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
                            const float* bfolds, float* fout, cudaStream_t st, bool f16);
+
+// FP32-class tcgen05 decoder forward (two-term FP16 split of weights and
+// activations; DeepSDF shape only).
+cudaError_t mlp_tcx_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
+                            const float* bfolds, float* fout, cudaStream_t st);
 
 // tcgen05 decoder adjoint over probes (same contract as mlp_fp32_adjoint;
 // `scratch` holds num_sms() * kTcAdjScratchPerCta bytes).

@@ -1,0 +1,501 @@
+// FP32-class tensor-core decoder forward for the DeepSDF shape (the same
+// decoder as mlp_tc.cu: 8 x 512, skip at 4, latent folded into per-shape
+// biases, Sec. B.1).
+//
+// Every GEMM operand is carried as an unevaluated sum of two FP16 numbers,
+// x = hi + lo with hi = fp16(x), lo = fp16(x - hi): 22 significant bits, so
+// that the products below are within a few FP32 ulps of the FP32 ones.  The
+// weights of layer l are scaled by 2^s_l before the split (the scale keeps
+// W_lo a normal FP16 number); the epilogue multiplies by 2^-s_l, exactly.
+//
+// Tiling: 64 queries per 128-row tile.  In TMEM lane quadrant q, rows
+// 32q + i (i < 16) hold the hi parts of the activations of query 16q + i and
+// rows 32q + 16 + i their lo parts.  Each layer runs its K loop twice, first
+// against W_lo, then against W_hi, into one FP32 accumulator, so rows
+// 32q + i and 32q + 16 + i hold a_hi (W_hi + W_lo) and a_lo (W_hi + W_lo);
+// their sum, one warp shuffle apart, is (a_hi + a_lo)(W_hi + W_lo).  All four
+// partial products are kept, so nothing is dropped beyond the two split
+// residuals.  Bias, ReLU, layer 0 (3 inputs), the xyz columns of layer 4 and
+// the head run in FP32 on CUDA cores, as in the BF16 kernel.
+//
+// Accuracy: emulated with exact accumulation this arithmetic is as close to
+// the FP64 decoder as FP32 CUDA-core arithmetic (~1e-7 in f), but the tensor
+// core's FP32 accumulator does not round to nearest: measured on B300 each
+// K step loses a fraction of an ulp of the running sum, always towards zero,
+// which leaves a systematic error of a few 1e-6 in f.  The small W_lo pass
+// runs first so that only the W_hi pass adds into a large accumulator.
+//
+// Pipeline (warp roles, 3-stage weight ring, split accumulator halves and
+// operand halves, bounded waits) is that of mlp_tc.cu; the work per query is
+// four times a BF16 query (two rows, two K passes).
+#include <cmath>
+#include <vector>
+
+#include "tc_common.cuh"
+
+namespace dist {
+
+namespace {
+
+constexpr int QPT = 64;   // queries per tile
+
+struct TCXArgs {
+  const TCConst* K;
+  const float* bfold0;
+  const float* bfold4;
+  RowSrc src;
+  float* fout;
+  int* err;
+  float inv_scale[NUM_GEMM];   // 2^-s_l of GEMM layer g
+};
+
+// v = m * scale + bias of GEMM layer g (the skip layer: folded bias + Wx4 p),
+// 16 columns from c.
+__device__ __forceinline__ void affine16(const TCConst* K, int g, const float* bf4, int c,
+                                         const float3& p, float scale, const float (&m)[16],
+                                         float (&v)[16]) {
+  if (g == 3) {
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+      const float4 b = ldg4(bf4 + c + i);
+      const float4 x = ldg4(K->wx4[0] + c + i);
+      const float4 y = ldg4(K->wx4[1] + c + i);
+      const float4 z = ldg4(K->wx4[2] + c + i);
+      v[i + 0] = fmaf(x.x, p.x, fmaf(y.x, p.y, fmaf(z.x, p.z, fmaf(m[i + 0], scale, b.x))));
+      v[i + 1] = fmaf(x.y, p.x, fmaf(y.y, p.y, fmaf(z.y, p.z, fmaf(m[i + 1], scale, b.y))));
+      v[i + 2] = fmaf(x.z, p.x, fmaf(y.z, p.y, fmaf(z.z, p.z, fmaf(m[i + 2], scale, b.z))));
+      v[i + 3] = fmaf(x.w, p.x, fmaf(y.w, p.y, fmaf(z.w, p.z, fmaf(m[i + 3], scale, b.w))));
+    }
+  } else {
+    const float* bias = K->bias[g];
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+      const float4 b = ldg4(bias + c + i);
+      v[i + 0] = fmaf(m[i + 0], scale, b.x);
+      v[i + 1] = fmaf(m[i + 1], scale, b.y);
+      v[i + 2] = fmaf(m[i + 2], scale, b.z);
+      v[i + 3] = fmaf(m[i + 3], scale, b.w);
+    }
+  }
+}
+
+// Layer 0 pre-activation, 16 columns from c: Wx0 p + b0'.
+__device__ __forceinline__ void layer0_16(const TCConst* K, const float* bf, int c, const float3& p,
+                                          float (&v)[16]) {
+#pragma unroll
+  for (int i = 0; i < 16; i += 4) {
+    const float4 b = ldg4(bf + c + i);
+    const float4 x = ldg4(K->wx0[0] + c + i);
+    const float4 y = ldg4(K->wx0[1] + c + i);
+    const float4 z = ldg4(K->wx0[2] + c + i);
+    v[i + 0] = fmaf(x.x, p.x, fmaf(y.x, p.y, fmaf(z.x, p.z, b.x)));
+    v[i + 1] = fmaf(x.y, p.x, fmaf(y.y, p.y, fmaf(z.y, p.z, b.y)));
+    v[i + 2] = fmaf(x.z, p.x, fmaf(y.z, p.y, fmaf(z.z, p.z, b.z)));
+    v[i + 3] = fmaf(x.w, p.x, fmaf(y.w, p.y, fmaf(z.w, p.z, b.w)));
+  }
+}
+
+// ReLU, then the two-term FP16 split of 16 values, packed in pairs.
+// `vmax` tracks the largest activation (an FP16 overflow check).
+__device__ __forceinline__ void relu_split16(float (&v)[16], uint32_t (&hi)[8], uint32_t (&lo)[8],
+                                             float& vmax) {
+#pragma unroll
+  for (int i = 0; i < 16; i += 2) {
+    const float a = fmaxf(v[i], 0.f), b = fmaxf(v[i + 1], 0.f);
+    vmax = fmaxf(vmax, fmaxf(a, b));
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi[i / 2] = *reinterpret_cast<const uint32_t*>(&h);
+    lo[i / 2] = *reinterpret_cast<const uint32_t*>(&l);
+  }
+}
+
+// Sum of the hi-row and lo-row accumulators of one query for the 16 columns
+// this lane owns in a 32-column chunk: lanes i and i + 16 exchange the half
+// of the chunk the other one keeps (16 shuffles).
+__device__ __forceinline__ void pair_sum16(const uint32_t (&r)[32], int part, float (&m)[16]) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float keep = __uint_as_float(part ? r[16 + i] : r[i]);
+    const float send = __uint_as_float(part ? r[i] : r[16 + i]);
+    m[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+mlp_tcx_kernel(const __grid_constant__ TCMaps maps, const TCXArgs a) {
+  constexpr uint32_t kIdesc = instr_desc<true>();
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint8_t* act = smem;
+  uint8_t* wst = smem + ACT_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wst + STAGES * STAGE_BYTES);
+  uint64_t* full = bars;                       // [STAGES]
+  uint64_t* empty = bars + STAGES;             // [STAGES]
+  uint64_t* acc_full = bars + 2 * STAGES;      // [2] MMA -> epilogue, per N half
+  uint64_t* act_full = bars + 2 * STAGES + 2;  // [2] epilogue -> MMA, per K half
+  uint64_t* drain = bars + 2 * STAGES + 4;
+  uint64_t* head_bar = bars + 2 * STAGES + 5;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  float* head_part = reinterpret_cast<float*>(smem + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+  const int n = rowsrc_count(a.src);
+  const int n_tiles = (n + QPT - 1) / QPT;
+  if ((int)blockIdx.x >= n_tiles) return;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(acc_full + h, 1);
+      mbar_init(act_full + h, NUM_EPI * 32);
+    }
+    mbar_init(drain, 1);
+    mbar_init(head_bar, (NUM_EPI - 4) * 32);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------ TMA producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t issued_parity[STAGES];
+      bool issued[STAGES];
+      for (int s = 0; s < STAGES; ++s) issued[s] = false;
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+        for (int g = 0; ok && g < NUM_GEMM; ++g) {
+          const int nkc = gemm_k(g) / BK;
+          for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
+            for (int kc = 0; kc < 2 * nkc; ++kc) {
+              if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) { ok = false; break; }
+              mbar_expect_tx(full + stage, STAGE_BYTES);
+              // W_lo pass first (columns K..2K-1), then W_hi
+              const int xk = kc < nkc ? nkc + kc : kc - nkc;
+              tma_load_2d(wst + stage * STAGE_BYTES, &maps.m[g], full + stage, xk * BK, nh * BN);
+              issued[stage] = true;
+              issued_parity[stage] = phase;
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.err, 1);
+      }
+      for (int s = 0; s < STAGES; ++s) {
+        if (!issued[s]) continue;
+        const unsigned long long t0 = globaltimer();
+        while (!mbar_try_wait(full + s, issued_parity[s]) && globaltimer() - t0 < kTimeoutNs) {
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      uint32_t act_phase[2] = {0u, 0u};
+      bool ok = true;
+      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+        for (int g = 0; ok && g < NUM_GEMM; ++g) {
+          const int nkc = gemm_k(g) / BK;      // operand chunks; the second pass reuses them
+          for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
+            for (int kc = 0; kc < 2 * nkc; ++kc) {
+              if (nh == 0 && kc < nkc && (kc & 3) == 0) {
+                const int h = kc >> 2;
+                if (!mbar_wait(act_full + h, act_phase[h], abort_flag)) { ok = false; break; }
+                act_phase[h] ^= 1u;
+                tc_fence_after();
+              }
+              if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
+              tc_fence_after();
+              const int ac = kc < nkc ? kc : kc - nkc;
+              const uint32_t a_base = smem_u32(act + ac * CHUNK_BYTES);
+              const uint32_t b_base = smem_u32(wst + stage * STAGE_BYTES);
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k)
+                mma_bf16(tmem + (uint32_t)(nh * BN), sw128_desc(a_base + 32 * k),
+                         sw128_desc(b_base + 32 * k), kIdesc, (kc | k) != 0);
+              mma_commit(empty + stage);
+              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+            }
+            if (ok) mma_commit(acc_full + nh);
+          }
+        }
+      }
+      if (!ok) {
+        *abort_flag = 1;
+        atomicOr(a.err, 2);
+      }
+      mma_commit(drain);
+      const unsigned long long t0 = globaltimer();
+      while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+      }
+    }
+  } else {
+    // --------------------------------------------------------- epilogue
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int grp = ew >> 2;                  // 128-column group inside a half
+    const int part = lane >> 4;               // 0: hi row, 1: lo row
+    const int jr = quad * 16 + (lane & 15);   // query inside the tile
+    const int rhi = quad * 32 + (lane & 15);  // its hi and lo operand rows
+    const int rlo = rhi + 16;
+    const int cq = grp * 128;
+    const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
+    const TCConst* K = a.K;
+    uint32_t acc_phase[2] = {0u, 0u};
+    uint32_t head_phase = 0;
+    bool ok = true;
+    float vmax = 0.f;
+    int tile = blockIdx.x;
+    int j = tile * QPT + jr;
+    bool valid = j < n;
+    float3 p = make_float3(0.f, 0.f, 0.f);
+    int shape = 0;
+    if (valid) rowsrc_load(a.src, j, p, shape);
+
+    // layer 0 of the current rows into operand half h
+    auto layer0 = [&](int h) {
+      const float* bf0 = a.bfold0 + (size_t)shape * 512;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int c = 256 * h + cq + 32 * t + 16 * part;
+        float v[16];
+        layer0_16(K, bf0, c, p, v);
+        uint32_t hi[8], lo[8];
+        relu_split16(v, hi, lo, vmax);
+        store_packed<8>(act, rhi, c, hi);
+        store_packed<8>(act, rlo, c, lo);
+      }
+    };
+    auto wait_acc = [&](int h) -> bool {
+      if (!mbar_wait(acc_full + h, acc_phase[h], abort_flag)) return false;
+      acc_phase[h] ^= 1u;
+      tc_fence_after();
+      return true;
+    };
+    auto release = [&](int h) {
+      tc_fence_before();
+      fence_async_shared();
+      mbar_arrive(act_full + h);
+    };
+    // one 32-column chunk of layer g at column c: v = affine(hi + lo rows)
+    auto chunk = [&](int g, const float* bf4, int c, float (&v)[16]) {
+      uint32_t r[32];
+      tmem_ld32(t_row + (uint32_t)c, r);
+      float m[16];
+      pair_sum16(r, part, m);
+      affine16(K, g, bf4, c + 16 * part, p, a.inv_scale[g], m, v);
+    };
+
+    for (int h = 0; h < 2; ++h) {
+      layer0(h);
+      fence_async_shared();
+      mbar_arrive(act_full + h);
+    }
+    for (; tile < n_tiles; tile += gridDim.x) {
+      const float* bf4 = a.bfold4 + (size_t)shape * 512;
+      const int next = tile + (int)gridDim.x;
+      const bool has_next = next < n_tiles;
+      for (int g = 0; g < NUM_GEMM - 1; ++g) {
+        if (!wait_acc(0)) { ok = false; break; }
+        if (gemm_n(g) == 256) {
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int c = cq + 32 * t;
+            float v[16];
+            chunk(g, bf4, c, v);
+            uint32_t hi[8], lo[8];
+            relu_split16(v, hi, lo, vmax);
+            store_packed<8>(act, rhi, c + 16 * part, hi);
+            store_packed<8>(act, rlo, c + 16 * part, lo);
+          }
+          release(0);
+          continue;
+        }
+        uint32_t held_hi[4][8], held_lo[4][8];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          float v[16];
+          chunk(g, bf4, cq + 32 * t, v);
+          relu_split16(v, held_hi[t], held_lo[t], vmax);
+        }
+        if (!wait_acc(1)) { ok = false; break; }
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int c = cq + 32 * t + 16 * part;
+          store_packed<8>(act, rhi, c, held_hi[t]);
+          store_packed<8>(act, rlo, c, held_lo[t]);
+        }
+        release(0);
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+          const int c = 256 + cq + 32 * t;
+          float v[16];
+          chunk(g, bf4, c, v);
+          uint32_t hi[8], lo[8];
+          relu_split16(v, hi, lo, vmax);
+          store_packed<8>(act, rhi, c + 16 * part, hi);
+          store_packed<8>(act, rlo, c + 16 * part, lo);
+        }
+        release(1);
+      }
+      if (!ok) break;
+      // ---- last layer: head; the operand tile takes the next tile's layer 0
+      const int cur_j = j;
+      const bool cur_valid = valid;
+      const float3 cur_p = p;
+      if (has_next) {
+        j = next * QPT + jr;
+        valid = j < n;
+        p = make_float3(0.f, 0.f, 0.f);
+        shape = 0;
+        if (valid) rowsrc_load(a.src, j, p, shape);
+      }
+      float head = 0.f;
+      auto head_chunk = [&](int c) {
+        uint32_t r[32];
+        tmem_ld32(t_row + (uint32_t)c, r);
+        float m[16], v[16];
+        pair_sum16(r, part, m);
+        affine16(K, NUM_GEMM - 1, bf4, c + 16 * part, cur_p, a.inv_scale[NUM_GEMM - 1], m, v);
+#pragma unroll
+        for (int i = 0; i < 16; i += 4) {
+          const float4 w = ldg4(K->w_head + c + 16 * part + i);
+          head = fmaf(fmaxf(v[i], 0.f), w.x,
+                      fmaf(fmaxf(v[i + 1], 0.f), w.y,
+                           fmaf(fmaxf(v[i + 2], 0.f), w.z, fmaf(fmaxf(v[i + 3], 0.f), w.w, head))));
+        }
+      };
+      if (!wait_acc(0)) { ok = false; break; }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) head_chunk(cq + 32 * t);
+      if (!wait_acc(1)) { ok = false; break; }
+      if (has_next) {
+        layer0(0);
+        release(0);
+      }
+#pragma unroll
+      for (int t = 0; t < 4; ++t) head_chunk(256 + cq + 32 * t);
+      if (has_next) {
+        layer0(1);
+        release(1);
+      } else {
+        tc_fence_before();
+      }
+      head += __shfl_xor_sync(0xffffffffu, head, 16);
+      // group 1 hands its partial sums to group 0 (rewritten only after the
+      // next tile's layers, in which group 0 takes part)
+      if (grp > 0) {
+        head_part[jr] = head;
+        mbar_arrive(head_bar);
+      } else {
+        if (!mbar_wait(head_bar, head_phase, abort_flag)) { ok = false; break; }
+        head += head_part[jr];
+        if (cur_valid && part == 0) a.fout[cur_j] = tanhf(head + __ldg(&K->b_head));
+      }
+      head_phase ^= 1u;
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      atomicOr(a.err, 4);
+    }
+    if (!(vmax <= 65504.f)) atomicOr(a.err, 64);   // an activation overflowed FP16
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    tmem_dealloc(tmem, 512);
+  }
+}
+
+}  // namespace
+
+// Weights of GEMM layers 1..7 as [N rows][2K cols] fp16: columns 0..K-1 hold
+// W_hi, K..2K-1 hold W_lo, both of W * 2^s_l.
+dist_status pack_tcx(dist_decoder* d, const float* const* W) {
+  auto enc = tensor_map_encoder();
+  DIST_CHECK(enc != nullptr, DIST_E_CUDA, "cuTensorMapEncodeTiled entry point not available");
+  const int L = 256, Hh = 253;
+  for (int g = 0; g < NUM_GEMM; ++g) {
+    const int l = g + 1;
+    const int N = gemm_n(g), K = gemm_k(g);
+    const int n_real = (l == 3) ? Hh : 512;
+    const int k_real = (l == 4) ? Hh : 512;
+    const int in_dim = (l == 4) ? Hh + L + 3 : 512;
+    float amax = 0.f;
+    for (int nn = 0; nn < n_real; ++nn)
+      for (int k = 0; k < k_real; ++k) amax = std::fmax(amax, std::fabs(W[l][(size_t)nn * in_dim + k]));
+    // largest power of two with amax * 2^s <= 2^14
+    int s = 0;
+    if (amax > 0.f) s = (int)std::floor(std::log2(16384.0 / (double)amax));
+    s = s < -24 ? -24 : (s > 24 ? 24 : s);
+    const float scale = std::ldexp(1.f, s);
+    d->tc.x_inv_scale[g] = std::ldexp(1.f, -s);
+    std::vector<uint16_t> h((size_t)N * 2 * K, 0);
+    for (int nn = 0; nn < n_real; ++nn)
+      for (int k = 0; k < k_real; ++k) {
+        const float w = W[l][(size_t)nn * in_dim + k] * scale;
+        const __half hi = __float2half_rn(w);
+        const __half lo = __float2half_rn(w - __half2float(hi));
+        h[(size_t)nn * 2 * K + k] = *reinterpret_cast<const uint16_t*>(&hi);
+        h[(size_t)nn * 2 * K + K + k] = *reinterpret_cast<const uint16_t*>(&lo);
+      }
+    void* q = nullptr;
+    DIST_CUDA_TRY(cudaMalloc(&q, h.size() * sizeof(uint16_t)));
+    d->allocations.push_back(q);
+    DIST_CUDA_TRY(cudaMemcpy(q, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * K), (cuuint64_t)N};
+    cuuint64_t strides[1] = {(cuuint64_t)(2 * K) * sizeof(uint16_t)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BN};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&d->tc.xmaps.m[g], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, q, dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (split weights)");
+  }
+  return DIST_OK;
+}
+
+cudaError_t mlp_tcx_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
+                            const float* bfolds, float* fout, cudaStream_t st) {
+  if (!dec->tc.ok) return cudaErrorNotSupported;
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(mlp_tcx_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  TCXArgs a;
+  a.K = dec->tc.cst;
+  a.bfold0 = bfold0;
+  a.bfold4 = bfolds;
+  a.src = src;
+  a.fout = fout;
+  a.err = dec->tc.err;
+  for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
+  mlp_tcx_kernel<<<num_sms(), THREADS, SMEM_BYTES, st>>>(dec->tc.xmaps, a);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+}  // namespace dist

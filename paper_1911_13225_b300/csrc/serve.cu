@@ -215,7 +215,10 @@ struct dist_server {
     }
     src.count = cnt + 2 * par + 1;
     src.idx = act[par][1];
-    DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, fbuf[1], st, is_tc(p.precision)));
+    if (fp32_on_tc(p))
+      DIST_CUDA_TRY(mlp_tcx_forward(dec, src, b0, bs, fbuf[1], st));
+    else
+      DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, fbuf[1], st, is_tc(p.precision)));
     DIST_CUDA_TRY(cudaMemsetAsync(cnt + 2 * (par ^ 1), 0, 2 * sizeof(int), st));
     int* in[2] = {act[par][0], act[par][1]};
     const float* f[2] = {fbuf[0], fbuf[1]};
@@ -367,10 +370,11 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
   DIST_CHECK(p->max_steps >= 1 && p->k_min >= 1 && p->k_min <= kMaxK && p->eps > 0.f &&
                  p->alpha > 0.f && p->radius > 0.f,
              DIST_E_INVALID, "dist_serve_create: bad trace parameters");
-  DIST_CHECK(p->precision == DIST_PREC_FP32 || is_tc(p->precision), DIST_E_INVALID,
-             "dist_serve_create: bad precision");
-  DIST_CHECK(!is_tc(p->precision) || dec->tc.ok, DIST_E_UNSUPPORTED,
-             "BF16 tensor-core MLP covers only the DeepSDF decoder shape");
+  DIST_CHECK(valid_precision(p->precision), DIST_E_INVALID, "dist_serve_create: bad precision");
+  DIST_CHECK(p->refine_engine == DIST_REFINE_TC || p->refine_engine == DIST_REFINE_SIMT,
+             DIST_E_INVALID, "dist_serve_create: bad refine_engine");
+  DIST_CHECK(!(is_tc(p->precision) || fp32_on_tc(*p)) || dec->tc.ok, DIST_E_UNSUPPORTED,
+             "the tensor-core decoder covers only the DeepSDF shape");
   dist_server* S = new dist_server();
   S->dec = dec;
   S->p = *p;

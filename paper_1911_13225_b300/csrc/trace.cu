@@ -599,13 +599,14 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
   DIST_CHECK(p->k_min >= 1 && p->k_min <= kMaxK, DIST_E_INVALID, "k_min must be 1..3");
   DIST_CHECK(p->eps > 0.f && p->alpha > 0.f && p->radius > 0.f && p->normal_delta >= 0.f,
              DIST_E_INVALID, "eps, alpha, radius must be > 0 and normal_delta >= 0");
-  DIST_CHECK(p->precision == DIST_PREC_FP32 || is_tc(p->precision), DIST_E_INVALID,
-             "bad precision");
+  DIST_CHECK(valid_precision(p->precision), DIST_E_INVALID, "bad precision");
   DIST_CHECK(p->refine_steps >= 0, DIST_E_INVALID, "refine_steps must be >= 0");
+  DIST_CHECK(p->refine_engine == DIST_REFINE_TC || p->refine_engine == DIST_REFINE_SIMT,
+             DIST_E_INVALID, "bad refine_engine");
   DIST_CHECK(p->grad_mode == DIST_GRAD_EXACT || p->grad_mode == DIST_GRAD_PAPER, DIST_E_INVALID,
              "bad grad_mode");
-  DIST_CHECK(!is_tc(p->precision) || dec->tc.ok, DIST_E_UNSUPPORTED,
-             "BF16 tensor-core MLP covers only the DeepSDF decoder shape (512 x 8, skip 4, latent 256)");
+  DIST_CHECK(!(is_tc(p->precision) || fp32_on_tc(*p)) || dec->tc.ok, DIST_E_UNSUPPORTED,
+             "the tensor-core decoder covers only the DeepSDF shape (512 x 8, skip 4, latent 256)");
   DIST_CHECK(o->depth && o->sil && o->mask && o->steps && o->d_hit && o->d_min && o->f_min,
              DIST_E_INVALID, "dist_trace_out: NULL required buffer");
   long long n_pix = 0;
@@ -881,7 +882,10 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
     src.count = cB + t;
     src.idx = ws->act[par][1];
     prof_mlp_begin(st, 1);
-    DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->fbuf[1], st, tc && t > 0));
+    if (fp32_on_tc(*p))
+      DIST_CUDA_TRY(mlp_tcx_forward(dec, src, b0, bs, ws->fbuf[1], st));
+    else
+      DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->fbuf[1], st, tc && t > 0));
     prof_mlp_end(st);
     StepLists L;
     L.cnt_in[0] = zero; L.cnt_in[1] = cB + t;
@@ -981,9 +985,9 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
   DIST_CHECK(n >= 1 && n <= ws->max_rays * kProbesPerRay, DIST_E_INVALID,
              "dist_sdf_eval: n must be 1..10 * workspace max_rays");
   DIST_CHECK(n_shapes >= 1 && n_shapes <= kMaxShapes, DIST_E_INVALID, "n_shapes out of range");
-  DIST_CHECK(precision == DIST_PREC_FP32 || (is_tc(precision) && !grad),
-             DIST_E_INVALID, "dist_sdf_eval: bad precision (BF16/FP16 have no gradient)");
-  DIST_CHECK(!is_tc(precision) || dec->tc.ok, DIST_E_UNSUPPORTED,
+  DIST_CHECK(precision == DIST_PREC_FP32 || (valid_precision(precision) && !grad),
+             DIST_E_INVALID, "dist_sdf_eval: bad precision (tensor-core kernels have no gradient)");
+  DIST_CHECK(precision == DIST_PREC_FP32 || dec->tc.ok, DIST_E_UNSUPPORTED,
              "BF16 tensor-core MLP covers only the DeepSDF decoder shape");
   cudaStream_t st = (cudaStream_t)stream;
   const DecoderF32& d = dec->f32;
@@ -1000,6 +1004,8 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
   src.pts = ws->probe_p;
   if (is_tc(precision)) {
     DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, f, st, precision == DIST_PREC_FP16));
+  } else if (precision == DIST_PREC_FP32_TC) {
+    DIST_CUDA_TRY(mlp_tcx_forward(dec, src, b0, bs, f, st));
   } else if (!grad) {
     DIST_CUDA_TRY(mlp_fp32_forward(d, src, b0, bs, f, st));
   } else {

@@ -45,6 +45,35 @@ def test_tensor_core_decoder(cuda_device, n, precision):
     assert np.max(d_or) < 5e-3 * scale and np.mean(d_or) < 1e-3 * scale
 
 
+@pytest.mark.parametrize("n", [1, 63, 64 * 5 + 7, 148 * 64 + 33, 148 * 64 * 3 + 5])
+def test_fp32_class_tensor_core_decoder(cuda_device, n):
+    """Two-term FP16 split on the tensor cores (precision FP32_TC).  The split
+    arithmetic is FP32-accurate; the tensor core's FP32 accumulation, which
+    does not round to nearest, leaves ~2e-6 (measured on B300).  Bound: the
+    FP32 SIMT kernel's bound against the FP64 oracle, 5e-6, at every point,
+    and at least 10x closer to the oracle than the FP16 kernel."""
+    from paper_1911_13225_b300 import api
+    spec = synth.DEEPSDF_SPEC
+    Ws, bs, Z = workload(spec, seed=4, n_shapes=3)
+    dec = gpu_decoder(spec, Ws, bs)
+    ws = api.Workspace(max(n, 1024))
+    rng = np.random.default_rng(n + 1)
+    pts = rng.uniform(-1, 1, (n, 3)).astype(np.float32)
+    shp = rng.integers(0, 3, n).astype(np.int32)
+    zt = torch.from_numpy(Z).to(cuda_device)
+    pt, st = torch.from_numpy(pts).to(cuda_device), torch.from_numpy(shp).to(cuda_device)
+    f_tc = to_np(api.sdf_eval(dec, zt, pt, st, ws, precision="fp32_tc")).astype(np.float64)
+    f_32 = to_np(api.sdf_eval(dec, zt, pt, st, ws, precision="fp32")).astype(np.float64)
+    f_16 = to_np(api.sdf_eval(dec, zt, pt, st, ws, precision="fp16")).astype(np.float64)
+    assert dec.device_error() == 0
+    fo = oracle_sdf(spec, Ws, bs, Z)(pts.astype(np.float64), shp)
+    e_tc, e_16 = np.abs(f_tc - fo), np.abs(f_16 - fo)
+    assert np.max(e_tc) < 5e-6
+    assert np.max(np.abs(f_tc - f_32)) < 5e-6
+    if n >= 64:
+        assert np.median(e_tc) * 10 < np.median(e_16)
+
+
 @pytest.mark.parametrize("spec,tol_f,tol_g", [(synth.SMALL_SPEC, 2e-6, 1e-5),
                                               (synth.DEEPSDF_SPEC, 5e-6, 2e-5)])
 @pytest.mark.parametrize("n", [1, 63, 64 * 5 + 7, 4099])

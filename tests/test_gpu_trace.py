@@ -19,13 +19,14 @@ DEPTH_TOL = 1e-5
 
 
 def _run(cuda_device, spec, cams, n_shapes=1, alpha=1.5, max_steps=50, k_min=1, seed=0,
-         normals=False, delta=0.0):
+         normals=False, delta=0.0, precision="fp32"):
     from paper_1911_13225_b300 import api
     Ws, bs, Z = workload(spec, seed=seed, n_shapes=n_shapes)
     dec = gpu_decoder(spec, Ws, bs)
     n = api.n_pixels(cams)
     ws = api.Workspace(n, max_steps)
-    params = api.TraceParams(max_steps=max_steps, alpha=alpha, k_min=k_min, normal_delta=delta)
+    params = api.TraceParams(max_steps=max_steps, alpha=alpha, k_min=k_min, normal_delta=delta,
+                             precision=precision)
     res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), cams, params, ws, normals=normals)
     torch.cuda.synchronize()
     sdf = oracle_sdf(spec, Ws, bs, Z)
@@ -34,19 +35,25 @@ def _run(cuda_device, spec, cams, n_shapes=1, alpha=1.5, max_steps=50, k_min=1, 
     return res, orc, sdf
 
 
-def _compare(res, orc, max_steps, tol_f):
-    amb = ambiguous_rays(orc, tol_f=tol_f, max_steps=max_steps, normals=orc["normal"])
+def _compare(res, orc, max_steps, tol_f, tol_d=1e-5, depth_tol=DEPTH_TOL, min_ok=0.9,
+             step_slack=0):
+    amb = ambiguous_rays(orc, tol_f=tol_f, tol_d=tol_d, max_steps=max_steps,
+                         normals=orc["normal"])
     ok = ~amb
-    assert ok.mean() > 0.9, f"too many ambiguous rays: {amb.mean():.3f}"
+    assert ok.mean() > min_ok, f"too many ambiguous rays: {amb.mean():.3f}"
     mask = to_np(res.mask).astype(bool)
     assert np.array_equal(mask[ok], orc["mask"][ok])
-    assert np.array_equal(to_np(res.steps)[ok], orc["steps"][ok])
+    if step_slack == 0:
+        assert np.array_equal(to_np(res.steps)[ok], orc["steps"][ok])
+    else:
+        ds = np.abs(to_np(res.steps)[ok].astype(np.int64) - orc["steps"][ok])
+        assert np.max(ds) <= step_slack and np.mean(ds > 0) < 0.01
     assert np.array_equal(to_np(res.status)[ok], orc["status"][ok])
     hit = ok & orc["mask"]
     assert hit.sum() > 0
-    assert np.max(np.abs(to_np(res.depth)[hit] - orc["depth"][hit])) < DEPTH_TOL
+    assert np.max(np.abs(to_np(res.depth)[hit] - orc["depth"][hit])) < depth_tol
     assert np.all(np.isinf(to_np(res.depth)[ok & ~orc["mask"]]))
-    assert np.max(np.abs(to_np(res.sil)[ok] - orc["sil"][ok])) < DEPTH_TOL
+    assert np.max(np.abs(to_np(res.sil)[ok] - orc["sil"][ok])) < depth_tol
     # invariant on every ray: S < 0 <=> hit
     assert np.array_equal(to_np(res.sil) < 0, mask)
     return ok
@@ -63,6 +70,25 @@ def test_deepsdf_decoder_ragged_tiles(cuda_device):
     cam = synth.look_at_camera(synth.random_viewpoints(1, seed=3)[0], 45, 37)
     res, orc, _ = _run(cuda_device, synth.DEEPSDF_SPEC, [cam])
     _compare(res, orc, 50, tol_f=1e-5)
+
+
+# FP32-class tensor-core queries (two-term FP16 split): f within ~2e-6 of the
+# FP64 decoder (the tensor core's FP32 accumulation truncates), so over ~20
+# steps of 1.5 f the sample positions drift by up to ~6e-5 from the oracle's;
+# the exit and convergence margins and the depth bar are set from that
+# (depth 1e-4 = 2 eps), not from the FP32 CUDA-core bar.  A drifted sample
+# can meet |f| < eps one step earlier or later than the oracle's: step counts
+# may differ by one on at most 1% of the rays.
+FP32TC = dict(tol_f=2e-5, tol_d=6e-5, depth_tol=1e-4, min_ok=0.75, step_slack=1)
+
+
+@pytest.mark.parametrize("alpha", [1.5, 1.0])
+def test_deepsdf_fp32_tc_trace(cuda_device, alpha):
+    vps = synth.random_viewpoints(2, seed=11)
+    cams = [synth.look_at_camera(vps[0], 64, 64), synth.look_at_camera(vps[1], 33, 50),
+            synth.look_at_camera(synth.random_viewpoints(1, seed=3)[0], 45, 37)]
+    res, orc, _ = _run(cuda_device, synth.DEEPSDF_SPEC, cams, alpha=alpha, precision="fp32_tc")
+    _compare(res, orc, 50, **FP32TC)
 
 
 def test_multi_camera_multi_shape_topk(cuda_device):
@@ -95,14 +121,15 @@ def test_normals_at_gpu_hits(cuda_device, delta):
     assert np.all(to_np(res.normal)[~m] == 0)
 
 
-@pytest.mark.parametrize("precision,eps_lo,refine,alpha_r", [
-    ("bf16", 1e-3, 0, 0.0), ("fp16", 1e-3, 0, 0.0), ("fp16", 1e-4, 1, 0.0), ("fp16", 2e-4, 1, 0.0),
-    ("bf16", 1e-3, 0, 1.0), ("bf16", 3e-4, 0, 1.0), ("fp16", 1e-4, 1, 1.0)])
+@pytest.mark.parametrize("precision,eps_lo,refine,alpha_r,engine", [
+    ("bf16", 1e-3, 0, 0.0, "tc"), ("fp16", 1e-3, 0, 0.0, "tc"), ("fp16", 1e-4, 1, 0.0, "tc"),
+    ("fp16", 2e-4, 1, 0.0, "tc"), ("bf16", 1e-3, 0, 1.0, "tc"), ("bf16", 3e-4, 0, 1.0, "tc"),
+    ("fp16", 1e-4, 1, 1.0, "tc"), ("bf16", 1e-3, 0, 0.0, "simt"), ("fp16", 1e-4, 1, 0.0, "simt")])
 @pytest.mark.parametrize("size,vp_seed", [(64, 3), (96, 8)])
 def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precision, eps_lo, refine,
-                                            alpha_r):
+                                            alpha_r, engine):
     """Tensor-core marching (BF16 or FP16 operands) until |f| < eps_lo, then
-    FP32 queries: converge to eps = 5e-5 (refine = 0) or accept after
+    FP32-class queries (tensor-core split or CUDA-core FP32): converge to eps = 5e-5 (refine = 0) or accept after
     `refine` FP32 queries within 4 eps_lo (unit final step).  Depth within
     2e-3 of the FP64 oracle on hits away from the silhouette; masks agree
     except near-silhouette rays."""
@@ -113,7 +140,7 @@ def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precisio
     cam = synth.look_at_camera(synth.random_viewpoints(1, seed=vp_seed)[0], size, size)
     ws = api.Workspace(size * size, 50)
     params = api.TraceParams(precision=precision, eps_bf16=eps_lo, refine_steps=refine,
-                             alpha_refine=alpha_r)
+                             alpha_refine=alpha_r, refine_engine=engine)
     res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), [cam], params, ws)
     assert dec.device_error() == 0
     orc = tracer.render(oracle_sdf(spec, Ws, bs, Z), [cam], record=True)
