@@ -34,38 +34,22 @@ struct TCArgs {
   int* err;
 };
 
-// Epilogue split: EPQ warps share a TMEM lane quadrant; inside each 256-column
-// half of the accumulator a thread owns CPT consecutive columns.
-constexpr int EPQ = NUM_EPI / 4;
-constexpr int CPT = 256 / EPQ;
-
-// Layer 0 for this thread's CPT columns of half h, written as operand.
-template <bool F16>
-__device__ __forceinline__ void layer0_store(const TCConst* K, const float* bf, int c0,
-                                             const float3& p, uint8_t* act, int row) {
-#pragma unroll
-  for (int cc = 0; cc < CPT; cc += 32) {
-    float v[32];
-    layer0_32(K, bf, c0 + cc, p, v);
-    store_act32<F16>(act, row, c0 + cc, v);
-  }
-}
-
 // Forward pipeline.  The accumulator of a 512-wide layer completes in two
 // 256-column halves (acc_full[0], acc_full[1]); the next layer's operand is
-// handed back in two 256-column K halves (act_full[0], act_full[1]).
-//   epilogue: after acc_full[0] it reads half 0 into registers while the
-//     tensor core computes half 1; once acc_full[1] says the layer's MMAs
-//     (which read the operand tile) are done, it writes half 0 of the new
-//     operand, releases act_full[0], then reads, converts and writes half 1
-//     and releases act_full[1].
-//   MMA: the next layer's first output half starts on K half 0 as soon as
-//     act_full[0] arrives, overlapping the epilogue's second half; act_full[1]
-//     also certifies that TMEM columns 256..511 have been read.
+// handed back in four 128-column K quarters (act_full[0..3]).
+//   epilogue (16 warps, four per TMEM lane quadrant, one 32-column chunk of
+//     each quarter per warp): after acc_full[0] it reads quarters 0 and 1
+//     into registers while the tensor core computes half 1; once
+//     acc_full[1] says the layer's MMAs (which read the operand tile) are
+//     done it writes them and releases act_full[0] and [1], then reads,
+//     converts and writes quarter 2, releases it, and quarter 3.
+//   MMA: the next layer's first output half starts on K quarter 0 as soon as
+//     act_full[0] arrives, so it overlaps the epilogue's second half;
+//     act_full[3] also certifies that TMEM columns 256..511 have been read.
 // On the last layer the released operand tile takes the next tile's layer 0,
 // so the next tile's GEMMs overlap this tile's head.
 template <bool F16>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(FWD_THREADS, 1)
 mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
   constexpr uint32_t kIdesc = instr_desc<F16>();
   extern __shared__ uint8_t smem_raw[];
@@ -77,10 +61,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
   uint64_t* full = bars;                       // [STAGES]
   uint64_t* empty = bars + STAGES;             // [STAGES]
   uint64_t* acc_full = bars + 2 * STAGES;      // [2] MMA -> epilogue, per N half
-  uint64_t* act_full = bars + 2 * STAGES + 2;  // [2] epilogue -> MMA, per K half
-  uint64_t* drain = bars + 2 * STAGES + 4;     // final MMA completion
-  uint64_t* head_bar = bars + 2 * STAGES + 5;  // head partial sums -> column group 0
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  uint64_t* act_full = bars + 2 * STAGES + 2;  // [4] epilogue -> MMA, per K quarter
+  uint64_t* drain = bars + 2 * STAGES + 6;     // final MMA completion
+  uint64_t* head_bar = bars + 2 * STAGES + 7;  // head partial sums -> column group 0
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* head_part = reinterpret_cast<float*>(smem + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES);
 
@@ -95,12 +79,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
-    for (int h = 0; h < 2; ++h) {
-      mbar_init(acc_full + h, 1);
-      mbar_init(act_full + h, NUM_EPI * 32);
-    }
+    for (int h = 0; h < 2; ++h) mbar_init(acc_full + h, 1);
+    for (int q = 0; q < 4; ++q) mbar_init(act_full + q, FWD_EPI * 32);
     mbar_init(drain, 1);
-    mbar_init(head_bar, (NUM_EPI - 4) * 32);
+    mbar_init(head_bar, (FWD_EPI - 4) * 32);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -150,16 +132,16 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t act_phase[2] = {0u, 0u};
+      uint32_t act_phase[4] = {0u, 0u, 0u, 0u};
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
             for (int kc = 0; kc < gemm_k(g) / BK; ++kc) {
-              if (nh == 0 && (kc & 3) == 0) {
-                const int h = kc >> 2;
-                if (!mbar_wait(act_full + h, act_phase[h], abort_flag)) { ok = false; break; }
-                act_phase[h] ^= 1u;
+              if (nh == 0 && (kc & 1) == 0) {
+                const int q = kc >> 1;
+                if (!mbar_wait(act_full + q, act_phase[q], abort_flag)) { ok = false; break; }
+                act_phase[q] ^= 1u;
                 tc_fence_after();
               }
               if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
@@ -189,11 +171,11 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
     }
   } else {
     // --------------------------------------------------------- epilogue
-    const int ew = warp - 2;                  // 0..NUM_EPI-1
+    const int ew = warp - 2;                  // 0..FWD_EPI-1
     const int quad = warp & 3;                // TMEM lane quadrant of this warp
-    const int grp = ew >> 2;                  // column group inside a half
+    const int grp = ew >> 2;                  // chunk inside each quarter
     const int row = quad * 32 + lane;         // tile row == TMEM lane
-    const int cq = grp * CPT;                 // first column inside a half
+    const int cg = grp * 32;                  // column of this warp inside a quarter
     const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
     const TCConst* K = a.K;
     uint32_t acc_phase[2] = {0u, 0u};
@@ -205,75 +187,77 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
     float3 p = make_float3(0.f, 0.f, 0.f);
     int shape = 0;
     if (valid) rowsrc_load(a.src, j, p, shape);
-    for (int h = 0; h < 2; ++h) {
-      layer0_store<F16>(K, a.bfold0 + (size_t)shape * 512, 256 * h + cq, p, act, row);
-      fence_async_shared();
-      mbar_arrive(act_full + h);
-    }
     auto wait_acc = [&](int h) -> bool {
       if (!mbar_wait(acc_full + h, acc_phase[h], abort_flag)) return false;
       acc_phase[h] ^= 1u;
       tc_fence_after();
       return true;
     };
-    auto release = [&](int h) {
+    auto release = [&](int q) {
       tc_fence_before();
       fence_async_shared();
-      mbar_arrive(act_full + h);
+      mbar_arrive(act_full + q);
     };
+    auto layer0 = [&](int q) {
+      float v[32];
+      layer0_32(K, a.bfold0 + (size_t)shape * 512, 128 * q + cg, p, v);
+      store_act32<F16>(act, row, 128 * q + cg, v);
+    };
+    for (int q = 0; q < 4; ++q) {
+      layer0(q);
+      release(q);
+    }
     for (; tile < n_tiles; tile += gridDim.x) {
       const float* bf4 = a.bfold4 + (size_t)shape * 512;
       const int next = tile + (int)gridDim.x;
       const bool has_next = next < n_tiles;
-      float head = 0.f;
+      // chunk of quarter q of layer g: v = relu(acc + bias)
+      auto chunk = [&](int g, int q, float (&v)[32]) {
+        uint32_t r[32];
+        tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
+        bias32(K, g, bf4, 128 * q + cg, p, r, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+      };
       for (int g = 0; g < NUM_GEMM - 1; ++g) {
         if (!wait_acc(0)) { ok = false; break; }
         if (gemm_n(g) == 256) {
           // one output half: the layer's MMAs are done, write directly
-#pragma unroll
-          for (int cc = 0; cc < CPT; cc += 32) {
-            uint32_t r[32];
-            tmem_ld32(t_row + (uint32_t)(cq + cc), r);
+          for (int q = 0; q < 2; ++q) {
             float v[32];
-            bias32(K, g, bf4, cq + cc, p, r, v);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
-            store_act32<F16>(act, row, cq + cc, v);
+            chunk(g, q, v);
+            store_act32<F16>(act, row, 128 * q + cg, v);
+            release(q);
           }
-          release(0);
           continue;
         }
-        uint32_t held[CPT / 2];
+        uint32_t held[2][16];
 #pragma unroll
-        for (int cc = 0; cc < CPT; cc += 16) {
-          uint32_t r[16];
-          tmem_ld16(t_row + (uint32_t)(cq + cc), r);
-          float v[16];
-          bias16(K, g, bf4, cq + cc, p, r, v);
+        for (int q = 0; q < 2; ++q) {
+          float v[32];
+          chunk(g, q, v);
 #pragma unroll
-          for (int i = 0; i < 8; ++i)
-            held[cc / 2 + i] = pack16<F16>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+          for (int i = 0; i < 16; ++i) held[q][i] = pack16<F16>(v[2 * i], v[2 * i + 1]);
         }
         if (!wait_acc(1)) { ok = false; break; }
-        store_packed<CPT / 2>(act, row, cq, held);
-        release(0);
 #pragma unroll
-        for (int cc = 0; cc < CPT; cc += 32) {
-          uint32_t r[32];
-          tmem_ld32(t_row + (uint32_t)(256 + cq + cc), r);
-          float v[32];
-          bias32(K, g, bf4, 256 + cq + cc, p, r, v);
-#pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
-          store_act32<F16>(act, row, 256 + cq + cc, v);
+        for (int q = 0; q < 2; ++q) {
+          store_packed<16>(act, row, 128 * q + cg, held[q]);
+          release(q);
         }
-        release(1);
+        for (int q = 2; q < 4; ++q) {
+          float v[32];
+          chunk(g, q, v);
+          store_act32<F16>(act, row, 128 * q + cg, v);
+          release(q);
+        }
       }
       if (!ok) break;
       // ---- last layer: head partial sums; the operand tile takes the next
       // tile's layer 0 once this layer's MMAs are done
       const int cur_j = j;
       const bool cur_valid = valid;
+      const float3 cur_p = p;
       if (has_next) {
         j = next * BM + row;
         valid = j < n;
@@ -281,49 +265,44 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
         shape = 0;
         if (valid) rowsrc_load(a.src, j, p, shape);
       }
+      float head = 0.f;
+      auto head_chunk = [&](int q) {
+        uint32_t r[32];
+        tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
+        float v[32];
+        bias32(K, NUM_GEMM - 1, bf4, 128 * q + cg, cur_p, r, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+        head = head32(K, 128 * q + cg, v, head);
+      };
       if (!wait_acc(0)) { ok = false; break; }
-#pragma unroll
-      for (int cc = 0; cc < CPT; cc += 32) {
-        uint32_t r[32];
-        tmem_ld32(t_row + (uint32_t)(cq + cc), r);
-        float v[32];
-        bias32(K, NUM_GEMM - 1, bf4, cq + cc, p, r, v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
-        head = head32(K, cq + cc, v, head);
-      }
+      head_chunk(0);
+      head_chunk(1);
       if (!wait_acc(1)) { ok = false; break; }
-      const float* bf0 = a.bfold0 + (size_t)shape * 512;
       if (has_next) {
-        layer0_store<F16>(K, bf0, cq, p, act, row);
+        layer0(0);
         release(0);
-      }
-#pragma unroll
-      for (int cc = 0; cc < CPT; cc += 32) {
-        uint32_t r[32];
-        tmem_ld32(t_row + (uint32_t)(256 + cq + cc), r);
-        float v[32];
-        bias32(K, NUM_GEMM - 1, bf4, 256 + cq + cc, p, r, v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
-        head = head32(K, 256 + cq + cc, v, head);
-      }
-      if (has_next) {
-        layer0_store<F16>(K, bf0, 256 + cq, p, act, row);
+        layer0(1);
         release(1);
-      } else {
-        tc_fence_before();
       }
-      // head: f = tanh(w . h7 + b); column groups 1.. hand their partial sums
-      // to group 0 (head_part is rewritten only after the next tile's layers,
-      // which group 0 takes part in, so one barrier phase per tile suffices)
+      for (int q = 2; q < 4; ++q) {
+        head_chunk(q);
+        if (has_next) {
+          layer0(q);
+          release(q);
+        }
+      }
+      if (!has_next) tc_fence_before();
+      // head: f = tanh(w . h7 + b); column groups 1..3 hand their partial
+      // sums to group 0 (head_part is rewritten only after the next tile's
+      // layers, which group 0 takes part in, so one phase per tile suffices)
       if (grp > 0) {
         head_part[(grp - 1) * BM + row] = head;
         mbar_arrive(head_bar);
       } else {
         if (!mbar_wait(head_bar, head_phase, abort_flag)) { ok = false; break; }
 #pragma unroll
-        for (int q = 0; q < EPQ - 1; ++q) head += head_part[q * BM + row];
+        for (int q = 0; q < FWD_GRPS - 1; ++q) head += head_part[q * BM + row];
         if (cur_valid) a.fout[cur_j] = tanhf(head + __ldg(&K->b_head));
       }
       head_phase ^= 1u;
@@ -856,10 +835,11 @@ cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const flo
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         FWD_SMEM_BYTES);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mlp_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               SMEM_BYTES);
+                               FWD_SMEM_BYTES);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -871,9 +851,9 @@ cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const flo
   a.fout = fout;
   a.err = dec->tc.err;
   if (f16)
-    mlp_tc_kernel<true><<<num_sms(), THREADS, SMEM_BYTES, st>>>(dec->tc.maps16, a);
+    mlp_tc_kernel<true><<<num_sms(), FWD_THREADS, FWD_SMEM_BYTES, st>>>(dec->tc.maps16, a);
   else
-    mlp_tc_kernel<false><<<num_sms(), THREADS, SMEM_BYTES, st>>>(dec->tc.maps, a);
+    mlp_tc_kernel<false><<<num_sms(), FWD_THREADS, FWD_SMEM_BYTES, st>>>(dec->tc.maps, a);
   count_launch(1);
   return cudaGetLastError();
 }

@@ -25,9 +25,9 @@
 // which leaves a systematic error of a few 1e-6 in f.  The small W_lo pass
 // runs first so that only the W_hi pass adds into a large accumulator.
 //
-// Pipeline (warp roles, 3-stage weight ring, split accumulator halves and
-// operand halves, bounded waits) is that of mlp_tc.cu; the work per query is
-// four times a BF16 query (two rows, two K passes).
+// Pipeline (warp roles, 3-stage weight ring, accumulator halves, operand
+// quarters, 16 epilogue warps, bounded waits) is that of mlp_tc.cu; the work
+// per query is four times a BF16 query (two rows, two K passes).
 #include <cmath>
 #include <vector>
 
@@ -123,7 +123,7 @@ __device__ __forceinline__ void pair_sum16(const uint32_t (&r)[32], int part, fl
   }
 }
 
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(FWD_THREADS, 1)
 mlp_tcx_kernel(const __grid_constant__ TCMaps maps, const TCXArgs a) {
   constexpr uint32_t kIdesc = instr_desc<true>();
   extern __shared__ uint8_t smem_raw[];
@@ -135,10 +135,10 @@ mlp_tcx_kernel(const __grid_constant__ TCMaps maps, const TCXArgs a) {
   uint64_t* full = bars;                       // [STAGES]
   uint64_t* empty = bars + STAGES;             // [STAGES]
   uint64_t* acc_full = bars + 2 * STAGES;      // [2] MMA -> epilogue, per N half
-  uint64_t* act_full = bars + 2 * STAGES + 2;  // [2] epilogue -> MMA, per K half
-  uint64_t* drain = bars + 2 * STAGES + 4;
-  uint64_t* head_bar = bars + 2 * STAGES + 5;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  uint64_t* act_full = bars + 2 * STAGES + 2;  // [4] epilogue -> MMA, per K quarter
+  uint64_t* drain = bars + 2 * STAGES + 6;
+  uint64_t* head_bar = bars + 2 * STAGES + 7;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* head_part = reinterpret_cast<float*>(smem + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES);
 
@@ -153,12 +153,10 @@ mlp_tcx_kernel(const __grid_constant__ TCMaps maps, const TCXArgs a) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
-    for (int h = 0; h < 2; ++h) {
-      mbar_init(acc_full + h, 1);
-      mbar_init(act_full + h, NUM_EPI * 32);
-    }
+    for (int h = 0; h < 2; ++h) mbar_init(acc_full + h, 1);
+    for (int q = 0; q < 4; ++q) mbar_init(act_full + q, FWD_EPI * 32);
     mbar_init(drain, 1);
-    mbar_init(head_bar, (NUM_EPI - 4) * 32);
+    mbar_init(head_bar, (FWD_EPI - 4) * 32);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -210,17 +208,17 @@ mlp_tcx_kernel(const __grid_constant__ TCMaps maps, const TCXArgs a) {
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t act_phase[2] = {0u, 0u};
+      uint32_t act_phase[4] = {0u, 0u, 0u, 0u};
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
           const int nkc = gemm_k(g) / BK;      // operand chunks; the second pass reuses them
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
             for (int kc = 0; kc < 2 * nkc; ++kc) {
-              if (nh == 0 && kc < nkc && (kc & 3) == 0) {
-                const int h = kc >> 2;
-                if (!mbar_wait(act_full + h, act_phase[h], abort_flag)) { ok = false; break; }
-                act_phase[h] ^= 1u;
+              if (nh == 0 && kc < nkc && (kc & 1) == 0) {
+                const int q = kc >> 1;
+                if (!mbar_wait(act_full + q, act_phase[q], abort_flag)) { ok = false; break; }
+                act_phase[q] ^= 1u;
                 tc_fence_after();
               }
               if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
@@ -252,12 +250,12 @@ mlp_tcx_kernel(const __grid_constant__ TCMaps maps, const TCXArgs a) {
     // --------------------------------------------------------- epilogue
     const int ew = warp - 2;
     const int quad = warp & 3;
-    const int grp = ew >> 2;                  // 128-column group inside a half
+    const int grp = ew >> 2;                  // 32-column chunk inside each quarter
     const int part = lane >> 4;               // 0: hi row, 1: lo row
     const int jr = quad * 16 + (lane & 15);   // query inside the tile
     const int rhi = quad * 32 + (lane & 15);  // its hi and lo operand rows
     const int rlo = rhi + 16;
-    const int cq = grp * 128;
+    const int cg = grp * 32;
     const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
     const TCConst* K = a.K;
     uint32_t acc_phase[2] = {0u, 0u};
@@ -271,44 +269,42 @@ mlp_tcx_kernel(const __grid_constant__ TCMaps maps, const TCXArgs a) {
     int shape = 0;
     if (valid) rowsrc_load(a.src, j, p, shape);
 
-    // layer 0 of the current rows into operand half h
-    auto layer0 = [&](int h) {
-      const float* bf0 = a.bfold0 + (size_t)shape * 512;
-#pragma unroll
-      for (int t = 0; t < 4; ++t) {
-        const int c = 256 * h + cq + 32 * t + 16 * part;
-        float v[16];
-        layer0_16(K, bf0, c, p, v);
-        uint32_t hi[8], lo[8];
-        relu_split16(v, hi, lo, vmax);
-        store_packed<8>(act, rhi, c, hi);
-        store_packed<8>(act, rlo, c, lo);
-      }
-    };
     auto wait_acc = [&](int h) -> bool {
       if (!mbar_wait(acc_full + h, acc_phase[h], abort_flag)) return false;
       acc_phase[h] ^= 1u;
       tc_fence_after();
       return true;
     };
-    auto release = [&](int h) {
+    auto release = [&](int q) {
       tc_fence_before();
       fence_async_shared();
-      mbar_arrive(act_full + h);
+      mbar_arrive(act_full + q);
     };
-    // one 32-column chunk of layer g at column c: v = affine(hi + lo rows)
-    auto chunk = [&](int g, const float* bf4, int c, float (&v)[16]) {
+    auto store_split = [&](int c, const uint32_t (&hi)[8], const uint32_t (&lo)[8]) {
+      store_packed<8>(act, rhi, c, hi);
+      store_packed<8>(act, rlo, c, lo);
+    };
+    // layer 0 of the current rows, quarter q (this lane's 16 columns)
+    auto layer0 = [&](int q) {
+      const int c = 128 * q + cg + 16 * part;
+      float v[16];
+      layer0_16(K, a.bfold0 + (size_t)shape * 512, c, p, v);
+      uint32_t hi[8], lo[8];
+      relu_split16(v, hi, lo, vmax);
+      store_split(c, hi, lo);
+    };
+    // quarter q of GEMM layer g: v = affine(hi row + lo row), this lane's 16 columns
+    auto chunk = [&](int g, const float* bf4, const float3& pp, int q, float (&v)[16]) {
       uint32_t r[32];
-      tmem_ld32(t_row + (uint32_t)c, r);
+      tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
       float m[16];
       pair_sum16(r, part, m);
-      affine16(K, g, bf4, c + 16 * part, p, a.inv_scale[g], m, v);
+      affine16(K, g, bf4, 128 * q + cg + 16 * part, pp, a.inv_scale[g], m, v);
     };
 
-    for (int h = 0; h < 2; ++h) {
-      layer0(h);
-      fence_async_shared();
-      mbar_arrive(act_full + h);
+    for (int q = 0; q < 4; ++q) {
+      layer0(q);
+      release(q);
     }
     for (; tile < n_tiles; tile += gridDim.x) {
       const float* bf4 = a.bfold4 + (size_t)shape * 512;
@@ -317,45 +313,37 @@ mlp_tcx_kernel(const __grid_constant__ TCMaps maps, const TCXArgs a) {
       for (int g = 0; g < NUM_GEMM - 1; ++g) {
         if (!wait_acc(0)) { ok = false; break; }
         if (gemm_n(g) == 256) {
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            const int c = cq + 32 * t;
+          for (int q = 0; q < 2; ++q) {
             float v[16];
-            chunk(g, bf4, c, v);
+            chunk(g, bf4, p, q, v);
             uint32_t hi[8], lo[8];
             relu_split16(v, hi, lo, vmax);
-            store_packed<8>(act, rhi, c + 16 * part, hi);
-            store_packed<8>(act, rlo, c + 16 * part, lo);
+            store_split(128 * q + cg + 16 * part, hi, lo);
+            release(q);
           }
-          release(0);
           continue;
         }
-        uint32_t held_hi[4][8], held_lo[4][8];
+        uint32_t held_hi[2][8], held_lo[2][8];
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
+        for (int q = 0; q < 2; ++q) {
           float v[16];
-          chunk(g, bf4, cq + 32 * t, v);
-          relu_split16(v, held_hi[t], held_lo[t], vmax);
+          chunk(g, bf4, p, q, v);
+          relu_split16(v, held_hi[q], held_lo[q], vmax);
         }
         if (!wait_acc(1)) { ok = false; break; }
 #pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int c = cq + 32 * t + 16 * part;
-          store_packed<8>(act, rhi, c, held_hi[t]);
-          store_packed<8>(act, rlo, c, held_lo[t]);
+        for (int q = 0; q < 2; ++q) {
+          store_split(128 * q + cg + 16 * part, held_hi[q], held_lo[q]);
+          release(q);
         }
-        release(0);
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int c = 256 + cq + 32 * t;
+        for (int q = 2; q < 4; ++q) {
           float v[16];
-          chunk(g, bf4, c, v);
+          chunk(g, bf4, p, q, v);
           uint32_t hi[8], lo[8];
           relu_split16(v, hi, lo, vmax);
-          store_packed<8>(act, rhi, c + 16 * part, hi);
-          store_packed<8>(act, rlo, c + 16 * part, lo);
+          store_split(128 * q + cg + 16 * part, hi, lo);
+          release(q);
         }
-        release(1);
       }
       if (!ok) break;
       // ---- last layer: head; the operand tile takes the next tile's layer 0
@@ -370,45 +358,46 @@ mlp_tcx_kernel(const __grid_constant__ TCMaps maps, const TCXArgs a) {
         if (valid) rowsrc_load(a.src, j, p, shape);
       }
       float head = 0.f;
-      auto head_chunk = [&](int c) {
-        uint32_t r[32];
-        tmem_ld32(t_row + (uint32_t)c, r);
-        float m[16], v[16];
-        pair_sum16(r, part, m);
-        affine16(K, NUM_GEMM - 1, bf4, c + 16 * part, cur_p, a.inv_scale[NUM_GEMM - 1], m, v);
+      auto head_chunk = [&](int q) {
+        float v[16];
+        chunk(NUM_GEMM - 1, bf4, cur_p, q, v);
+        const int c = 128 * q + cg + 16 * part;
 #pragma unroll
         for (int i = 0; i < 16; i += 4) {
-          const float4 w = ldg4(K->w_head + c + 16 * part + i);
+          const float4 w = ldg4(K->w_head + c + i);
           head = fmaf(fmaxf(v[i], 0.f), w.x,
                       fmaf(fmaxf(v[i + 1], 0.f), w.y,
                            fmaf(fmaxf(v[i + 2], 0.f), w.z, fmaf(fmaxf(v[i + 3], 0.f), w.w, head))));
         }
       };
       if (!wait_acc(0)) { ok = false; break; }
-#pragma unroll
-      for (int t = 0; t < 4; ++t) head_chunk(cq + 32 * t);
+      head_chunk(0);
+      head_chunk(1);
       if (!wait_acc(1)) { ok = false; break; }
       if (has_next) {
         layer0(0);
         release(0);
-      }
-#pragma unroll
-      for (int t = 0; t < 4; ++t) head_chunk(256 + cq + 32 * t);
-      if (has_next) {
         layer0(1);
         release(1);
-      } else {
-        tc_fence_before();
       }
+      for (int q = 2; q < 4; ++q) {
+        head_chunk(q);
+        if (has_next) {
+          layer0(q);
+          release(q);
+        }
+      }
+      if (!has_next) tc_fence_before();
       head += __shfl_xor_sync(0xffffffffu, head, 16);
-      // group 1 hands its partial sums to group 0 (rewritten only after the
-      // next tile's layers, in which group 0 takes part)
+      // groups 1..3 hand their partial sums to group 0 (rewritten only after
+      // the next tile's layers, in which group 0 takes part)
       if (grp > 0) {
-        head_part[jr] = head;
+        head_part[(grp - 1) * QPT + jr] = head;
         mbar_arrive(head_bar);
       } else {
         if (!mbar_wait(head_bar, head_phase, abort_flag)) { ok = false; break; }
-        head += head_part[jr];
+#pragma unroll
+        for (int q = 0; q < FWD_GRPS - 1; ++q) head += head_part[q * QPT + jr];
         if (cur_valid && part == 0) a.fout[cur_j] = tanhf(head + __ldg(&K->b_head));
       }
       head_phase ^= 1u;
@@ -481,7 +470,8 @@ cudaError_t mlp_tcx_forward(const dist_decoder* dec, const RowSrc& src, const fl
   static bool configured = false;
   if (!configured) {
     cudaError_t e = cudaFuncSetAttribute(mlp_tcx_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         FWD_SMEM_BYTES);
     if (e != cudaSuccess) return e;
     configured = true;
   }
@@ -493,7 +483,7 @@ cudaError_t mlp_tcx_forward(const dist_decoder* dec, const RowSrc& src, const fl
   a.fout = fout;
   a.err = dec->tc.err;
   for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
-  mlp_tcx_kernel<<<num_sms(), THREADS, SMEM_BYTES, st>>>(dec->tc.xmaps, a);
+  mlp_tcx_kernel<<<num_sms(), FWD_THREADS, FWD_SMEM_BYTES, st>>>(dec->tc.xmaps, a);
   count_launch(1);
   return cudaGetLastError();
 }

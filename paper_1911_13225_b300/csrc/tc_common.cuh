@@ -24,6 +24,13 @@ constexpr int BAR_BYTES = 256;
 constexpr int SMEM_BYTES =
     1024 + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES + (NUM_EPI / 4 - 1) * BM * 4;
 constexpr unsigned long long kTimeoutNs = 1000000000ull;
+// Forward kernels: 16 epilogue warps, four per TMEM lane quadrant.
+constexpr int FWD_EPI = 16;
+constexpr int FWD_THREADS = 64 + FWD_EPI * 32;
+constexpr int FWD_GRPS = FWD_EPI / 4;
+constexpr int FWD_SMEM_BYTES =
+    1024 + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES + (FWD_GRPS - 1) * BM * 4;
+static_assert(FWD_SMEM_BYTES <= 232448, "forward kernel shared memory");
 
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
 // B bf16 (10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
