@@ -267,6 +267,12 @@ cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const flo
 cudaError_t mlp_tcx_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
                             const float* bfolds, float* fout, cudaStream_t st);
 
+// Both in one launch: src16 with 16-bit operands into f16out, srcx
+// FP32-class into fxout (either list may be empty: count null, n_rows 0).
+cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f16out,
+                         const RowSrc& srcx, float* fxout, const float* bfold0,
+                         const float* bfolds, cudaStream_t st, bool f16);
+
 // tcgen05 decoder adjoint over probes (same contract as mlp_fp32_adjoint;
 // `scratch` holds num_sms() * kTcAdjScratchPerCta bytes).
 cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const float4* pq,

@@ -1,22 +1,40 @@
-// BF16 tcgen05 decoder forward for the DeepSDF shape: 8 hidden layers of
-// 512, latent 256 folded into per-shape biases of layer 0 and the skip
-// layer 4, ReLU, tanh head (Sec. B.1).  GEMM layers 1..7 run on the 5th
-// generation tensor cores with FP32 accumulation in tensor memory; layer 0
-// (3 inputs), the xyz columns of layer 4 and the 512 -> 1 head run on CUDA
-// cores in FP32 inside the epilogue.
+// tcgen05 decoder forward for the DeepSDF shape: 8 hidden layers of 512,
+// latent 256 folded into per-shape biases of layer 0 and the skip layer 4,
+// ReLU, tanh head (Sec. B.1).  GEMM layers 1..7 run on the 5th generation
+// tensor cores with FP32 accumulation in tensor memory; layer 0 (3 inputs),
+// the xyz columns of layer 4 and the 512 -> 1 head run on CUDA cores in FP32
+// inside the epilogue.  One launch decodes two row lists: 16-bit operands
+// (BF16 or FP16) and FP32-class operands (each a sum of two FP16 numbers).
 //
 // One persistent CTA per SM, 128-row tiles (one row per TMEM lane):
-//   warp 0     TMA producer: weight slices [256 N x 64 K] bf16 (128B swizzle)
-//              into a 3-stage ring;
-//   warp 1     TMEM owner and single-thread MMA issuer
-//              (M = 128, N = 256, K = 16 per instruction);
-//   warps 2-9  epilogue: two warps per TMEM lane quadrant split the columns;
-//              tcgen05.ld the accumulator, add bias (+ xyz term), ReLU,
-//              round to bf16 and write the next layer's A operand into the
-//              shared activation tile in the same 128B-swizzled K-major
-//              layout the MMA descriptors describe.
+//   warp 0      TMA producer: weight slices [256 N x 64 K] (128B swizzle)
+//               into a 3-stage ring;
+//   warp 1      TMEM owner and single-thread MMA issuer
+//               (M = 128, N = 256, K = 16 per instruction);
+//   warps 2-17  epilogue: four warps per TMEM lane quadrant split the
+//               columns; tcgen05.ld the accumulator, add bias (+ xyz term),
+//               ReLU, round to the operand format and write the next layer's
+//               A operand into the shared activation tile in the same
+//               128B-swizzled K-major layout the MMA descriptors describe.
 // Activations never leave the SM.  Every wait is bounded (1 s): on timeout
 // the CTA raises an error word, drains its MMAs and frees its TMEM.
+//
+// FP32-class tiles: 64 queries per tile.  In TMEM lane quadrant q, rows
+// 32q + i (i < 16) hold the hi parts of the activations of query 16q + i and
+// rows 32q + 16 + i their lo parts.  Each layer runs its K loop twice, first
+// against W_lo, then against W_hi (weights of layer l scaled by 2^s_l so
+// that W_lo stays a normal FP16 number), into one FP32 accumulator, so rows
+// 32q + i and 32q + 16 + i hold a_hi (W_hi + W_lo) and a_lo (W_hi + W_lo);
+// their sum, one warp shuffle apart, is (a_hi + a_lo)(W_hi + W_lo): all four
+// partial products, nothing dropped beyond the two split residuals.  The
+// work per query is four times a 16-bit query.
+// Accuracy: emulated with exact accumulation this arithmetic is as close to
+// the FP64 decoder as FP32 CUDA-core arithmetic (~1e-7 in f), but the tensor
+// core's FP32 accumulator does not round to nearest: measured on B300 each
+// K step loses a fraction of an ulp of the running sum, always towards zero,
+// which leaves a systematic error of ~2e-6 in f.  The small W_lo pass runs
+// first so that only the W_hi pass adds into a large accumulator.
+#include <cmath>
 #include <vector>
 
 #include "tc_common.cuh"
@@ -25,18 +43,35 @@ namespace dist {
 
 namespace {
 
+// Forward arguments: two row lists decoded in one launch.  List 0 runs with
+// 16-bit operands (BF16, or FP16 with the F16 variant), 128 rows per tile;
+// list 1 is FP32-class: every operand a sum of two FP16 numbers (hi + lo,
+// weights scaled by 2^s_l), 64 queries per tile, see tc_common.cuh.
 struct TCArgs {
   const TCConst* K;              // epilogue constants (device)
   const float* bfold0;           // [shape][512] folded bias of layer 0
   const float* bfold4;           // [shape][512] folded bias of the skip layer 4
-  RowSrc src;
-  float* fout;
+  RowSrc src[2];
+  float* fout[2];
   int* err;
+  float inv_scale[NUM_GEMM];     // list 1: 2^-s_l of GEMM layer g
 };
 
-// Forward pipeline.  The accumulator of a 512-wide layer completes in two
-// 256-column halves (acc_full[0], acc_full[1]); the next layer's operand is
-// handed back in four 128-column K quarters (act_full[0..3]).
+constexpr int QPT_X = 64;        // FP32-class queries per tile
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                             uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+
+// Forward pipeline.  A tile is one of the two kinds; the FP32-class tiles
+// come first in tile order (they take twice as long).  A tile's K loop runs
+// once (16-bit) or twice (FP32-class: against W_lo, then W_hi).  The
+// accumulator of a 512-wide layer completes in two 256-column halves
+// (acc_full[0], acc_full[1]); the next layer's operand is handed back in four
+// 128-column K quarters (act_full[0..3]).
 //   epilogue (16 warps, four per TMEM lane quadrant, one 32-column chunk of
 //     each quarter per warp): after acc_full[0] it reads quarters 0 and 1
 //     into registers while the tensor core computes half 1; once
@@ -46,12 +81,13 @@ struct TCArgs {
 //   MMA: the next layer's first output half starts on K quarter 0 as soon as
 //     act_full[0] arrives, so it overlaps the epilogue's second half;
 //     act_full[3] also certifies that TMEM columns 256..511 have been read.
-// On the last layer the released operand tile takes the next tile's layer 0,
-// so the next tile's GEMMs overlap this tile's head.
+// On the last layer the released operand tile takes the next tile's layer 0
+// (in the next tile's format), so the next tile's GEMMs overlap this tile's
+// head.
 template <bool F16>
 __global__ void __launch_bounds__(FWD_THREADS, 1)
-mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
-  constexpr uint32_t kIdesc = instr_desc<F16>();
+mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMaps xmaps,
+              const TCArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -70,8 +106,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  const int n = rowsrc_count(a.src);
-  const int n_tiles = (n + BM - 1) / BM;
+  const int n0 = rowsrc_count(a.src[0]);
+  const int n1 = rowsrc_count(a.src[1]);
+  const int t1 = (n1 + QPT_X - 1) / QPT_X;     // FP32-class tiles: [0, t1)
+  const int n_tiles = t1 + (n0 + BM - 1) / BM;
   if ((int)blockIdx.x >= n_tiles) return;
 
   if (threadIdx.x == 0) {
@@ -102,12 +140,17 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
       for (int s = 0; s < STAGES; ++s) issued[s] = false;
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+        const bool xt = tile < t1;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
+          const CUtensorMap* map = xt ? &xmaps.m[g] : &maps.m[g];
+          const int nkc = gemm_k(g) / BK;
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
-            for (int kc = 0; kc < gemm_k(g) / BK; ++kc) {
+            for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
               if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) { ok = false; break; }
               mbar_expect_tx(full + stage, STAGE_BYTES);
-              tma_load_2d(wst + stage * STAGE_BYTES, &maps.m[g], full + stage, kc * BK, nh * BN);
+              // FP32-class: the W_lo pass (columns K..2K-1) first, then W_hi
+              const int xk = !xt ? kc : (kc < nkc ? nkc + kc : kc - nkc);
+              tma_load_2d(wst + stage * STAGE_BYTES, map, full + stage, xk * BK, nh * BN);
               issued[stage] = true;
               issued_parity[stage] = phase;
               if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -135,10 +178,13 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
       uint32_t act_phase[4] = {0u, 0u, 0u, 0u};
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+        const bool xt = tile < t1;
+        const uint32_t idesc = xt ? instr_desc<true>() : instr_desc<F16>();
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
+          const int nkc = gemm_k(g) / BK;
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
-            for (int kc = 0; kc < gemm_k(g) / BK; ++kc) {
-              if (nh == 0 && (kc & 1) == 0) {
+            for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
+              if (nh == 0 && kc < nkc && (kc & 1) == 0) {
                 const int q = kc >> 1;
                 if (!mbar_wait(act_full + q, act_phase[q], abort_flag)) { ok = false; break; }
                 act_phase[q] ^= 1u;
@@ -146,12 +192,12 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
               }
               if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
               tc_fence_after();
-              const uint32_t a_base = smem_u32(act + kc * CHUNK_BYTES);
+              const uint32_t a_base = smem_u32(act + (kc < nkc ? kc : kc - nkc) * CHUNK_BYTES);
               const uint32_t b_base = smem_u32(wst + stage * STAGE_BYTES);
 #pragma unroll
               for (int k = 0; k < BK / 16; ++k)
                 mma_bf16(tmem + (uint32_t)(nh * BN), sw128_desc(a_base + 32 * k),
-                         sw128_desc(b_base + 32 * k), kIdesc, (kc | k) != 0);
+                         sw128_desc(b_base + 32 * k), idesc, (kc | k) != 0);
               mma_commit(empty + stage);
               if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
@@ -171,22 +217,38 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
     }
   } else {
     // --------------------------------------------------------- epilogue
+    // 16-bit tile: this thread owns tile row 32 quad + lane.  FP32-class
+    // tile: lanes i and i + 16 of a warp own query 16 quad + i, lane i its
+    // hi operand row 32 quad + i and lane i + 16 its lo row 32 quad + 16 + i;
+    // each keeps 16 of the warp's 32 columns after their pair sum.
     const int ew = warp - 2;                  // 0..FWD_EPI-1
     const int quad = warp & 3;                // TMEM lane quadrant of this warp
-    const int grp = ew >> 2;                  // chunk inside each quarter
-    const int row = quad * 32 + lane;         // tile row == TMEM lane
-    const int cg = grp * 32;                  // column of this warp inside a quarter
+    const int grp = ew >> 2;                  // 32-column chunk inside each quarter
+    const int cg = grp * 32;
+    const int row = quad * 32 + lane;         // 16-bit tiles
+    const int part = lane >> 4;               // FP32-class tiles
+    const int jr = quad * 16 + (lane & 15);
+    const int rhi = quad * 32 + (lane & 15);
+    const int rlo = rhi + 16;
     const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
     const TCConst* K = a.K;
     uint32_t acc_phase[2] = {0u, 0u};
     uint32_t head_phase = 0;
     bool ok = true;
-    int tile = blockIdx.x;
-    int j = tile * BM + row;
-    bool valid = j < n;
+    float vmax = 0.f;
+
+    // rows of tile t for this thread
+    bool xt = false, valid = false;
+    int j = 0, shape = 0;
     float3 p = make_float3(0.f, 0.f, 0.f);
-    int shape = 0;
-    if (valid) rowsrc_load(a.src, j, p, shape);
+    auto load_rows = [&](int t) {
+      xt = t < t1;
+      j = xt ? t * QPT_X + jr : (t - t1) * BM + row;
+      valid = j < (xt ? n1 : n0);
+      p = make_float3(0.f, 0.f, 0.f);
+      shape = 0;
+      if (valid) rowsrc_load(a.src[xt ? 1 : 0], j, p, shape);
+    };
     auto wait_acc = [&](int h) -> bool {
       if (!mbar_wait(acc_full + h, acc_phase[h], abort_flag)) return false;
       acc_phase[h] ^= 1u;
@@ -198,112 +260,166 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
       fence_async_shared();
       mbar_arrive(act_full + q);
     };
-    auto layer0 = [&](int q) {
-      float v[32];
-      layer0_32(K, a.bfold0 + (size_t)shape * 512, 128 * q + cg, p, v);
-      store_act32<F16>(act, row, 128 * q + cg, v);
+    // operand words of quarter q: 16 packed pairs (16-bit tile) or 8 hi + 8
+    // lo pairs (FP32-class tile), written to the operand tile by put()
+    auto put = [&](int q, const uint32_t (&h)[16]) {
+      if (!xt) {
+        store_packed<16>(act, row, 128 * q + cg, h);
+      } else {
+        const int c = 128 * q + cg + 16 * part;
+        const uint32_t ch = (uint32_t)((c >> 6) * CHUNK_BYTES);
+        const uint32_t u = (uint32_t)((c & 63) >> 3);
+        const uint32_t base = smem_u32(act) + ch;
+        st_shared_v4(base + swz(rhi, u), h[0], h[1], h[2], h[3]);
+        st_shared_v4(base + swz(rhi, u + 1), h[4], h[5], h[6], h[7]);
+        st_shared_v4(base + swz(rlo, u), h[8], h[9], h[10], h[11]);
+        st_shared_v4(base + swz(rlo, u + 1), h[12], h[13], h[14], h[15]);
+      }
     };
+    auto split_pack = [&](float (&v)[16], uint32_t (&h)[16]) {
+      uint32_t hi[8], lo[8];
+      relu_split16(v, hi, lo, vmax);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        h[i] = hi[i];
+        h[8 + i] = lo[i];
+      }
+    };
+    // layer 0 of the current rows, quarter q
+    auto layer0 = [&](int q, uint32_t (&h)[16]) {
+      const float* bf0 = a.bfold0 + (size_t)shape * 512;
+      if (!xt) {
+        float v[32];
+        layer0_32(K, bf0, 128 * q + cg, p, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) h[i] = pack16<F16>(v[2 * i], v[2 * i + 1]);
+      } else {
+        float v[16];
+        layer0_16(K, bf0, 128 * q + cg + 16 * part, p, v);
+        split_pack(v, h);
+      }
+    };
+    // quarter q of GEMM layer g (rows at p): operand words of relu(acc + bias)
+    auto hold = [&](int g, const float* bf4, const float3& pp, int q, uint32_t (&h)[16]) {
+      uint32_t r[32];
+      tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
+      if (!xt) {
+        float v[32];
+        bias32(K, g, bf4, 128 * q + cg, pp, r, v);
+#pragma unroll
+        for (int i = 0; i < 16; ++i)
+          h[i] = pack16<F16>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+      } else {
+        float m[16], v[16];
+        pair_sum16(r, part, m);
+        affine16(K, g, bf4, 128 * q + cg + 16 * part, pp, a.inv_scale[g], m, v);
+        split_pack(v, h);
+      }
+    };
+    // quarter q of the last layer of a tile of kind `kx` into the head sum
+    auto head_q = [&](bool kx, const float* bf4, const float3& pp, int q, float acc) -> float {
+      uint32_t r[32];
+      tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
+      if (!kx) {
+        float v[32];
+        bias32(K, NUM_GEMM - 1, bf4, 128 * q + cg, pp, r, v);
+#pragma unroll
+        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+        return head32(K, 128 * q + cg, v, acc);
+      }
+      float m[16], v[16];
+      pair_sum16(r, part, m);
+      const int c = 128 * q + cg + 16 * part;
+      affine16(K, NUM_GEMM - 1, bf4, c, pp, a.inv_scale[NUM_GEMM - 1], m, v);
+#pragma unroll
+      for (int i = 0; i < 16; i += 4) {
+        const float4 w = ldg4(K->w_head + c + i);
+        acc = fmaf(fmaxf(v[i], 0.f), w.x,
+                   fmaf(fmaxf(v[i + 1], 0.f), w.y,
+                        fmaf(fmaxf(v[i + 2], 0.f), w.z, fmaf(fmaxf(v[i + 3], 0.f), w.w, acc))));
+      }
+      return acc;
+    };
+
+    int tile = blockIdx.x;
+    load_rows(tile);
     for (int q = 0; q < 4; ++q) {
-      layer0(q);
+      uint32_t h[16];
+      layer0(q, h);
+      put(q, h);
       release(q);
     }
     for (; tile < n_tiles; tile += gridDim.x) {
       const float* bf4 = a.bfold4 + (size_t)shape * 512;
       const int next = tile + (int)gridDim.x;
       const bool has_next = next < n_tiles;
-      // chunk of quarter q of layer g: v = relu(acc + bias)
-      auto chunk = [&](int g, int q, float (&v)[32]) {
-        uint32_t r[32];
-        tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
-        bias32(K, g, bf4, 128 * q + cg, p, r, v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
-      };
       for (int g = 0; g < NUM_GEMM - 1; ++g) {
         if (!wait_acc(0)) { ok = false; break; }
         if (gemm_n(g) == 256) {
           // one output half: the layer's MMAs are done, write directly
           for (int q = 0; q < 2; ++q) {
-            float v[32];
-            chunk(g, q, v);
-            store_act32<F16>(act, row, 128 * q + cg, v);
+            uint32_t h[16];
+            hold(g, bf4, p, q, h);
+            put(q, h);
             release(q);
           }
           continue;
         }
-        uint32_t held[2][16];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          float v[32];
-          chunk(g, q, v);
-#pragma unroll
-          for (int i = 0; i < 16; ++i) held[q][i] = pack16<F16>(v[2 * i], v[2 * i + 1]);
-        }
+        uint32_t h0[16], h1[16];
+        hold(g, bf4, p, 0, h0);
+        hold(g, bf4, p, 1, h1);
         if (!wait_acc(1)) { ok = false; break; }
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          store_packed<16>(act, row, 128 * q + cg, held[q]);
-          release(q);
-        }
+        put(0, h0);
+        release(0);
+        put(1, h1);
+        release(1);
         for (int q = 2; q < 4; ++q) {
-          float v[32];
-          chunk(g, q, v);
-          store_act32<F16>(act, row, 128 * q + cg, v);
+          uint32_t h[16];
+          hold(g, bf4, p, q, h);
+          put(q, h);
           release(q);
         }
       }
       if (!ok) break;
       // ---- last layer: head partial sums; the operand tile takes the next
       // tile's layer 0 once this layer's MMAs are done
+      const bool cur_xt = xt;
       const int cur_j = j;
       const bool cur_valid = valid;
       const float3 cur_p = p;
-      if (has_next) {
-        j = next * BM + row;
-        valid = j < n;
-        p = make_float3(0.f, 0.f, 0.f);
-        shape = 0;
-        if (valid) rowsrc_load(a.src, j, p, shape);
-      }
       float head = 0.f;
-      auto head_chunk = [&](int q) {
-        uint32_t r[32];
-        tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
-        float v[32];
-        bias32(K, NUM_GEMM - 1, bf4, 128 * q + cg, cur_p, r, v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
-        head = head32(K, 128 * q + cg, v, head);
-      };
       if (!wait_acc(0)) { ok = false; break; }
-      head_chunk(0);
-      head_chunk(1);
+      head = head_q(cur_xt, bf4, cur_p, 0, head);
+      head = head_q(cur_xt, bf4, cur_p, 1, head);
       if (!wait_acc(1)) { ok = false; break; }
-      if (has_next) {
-        layer0(0);
-        release(0);
-        layer0(1);
-        release(1);
-      }
-      for (int q = 2; q < 4; ++q) {
-        head_chunk(q);
+      // from here on xt/j/p/shape describe the next tile's rows (layer 0 in
+      // its format); quarter q's layer 0 is released once this tile's
+      // quarter q has been read from TMEM
+      if (has_next) load_rows(next);
+      for (int q = 0; q < 4; ++q) {
+        if (q >= 2) head = head_q(cur_xt, bf4, cur_p, q, head);
         if (has_next) {
-          layer0(q);
+          uint32_t h[16];
+          layer0(q, h);
+          put(q, h);
           release(q);
         }
       }
       if (!has_next) tc_fence_before();
+      if (cur_xt) head += __shfl_xor_sync(0xffffffffu, head, 16);
       // head: f = tanh(w . h7 + b); column groups 1..3 hand their partial
       // sums to group 0 (head_part is rewritten only after the next tile's
       // layers, which group 0 takes part in, so one phase per tile suffices)
+      const int hr = cur_xt ? jr : row;
       if (grp > 0) {
-        head_part[(grp - 1) * BM + row] = head;
+        head_part[(grp - 1) * BM + hr] = head;
         mbar_arrive(head_bar);
       } else {
         if (!mbar_wait(head_bar, head_phase, abort_flag)) { ok = false; break; }
 #pragma unroll
-        for (int q = 0; q < FWD_GRPS - 1; ++q) head += head_part[q * BM + row];
-        if (cur_valid) a.fout[cur_j] = tanhf(head + __ldg(&K->b_head));
+        for (int q = 0; q < FWD_GRPS - 1; ++q) head += head_part[q * BM + hr];
+        if (cur_valid && (!cur_xt || part == 0))
+          a.fout[cur_xt ? 1 : 0][cur_j] = tanhf(head + __ldg(&K->b_head));
       }
       head_phase ^= 1u;
     }
@@ -311,6 +427,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const TCArgs a) {
       *abort_flag = 1;
       atomicOr(a.err, 4);
     }
+    if (!(vmax <= 65504.f)) atomicOr(a.err, 64);   // an FP32-class activation overflowed FP16
   }
   tc_fence_before();
   __syncthreads();
@@ -731,7 +848,51 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
 
 }  // namespace
 
-dist_status pack_tcx(dist_decoder* d, const float* const* W);   // mlp_tcx.cu
+// Weights of GEMM layers 1..7 as [N rows][2K cols] fp16: columns 0..K-1 hold
+// W_hi, K..2K-1 hold W_lo, both of W * 2^s_l.
+dist_status pack_tcx(dist_decoder* d, const float* const* W) {
+  auto enc = tensor_map_encoder();
+  DIST_CHECK(enc != nullptr, DIST_E_CUDA, "cuTensorMapEncodeTiled entry point not available");
+  const int L = 256, Hh = 253;
+  for (int g = 0; g < NUM_GEMM; ++g) {
+    const int l = g + 1;
+    const int N = gemm_n(g), K = gemm_k(g);
+    const int n_real = (l == 3) ? Hh : 512;
+    const int k_real = (l == 4) ? Hh : 512;
+    const int in_dim = (l == 4) ? Hh + L + 3 : 512;
+    float amax = 0.f;
+    for (int nn = 0; nn < n_real; ++nn)
+      for (int k = 0; k < k_real; ++k) amax = std::fmax(amax, std::fabs(W[l][(size_t)nn * in_dim + k]));
+    // largest power of two with amax * 2^s <= 2^14
+    int s = 0;
+    if (amax > 0.f) s = (int)std::floor(std::log2(16384.0 / (double)amax));
+    s = s < -24 ? -24 : (s > 24 ? 24 : s);
+    const float scale = std::ldexp(1.f, s);
+    d->tc.x_inv_scale[g] = std::ldexp(1.f, -s);
+    std::vector<uint16_t> h((size_t)N * 2 * K, 0);
+    for (int nn = 0; nn < n_real; ++nn)
+      for (int k = 0; k < k_real; ++k) {
+        const float w = W[l][(size_t)nn * in_dim + k] * scale;
+        const __half hi = __float2half_rn(w);
+        const __half lo = __float2half_rn(w - __half2float(hi));
+        h[(size_t)nn * 2 * K + k] = *reinterpret_cast<const uint16_t*>(&hi);
+        h[(size_t)nn * 2 * K + K + k] = *reinterpret_cast<const uint16_t*>(&lo);
+      }
+    void* q = nullptr;
+    DIST_CUDA_TRY(cudaMalloc(&q, h.size() * sizeof(uint16_t)));
+    d->allocations.push_back(q);
+    DIST_CUDA_TRY(cudaMemcpy(q, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    cuuint64_t dims[2] = {(cuuint64_t)(2 * K), (cuuint64_t)N};
+    cuuint64_t strides[1] = {(cuuint64_t)(2 * K) * sizeof(uint16_t)};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BN};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(&d->tc.xmaps.m[g], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, q, dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (split weights)");
+  }
+  return DIST_OK;
+}
 
 dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* b) {
   d->tc.ok = false;
@@ -829,8 +990,9 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
   return DIST_OK;
 }
 
-cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
-                           const float* bfolds, float* fout, cudaStream_t st, bool f16) {
+cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f16out,
+                         const RowSrc& srcx, float* fxout, const float* bfold0,
+                         const float* bfolds, cudaStream_t st, bool f16) {
   if (!dec->tc.ok) return cudaErrorNotSupported;
   static bool configured = false;
   if (!configured) {
@@ -847,15 +1009,32 @@ cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const flo
   a.K = dec->tc.cst;
   a.bfold0 = bfold0;
   a.bfold4 = bfolds;
-  a.src = src;
-  a.fout = fout;
+  a.src[0] = src16;
+  a.src[1] = srcx;
+  a.fout[0] = f16out;
+  a.fout[1] = fxout;
   a.err = dec->tc.err;
+  for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
   if (f16)
-    mlp_tc_kernel<true><<<num_sms(), FWD_THREADS, FWD_SMEM_BYTES, st>>>(dec->tc.maps16, a);
+    mlp_tc_kernel<true><<<num_sms(), FWD_THREADS, FWD_SMEM_BYTES, st>>>(dec->tc.maps16,
+                                                                       dec->tc.xmaps, a);
   else
-    mlp_tc_kernel<false><<<num_sms(), FWD_THREADS, FWD_SMEM_BYTES, st>>>(dec->tc.maps, a);
+    mlp_tc_kernel<false><<<num_sms(), FWD_THREADS, FWD_SMEM_BYTES, st>>>(dec->tc.maps,
+                                                                        dec->tc.xmaps, a);
   count_launch(1);
   return cudaGetLastError();
+}
+
+cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
+                           const float* bfolds, float* fout, cudaStream_t st, bool f16) {
+  RowSrc none{};
+  return mlp_tc_fused(dec, src, fout, none, nullptr, bfold0, bfolds, st, f16);
+}
+
+cudaError_t mlp_tcx_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
+                            const float* bfolds, float* fout, cudaStream_t st) {
+  RowSrc none{};
+  return mlp_tc_fused(dec, none, nullptr, src, fout, bfold0, bfolds, st, false);
 }
 
 cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const float4* pq,

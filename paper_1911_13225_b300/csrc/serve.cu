@@ -208,17 +208,24 @@ struct dist_server {
     const float* bs = bfold + (size_t)max_req * 512;
     RowSrc src{};
     src.st = stt; src.dir = dir; src.cams = cams;
-    if (is_tc(p.precision)) {
+    RowSrc sx = src;
+    sx.count = cnt + 2 * par + 1;
+    sx.idx = act[par][1];
+    if (fp32_on_tc(p)) {
+      // both lists in one launch (an empty 16-bit list for FP32_TC)
       src.count = cnt + 2 * par;
       src.idx = act[par][0];
-      DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, fbuf[0], st, p.precision == DIST_PREC_FP16));
+      DIST_CUDA_TRY(mlp_tc_fused(dec, src, fbuf[0], sx, fbuf[1], b0, bs, st,
+                                 p.precision == DIST_PREC_FP16));
+    } else {
+      if (is_tc(p.precision)) {
+        src.count = cnt + 2 * par;
+        src.idx = act[par][0];
+        DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, fbuf[0], st,
+                                     p.precision == DIST_PREC_FP16));
+      }
+      DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, sx, b0, bs, fbuf[1], st, is_tc(p.precision)));
     }
-    src.count = cnt + 2 * par + 1;
-    src.idx = act[par][1];
-    if (fp32_on_tc(p))
-      DIST_CUDA_TRY(mlp_tcx_forward(dec, src, b0, bs, fbuf[1], st));
-    else
-      DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, fbuf[1], st, is_tc(p.precision)));
     DIST_CUDA_TRY(cudaMemsetAsync(cnt + 2 * (par ^ 1), 0, 2 * sizeof(int), st));
     int* in[2] = {act[par][0], act[par][1]};
     const float* f[2] = {fbuf[0], fbuf[1]};

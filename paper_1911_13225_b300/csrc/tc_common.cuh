@@ -293,6 +293,82 @@ __device__ __forceinline__ float head32(const TCConst* K, int c, const float (&v
   return acc;
 }
 
+// ---- FP32-class (two-term FP16 split) epilogue pieces
+
+// v = m * scale + bias of GEMM layer g (the skip layer: folded bias + Wx4 p),
+// 16 columns from c.
+__device__ __forceinline__ void affine16(const TCConst* K, int g, const float* bf4, int c,
+                                         const float3& p, float scale, const float (&m)[16],
+                                         float (&v)[16]) {
+  if (g == 3) {
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+      const float4 b = ldg4(bf4 + c + i);
+      const float4 x = ldg4(K->wx4[0] + c + i);
+      const float4 y = ldg4(K->wx4[1] + c + i);
+      const float4 z = ldg4(K->wx4[2] + c + i);
+      v[i + 0] = fmaf(x.x, p.x, fmaf(y.x, p.y, fmaf(z.x, p.z, fmaf(m[i + 0], scale, b.x))));
+      v[i + 1] = fmaf(x.y, p.x, fmaf(y.y, p.y, fmaf(z.y, p.z, fmaf(m[i + 1], scale, b.y))));
+      v[i + 2] = fmaf(x.z, p.x, fmaf(y.z, p.y, fmaf(z.z, p.z, fmaf(m[i + 2], scale, b.z))));
+      v[i + 3] = fmaf(x.w, p.x, fmaf(y.w, p.y, fmaf(z.w, p.z, fmaf(m[i + 3], scale, b.w))));
+    }
+  } else {
+    const float* bias = K->bias[g];
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+      const float4 b = ldg4(bias + c + i);
+      v[i + 0] = fmaf(m[i + 0], scale, b.x);
+      v[i + 1] = fmaf(m[i + 1], scale, b.y);
+      v[i + 2] = fmaf(m[i + 2], scale, b.z);
+      v[i + 3] = fmaf(m[i + 3], scale, b.w);
+    }
+  }
+}
+
+// Layer 0 pre-activation, 16 columns from c: Wx0 p + b0'.
+__device__ __forceinline__ void layer0_16(const TCConst* K, const float* bf, int c, const float3& p,
+                                          float (&v)[16]) {
+#pragma unroll
+  for (int i = 0; i < 16; i += 4) {
+    const float4 b = ldg4(bf + c + i);
+    const float4 x = ldg4(K->wx0[0] + c + i);
+    const float4 y = ldg4(K->wx0[1] + c + i);
+    const float4 z = ldg4(K->wx0[2] + c + i);
+    v[i + 0] = fmaf(x.x, p.x, fmaf(y.x, p.y, fmaf(z.x, p.z, b.x)));
+    v[i + 1] = fmaf(x.y, p.x, fmaf(y.y, p.y, fmaf(z.y, p.z, b.y)));
+    v[i + 2] = fmaf(x.z, p.x, fmaf(y.z, p.y, fmaf(z.z, p.z, b.z)));
+    v[i + 3] = fmaf(x.w, p.x, fmaf(y.w, p.y, fmaf(z.w, p.z, b.w)));
+  }
+}
+
+// ReLU, then the two-term FP16 split of 16 values, packed in pairs.
+// `vmax` tracks the largest activation (an FP16 overflow check).
+__device__ __forceinline__ void relu_split16(float (&v)[16], uint32_t (&hi)[8], uint32_t (&lo)[8],
+                                             float& vmax) {
+#pragma unroll
+  for (int i = 0; i < 16; i += 2) {
+    const float a = fmaxf(v[i], 0.f), b = fmaxf(v[i + 1], 0.f);
+    vmax = fmaxf(vmax, fmaxf(a, b));
+    const __half2 h = __floats2half2_rn(a, b);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+    hi[i / 2] = *reinterpret_cast<const uint32_t*>(&h);
+    lo[i / 2] = *reinterpret_cast<const uint32_t*>(&l);
+  }
+}
+
+// Sum of the hi-row and lo-row accumulators of one query for the 16 columns
+// this lane owns in a 32-column chunk: lanes i and i + 16 exchange the half
+// of the chunk the other one keeps (16 shuffles).
+__device__ __forceinline__ void pair_sum16(const uint32_t (&r)[32], int part, float (&m)[16]) {
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const float keep = __uint_as_float(part ? r[16 + i] : r[i]);
+    const float send = __uint_as_float(part ? r[i] : r[16 + i]);
+    m[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+}
+
 // cuTensorMapEncodeTiled through the runtime's driver entry point query.
 inline PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;

@@ -850,11 +850,42 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
   const int step_grid = num_sms() * 4;
   RowSrc src{};
   src.st = ws->st; src.dir = ws->dir; src.cams = ws->cams;
+  if (tc && fp32_on_tc(*p) && p->refine_steps == 0) {
+    // Tensor-core march with FP32-class tensor-core queries that run to
+    // convergence: one launch per step decodes both lists (16-bit rows and
+    // handed-over rays), so the two share the latency of the shrinking tail
+    // of steps.  (With refine_steps > 0 a handed-over ray needs only a few
+    // FP32-class queries, and one deferred batch of them, below, is
+    // cheaper.)
+    for (int s = 0; s < M; ++s) {
+      const int par = s & 1;
+      RowSrc sx = src;
+      src.count = cA + s;
+      src.idx = ws->act[par][0];
+      sx.count = cB + s;
+      sx.idx = ws->act[par][1];
+      prof_mlp_begin(st, 0);
+      DIST_CUDA_TRY(mlp_tc_fused(dec, src, ws->fbuf[0], sx, ws->fbuf[1], b0, bs, st,
+                                 p->precision == DIST_PREC_FP16));
+      prof_mlp_end(st);
+      StepLists L;
+      L.cnt_in[0] = cA + s; L.cnt_in[1] = cB + s;
+      L.cnt_out[0] = cA + s + 1; L.cnt_out[1] = cB + s + 1;
+      L.in[0] = ws->act[par][0]; L.in[1] = ws->act[par][1];
+      L.f[0] = ws->fbuf[0]; L.f[1] = ws->fbuf[1];
+      L.out[0] = ws->act[par ^ 1][0]; L.out[1] = ws->act[par ^ 1][1];
+      step_kernel<<<step_grid, 256, 0, st>>>(a, L, o->queries);
+      DIST_LAUNCH_CHECK();
+    }
+    if (o->normal) return normals_impl(dec, p, o, o->normal, ws, n_cams, n_pix, st);
+    return DIST_OK;
+  }
   if (tc) {
-    // Tensor-core march.  Rays whose low-precision |f| is small enough move
-    // to one FP32 list that grows over all steps: their FP32 queries run
-    // together afterwards instead of as a small launch every step.  A ray's
-    // result does not depend on when its queries run.
+    // Tensor-core march with FP32 CUDA-core queries.  Rays whose
+    // low-precision |f| is small enough move to one FP32 list that grows
+    // over all steps: their FP32 queries run together afterwards instead of
+    // as a small launch every step.  A ray's result does not depend on when
+    // its queries run.
     for (int s = 0; s < M; ++s) {
       const int par = s & 1;
       src.count = cA + s;
