@@ -308,9 +308,120 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "clocks": clk,
     }
+    if not args.no_serve:
+        line["serving"] = run_serving(args, dec, params, dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_crop)
     return line
+
+
+# ----------------------------------------------------------------- serving
+
+SERVE_SIZES = (64, 128, 256, 512)
+
+
+def serve_requests(n, seed=777):
+    """Seeded mixed load: 70% render, 30% render+backward, square images with
+    sides uniform over SERVE_SIZES, a N(0, 0.01^2) 256-d latent per request,
+    viewpoints uniform on the radius-2.5 sphere."""
+    import synth
+    rng = np.random.default_rng(seed)
+    vps = synth.random_viewpoints(n, seed=seed)
+    out = []
+    for i in range(n):
+        side = int(rng.choice(SERVE_SIZES))
+        kind = "backward" if rng.random() < 0.3 else "render"
+        z = rng.normal(0.0, 0.01, 256).astype(np.float32)
+        z_tgt = rng.normal(0.0, 0.01, 256).astype(np.float32)
+        out.append((synth.look_at_camera(vps[i], side, side, shape=0), z, kind, z_tgt))
+    return out
+
+
+def run_serving(args, dec, params, dev):
+    """Continuous-batching server under a Poisson stream of the mixed load:
+    saturated throughput first (all requests submitted at once), then arrivals
+    at `load` x that rate; latency = arrival -> poll-done."""
+    import torch
+    from paper_1911_13225_b300 import api, _abi
+    from paper_1911_13225_b300.serve import Server
+    reqs = serve_requests(args.serve_requests)
+    ws = api.Workspace(512 * 512, MAX_STEPS)
+    tgts = []
+    for cam, z, kind, z_tgt in reqs:      # targets of the backward requests (untimed)
+        if kind == "backward":
+            zt = torch.from_numpy(z_tgt[None]).to(dev)
+            tgts.append(api.trace(dec, zt, [cam], params, ws).depth.cpu().numpy())
+        else:
+            tgts.append(None)
+    srv = Server(dec, params, max_rays=4 * 512 * 512, mem_budget=8 << 30, max_requests=64)
+
+    def submit(i):
+        cam, z, kind, _ = reqs[i]
+        try:
+            return srv.submit(cam, z, kind, tgts[i])
+        except _abi.DistError as e:
+            if e.status == _abi.DIST_E_BUSY:
+                return None
+            raise
+
+    def drive(arrivals):
+        """Submit request i at time arrivals[i] (from t0); returns latencies."""
+        n = len(arrivals)
+        pending, live, lat = 0, {}, np.zeros(n)
+        t0 = time.perf_counter()
+        while pending < n or live:
+            now = time.perf_counter() - t0
+            while pending < n and arrivals[pending] <= now:
+                t = submit(pending)
+                if t is None:
+                    break
+                live[pending] = t
+                pending += 1
+            for i in list(live):
+                if srv.poll(live[i]):
+                    lat[i] = (live[i].t_done - t0) - arrivals[i]
+                    del live[i]
+            time.sleep(5e-5)
+        return lat, time.perf_counter() - t0
+
+    rays = np.array([int(c["H"]) * int(c["W"]) for c, _, _, _ in reqs], dtype=np.float64)
+    drive(np.zeros(min(16, len(reqs))))                      # warm-up
+    _, t_sat = drive(np.zeros(len(reqs)))
+    sat_req_s = len(reqs) / t_sat
+    rng = np.random.default_rng(4242)
+    arr = np.cumsum(rng.exponential(1.0 / (args.serve_load * sat_req_s), len(reqs)))
+    arr -= arr[0]
+    lat, t_run = drive(arr)
+    srv.close()
+
+    # the plain per-request FP32 CUDA-core trace (+ backward), one at a time
+    p32 = api.TraceParams(max_steps=MAX_STEPS, precision="fp32")
+    sample = list(range(min(args.serve_fp32_sample, len(reqs))))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in sample:
+        cam, z, kind, _ = reqs[i]
+        zt = torch.from_numpy(z[None]).to(dev)
+        res = api.trace(dec, zt, [cam], p32, ws)
+        if kind == "backward":
+            tg = {"depth": torch.from_numpy(tgts[i]).to(dev)}
+            _, gd, _, _, dz = api.loss(res, tg, zt, ws)
+            api.backward(dec, zt, [cam], p32, ws, res, g_depth=gd, dz=dz)
+        torch.cuda.synchronize()
+    t32 = time.perf_counter() - t0
+    return {
+        "requests": len(reqs), "mix": "70% render / 30% render+backward (L1 depth), sides "
+        "uniform over {64,128,256,512}, seeded 256-d latents, shared 8x512 decoder",
+        "admission": "device-memory budget 8 GiB, 64 slots, 4x512^2 pooled rays",
+        "saturated_rays_per_s": float(rays.sum() / t_sat),
+        "saturated_requests_per_s": sat_req_s,
+        "load": args.serve_load,
+        "poisson_rays_per_s": float(rays.sum() / t_run),
+        "p50_ms": float(np.percentile(lat, 50) * 1e3),
+        "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "fp32_per_request_rays_per_s": float(rays[sample].sum() / t32),
+        "fp32_sample_requests": len(sample),
+    }
 
 
 # ------------------------------------------------------------ oracle arm
@@ -408,6 +519,11 @@ def main():
     ap.add_argument("--cpu-crop", type=int, default=96)
     ap.add_argument("--ref-crop", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-load", type=float, default=0.8,
+                    help="Poisson arrival rate as a fraction of the saturated request rate")
+    ap.add_argument("--serve-fp32-sample", type=int, default=12)
     args = ap.parse_args()
     global SIZE
     SIZE = args.size

@@ -41,6 +41,37 @@ __device__ __forceinline__ int warp_append_n(int k, int* counter) {
   return base + incl - k;
 }
 
+// Block-aggregated append to two lists: one atomic per list per block call
+// (warp-level appends put one atomic per warp on the same two counters).
+// Every thread of the block must call it; it synchronises the block.
+template <int WARPS>
+__device__ __forceinline__ void block_append2(bool p0, bool p1, int* c0, int* c1, int& s0,
+                                              int& s1) {
+  __shared__ int wcnt[2][WARPS];
+  __shared__ int wbase[2][WARPS];
+  const int lane = lane_id(), w = threadIdx.x >> 5;
+  const unsigned m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
+  if (lane == 0) {
+    wcnt[0][w] = __popc(m0);
+    wcnt[1][w] = __popc(m1);
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int l = threadIdx.x;
+    int tot = 0;
+    for (int q = 0; q < WARPS; ++q) {
+      wbase[l][q] = tot;
+      tot += wcnt[l][q];
+    }
+    const int b = tot ? atomicAdd(l ? c1 : c0, tot) : 0;
+    for (int q = 0; q < WARPS; ++q) wbase[l][q] += b;
+  }
+  __syncthreads();
+  const unsigned below = (1u << lane) - 1u;
+  s0 = p0 ? wbase[0][w] + __popc(m0 & below) : -1;
+  s1 = p1 ? wbase[1][w] + __popc(m1 & below) : -1;
+}
+
 __device__ __forceinline__ int find_cam(const CamDev* cams, int n_cams, long long i) {
   int lo = 0, hi = n_cams - 1;
   while (lo < hi) {
@@ -188,7 +219,9 @@ struct StepLists {
 // BF16-phase rays (list 0) use eps_bf16 to switch to FP32 queries at the
 // same point; their samples enter the |f| tracking as max(|f|, eps) so that
 // only FP32 samples can make the silhouette negative.
-__global__ void step_kernel(TraceArgs a, StepLists L, unsigned long long* queries) {
+constexpr int kStepThreads = 256;
+__global__ void __launch_bounds__(kStepThreads) step_kernel(TraceArgs a, StepLists L,
+                                                            unsigned long long* queries) {
   const int n0 = *L.cnt_in[0], n1 = *L.cnt_in[1];
   const int n = n0 + n1;
   if (queries && blockIdx.x == 0 && threadIdx.x == 0) {
@@ -196,8 +229,9 @@ __global__ void step_kernel(TraceArgs a, StepLists L, unsigned long long* querie
     atomicAdd(queries + 1, (unsigned long long)n1);
   }
   const int stride = gridDim.x * blockDim.x;
-  for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < n; base += stride) {
-    const int j = base + lane_id();
+  // block-uniform rounds (block_append2 synchronises the block)
+  for (int r0 = blockIdx.x * blockDim.x; r0 < n; r0 += stride) {
+    const int j = r0 + threadIdx.x;
     int keep = -1, ray = -1;
     if (j < n) {
       const int list = j < n0 ? 0 : 1;
@@ -270,9 +304,9 @@ __global__ void step_kernel(TraceArgs a, StepLists L, unsigned long long* querie
       }
       if (outcome >= 0 && a.o.status) a.o.status[i] = outcome;
     }
-    const int s0 = warp_append(keep == 0, L.cnt_out[0]);
+    int s0, s1;
+    block_append2<kStepThreads / 32>(keep == 0, keep == 1, L.cnt_out[0], L.cnt_out[1], s0, s1);
     if (s0 >= 0) L.out[0][s0] = ray;
-    const int s1 = warp_append(keep == 1, L.cnt_out[1]);
     if (s1 >= 0) L.out[1][s1] = ray;
   }
 }
@@ -451,16 +485,35 @@ __global__ void fd_coef_kernel(const float* f6, const int* pix, const int* count
 }
 
 // dz[s][k] += sum_j Wz0[j][k] G0[s][j] + sum_j Wzs[j][k] Gs[s][j]  (FP64).
-__global__ void latent_finalize_kernel(DecoderF32 d, const double* G0, const double* Gs,
-                                       int n_shapes, float* dz) {
+// dz[s] += W_z0^T G0[s] + W_zs^T Gs[s] (Eq. 2's latent factor), in FP64.
+// Block (k-chunk of 32, shape s): lane = latent index, the 16 warps split the
+// width and a fixed-order shared-memory sum combines them (deterministic).
+constexpr int kFinalizeWarps = 16;
+__global__ void __launch_bounds__(kFinalizeWarps * 32)
+latent_finalize_kernel(DecoderF32 d, const double* G0, const double* Gs, int n_shapes, float* dz) {
+  __shared__ double part[kFinalizeWarps][32];
   const int s = blockIdx.y;
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < d.latent; k += gridDim.x * blockDim.x) {
-    double acc = 0.0;
-    for (int j = 0; j < d.width; ++j) {
-      acc += (double)d.Wz0[(size_t)j * d.latent + k] * G0[(size_t)s * d.width + j];
-      if (d.skip > 0) acc += (double)d.Wzs[(size_t)j * d.latent + k] * Gs[(size_t)s * d.width + j];
+  const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
+  const int k = blockIdx.x * 32 + lane;
+  const int per = (d.width + kFinalizeWarps - 1) / kFinalizeWarps;
+  const int j0 = w * per, j1 = min(d.width, j0 + per);
+  double acc = 0.0;
+  if (k < d.latent) {
+    const double* g0 = G0 + (size_t)s * d.width;
+    const double* gs = Gs + (size_t)s * d.width;
+    for (int j = j0; j < j1; ++j) {
+      acc = fma((double)d.Wz0[(size_t)j * d.latent + k], g0[j], acc);
+      if (d.skip > 0) acc = fma((double)d.Wzs[(size_t)j * d.latent + k], gs[j], acc);
     }
-    dz[(size_t)s * d.latent + k] += (float)acc;
+  }
+  part[w][lane] = acc;
+  __syncthreads();
+  if (w == 0 && k < d.latent) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kFinalizeWarps; ++q) t += part[q][lane];
+    dz[(size_t)s * d.latent + k] += (float)t;
   }
 }
 
@@ -777,7 +830,7 @@ cudaError_t pool_step(const RayPool& P, const int* cnt_in, int* cnt_out, int* co
   L.cnt_in[0] = cnt_in; L.cnt_in[1] = cnt_in + 1;
   L.cnt_out[0] = cnt_out; L.cnt_out[1] = cnt_out + 1;
   for (int k = 0; k < 2; ++k) { L.in[k] = in[k]; L.f[k] = f[k]; L.out[k] = out[k]; }
-  step_kernel<<<num_sms() * 4, 256, 0, st>>>(pool_args(P), L, P.o.queries);
+  step_kernel<<<num_sms() * 4, kStepThreads, 0, st>>>(pool_args(P), L, P.o.queries);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -811,8 +864,8 @@ cudaError_t pool_loss_depth(long long n, const float* depth, const uint8_t* mask
 
 cudaError_t pool_latent_finalize(const DecoderF32& d, const double* G0, const double* Gs,
                                  float* dz, cudaStream_t st) {
-  dim3 fg((d.latent + 127) / 128, 1);
-  latent_finalize_kernel<<<fg, 128, 0, st>>>(d, G0, Gs, 1, dz);
+  dim3 fg((d.latent + 31) / 32, 1);
+  latent_finalize_kernel<<<fg, kFinalizeWarps * 32, 0, st>>>(d, G0, Gs, 1, dz);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -874,7 +927,7 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
       L.in[0] = ws->act[par][0]; L.in[1] = ws->act[par][1];
       L.f[0] = ws->fbuf[0]; L.f[1] = ws->fbuf[1];
       L.out[0] = ws->act[par ^ 1][0]; L.out[1] = ws->act[par ^ 1][1];
-      step_kernel<<<step_grid, 256, 0, st>>>(a, L, o->queries);
+      step_kernel<<<step_grid, kStepThreads, 0, st>>>(a, L, o->queries);
       DIST_LAUNCH_CHECK();
     }
     if (o->normal) return normals_impl(dec, p, o, o->normal, ws, n_cams, n_pix, st);
@@ -900,7 +953,7 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
       L.in[0] = ws->act[par][0]; L.in[1] = ws->act[0][1];
       L.f[0] = ws->fbuf[0]; L.f[1] = ws->fbuf[1];
       L.out[0] = ws->act[par ^ 1][0]; L.out[1] = ws->act[0][1];
-      step_kernel<<<step_grid, 256, 0, st>>>(a, L, o->queries);
+      step_kernel<<<step_grid, kStepThreads, 0, st>>>(a, L, o->queries);
       DIST_LAUNCH_CHECK();
     }
   }
@@ -924,7 +977,7 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
     L.in[0] = ws->act[0][0]; L.in[1] = ws->act[par][1];
     L.f[0] = ws->fbuf[0]; L.f[1] = ws->fbuf[1];
     L.out[0] = ws->act[0][0]; L.out[1] = ws->act[par ^ 1][1];
-    step_kernel<<<step_grid, 256, 0, st>>>(a, L, o->queries);
+    step_kernel<<<step_grid, kStepThreads, 0, st>>>(a, L, o->queries);
     DIST_LAUNCH_CHECK();
   }
   if (o->normal) return normals_impl(dec, p, o, o->normal, ws, n_cams, n_pix, st);
@@ -1003,8 +1056,8 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
     DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p + off, ws->probe_q + off, ws->probe_count + 1,
                                    b0, bs, nullptr, G0, Gs, 1, st));
   }
-  dim3 fg((d.latent + 127) / 128, n_shapes);
-  latent_finalize_kernel<<<fg, 128, 0, st>>>(d, G0, Gs, n_shapes, dz);
+  dim3 fg((d.latent + 31) / 32, n_shapes);
+  latent_finalize_kernel<<<fg, kFinalizeWarps * 32, 0, st>>>(d, G0, Gs, n_shapes, dz);
   DIST_LAUNCH_CHECK();
   return DIST_OK;
 }
