@@ -27,6 +27,12 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 FLOP_PER_QUERY = 3_146_752          # 8x512 decoder, latent folded into per-shape biases
+# dram__bytes_read.sum + dram__bytes_write.sum of one mlp_tc_kernel launch (ncu, the
+# first march launch of a 256x256 trace: 65,536 rows); the weights dominate it, so it
+# is not scaled by rows.  Taken on the current kernel; None once the kernel changes.
+TC_TRAFFIC_BYTES = 5.45e6 + 1.3e3
+TC_TRAFFIC_NOTE = ("ncu dram read+write, first march launch of a 256x256 BF16 trace "
+                   "(65,536 rows; weights once + ray state), not scaled")
 SIZE = 512
 MAX_STEPS = 50
 WORKLOAD = ("DeepSDF-shaped decoder 8x512 (latent 256, skip@4, ReLU, tanh), geometric init "
@@ -251,7 +257,8 @@ def run_ours(args, rank, world, local_rank):
                           + "; fp16 and bf16 share the dense tensor rate)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "peak_source": f"{peak_src} bf16 burst",
-                "traffic": None}
+                "traffic": TC_TRAFFIC_BYTES,
+                "traffic_note": TC_TRAFFIC_NOTE}
         if fused:
             tq = queries[0] + 4 * queries[1]
             roof["tensor_tflops_executed"] = tq * FLOP_PER_QUERY / (k_ms * 1e-3) / 1e12 \
