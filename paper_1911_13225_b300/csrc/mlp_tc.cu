@@ -59,12 +59,6 @@ struct TCArgs {
 
 constexpr int QPT_X = 64;        // FP32-class queries per tile
 
-__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
-                                             uint32_t d) {
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
-               "r"(d)
-               : "memory");
-}
 
 // Forward pipeline.  A tile is one of the two kinds; the FP32-class tiles
 // come first in tile order (they take twice as long).  A tile's K loop runs
@@ -316,29 +310,13 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         split_pack(v, h);
       }
     };
-    // quarter q of the last layer of a tile of kind `kx` into the head sum
-    auto head_q = [&](bool kx, const float* bf4, const float3& pp, int q, float acc) -> float {
+    // head term of the 32-column chunk of quarter q of the last layer (tile
+    // kind `kx`): its own sum, so that the per-row total is the same fixed-
+    // order sum of 16 chunk sums as in the cluster latency mode
+    auto head_q = [&](bool kx, const float* bf4, const float3& pp, int q) -> float {
       uint32_t r[32];
       tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
-      if (!kx) {
-        float v[32];
-        bias32(K, NUM_GEMM - 1, bf4, 128 * q + cg, pp, r, v);
-#pragma unroll
-        for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
-        return head32(K, 128 * q + cg, v, acc);
-      }
-      float m[16], v[16];
-      pair_sum16(r, part, m);
-      const int c = 128 * q + cg + 16 * part;
-      affine16(K, NUM_GEMM - 1, bf4, c, pp, a.inv_scale[NUM_GEMM - 1], m, v);
-#pragma unroll
-      for (int i = 0; i < 16; i += 4) {
-        const float4 w = ldg4(K->w_head + c + i);
-        acc = fmaf(fmaxf(v[i], 0.f), w.x,
-                   fmaf(fmaxf(v[i + 1], 0.f), w.y,
-                        fmaf(fmaxf(v[i + 2], 0.f), w.z, fmaf(fmaxf(v[i + 3], 0.f), w.w, acc))));
-      }
-      return acc;
+      return head_chunk_sum<F16>(K, kx, bf4, pp, 128 * q + cg, part, a.inv_scale[NUM_GEMM - 1], r);
     };
 
     int tile = blockIdx.x;
@@ -389,15 +367,15 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       const float3 cur_p = p;
       float head = 0.f;
       if (!wait_acc(0)) { ok = false; break; }
-      head = head_q(cur_xt, bf4, cur_p, 0, head);
-      head = head_q(cur_xt, bf4, cur_p, 1, head);
+      head += head_q(cur_xt, bf4, cur_p, 0);
+      head += head_q(cur_xt, bf4, cur_p, 1);
       if (!wait_acc(1)) { ok = false; break; }
       // from here on xt/j/p/shape describe the next tile's rows (layer 0 in
       // its format); quarter q's layer 0 is released once this tile's
       // quarter q has been read from TMEM
       if (has_next) load_rows(next);
       for (int q = 0; q < 4; ++q) {
-        if (q >= 2) head = head_q(cur_xt, bf4, cur_p, q, head);
+        if (q >= 2) head += head_q(cur_xt, bf4, cur_p, q);
         if (has_next) {
           uint32_t h[16];
           layer0(q, h);
@@ -406,7 +384,6 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         }
       }
       if (!has_next) tc_fence_before();
-      if (cur_xt) head += __shfl_xor_sync(0xffffffffu, head, 16);
       // head: f = tanh(w . h7 + b); column groups 1..3 hand their partial
       // sums to group 0 (head_part is rewritten only after the next tile's
       // layers, which group 0 takes part in, so one phase per tile suffices)

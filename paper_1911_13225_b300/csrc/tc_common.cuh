@@ -213,6 +213,13 @@ __device__ __forceinline__ void store_act32(uint8_t* act, int r, int c, const fl
   }
 }
 
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
+                                             uint32_t d) {
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
+               "r"(d)
+               : "memory");
+}
+
 // Store NP packed pairs (columns c..c+2*NP-1, c % 8 == 0) of row r.
 template <int NP>
 __device__ __forceinline__ void store_packed(uint8_t* act, int r, int c, const uint32_t (&h)[NP]) {
@@ -367,6 +374,40 @@ __device__ __forceinline__ void pair_sum16(const uint32_t (&r)[32], int part, fl
     const float send = __uint_as_float(part ? r[i] : r[16 + i]);
     m[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
   }
+}
+
+// Head term w_head . relu(acc + bias) of one 32-column chunk at column c of
+// the last GEMM layer, summed from zero in a fixed order, for the row of this
+// thread (16-bit tile) or of this lane pair (FP32-class tile: each lane sums
+// its 16 columns, then the pair adds the two halves).  The forward kernels
+// add these chunk sums in one fixed order, so a row's f does not depend on
+// which kernel or batch decoded it.
+template <bool F16>
+__device__ __forceinline__ float head_chunk_sum(const TCConst* K, bool kx, const float* bf4,
+                                                const float3& pp, int c, int part, float scale,
+                                                const uint32_t (&r)[32]) {
+  if (!kx) {
+    float v[32];
+    bias32(K, NUM_GEMM - 1, bf4, c, pp, r, v);
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = fmaxf(v[i], 0.f);
+    return head32(K, c, v, 0.f);
+  }
+  float m[16], v[16];
+  pair_sum16(r, part, m);
+  const int cc = c + 16 * part;
+  affine16(K, NUM_GEMM - 1, bf4, cc, pp, scale, m, v);
+  float acc = 0.f;
+#pragma unroll
+  for (int i = 0; i < 16; i += 4) {
+    const float4 w = ldg4(K->w_head + cc + i);
+    acc = fmaf(fmaxf(v[i], 0.f), w.x,
+               fmaf(fmaxf(v[i + 1], 0.f), w.y,
+                    fmaf(fmaxf(v[i + 2], 0.f), w.z, fmaf(fmaxf(v[i + 3], 0.f), w.w, acc))));
+  }
+  // part 0 holds the chunk's first 16 columns: first + second, in both lanes
+  const float other = __shfl_xor_sync(0xffffffffu, acc, 16);
+  return part ? other + acc : acc + other;
 }
 
 // cuTensorMapEncodeTiled through the runtime's driver entry point query.
