@@ -100,6 +100,12 @@ int dist_decoder_has_bf16(const dist_decoder* dec);
  * synchronises the device, returns the word in *code (0 = no timeout since
  * the last call) and clears it. */
 dist_status dist_decoder_device_error(const dist_decoder* dec, int32_t* code);
+/* Not from the paper: kernel variant of the tensor-core forward.  enable = 1
+ * runs it on CTA pairs that share each MMA (2-SM tensor core instructions,
+ * each SM streaming half of every weight tile); 0 (the default, faster on
+ * B300) runs one CTA per tile.  Results are bitwise identical.
+ * DIST_E_UNSUPPORTED for a decoder without the tensor-core path. */
+dist_status dist_decoder_set_tc_pair(dist_decoder* dec, int enable);
 
 /* ----------------------------------------------------------------- camera */
 

@@ -103,6 +103,11 @@ class Decoder:
         check(lib().dist_decoder_device_error(self.handle, byref(code)), "dist_decoder_device_error")
         return int(code.value)
 
+    def set_tc_pair(self, enable: bool) -> None:
+        """Tensor-core forward on CTA pairs (2-SM MMAs) or one CTA per tile (default)."""
+        check(lib().dist_decoder_set_tc_pair(self.handle, int(bool(enable))),
+              "dist_decoder_set_tc_pair")
+
     def close(self):
         if self.handle:
             lib().dist_decoder_destroy(self.handle)

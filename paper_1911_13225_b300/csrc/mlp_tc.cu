@@ -78,49 +78,67 @@ constexpr int QPT_X = 64;        // FP32-class queries per tile
 // On the last layer the released operand tile takes the next tile's layer 0
 // (in the next tile's format), so the next tile's GEMMs overlap this tile's
 // head.
-template <bool F16>
+//
+// PAIR: the CTAs run as clusters of two on the 2-SM tensor core path
+// (cta_group::2): a tile is 256 rows (128 FP32-class queries), 128 per CTA;
+// the even CTA issues M = 256 MMAs whose B operand (the weight stage, N =
+// 256) is split by rows between the two CTAs, so each SM streams half of
+// every weight tile.  Both CTAs load their half of each stage (completing on
+// the even CTA's full barrier), commits arrive on both CTAs' barriers, and
+// every epilogue warp of both CTAs arrives on the even CTA's act_full.
+template <bool F16, bool PAIR>
 __global__ void __launch_bounds__(FWD_THREADS, 1)
 mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMaps xmaps,
               const TCArgs a) {
+  constexpr int NST = PAIR ? 2 * STAGES : STAGES;            // weight ring stages
+  constexpr int SB = PAIR ? STAGE_BYTES / 2 : STAGE_BYTES;   // bytes per stage per CTA
+  constexpr int MUL = PAIR ? 2 : 1;                          // CTAs per tile
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   uint8_t* act = smem;
   uint8_t* wst = smem + ACT_BYTES;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(wst + STAGES * STAGE_BYTES);
-  uint64_t* full = bars;                       // [STAGES]
-  uint64_t* empty = bars + STAGES;             // [STAGES]
-  uint64_t* acc_full = bars + 2 * STAGES;      // [2] MMA -> epilogue, per N half
-  uint64_t* act_full = bars + 2 * STAGES + 2;  // [4] epilogue -> MMA, per K quarter
-  uint64_t* drain = bars + 2 * STAGES + 6;     // final MMA completion
-  uint64_t* head_bar = bars + 2 * STAGES + 7;  // head partial sums -> column group 0
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 8);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wst + NST * SB);
+  uint64_t* full = bars;                     // [NST]
+  uint64_t* empty = bars + NST;              // [NST]
+  uint64_t* acc_full = bars + 2 * NST;       // [2] MMA -> epilogue, per N half
+  uint64_t* act_full = bars + 2 * NST + 2;   // [4] epilogue -> MMA, per K quarter
+  uint64_t* drain = bars + 2 * NST + 6;      // final MMA completion
+  uint64_t* head_bar = bars + 2 * NST + 7;   // head partial sums -> column group 0
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  float* head_part = reinterpret_cast<float*>(smem + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES);
+  float* head_part = reinterpret_cast<float*>(smem + ACT_BYTES + NST * SB + BAR_BYTES);
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const int rank = PAIR ? (int)cluster_rank() : 0;          // 0: issues the pair's MMAs
+  const int pid = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+  const int npid = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
   const int n0 = rowsrc_count(a.src[0]);
   const int n1 = rowsrc_count(a.src[1]);
-  const int t1 = (n1 + QPT_X - 1) / QPT_X;     // FP32-class tiles: [0, t1)
-  const int n_tiles = t1 + (n0 + BM - 1) / BM;
-  if ((int)blockIdx.x >= n_tiles) return;
+  const int t1 = (n1 + MUL * QPT_X - 1) / (MUL * QPT_X);   // FP32-class tiles: [0, t1)
+  const int n_tiles = t1 + (n0 + MUL * BM - 1) / (MUL * BM);
+  if (pid >= n_tiles) return;                               // uniform over a pair
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
     for (int h = 0; h < 2; ++h) mbar_init(acc_full + h, 1);
-    for (int q = 0; q < 4; ++q) mbar_init(act_full + q, FWD_EPI * 32);
+    for (int q = 0; q < 4; ++q) mbar_init(act_full + q, MUL * FWD_EPI);
     mbar_init(drain, 1);
     mbar_init(head_bar, (FWD_EPI - 4) * 32);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(tmem_slot, 512);
+  if (warp == 1) {
+    if (PAIR) tmem_alloc_pair(tmem_slot, 512);
+    else tmem_alloc(tmem_slot, 512);
+  }
   tc_fence_before();
   __syncthreads();
+  if (PAIR) cluster_sync_all();   // the even CTA's barriers exist before the odd one uses them
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -129,11 +147,12 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
-      uint32_t issued_parity[STAGES];
-      bool issued[STAGES];
-      for (int s = 0; s < STAGES; ++s) issued[s] = false;
+      uint32_t issued_parity[NST];
+      bool issued[NST];
+      for (int s = 0; s < NST; ++s) issued[s] = false;
       bool ok = true;
-      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+      const uint32_t full_lead = PAIR ? map_rank(smem_u32(full), 0u) : 0u;
+      for (int tile = pid; ok && tile < n_tiles; tile += npid) {
         const bool xt = tile < t1;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
           const CUtensorMap* map = xt ? &xmaps.m[g] : &maps.m[g];
@@ -141,13 +160,17 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
             for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
               if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) { ok = false; break; }
-              mbar_expect_tx(full + stage, STAGE_BYTES);
+              if (rank == 0) mbar_expect_tx(full + stage, MUL * SB);
               // FP32-class: the W_lo pass (columns K..2K-1) first, then W_hi
               const int xk = !xt ? kc : (kc < nkc ? nkc + kc : kc - nkc);
-              tma_load_2d(wst + stage * STAGE_BYTES, map, full + stage, xk * BK, nh * BN);
+              if (PAIR)
+                tma_load_2d_pair(wst + stage * SB, map, full_lead + 8u * (uint32_t)stage,
+                                 xk * BK, nh * BN + 128 * rank);
+              else
+                tma_load_2d(wst + stage * SB, map, full + stage, xk * BK, nh * BN);
               issued[stage] = true;
               issued_parity[stage] = phase;
-              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+              if (++stage == NST) { stage = 0; phase ^= 1u; }
             }
           }
         }
@@ -156,8 +179,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         *abort_flag = 1;
         atomicOr(a.err, 1);
       }
-      // every issued copy must land before the CTA exits
-      for (int s = 0; s < STAGES; ++s) {
+      // every issued copy must land before the CTA exits (the odd CTA of a
+      // pair cannot see its copies land: the even one waits for both halves
+      // and the pair synchronises before exit)
+      for (int s = 0; s < NST && rank == 0; ++s) {
         if (!issued[s]) continue;
         const unsigned long long t0 = globaltimer();
         while (!mbar_try_wait(full + s, issued_parity[s]) && globaltimer() - t0 < kTimeoutNs) {
@@ -166,36 +191,47 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     }
   } else if (warp == 1) {
     // ------------------------------------------------------- MMA issuer
-    if (lane == 0) {
+    if (lane == 0 && rank == 0) {
       int stage = 0;
       uint32_t phase = 0;
       uint32_t act_phase[4] = {0u, 0u, 0u, 0u};
       bool ok = true;
-      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+      auto commit = [&](uint64_t* bar) {
+        if (PAIR) mma_commit_pair(bar);
+        else mma_commit(bar);
+      };
+      for (int tile = pid; ok && tile < n_tiles; tile += npid) {
         const bool xt = tile < t1;
-        const uint32_t idesc = xt ? instr_desc<true>() : instr_desc<F16>();
+        const uint32_t idesc = instr_desc_m(xt || F16, MUL * BM);
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
           const int nkc = gemm_k(g) / BK;
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
             for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
               if (nh == 0 && kc < nkc && (kc & 1) == 0) {
                 const int q = kc >> 1;
-                if (!mbar_wait(act_full + q, act_phase[q], abort_flag)) { ok = false; break; }
+                const bool got = PAIR ? mbar_wait_cl(act_full + q, act_phase[q], abort_flag)
+                                      : mbar_wait(act_full + q, act_phase[q], abort_flag);
+                if (!got) { ok = false; break; }
                 act_phase[q] ^= 1u;
                 tc_fence_after();
               }
               if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
               tc_fence_after();
               const uint32_t a_base = smem_u32(act + (kc < nkc ? kc : kc - nkc) * CHUNK_BYTES);
-              const uint32_t b_base = smem_u32(wst + stage * STAGE_BYTES);
+              const uint32_t b_base = smem_u32(wst + stage * SB);
 #pragma unroll
-              for (int k = 0; k < BK / 16; ++k)
-                mma_bf16(tmem + (uint32_t)(nh * BN), sw128_desc(a_base + 32 * k),
-                         sw128_desc(b_base + 32 * k), idesc, (kc | k) != 0);
-              mma_commit(empty + stage);
-              if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+              for (int k = 0; k < BK / 16; ++k) {
+                if (PAIR)
+                  mma_pair(tmem + (uint32_t)(nh * BN), sw128_desc(a_base + 32 * k),
+                           sw128_desc(b_base + 32 * k), idesc, (kc | k) != 0);
+                else
+                  mma_bf16(tmem + (uint32_t)(nh * BN), sw128_desc(a_base + 32 * k),
+                           sw128_desc(b_base + 32 * k), idesc, (kc | k) != 0);
+              }
+              commit(empty + stage);
+              if (++stage == NST) { stage = 0; phase ^= 1u; }
             }
-            if (ok) mma_commit(acc_full + nh);
+            if (ok) commit(acc_full + nh);
           }
         }
       }
@@ -204,7 +240,9 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         atomicOr(a.err, 2);
       }
       // all issued MMAs complete before TMEM is released
-      mma_commit(drain);
+      commit(drain);
+    }
+    if (lane == 0) {
       const unsigned long long t0 = globaltimer();
       while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
       }
@@ -237,7 +275,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     float3 p = make_float3(0.f, 0.f, 0.f);
     auto load_rows = [&](int t) {
       xt = t < t1;
-      j = xt ? t * QPT_X + jr : (t - t1) * BM + row;
+      j = xt ? (t * MUL + rank) * QPT_X + jr : ((t - t1) * MUL + rank) * BM + row;
       valid = j < (xt ? n1 : n0);
       p = make_float3(0.f, 0.f, 0.f);
       shape = 0;
@@ -249,10 +287,16 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       tc_fence_after();
       return true;
     };
+    // one arrival per warp on act_full[q] (in a pair, the even CTA's)
+    const uint32_t act_full_lead = PAIR ? map_rank(smem_u32(act_full), 0u) : 0u;
     auto release = [&](int q) {
-      tc_fence_before();
       fence_async_shared();
-      mbar_arrive(act_full + q);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        if (PAIR) mbar_arrive_remote(act_full_lead + 8u * (uint32_t)q);
+        else mbar_arrive(act_full + q);
+      }
     };
     // operand words of quarter q: 16 packed pairs (16-bit tile) or 8 hi + 8
     // lo pairs (FP32-class tile), written to the operand tile by put()
@@ -319,7 +363,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       return head_chunk_sum<F16>(K, kx, bf4, pp, 128 * q + cg, part, a.inv_scale[NUM_GEMM - 1], r);
     };
 
-    int tile = blockIdx.x;
+    int tile = pid;
     load_rows(tile);
     for (int q = 0; q < 4; ++q) {
       uint32_t h[16];
@@ -327,9 +371,9 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       put(q, h);
       release(q);
     }
-    for (; tile < n_tiles; tile += gridDim.x) {
+    for (; tile < n_tiles; tile += npid) {
       const float* bf4 = a.bfold4 + (size_t)shape * 512;
-      const int next = tile + (int)gridDim.x;
+      const int next = tile + npid;
       const bool has_next = next < n_tiles;
       for (int g = 0; g < NUM_GEMM - 1; ++g) {
         if (!wait_acc(0)) { ok = false; break; }
@@ -410,8 +454,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    tmem_dealloc(tmem, 512);
+    if (PAIR) tmem_dealloc_pair(tmem, 512);
+    else tmem_dealloc(tmem, 512);
   }
+  if (PAIR) cluster_sync_all();   // neither CTA leaves while its peer may still use it
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -867,6 +913,11 @@ dist_status pack_tcx(dist_decoder* d, const float* const* W) {
                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (split weights)");
+    cuuint32_t pbox[2] = {(cuuint32_t)BK, (cuuint32_t)(BN / 2)};
+    r = enc(&d->tc.pxmaps.m[g], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, q, dims, strides, pbox, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (split, half box)");
   }
   return DIST_OK;
 }
@@ -936,6 +987,13 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed");
+      cuuint32_t pbox[2] = {(cuuint32_t)BK, (cuuint32_t)(BN / 2)};
+      CUtensorMap* mp = f16 ? &d->tc.pmaps16.m[g] : &d->tc.pmaps.m[g];
+      r = enc(mp, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p,
+              dims, strides, pbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (half box)");
       // the transpose [K rows][N cols] for the adjoint's backward GEMM
       std::vector<uint16_t> t((size_t)K * N, 0);
       for (int nn = 0; nn < N; ++nn)
@@ -963,25 +1021,48 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
   d->allocations.push_back(e);
   DIST_CUDA_TRY(cudaMemset(e, 0, sizeof(int)));
   d->tc.err = static_cast<int*>(e);
+  // measured on B300: the CTA-pair variant is slower (973 vs 1183 TFLOP/s on
+  // large launches, 92 vs 78 us for one tile), so one CTA per tile is the default
+  d->tc.pair = false;
   d->tc.ok = true;
   return DIST_OK;
+}
+
+template <bool F16, bool PAIR>
+cudaError_t launch_fused(const dist_decoder* dec, const TCArgs& a, cudaStream_t st) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<F16, PAIR>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         FWD_SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  const TCMaps& maps = PAIR ? (F16 ? dec->tc.pmaps16 : dec->tc.pmaps)
+                            : (F16 ? dec->tc.maps16 : dec->tc.maps);
+  const TCMaps& xmaps = PAIR ? dec->tc.pxmaps : dec->tc.xmaps;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(PAIR ? (num_sms() / 2) * 2 : num_sms());
+  cfg.blockDim = dim3(FWD_THREADS);
+  cfg.dynamicSmemBytes = FWD_SMEM_BYTES;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = PAIR ? 2 : 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, mlp_tc_kernel<F16, PAIR>, maps, xmaps, a);
+  count_launch(1);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
 }
 
 cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f16out,
                          const RowSrc& srcx, float* fxout, const float* bfold0,
                          const float* bfolds, cudaStream_t st, bool f16) {
   if (!dec->tc.ok) return cudaErrorNotSupported;
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         FWD_SMEM_BYTES);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mlp_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               FWD_SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
   TCArgs a;
   a.K = dec->tc.cst;
   a.bfold0 = bfold0;
@@ -992,14 +1073,9 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
   a.fout[1] = fxout;
   a.err = dec->tc.err;
   for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
-  if (f16)
-    mlp_tc_kernel<true><<<num_sms(), FWD_THREADS, FWD_SMEM_BYTES, st>>>(dec->tc.maps16,
-                                                                       dec->tc.xmaps, a);
-  else
-    mlp_tc_kernel<false><<<num_sms(), FWD_THREADS, FWD_SMEM_BYTES, st>>>(dec->tc.maps,
-                                                                        dec->tc.xmaps, a);
-  count_launch(1);
-  return cudaGetLastError();
+  if (dec->tc.pair)
+    return f16 ? launch_fused<true, true>(dec, a, st) : launch_fused<false, true>(dec, a, st);
+  return f16 ? launch_fused<true, false>(dec, a, st) : launch_fused<false, false>(dec, a, st);
 }
 
 cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,

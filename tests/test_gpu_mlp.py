@@ -45,6 +45,32 @@ def test_tensor_core_decoder(cuda_device, n, precision):
     assert np.max(d_or) < 5e-3 * scale and np.mean(d_or) < 1e-3 * scale
 
 
+@pytest.mark.parametrize("n", [1, 200, 128 * 3 + 5, 148 * 128 + 77, 148 * 128 * 3 + 300])
+def test_pair_and_single_cta_kernels_agree_bitwise(cuda_device, n):
+    """The 2-SM (CTA-pair) and one-CTA variants of the tensor-core forward
+    accumulate every output in the same K order: identical bits, for 16-bit
+    and FP32-class rows, odd tile counts included."""
+    from paper_1911_13225_b300 import api
+    spec = synth.DEEPSDF_SPEC
+    Ws, bs, Z = workload(spec, seed=6, n_shapes=2)
+    dec = gpu_decoder(spec, Ws, bs)
+    ws = api.Workspace(max(n, 1024))
+    rng = np.random.default_rng(n + 5)
+    pts = torch.from_numpy(rng.uniform(-0.9, 0.9, (n, 3)).astype(np.float32)).to(cuda_device)
+    shp = torch.from_numpy(rng.integers(0, 2, n).astype(np.int32)).to(cuda_device)
+    zt = torch.from_numpy(Z).to(cuda_device)
+    out = {}
+    for pair in (True, False):
+        dec.set_tc_pair(pair)
+        for prec in ("bf16", "fp16", "fp32_tc"):
+            out[pair, prec] = to_np(api.sdf_eval(dec, zt, pts, shp, ws, precision=prec))
+    dec.set_tc_pair(False)
+    assert dec.device_error() == 0
+    for prec in ("bf16", "fp16", "fp32_tc"):
+        np.testing.assert_array_equal(out[True, prec], out[False, prec])
+    assert np.all(np.isfinite(out[True, "fp32_tc"]))
+
+
 @pytest.mark.parametrize("n", [1, 63, 64 * 5 + 7, 148 * 64 + 33, 148 * 64 * 3 + 5])
 def test_fp32_class_tensor_core_decoder(cuda_device, n):
     """Two-term FP16 split on the tensor cores (precision FP32_TC).  The split
