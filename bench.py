@@ -167,7 +167,7 @@ def run_ours(args, rank, world, local_rank):
         precision = "bf16" if dec.has_bf16 else "fp32"
     params = api.TraceParams(max_steps=MAX_STEPS, precision=precision, eps_bf16=args.eps_lo,
                              refine_steps=args.refine, alpha_refine=args.alpha_refine,
-                             refine_engine=args.refine_engine)
+                             refine_engine=args.refine_engine, refine_rule=args.refine_rule)
     ws = api.Workspace(SIZE * SIZE, MAX_STEPS)
     z = torch.from_numpy(Z).to(dev)
     # target: depth of the second latent (untimed setup)
@@ -301,7 +301,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": WORKLOAD.replace("512x512", f"{SIZE}x{SIZE}"),
                    "rays_per_step": rays, "precision": precision,
                    "eps_lo": args.eps_lo, "refine_steps": args.refine,
-                   "refine_engine": args.refine_engine,
+                   "refine_engine": args.refine_engine, "refine_rule": args.refine_rule,
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MB write, untimed)"},
         "sdf_queries_per_s": float(queries.sum()) * world / (total_ms * 1e-3),
@@ -315,11 +315,61 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "clocks": clk,
     }
+    line["fp32_trace"] = fp32_trace_rate(api, dec, cam, z, tgt, stream)
+    line["roofline"]["large_launch"] = large_launch_rate(api, dec, z, precision, peaks["bf16_tflops"])
     if not args.no_serve:
         line["serving"] = run_serving(args, dec, params, dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_crop)
     return line
+
+
+# ------------------------------------------------- FP32 trace, large launches
+
+def fp32_trace_rate(api, dec, cam, z, tgt, stream, steps=3):
+    """The plain FP32 GPU trace (CUDA-core decoder, FP32 adjoint) on the same
+    workload and step, timed the same way (after one warm-up step)."""
+    import torch
+    p32 = api.TraceParams(max_steps=MAX_STEPS, precision="fp32")
+    ws = api.Workspace(SIZE * SIZE, MAX_STEPS)
+    step = Step(api, dec, ws, cam, p32, z, tgt)
+    step(stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step(stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": SIZE * SIZE / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
+            "steps": steps, "note": "precision fp32: mlp_fp32_fwd_kernel + FP32 adjoint"}
+
+
+def large_launch_rate(api, dec, z, precision, peak, n=262144 * 2, reps=5):
+    """The decoder kernel alone on one large launch (dist_sdf_eval, n random
+    points in the unit ball region): the rate the march's first steps run at."""
+    import torch
+    if precision not in ("bf16", "fp16", "fp32_tc"):
+        return None
+    dev = z.device
+    g = torch.Generator(device="cpu").manual_seed(7)
+    pts = (torch.rand(n, 3, generator=g) * 1.4 - 0.7).to(dev)
+    sh = torch.zeros(n, dtype=torch.int32, device=dev)
+    ws = api.Workspace(n)
+    for _ in range(2):
+        api.sdf_eval(dec, z, pts, sh, ws, precision=precision)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        api.sdf_eval(dec, z, pts, sh, ws, precision=precision)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    tf = n * FLOP_PER_QUERY / (ms * 1e-3) / 1e12
+    return {"rows": n, "ms": ms, "achieved": tf, "peak": peak, "frac": tf / peak,
+            "note": "dist_sdf_eval of one launch (fold + pack + decoder), algorithmic FLOPs"}
 
 
 # ----------------------------------------------------------------- serving
@@ -515,6 +565,8 @@ def main():
                     choices=["auto", "bf16", "fp16", "fp32", "fp32_tc"])
     ap.add_argument("--refine-engine", default="tc", choices=["tc", "simt"],
                     help="kernel of the FP32-class queries after a BF16/FP16 hand-over")
+    ap.add_argument("--refine-rule", default="march", choices=["march", "secant"],
+                    help="step rule of the FP32-class queries after a BF16/FP16 hand-over")
     ap.add_argument("--eps-lo", type=float, default=1e-3,
                     help="|f| below which a BF16/FP16 ray switches to FP32 queries")
     ap.add_argument("--refine", type=int, default=0,

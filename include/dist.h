@@ -61,6 +61,13 @@ typedef enum {
 
 /* Kernel of the FP32-class queries after a BF16/FP16 hand-over. */
 typedef enum { DIST_REFINE_TC = 0, DIST_REFINE_SIMT = 1 } dist_refine_engine;
+
+/* Step rule of the FP32-class queries after a BF16/FP16 hand-over: MARCH
+ * keeps the paper's aggressive step (alpha_refine); SECANT takes one unit
+ * step (Eq. 1's final step) and then secant steps through the last two
+ * FP32-class samples (a step with a slope above -1e-3 or longer than 8 |f|
+ * falls back to the aggressive step).  Either converges on |f| < eps. */
+typedef enum { DIST_REFINE_MARCH = 0, DIST_REFINE_SECANT = 1 } dist_refine_rule;
 typedef enum { DIST_GRAD_EXACT = 0, DIST_GRAD_PAPER = 1 } dist_grad_mode;
 
 /* Ray outcome codes written to dist_trace_out.status. */
@@ -145,11 +152,13 @@ typedef struct {
   int refine_engine;   /* BF16/FP16 path: dist_refine_engine of the queries
                           after the hand-over (TC: the FP32_TC kernel,
                           SIMT: FP32 CUDA-core kernel)                      */
+  int refine_rule;     /* BF16/FP16 path: dist_refine_rule of the queries
+                          after the hand-over                               */
 } dist_trace_params;
 
 /* Fill `p` with the paper's defaults: max_steps 50, eps 5e-5, alpha 1.5,
  * k_min 1, normal_delta 0, exact gradients, FP32, eps_bf16 1e-3, radius 1,
- * refine_steps 0, alpha_refine 0, refine_engine TC. */
+ * refine_steps 0, alpha_refine 0, refine_engine TC, refine_rule MARCH. */
 void dist_trace_params_default(dist_trace_params* p);
 
 /* -------------------------------------------------------------- workspace */

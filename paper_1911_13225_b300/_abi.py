@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "DIST_OK", 1: "DIST_E_INVALID", 2: "DIST_E_NOMEM", 3: "DIST_E
 PREC_FP32, PREC_BF16, PREC_FP16, PREC_FP32_TC = 0, 1, 2, 3
 PRECISIONS = {"fp32": PREC_FP32, "bf16": PREC_BF16, "fp16": PREC_FP16, "fp32_tc": PREC_FP32_TC}
 REFINE_ENGINES = {"tc": 0, "simt": 1}
+REFINE_RULES = {"march": 0, "secant": 1}
 GRAD_EXACT, GRAD_PAPER = 0, 1
 RAY_INIT_MISS, RAY_HIT, RAY_LEFT, RAY_MAX_STEPS = 0, 1, 2, 3
 REQ_RENDER, REQ_RENDER_BACKWARD = 0, 1
@@ -51,7 +52,7 @@ class TraceParams(Structure):
     _fields_ = [("max_steps", c_int), ("eps", c_float), ("alpha", c_float), ("k_min", c_int),
                 ("normal_delta", c_float), ("grad_mode", c_int), ("precision", c_int),
                 ("eps_bf16", c_float), ("radius", c_float), ("refine_steps", c_int),
-                ("alpha_refine", c_float), ("refine_engine", c_int)]
+                ("alpha_refine", c_float), ("refine_engine", c_int), ("refine_rule", c_int)]
 
 
 class TraceOut(Structure):

@@ -44,6 +44,7 @@ class TraceParams:
     refine_steps: int = 0         # 0: FP32 convergence; n: accept after n FP32 queries
     alpha_refine: float = 0.0     # step factor of the FP32 phase (0: alpha)
     refine_engine: str = "tc"     # FP32-class queries after the hand-over: "tc" | "simt"
+    refine_rule: str = "march"    # their step rule: "march" (alpha) | "secant"
 
     def c(self) -> _abi.TraceParams:
         return _abi.TraceParams(
@@ -52,7 +53,7 @@ class TraceParams:
             _abi.GRAD_EXACT if self.grad_mode == "exact" else _abi.GRAD_PAPER,
             _abi.PRECISIONS[self.precision], float(self.eps_bf16), float(self.radius),
             int(self.refine_steps), float(self.alpha_refine),
-            _abi.REFINE_ENGINES[self.refine_engine])
+            _abi.REFINE_ENGINES[self.refine_engine], _abi.REFINE_RULES[self.refine_rule])
 
 
 def camera_struct(cam) -> _abi.Camera:

@@ -71,6 +71,7 @@ void dist_trace_params_default(dist_trace_params* p) {
   p->refine_steps = 0;
   p->alpha_refine = 0.f;
   p->refine_engine = DIST_REFINE_TC;
+  p->refine_rule = DIST_REFINE_MARCH;
 }
 
 dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* const* W,
@@ -194,6 +195,7 @@ dist_status dist_workspace_create(int64_t max_rays, int max_steps, dist_workspac
   WS_ALLOC(st, n * sizeof(float4));
   WS_ALLOC(fq, n * sizeof(int));
   WS_ALLOC(fprev, n * sizeof(float));
+  WS_ALLOC(dprev, n * sizeof(float));
   WS_ALLOC(act[0][0], n * sizeof(int));
   WS_ALLOC(act[0][1], n * sizeof(int));
   WS_ALLOC(act[1][0], n * sizeof(int));

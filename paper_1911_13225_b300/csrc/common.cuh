@@ -148,7 +148,9 @@ struct dist_workspace {
   float4* dir;        // (vx, vy, vz, 1/sqrt(x~^2+y~^2+1))
   float4* st;         // (d, t_in, t_out, camera index as int bits)
   int* fq;            // FP32 queries a ray made after its low-precision phase
-  float* fprev;       // previous low-precision sample of each ray
+  float* fprev;       // previous low-precision sample of each ray (its FP32-class
+                      // sample after the hand-over, secant rule)
+  float* dprev;       // distance of the previous FP32-class sample (secant rule)
   int* act[2][2];     // [parity][0 = BF16 list, 1 = FP32 list] active ray ids
   float* fbuf[2];     // MLP outputs for the two lists
   int* counts;        // [(max_steps + 2) * 2] list lengths per step
@@ -239,7 +241,9 @@ struct RayPool {
   float4* dir;
   int* fq;
   float* fprev;
+  float* dprev;
   int refine;
+  int secant;
   float alpha_fp32;
   dist_trace_out o;
   int K;

@@ -59,9 +59,9 @@ __global__ void count_slots_kernel(const int* l0, const int* c0, const int* l1, 
 }
 
 size_t bytes_per_pixel(int K) {
-  // ray state, lists, MLP outputs, per-pixel outputs, target, upstream
-  // gradient and backward probes
-  return 16 + 16 + 8 + 16 + 8 + (4 + 4 + 1 + 4 + 4 + 4 + 8 * K) + 4 + 4 + (16 + 16 + 4);
+  // ray state (incl. the refinement samples), lists, MLP outputs, per-pixel
+  // outputs, target, upstream gradient and backward probes
+  return 16 + 16 + 12 + 16 + 8 + (4 + 4 + 1 + 4 + 4 + 4 + 8 * K) + 4 + 4 + (16 + 16 + 4);
 }
 
 }  // namespace
@@ -82,6 +82,7 @@ struct dist_server {
   float4* stt = nullptr;
   int* fq = nullptr;
   float* fprev = nullptr;
+  float* dprev = nullptr;
   int* act[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
   float* fbuf[2] = {nullptr, nullptr};
   int* cnt = nullptr;             // [parity][list]
@@ -118,8 +119,9 @@ struct dist_server {
 
   RayPool pool() const {
     RayPool P;
-    P.cams = cams; P.st = stt; P.dir = dir; P.fq = fq; P.fprev = fprev;
+    P.cams = cams; P.st = stt; P.dir = dir; P.fq = fq; P.fprev = fprev; P.dprev = dprev;
     P.refine = is_tc(p.precision) ? p.refine_steps : 0;
+    P.secant = is_tc(p.precision) && p.refine_rule == DIST_REFINE_SECANT ? 1 : 0;
     P.alpha_fp32 = (is_tc(p.precision) && p.alpha_refine > 0.f) ? p.alpha_refine : p.alpha;
     std::memset(&P.o, 0, sizeof(P.o));
     P.o.depth = depth; P.o.sil = sil; P.o.mask = mask; P.o.steps = steps; P.o.status = status;
@@ -380,6 +382,8 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
   DIST_CHECK(valid_precision(p->precision), DIST_E_INVALID, "dist_serve_create: bad precision");
   DIST_CHECK(p->refine_engine == DIST_REFINE_TC || p->refine_engine == DIST_REFINE_SIMT,
              DIST_E_INVALID, "dist_serve_create: bad refine_engine");
+  DIST_CHECK(p->refine_rule == DIST_REFINE_MARCH || p->refine_rule == DIST_REFINE_SECANT,
+             DIST_E_INVALID, "dist_serve_create: bad refine_rule");
   DIST_CHECK(!(is_tc(p->precision) || fp32_on_tc(*p)) || dec->tc.ok, DIST_E_UNSUPPORTED,
              "the tensor-core decoder covers only the DeepSDF shape");
   dist_server* S = new dist_server();
@@ -403,6 +407,7 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
   SV_ALLOC(stt, n * sizeof(float4));
   SV_ALLOC(fq, n * sizeof(int));
   SV_ALLOC(fprev, n * sizeof(float));
+  SV_ALLOC(dprev, n * sizeof(float));
   SV_ALLOC(act[0][0], n * sizeof(int));
   SV_ALLOC(act[0][1], n * sizeof(int));
   SV_ALLOC(act[1][0], n * sizeof(int));

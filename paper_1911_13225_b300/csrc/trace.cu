@@ -134,11 +134,13 @@ struct TraceArgs {
   int max_steps;
   float alpha_fp32;     // step factor of FP32-list rays
   int refine;           // refine_steps for a tensor-core march, else 0
+  int secant;           // secant rule for FP32-list rays of a tensor-core march
   dist_trace_out o;
   float4* st;
   float4* dir;
   int* fq;              // FP32 queries per ray after the low-precision phase
-  float* fprev;         // previous low-precision sample of each ray
+  float* fprev;         // previous low-precision sample (then FP32-class, secant)
+  float* dprev;         // distance of the previous FP32-class sample (secant)
 };
 
 // One thread per pixel (Sec. 3.2 "Initialization"): the ray through the
@@ -262,12 +264,13 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(TraceArgs a, StepLis
       int outcome = -1;   // -1 keep marching
       float dn = d;
       bool accepted = false;
-      if (list == 1 && a.refine > 0) {
+      int q = 0;
+      if (list == 1 && (a.refine > 0 || a.secant)) {
         // FP32 refinement after a tensor-core march: after `refine` FP32
         // queries a ray within 4 eps_bf16 of the surface is accepted
-        const int q = a.fq[i] + 1;
+        q = a.fq[i] + 1;
         a.fq[i] = q;
-        accepted = q >= a.refine && af >= a.eps && af < 4.f * a.eps_bf16;
+        accepted = a.refine > 0 && q >= a.refine && af >= a.eps && af < 4.f * a.eps_bf16;
       }
       bool crossed = false;
       if (list == 0) {
@@ -283,6 +286,19 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(TraceArgs a, StepLis
         keep = 1;       // switch to FP32 queries at the same point
       } else {
         dn = fmaf(list == 1 ? a.alpha_fp32 : a.alpha, f, d);
+        if (list == 1 && a.secant) {
+          // unit step first, then secant steps through the last two samples
+          if (q == 1) {
+            dn = d + f;
+          } else {
+            const float dd = d - a.dprev[i];
+            const float sl = dd != 0.f ? (f - a.fprev[i]) / dd : 0.f;
+            const float stp = sl < -1e-3f ? -f / sl : 0.f;
+            if (sl < -1e-3f && fabsf(stp) <= 8.f * af) dn = d + stp;
+          }
+          a.dprev[i] = d;
+          a.fprev[i] = f;
+        }
         if (dn > s.z || dn < s.y) outcome = DIST_RAY_LEFT;
         else keep = list;
       }
@@ -656,6 +672,8 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
   DIST_CHECK(p->refine_steps >= 0, DIST_E_INVALID, "refine_steps must be >= 0");
   DIST_CHECK(p->refine_engine == DIST_REFINE_TC || p->refine_engine == DIST_REFINE_SIMT,
              DIST_E_INVALID, "bad refine_engine");
+  DIST_CHECK(p->refine_rule == DIST_REFINE_MARCH || p->refine_rule == DIST_REFINE_SECANT,
+             DIST_E_INVALID, "bad refine_rule");
   DIST_CHECK(p->grad_mode == DIST_GRAD_EXACT || p->grad_mode == DIST_GRAD_PAPER, DIST_E_INVALID,
              "bad grad_mode");
   DIST_CHECK(!(is_tc(p->precision) || fp32_on_tc(*p)) || dec->tc.ok, DIST_E_UNSUPPORTED,
@@ -706,8 +724,10 @@ TraceArgs make_args(const dist_trace_params* p, const dist_trace_out* o, dist_wo
   a.pix0 = 0; a.cam_fixed = -1;
   a.eps = p->eps; a.alpha = p->alpha; a.eps_bf16 = p->eps_bf16; a.max_steps = p->max_steps;
   a.refine = is_tc(p->precision) ? p->refine_steps : 0;
+  a.secant = is_tc(p->precision) && p->refine_rule == DIST_REFINE_SECANT ? 1 : 0;
   a.alpha_fp32 = (is_tc(p->precision) && p->alpha_refine > 0.f) ? p->alpha_refine : p->alpha;
   a.o = *o; a.st = ws->st; a.dir = ws->dir; a.fq = ws->fq; a.fprev = ws->fprev;
+  a.dprev = ws->dprev;
   return a;
 }
 
@@ -800,7 +820,8 @@ static TraceArgs pool_args(const RayPool& P) {
   a.cams = P.cams; a.n_cams = 0; a.n_pix = 0; a.pix0 = 0; a.cam_fixed = -1;
   a.radius = P.radius; a.K = P.K; a.eps = P.eps; a.alpha = P.alpha; a.eps_bf16 = P.eps_bf16;
   a.max_steps = P.max_steps; a.o = P.o; a.st = P.st; a.dir = P.dir;
-  a.fq = P.fq; a.fprev = P.fprev; a.refine = P.refine; a.alpha_fp32 = P.alpha_fp32;
+  a.fq = P.fq; a.fprev = P.fprev; a.dprev = P.dprev; a.refine = P.refine;
+  a.secant = P.secant; a.alpha_fp32 = P.alpha_fp32;
   return a;
 }
 

@@ -121,15 +121,20 @@ def test_normals_at_gpu_hits(cuda_device, delta):
     assert np.all(to_np(res.normal)[~m] == 0)
 
 
-@pytest.mark.parametrize("precision,eps_lo,refine,alpha_r,engine", [
-    ("bf16", 1e-3, 0, 0.0, "tc"), ("fp16", 1e-3, 0, 0.0, "tc"), ("fp16", 1e-4, 1, 0.0, "tc"),
-    ("fp16", 2e-4, 1, 0.0, "tc"), ("bf16", 1e-3, 0, 1.0, "tc"), ("bf16", 3e-4, 0, 1.0, "tc"),
-    ("fp16", 1e-4, 1, 1.0, "tc"), ("bf16", 1e-3, 0, 0.0, "simt"), ("fp16", 1e-4, 1, 0.0, "simt")])
+@pytest.mark.parametrize("precision,eps_lo,refine,alpha_r,engine,rule", [
+    ("bf16", 1e-3, 0, 0.0, "tc", "march"), ("fp16", 1e-3, 0, 0.0, "tc", "march"),
+    ("fp16", 1e-4, 1, 0.0, "tc", "march"), ("fp16", 2e-4, 1, 0.0, "tc", "march"),
+    ("bf16", 1e-3, 0, 1.0, "tc", "march"), ("bf16", 3e-4, 0, 1.0, "tc", "march"),
+    ("fp16", 1e-4, 1, 1.0, "tc", "march"), ("bf16", 1e-3, 0, 0.0, "simt", "march"),
+    ("fp16", 1e-4, 1, 0.0, "simt", "march"), ("bf16", 1e-3, 0, 0.0, "tc", "secant"),
+    ("fp16", 1e-3, 0, 0.0, "tc", "secant"), ("bf16", 3e-3, 0, 0.0, "tc", "secant"),
+    ("bf16", 1e-3, 0, 0.0, "simt", "secant")])
 @pytest.mark.parametrize("size,vp_seed", [(64, 3), (96, 8)])
 def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precision, eps_lo, refine,
-                                            alpha_r, engine):
+                                            alpha_r, engine, rule):
     """Tensor-core marching (BF16 or FP16 operands) until |f| < eps_lo, then
-    FP32-class queries (tensor-core split or CUDA-core FP32): converge to eps = 5e-5 (refine = 0) or accept after
+    FP32-class queries (tensor-core split or CUDA-core FP32; aggressive or
+    secant steps): converge to eps = 5e-5 (refine = 0) or accept after
     `refine` FP32 queries within 4 eps_lo (unit final step).  Depth within
     2e-3 of the FP64 oracle on hits away from the silhouette; masks agree
     except near-silhouette rays."""
@@ -140,7 +145,7 @@ def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precisio
     cam = synth.look_at_camera(synth.random_viewpoints(1, seed=vp_seed)[0], size, size)
     ws = api.Workspace(size * size, 50)
     params = api.TraceParams(precision=precision, eps_bf16=eps_lo, refine_steps=refine,
-                             alpha_refine=alpha_r, refine_engine=engine)
+                             alpha_refine=alpha_r, refine_engine=engine, refine_rule=rule)
     res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), [cam], params, ws)
     assert dec.device_error() == 0
     orc = tracer.render(oracle_sdf(spec, Ws, bs, Z), [cam], record=True)
