@@ -337,21 +337,33 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         split_pack(v, h);
       }
     };
-    // quarter q of GEMM layer g (rows at p): operand words of relu(acc + bias)
+    // quarter q of GEMM layer g (rows at p): operand words of relu(acc + bias).
+    // Layer 3's padding columns 253..255 carry the ray point instead (the
+    // skip layer's GEMM multiplies them by its xyz weights).
     auto hold = [&](int g, const float* bf4, const float3& pp, int q, uint32_t (&h)[16]) {
       uint32_t r[32];
       tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
+      const bool point = g == 2 && 128 * q + cg == 224;
       if (!xt) {
         float v[32];
-        bias32(K, g, bf4, 128 * q + cg, pp, r, v);
+        bias32(K, g, bf4, 128 * q + cg, pp, r, v, false);
 #pragma unroll
         for (int i = 0; i < 16; ++i)
           h[i] = pack16<F16>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+        if (point) {
+          h[14] = pack16<F16>(fmaxf(v[28], 0.f), pp.x);
+          h[15] = pack16<F16>(pp.y, pp.z);
+        }
       } else {
         float m[16], v[16];
         pair_sum16(r, part, m);
-        affine16(K, g, bf4, 128 * q + cg + 16 * part, pp, a.inv_scale[g], m, v);
+        affine16(K, g, bf4, 128 * q + cg + 16 * part, pp, a.inv_scale[g], m, v, false);
+        const float v12 = fmaxf(v[12], 0.f);
         split_pack(v, h);
+        if (point && part == 1) {      // this lane's columns 240..255
+          split_pair(v12, pp.x, h[6], h[14]);
+          split_pair(pp.y, pp.z, h[7], h[15]);
+        }
       }
     };
     // head term of the 32-column chunk of quarter q of the last layer (tile
@@ -413,13 +425,23 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       if (!wait_acc(0)) { ok = false; break; }
       head += head_q(cur_xt, bf4, cur_p, 0);
       head += head_q(cur_xt, bf4, cur_p, 1);
-      if (!wait_acc(1)) { ok = false; break; }
       // from here on xt/j/p/shape describe the next tile's rows (layer 0 in
-      // its format); quarter q's layer 0 is released once this tile's
-      // quarter q has been read from TMEM
-      if (has_next) load_rows(next);
-      for (int q = 0; q < 4; ++q) {
-        if (q >= 2) head += head_q(cur_xt, bf4, cur_p, q);
+      // its format); quarter q is released once this tile's quarter q has
+      // been read from TMEM.  (Computing quarters 0-1 of it before acc_full[1]
+      // needs 32 more live registers than the 96 a thread has and spills.)
+      if (!wait_acc(1)) { ok = false; break; }
+      if (has_next) {
+        load_rows(next);
+        uint32_t n0h[16];
+        layer0(0, n0h);
+        put(0, n0h);
+        release(0);
+        layer0(1, n0h);
+        put(1, n0h);
+        release(1);
+      }
+      for (int q = 2; q < 4; ++q) {
+        head += head_q(cur_xt, bf4, cur_p, q);
         if (has_next) {
           uint32_t h[16];
           layer0(q, h);
@@ -871,6 +893,13 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
 
 }  // namespace
 
+// Source column in W_l of GEMM column k: the skip layer's GEMM runs over its
+// 253 h columns and, in the three padding columns 253..255, its xyz columns,
+// so that with the ray point written into those operand columns the tensor
+// cores add W_xyz p.  (The adjoint writes zeros there and adds W_xyz p in its
+// epilogue; the transposed copy's extra rows meet a zero ReLU mask.)
+static int skip_col(int l, int k) { return (l == 4 && k >= 253) ? 253 + 256 + (k - 253) : k; }
+
 // Weights of GEMM layers 1..7 as [N rows][2K cols] fp16: columns 0..K-1 hold
 // W_hi, K..2K-1 hold W_lo, both of W * 2^s_l.
 dist_status pack_tcx(dist_decoder* d, const float* const* W) {
@@ -881,11 +910,12 @@ dist_status pack_tcx(dist_decoder* d, const float* const* W) {
     const int l = g + 1;
     const int N = gemm_n(g), K = gemm_k(g);
     const int n_real = (l == 3) ? Hh : 512;
-    const int k_real = (l == 4) ? Hh : 512;
+    const int k_real = (l == 4) ? Hh + 3 : 512;
     const int in_dim = (l == 4) ? Hh + L + 3 : 512;
     float amax = 0.f;
     for (int nn = 0; nn < n_real; ++nn)
-      for (int k = 0; k < k_real; ++k) amax = std::fmax(amax, std::fabs(W[l][(size_t)nn * in_dim + k]));
+      for (int k = 0; k < k_real; ++k)
+        amax = std::fmax(amax, std::fabs(W[l][(size_t)nn * in_dim + skip_col(l, k)]));
     // largest power of two with amax * 2^s <= 2^14
     int s = 0;
     if (amax > 0.f) s = (int)std::floor(std::log2(16384.0 / (double)amax));
@@ -895,7 +925,7 @@ dist_status pack_tcx(dist_decoder* d, const float* const* W) {
     std::vector<uint16_t> h((size_t)N * 2 * K, 0);
     for (int nn = 0; nn < n_real; ++nn)
       for (int k = 0; k < k_real; ++k) {
-        const float w = W[l][(size_t)nn * in_dim + k] * scale;
+        const float w = W[l][(size_t)nn * in_dim + skip_col(l, k)] * scale;
         const __half hi = __float2half_rn(w);
         const __half lo = __float2half_rn(w - __half2float(hi));
         h[(size_t)nn * 2 * K + k] = *reinterpret_cast<const uint16_t*>(&hi);
@@ -960,11 +990,11 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
       const int N = gemm_n(g), K = gemm_k(g);
       std::vector<uint16_t> h((size_t)N * K, 0);   // +0 in both formats
       const int n_real = (l == 3) ? Hh : 512;
-      const int k_real = (l == 4) ? Hh : 512;
+      const int k_real = (l == 4) ? Hh + 3 : 512;
       const int in_dim = (l == 4) ? Hh + L + 3 : 512;
       for (int n = 0; n < n_real; ++n)
         for (int k = 0; k < k_real; ++k) {
-          const float w = W[l][(size_t)n * in_dim + k];
+          const float w = W[l][(size_t)n * in_dim + skip_col(l, k)];
           if (f16) {
             __half v = __float2half_rn(w);
             h[(size_t)n * K + k] = *reinterpret_cast<uint16_t*>(&v);

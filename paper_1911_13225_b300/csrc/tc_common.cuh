@@ -360,12 +360,23 @@ __device__ __forceinline__ void layer0_32(const TCConst* K, const float* bf, int
   }
 }
 
-// v = accumulator + bias of GEMM layer g (the skip layer: folded bias +
-// Wx4 p), columns c..c+W-1.
+// v = accumulator + bias of GEMM layer g (the skip layer: folded bias, plus
+// Wx4 p when `xyz`; the forward kernel has the tensor cores add Wx4 p),
+// columns c..c+W-1.
 template <int W>
 __device__ __forceinline__ void bias_cols(const TCConst* K, int g, const float* bf4, int c,
-                                          const float3& p, const uint32_t (&r)[W], float (&v)[W]) {
-  if (g == 3) {
+                                          const float3& p, const uint32_t (&r)[W], float (&v)[W],
+                                          bool xyz = true) {
+  if (g == 3 && !xyz) {
+#pragma unroll
+    for (int i = 0; i < W; i += 4) {
+      const float4 b = ldg4(bf4 + c + i);
+      v[i + 0] = __uint_as_float(r[i + 0]) + b.x;
+      v[i + 1] = __uint_as_float(r[i + 1]) + b.y;
+      v[i + 2] = __uint_as_float(r[i + 2]) + b.z;
+      v[i + 3] = __uint_as_float(r[i + 3]) + b.w;
+    }
+  } else if (g == 3) {
 #pragma unroll
     for (int i = 0; i < W; i += 4) {
       const float4 b = ldg4(bf4 + c + i);
@@ -390,8 +401,9 @@ __device__ __forceinline__ void bias_cols(const TCConst* K, int g, const float* 
   }
 }
 __device__ __forceinline__ void bias32(const TCConst* K, int g, const float* bf4, int c,
-                                       const float3& p, const uint32_t (&r)[32], float (&v)[32]) {
-  bias_cols<32>(K, g, bf4, c, p, r, v);
+                                       const float3& p, const uint32_t (&r)[32], float (&v)[32],
+                                       bool xyz = true) {
+  bias_cols<32>(K, g, bf4, c, p, r, v, xyz);
 }
 __device__ __forceinline__ void bias16(const TCConst* K, int g, const float* bf4, int c,
                                        const float3& p, const uint32_t (&r)[16], float (&v)[16]) {
@@ -409,12 +421,21 @@ __device__ __forceinline__ float head32(const TCConst* K, int c, const float (&v
 
 // ---- FP32-class (two-term FP16 split) epilogue pieces
 
-// v = m * scale + bias of GEMM layer g (the skip layer: folded bias + Wx4 p),
-// 16 columns from c.
+// v = m * scale + bias of GEMM layer g (the skip layer: folded bias, plus
+// Wx4 p when `xyz`), 16 columns from c.
 __device__ __forceinline__ void affine16(const TCConst* K, int g, const float* bf4, int c,
                                          const float3& p, float scale, const float (&m)[16],
-                                         float (&v)[16]) {
-  if (g == 3) {
+                                         float (&v)[16], bool xyz = true) {
+  if (g == 3 && !xyz) {
+#pragma unroll
+    for (int i = 0; i < 16; i += 4) {
+      const float4 b = ldg4(bf4 + c + i);
+      v[i + 0] = fmaf(m[i + 0], scale, b.x);
+      v[i + 1] = fmaf(m[i + 1], scale, b.y);
+      v[i + 2] = fmaf(m[i + 2], scale, b.z);
+      v[i + 3] = fmaf(m[i + 3], scale, b.w);
+    }
+  } else if (g == 3) {
 #pragma unroll
     for (int i = 0; i < 16; i += 4) {
       const float4 b = ldg4(bf4 + c + i);
@@ -469,6 +490,16 @@ __device__ __forceinline__ void relu_split16(float (&v)[16], uint32_t (&hi)[8], 
     hi[i / 2] = *reinterpret_cast<const uint32_t*>(&h);
     lo[i / 2] = *reinterpret_cast<const uint32_t*>(&l);
   }
+}
+
+// The two-term FP16 split of a pair without ReLU (operand columns that carry
+// the ray point).
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(a, b);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(a - hf.x, b - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
 // Sum of the hi-row and lo-row accumulators of one query for the 16 columns

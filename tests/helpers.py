@@ -51,9 +51,9 @@ def lowp_decoder_reference(Ws, bs, Z, pts, shape, precision, latent=256, skip=4)
 def bf16_decoder_reference(Ws, bs, Z, pts, shape, latent=256, skip=4, rnd=None):
     """The DeepSDF decoder evaluated the way the BF16 tensor-core kernel does:
     GEMM layers 1..7 with bf16-rounded weights and bf16-rounded input
-    activations (fp64 accumulation), layer 0, the skip layer's xyz columns,
-    the folded latent biases and the head in full precision.  ``rnd``
-    replaces the bf16 rounding (e.g. by fp16)."""
+    activations (fp64 accumulation; the skip layer's xyz term through the
+    same rounded GEMM), layer 0, the folded latent biases and the head in
+    full precision.  ``rnd`` replaces the bf16 rounding (e.g. by fp16)."""
     bf16_round_ = rnd or bf16_round
     W = [np.asarray(w, dtype=np.float64) for w in Ws]
     b = [np.asarray(v, dtype=np.float64) for v in bs]
@@ -66,7 +66,10 @@ def bf16_decoder_reference(Ws, bs, Z, pts, shape, latent=256, skip=4, rnd=None):
     for l in range(1, len(W) - 1):
         hb = bf16_round_(h)
         if l == skip:
-            a = hb @ bf16_round_(W[l][:, :hk]).T + p @ W[l][:, hk + latent:].T + bs_
+            # the kernel's skip-layer GEMM also runs over the point (the
+            # operand's padding columns), rounded like the activations
+            a = hb @ bf16_round_(W[l][:, :hk]).T + \
+                bf16_round_(p) @ bf16_round_(W[l][:, hk + latent:]).T + bs_
         else:
             a = hb @ bf16_round_(W[l]).T + b[l]
         h = np.maximum(a, 0.0)
