@@ -345,13 +345,20 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
       const bool point = g == 2 && 128 * q + cg == 224;
       if (!xt) {
-        float v[32];
-        bias32(K, g, bf4, 128 * q + cg, pp, r, v, false);
+        // bias, ReLU and packing in place, 4 columns at a time (keeps the
+        // live registers to the accumulator words and the packed result)
+        const float* bias = g == 3 ? bf4 : K->bias[g];
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          h[i] = pack16<F16>(fmaxf(v[2 * i], 0.f), fmaxf(v[2 * i + 1], 0.f));
+        for (int i = 0; i < 32; i += 4) {
+          const float4 b = ldg4(bias + 128 * q + cg + i);
+          h[i / 2] = pack16<F16>(fmaxf(__uint_as_float(r[i]) + b.x, 0.f),
+                                 fmaxf(__uint_as_float(r[i + 1]) + b.y, 0.f));
+          h[i / 2 + 1] = pack16<F16>(fmaxf(__uint_as_float(r[i + 2]) + b.z, 0.f),
+                                     fmaxf(__uint_as_float(r[i + 3]) + b.w, 0.f));
+        }
         if (point) {
-          h[14] = pack16<F16>(fmaxf(v[28], 0.f), pp.x);
+          const float b28 = __ldg(K->bias[g] + 252);
+          h[14] = pack16<F16>(fmaxf(__uint_as_float(r[28]) + b28, 0.f), pp.x);
           h[15] = pack16<F16>(pp.y, pp.z);
         }
       } else {
@@ -426,18 +433,20 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       head += head_q(cur_xt, bf4, cur_p, 0);
       head += head_q(cur_xt, bf4, cur_p, 1);
       // from here on xt/j/p/shape describe the next tile's rows (layer 0 in
-      // its format); quarter q is released once this tile's quarter q has
-      // been read from TMEM.  (Computing quarters 0-1 of it before acc_full[1]
-      // needs 32 more live registers than the 96 a thread has and spills.)
-      if (!wait_acc(1)) { ok = false; break; }
+      // its format): quarters 0 and 1 of it are computed while the tensor
+      // core finishes this layer; quarter q is released once this tile's
+      // quarter q has been read from TMEM
+      uint32_t n0h[16], n1h[16];
       if (has_next) {
         load_rows(next);
-        uint32_t n0h[16];
         layer0(0, n0h);
+        layer0(1, n1h);
+      }
+      if (!wait_acc(1)) { ok = false; break; }
+      if (has_next) {
         put(0, n0h);
         release(0);
-        layer0(1, n0h);
-        put(1, n0h);
+        put(1, n1h);
         release(1);
       }
       for (int q = 2; q < 4; ++q) {
