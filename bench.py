@@ -41,6 +41,21 @@ WORKLOAD = ("DeepSDF-shaped decoder 8x512 (latent 256, skip@4, ReLU, tanh), geom
             "alpha 1.5, exact implicit latent gradient")
 
 
+def max_over_ranks(values, device):
+    """Element-wise maximum of `values` over all ranks of the default process
+    group (the slowest rank's time is the job's time)."""
+    import torch
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def job_rate(units_per_rank_step, world, steps, max_total_ms):
+    """Whole-job throughput: the units every rank processed over `steps`,
+    divided by the slowest rank's time."""
+    return units_per_rank_step * world * steps / (max_total_ms * 1e-3)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -232,15 +247,13 @@ def run_ours(args, rank, world, local_rank):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
     if world > 1:
-        t = torch.tensor([total_ms, e2e_s], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms, e2e_s = float(t[0]), float(t[1])
+        total_ms, e2e_s = max_over_ranks([total_ms, e2e_s], dev)
     if rank != 0:
         return None
 
     ms_per_step = total_ms / args.steps
     rays = SIZE * SIZE
-    value = rays * world * args.steps / (total_ms * 1e-3)
+    value = job_rate(rays, world, args.steps, total_ms)
     peaks, peak_src = load_peaks()
     if precision in ("bf16", "fp16"):
         k_ms, k_q, k_n = ms_arr[0], queries[0], cnt_arr[0]
