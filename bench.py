@@ -4,9 +4,10 @@
 A step is the whole hot path once over a 512x512 image of the DeepSDF-shaped
 decoder (8 hidden layers of 512, latent 256, skip at layer 4): ray generation
 with unit-sphere initialisation, up to 50 march iterations (active-ray
-compaction, decoder queries, converge/step), depth / silhouette / normals,
-the L1 depth loss against a depth map rendered from a second seeded latent,
-and the latent gradient (exact implicit adjoint, FP64 reductions).
+compaction, decoder queries, converge/step), depth / silhouette / mask, the
+L1 depth loss against a depth map rendered from a second seeded latent, and
+the latent gradient (exact implicit adjoint, FP64 reductions).  Normals are
+rendered only with --normals (the L1 depth loss does not use them).
 
 Prints one JSON line.  ``--impl reference`` times the FP64 CPU oracle on a
 bounded crop of the same workload instead.
@@ -130,7 +131,7 @@ class ClockSampler:
 class Step:
     """Preallocated buffers and C structs for one fwd+bwd step through the C ABI."""
 
-    def __init__(self, api, dec, ws, cam, params, z, tgt_depth):
+    def __init__(self, api, dec, ws, cam, params, z, tgt_depth, normals=False):
         import torch
         from ctypes import byref, c_void_p
         from paper_1911_13225_b300 import _abi
@@ -139,7 +140,7 @@ class Step:
         self.z = z
         self.tgt = tgt_depth
         n = SIZE * SIZE
-        self.res = api.alloc_result(n, params.k_min, z.device, normals=True)
+        self.res = api.alloc_result(n, params.k_min, z.device, normals=normals)
         dev = z.device
         self.g_depth = torch.empty(n, device=dev)
         self.dz = torch.zeros_like(z)
@@ -188,7 +189,7 @@ def run_ours(args, rank, world, local_rank):
     # target: depth of the second latent (untimed setup)
     tgt = api.trace(dec, z, [dict(cam, shape=1)], params, ws).depth.clone()
     stream = torch.cuda.current_stream()
-    step = Step(api, dec, ws, cam, params, z, tgt)
+    step = Step(api, dec, ws, cam, params, z, tgt, normals=args.normals)
     flush = torch.empty(256 * 1024 * 1024 // 4, device=dev)
 
     for _ in range(args.warmup):
@@ -315,6 +316,8 @@ def run_ours(args, rank, world, local_rank):
                    "rays_per_step": rays, "precision": precision,
                    "eps_lo": args.eps_lo, "refine_steps": args.refine,
                    "refine_engine": args.refine_engine, "refine_rule": args.refine_rule,
+                   "normals": "rendered (analytic, adjoint at the hits)" if args.normals
+                              else "not rendered (unused by the L1 depth loss)",
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MB write, untimed)"},
         "sdf_queries_per_s": float(queries.sum()) * world / (total_ms * 1e-3),
@@ -514,16 +517,25 @@ def _blas_threads():
         return os.cpu_count() or 1
 
 
-def oracle_step(spec, Ws, bs, Z, cam):
+def oracle_sdf(spec, Ws, bs, Z):
+    from oracle.mlp import from_synth
+    from oracle.sdf import MLPSDF
+    return MLPSDF(from_synth(Ws, bs, spec), Z.astype(np.float64))
+
+
+def oracle_target(sdf, cam):
+    """The L1 target: depth of the second latent (rendered once, untimed)."""
+    from oracle import tracer
+    return tracer.render(sdf, [dict(cam, shape=1)], max_steps=MAX_STEPS, with_normals=False)["depth"]
+
+
+def oracle_step(spec, sdf, cam, tgt_depth):
+    """The oracle's step on `cam`: forward render, L1 loss, exact latent gradient."""
     from oracle import tracer
     from oracle.grad import latent_vjp
     from oracle.loss import loss_terms
-    from oracle.mlp import from_synth
-    from oracle.sdf import MLPSDF
-    sdf = MLPSDF(from_synth(Ws, bs, spec), Z.astype(np.float64))
-    out = tracer.render(sdf, [cam], max_steps=MAX_STEPS)
-    tgt = tracer.render(sdf, [dict(cam, shape=1)], max_steps=MAX_STEPS, with_normals=False)
-    L, gd, _, _ = loss_terms(out, {"depth": tgt["depth"]})
+    out = tracer.render(sdf, [cam], max_steps=MAX_STEPS, with_normals=False)
+    L, gd, _, _ = loss_terms(out, {"depth": tgt_depth})
     G = latent_vjp(sdf, out, 2, spec.latent_dim, g_depth=gd)
     return L, G
 
@@ -533,14 +545,16 @@ def cpu_baseline(crop):
     spec = synth.DEEPSDF_SPEC
     Ws, bs, Z, cam = make_workload(spec)
     c = _crop_camera(cam, crop)
+    sdf = oracle_sdf(spec, Ws, bs, Z)
+    tgt = oracle_target(sdf, c)
     t0 = time.perf_counter()
-    oracle_step(spec, Ws, bs, Z, c)
+    oracle_step(spec, sdf, c, tgt)
     dt = time.perf_counter() - t0
     return {"value": crop * crop / dt, "unit": "rays/s", "cores": _blas_threads(),
             "kind": "oracle",
             "sample": f"central {crop}x{crop} crop of the 512x512 view (same decoder, latents, "
-                      f"camera); forward + target render + L1 loss + exact latent gradient; "
-                      f"{dt:.1f} s wall"}
+                      f"camera, target rendered beforehand); forward + L1 loss + exact latent "
+                      f"gradient; {dt:.1f} s wall"}
 
 
 def run_reference(args):
@@ -548,11 +562,13 @@ def run_reference(args):
     spec = synth.DEEPSDF_SPEC
     Ws, bs, Z, cam = make_workload(spec)
     c = _crop_camera(cam, args.ref_crop)
+    sdf = oracle_sdf(spec, Ws, bs, Z)
+    tgt = oracle_target(sdf, c)
     for _ in range(args.warmup):
-        oracle_step(spec, Ws, bs, Z, c)
+        oracle_step(spec, sdf, c, tgt)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle_step(spec, Ws, bs, Z, c)
+        oracle_step(spec, sdf, c, tgt)
     dt = time.perf_counter() - t0
     v = args.ref_crop ** 2 * args.steps / dt
     return {
@@ -591,6 +607,8 @@ def main():
     ap.add_argument("--cpu-crop", type=int, default=96)
     ap.add_argument("--ref-crop", type=int, default=48)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--normals", action="store_true",
+                    help="also render analytic normals in the forward pass")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-load", type=float, default=0.8,
