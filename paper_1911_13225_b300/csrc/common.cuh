@@ -255,6 +255,10 @@ cudaError_t pool_raygen(const RayPool& P, int cam, long long pix0, long long n, 
                         int* count0, cudaStream_t st);
 cudaError_t pool_step(const RayPool& P, const int* cnt_in, int* cnt_out, int* const in[2],
                       const float* const f[2], int* const out[2], cudaStream_t st);
+struct StepFuse;
+
+// The same step update, applied by the fused decoder kernel (StepFuse).
+void pool_step_fuse(const RayPool& P, int* cnt_out, int* const out[2], StepFuse* sf);
 cudaError_t pool_probes_depth(const RayPool& P, int cam, long long pix0, long long n,
                               const float* g_depth, float4* pp, float4* pq, int* pix, int* count,
                               cudaStream_t st);
@@ -275,9 +279,12 @@ cudaError_t mlp_tcx_forward(const dist_decoder* dec, const RowSrc& src, const fl
 
 // Both in one launch: src16 with 16-bit operands into f16out, srcx
 // FP32-class into fxout (either list may be empty: count null, n_rows 0).
+// With `step` (rays mode only) the kernel applies the march step update to
+// each queried ray instead of writing f: see StepFuse.
 cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f16out,
                          const RowSrc& srcx, float* fxout, const float* bfold0,
-                         const float* bfolds, cudaStream_t st, bool f16);
+                         const float* bfolds, cudaStream_t st, bool f16,
+                         const StepFuse* step = nullptr);
 
 // tcgen05 decoder adjoint over probes (same contract as mlp_fp32_adjoint;
 // `scratch` holds num_sms() * kTcAdjScratchPerCta bytes).

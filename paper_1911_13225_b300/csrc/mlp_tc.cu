@@ -35,8 +35,10 @@
 // which leaves a systematic error of ~2e-6 in f.  The small W_lo pass runs
 // first so that only the W_hi pass adds into a large accumulator.
 #include <cmath>
+#include <cstring>
 #include <vector>
 
+#include "step.cuh"
 #include "tc_common.cuh"
 
 namespace dist {
@@ -55,6 +57,8 @@ struct TCArgs {
   float* fout[2];
   int* err;
   float inv_scale[NUM_GEMM];     // list 1: 2^-s_l of GEMM layer g
+  int fuse_step;                 // apply `step` to each row instead of writing f
+  StepFuse step;
 };
 
 constexpr int QPT_X = 64;        // FP32-class queries per tile
@@ -93,6 +97,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   constexpr int NST = PAIR ? 2 * STAGES : STAGES;            // weight ring stages
   constexpr int SB = PAIR ? STAGE_BYTES / 2 : STAGE_BYTES;   // bytes per stage per CTA
   constexpr int MUL = PAIR ? 2 : 1;                          // CTAs per tile
+  static_assert((2 * NST + 10) * 8 + 8 <= BAR_BYTES, "barrier block");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -105,7 +110,9 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   uint64_t* act_full = bars + 2 * NST + 2;   // [4] epilogue -> MMA, per K quarter
   uint64_t* drain = bars + 2 * NST + 6;      // final MMA completion
   uint64_t* head_bar = bars + 2 * NST + 7;   // head partial sums -> column group 0
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 8);
+  uint64_t* step_full = bars + 2 * NST + 8;  // f of a tile's rows -> step warps
+  uint64_t* step_empty = bars + 2 * NST + 9; // step warps have read them
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * NST + 10);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* head_part = reinterpret_cast<float*>(smem + ACT_BYTES + NST * SB + BAR_BYTES);
 
@@ -119,6 +126,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   const int t1 = (n1 + MUL * QPT_X - 1) / (MUL * QPT_X);   // FP32-class tiles: [0, t1)
   const int n_tiles = t1 + (n0 + MUL * BM - 1) / (MUL * BM);
   if (pid >= n_tiles) return;                               // uniform over a pair
+  if (a.fuse_step && a.step.queries && pid == 0 && rank == 0 && threadIdx.x == 0) {
+    atomicAdd(a.step.queries + 0, (unsigned long long)n0);
+    atomicAdd(a.step.queries + 1, (unsigned long long)n1);
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -129,6 +140,8 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     for (int q = 0; q < 4; ++q) mbar_init(act_full + q, MUL * FWD_EPI);
     mbar_init(drain, 1);
     mbar_init(head_bar, (FWD_EPI - 4) * 32);
+    mbar_init(step_full, 4);
+    mbar_init(step_empty, FWD_STEP_WARPS);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -245,6 +258,49 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     if (lane == 0) {
       const unsigned long long t0 = globaltimer();
       while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
+      }
+    }
+  } else if (warp >= 2 + FWD_EPI) {
+    // ----------------------------------------------------- march step
+    // With a fused step, thread s applies the step update to rows s, s + 64
+    // of each of this CTA's tiles once column group 0 has put their f in
+    // head_part (the step update is off the decoder's critical path).
+    if (a.fuse_step) {
+      constexpr int SW = FWD_STEP_WARPS * 32;
+      constexpr int RPT = BM / SW;   // rows per step thread
+      const int s = threadIdx.x - (2 + FWD_EPI) * 32;
+      uint32_t sphase = 0;
+      for (int t = pid; t < n_tiles; t += npid) {
+        const bool xt = t < t1;
+        const int list = xt ? 1 : 0;
+        const int j0 = xt ? (t * MUL + rank) * QPT_X : ((t - t1) * MUL + rank) * BM;
+        const int rows = xt ? QPT_X : BM;
+        const int n = xt ? n1 : n0;
+        if (!mbar_wait(step_full, sphase, abort_flag)) {
+          *abort_flag = 1;
+          atomicOr(a.err, 4);
+          break;
+        }
+        sphase ^= 1u;
+        float f[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) f[k] = head_part[s + k * SW];
+        __syncwarp();
+        if (lane == 0) mbar_arrive(step_empty);
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const int r = s + k * SW;
+          const int j = j0 + r;
+          int keep = -1, ray = 0;
+          if (r < rows && j < n) {
+            ray = a.src[list].idx[j];
+            keep = step_ray(a.step.t, list, ray, f[k]);
+          }
+          const int s0 = warp_append(keep == 0, a.step.cnt_out[0]);
+          const int s1 = warp_append(keep == 1, a.step.cnt_out[1]);
+          if (s0 >= 0) a.step.out[0][s0] = ray;
+          if (s1 >= 0) a.step.out[1][s1] = ray;
+        }
       }
     }
   } else {
@@ -382,6 +438,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       return head_chunk_sum<F16>(K, kx, bf4, pp, 128 * q + cg, part, a.inv_scale[NUM_GEMM - 1], r);
     };
 
+    uint32_t step_phase = 0;   // column group 1: step_empty parity
     int tile = pid;
     load_rows(tile);
     for (int q = 0; q < 4; ++q) {
@@ -464,14 +521,29 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       // layers, which group 0 takes part in, so one phase per tile suffices)
       const int hr = cur_xt ? jr : row;
       if (grp > 0) {
+        // with a fused step, head_part[0..BM) carries the previous tile's f
+        // to the step warps: group 1 overwrites it once they have read it
+        if (a.fuse_step && grp == 1 && tile != pid) {
+          if (!mbar_wait(step_empty, step_phase, abort_flag)) { ok = false; break; }
+          step_phase ^= 1u;
+        }
         head_part[(grp - 1) * BM + hr] = head;
         mbar_arrive(head_bar);
       } else {
         if (!mbar_wait(head_bar, head_phase, abort_flag)) { ok = false; break; }
 #pragma unroll
         for (int q = 0; q < FWD_GRPS - 1; ++q) head += head_part[q * BM + hr];
-        if (cur_valid && (!cur_xt || part == 0))
+        const bool mine = cur_valid && (!cur_xt || part == 0);
+        if (a.fuse_step) {
+          // f to the step warps (rows past the list end included); in an
+          // FP32-class tile both lanes of a query read slot hr above
+          __syncwarp();
+          if (!cur_xt || part == 0) head_part[hr] = tanhf(head + __ldg(&K->b_head));
+          __syncwarp();
+          if (lane == 0) mbar_arrive(step_full);
+        } else if (mine) {
           a.fout[cur_xt ? 1 : 0][cur_j] = tanhf(head + __ldg(&K->b_head));
+        }
       }
       head_phase ^= 1u;
     }
@@ -1100,7 +1172,8 @@ cudaError_t launch_fused(const dist_decoder* dec, const TCArgs& a, cudaStream_t 
 
 cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f16out,
                          const RowSrc& srcx, float* fxout, const float* bfold0,
-                         const float* bfolds, cudaStream_t st, bool f16) {
+                         const float* bfolds, cudaStream_t st, bool f16,
+                         const StepFuse* step) {
   if (!dec->tc.ok) return cudaErrorNotSupported;
   TCArgs a;
   a.K = dec->tc.cst;
@@ -1112,6 +1185,9 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
   a.fout[1] = fxout;
   a.err = dec->tc.err;
   for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
+  a.fuse_step = step ? 1 : 0;
+  if (step) a.step = *step;
+  else memset(&a.step, 0, sizeof(a.step));
   if (dec->tc.pair)
     return f16 ? launch_fused<true, true>(dec, a, st) : launch_fused<false, true>(dec, a, st);
   return f16 ? launch_fused<true, false>(dec, a, st) : launch_fused<false, false>(dec, a, st);

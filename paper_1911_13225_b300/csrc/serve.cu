@@ -23,7 +23,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "common.cuh"
+#include "step.cuh"
 
 namespace dist {
 namespace {
@@ -213,12 +213,17 @@ struct dist_server {
     RowSrc sx = src;
     sx.count = cnt + 2 * par + 1;
     sx.idx = act[par][1];
+    int* out[2] = {act[par ^ 1][0], act[par ^ 1][1]};
+    DIST_CUDA_TRY(cudaMemsetAsync(cnt + 2 * (par ^ 1), 0, 2 * sizeof(int), st));
     if (fp32_on_tc(p)) {
-      // both lists in one launch (an empty 16-bit list for FP32_TC)
+      // both lists in one launch (an empty 16-bit list for FP32_TC), which
+      // also applies the step update
       src.count = cnt + 2 * par;
       src.idx = act[par][0];
+      StepFuse sf;
+      pool_step_fuse(P, cnt + 2 * (par ^ 1), out, &sf);
       DIST_CUDA_TRY(mlp_tc_fused(dec, src, fbuf[0], sx, fbuf[1], b0, bs, st,
-                                 p.precision == DIST_PREC_FP16));
+                                 p.precision == DIST_PREC_FP16, &sf));
     } else {
       if (is_tc(p.precision)) {
         src.count = cnt + 2 * par;
@@ -227,12 +232,10 @@ struct dist_server {
                                      p.precision == DIST_PREC_FP16));
       }
       DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, sx, b0, bs, fbuf[1], st, is_tc(p.precision)));
+      int* in[2] = {act[par][0], act[par][1]};
+      const float* f[2] = {fbuf[0], fbuf[1]};
+      DIST_CUDA_TRY(pool_step(P, cnt + 2 * par, cnt + 2 * (par ^ 1), in, f, out, st));
     }
-    DIST_CUDA_TRY(cudaMemsetAsync(cnt + 2 * (par ^ 1), 0, 2 * sizeof(int), st));
-    int* in[2] = {act[par][0], act[par][1]};
-    const float* f[2] = {fbuf[0], fbuf[1]};
-    int* out[2] = {act[par ^ 1][0], act[par ^ 1][1]};
-    DIST_CUDA_TRY(pool_step(P, cnt + 2 * par, cnt + 2 * (par ^ 1), in, f, out, st));
     par ^= 1;
     DIST_CUDA_TRY(cudaMemsetAsync(slot_active, 0, max_req * sizeof(int), st));
     count_slots_kernel<<<num_sms(), 256, max_req * sizeof(int), st>>>(

@@ -1,0 +1,143 @@
+// Internal: the per-ray step/converge update of the march (Alg. 1, Sec. 3.2,
+// Eq. 1), shared by the step kernel and the decoder kernel's epilogue.
+#pragma once
+
+#include "common.cuh"
+
+namespace dist {
+
+constexpr float kInf = __builtin_huge_valf();
+
+struct TraceArgs {
+  const CamDev* cams;
+  int n_cams;
+  long long n_pix;
+  long long pix0;       // first pixel index handled (0 for a whole batch)
+  int cam_fixed;        // >= 0: every pixel belongs to this camera
+  float radius;
+  int K;
+  float eps, alpha, eps_bf16;
+  int max_steps;
+  float alpha_fp32;     // step factor of FP32-list rays
+  int refine;           // refine_steps for a tensor-core march, else 0
+  int secant;           // secant rule for FP32-list rays of a tensor-core march
+  dist_trace_out o;
+  float4* st;
+  float4* dir;
+  int* fq;              // FP32 queries per ray after the low-precision phase
+  float* fprev;         // previous low-precision sample (then FP32-class, secant)
+  float* dprev;         // distance of the previous FP32-class sample (secant)
+};
+
+// The step update applied by the decoder kernel itself: the thread that
+// computes a ray's f updates the ray and appends it to the next step's list.
+struct StepFuse {
+  TraceArgs t;
+  int* out[2];                   // next step's lists (0: 16-bit, 1: FP32-class)
+  int* cnt_out[2];               // their append counters
+  unsigned long long* queries;   // per-list query counters, or null
+};
+
+__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+
+// Warp-aggregated append over the lanes in `active`: one atomic per warp.
+__device__ __forceinline__ int warp_append(bool pred, int* counter,
+                                           unsigned active = 0xffffffffu) {
+  const unsigned m = __ballot_sync(active, pred);
+  if (m == 0) return -1;
+  const int leader = __ffs(m) - 1;
+  int base = 0;
+  if (lane_id() == leader) base = atomicAdd(counter, __popc(m));
+  base = __shfl_sync(active, base, leader);
+  return pred ? base + __popc(m & ((1u << lane_id()) - 1u)) : -1;
+}
+
+// One query's update of ray i (list 0: low-precision, 1: FP32 / FP32-class)
+// with decoder value f: step count, the k smallest |f| (silhouette and the
+// paper's gradient), hand-over, convergence (|f| < eps: hit at the unit final
+// step d + f), the aggressive step d += alpha f, leaving the bounding sphere
+// and the step budget.  Returns the list the ray continues in, or -1.
+__device__ __forceinline__ int step_ray(const TraceArgs& a, int list, int i, float f) {
+  int keep = -1;
+  float4 s = a.st[i];
+  const float d = s.x;
+  const int steps = a.o.steps[i] + 1;
+  a.o.steps[i] = steps;
+  const float af = fabsf(f);
+  const float track = list == 0 ? fmaxf(af, a.eps) : af;
+  // k smallest |f|, ascending
+  float* fm = a.o.f_min + (size_t)i * a.K;
+  float* dm = a.o.d_min + (size_t)i * a.K;
+  {
+    float cf = copysignf(track, f), cd = d;
+    for (int k = 0; k < a.K; ++k) {
+      const float ok = fm[k];
+      if (fabsf(cf) < fabsf(ok)) {
+        const float od = dm[k];
+        fm[k] = cf; dm[k] = cd;
+        cf = ok; cd = od;
+      }
+    }
+  }
+  int outcome = -1;   // -1 keep marching
+  float dn = d;
+  bool accepted = false;
+  int q = 0;
+  if (list == 1 && (a.refine > 0 || a.secant)) {
+    // FP32 refinement after a tensor-core march: after `refine` FP32
+    // queries a ray within 4 eps_bf16 of the surface is accepted
+    q = a.fq[i] + 1;
+    a.fq[i] = q;
+    accepted = a.refine > 0 && q >= a.refine && af >= a.eps && af < 4.f * a.eps_bf16;
+  }
+  bool crossed = false;
+  if (list == 0) {
+    // a low-precision march that steps across the surface close to it
+    // hands over to FP32 even if its noisy |f| never drops below eps_bf16
+    const float fp = a.fprev[i];
+    a.fprev[i] = f;
+    crossed = fp != 0.f && ((fp > 0.f) != (f > 0.f)) && af < 16.f * a.eps_bf16;
+  }
+  if (list == 1 && (af < a.eps || accepted)) {
+    outcome = DIST_RAY_HIT;
+  } else if (list == 0 && (af < a.eps_bf16 || crossed)) {
+    keep = 1;       // switch to FP32 queries at the same point
+  } else {
+    dn = fmaf(list == 1 ? a.alpha_fp32 : a.alpha, f, d);
+    if (list == 1 && a.secant) {
+      // unit step first, then secant steps through the last two samples
+      if (q == 1) {
+        dn = d + f;
+      } else {
+        const float dd = d - a.dprev[i];
+        const float sl = dd != 0.f ? (f - a.fprev[i]) / dd : 0.f;
+        const float stp = sl < -1e-3f ? -f / sl : 0.f;
+        if (sl < -1e-3f && fabsf(stp) <= 8.f * af) dn = d + stp;
+      }
+      a.dprev[i] = d;
+      a.fprev[i] = f;
+    }
+    if (dn > s.z || dn < s.y) outcome = DIST_RAY_LEFT;
+    else keep = list;
+  }
+  if (outcome < 0 && steps >= a.max_steps) { outcome = DIST_RAY_MAX_STEPS; keep = -1; }
+  if (outcome == DIST_RAY_HIT) {
+    const float dh = d + f;
+    a.o.d_hit[i] = dh;
+    a.o.depth[i] = dh * a.dir[i].w;
+    a.o.mask[i] = 1;
+    a.o.sil[i] = accepted ? af - 4.f * a.eps_bf16 : fabsf(fm[0]) - a.eps;
+  } else if (outcome >= 0) {
+    a.o.d_hit[i] = kInf;
+    a.o.depth[i] = kInf;
+    a.o.mask[i] = 0;
+    a.o.sil[i] = fabsf(fm[0]) - a.eps;
+  } else if (keep == list) {
+    s.x = dn;
+    a.st[i] = s;
+  }
+  if (outcome >= 0 && a.o.status) a.o.status[i] = outcome;
+  return keep;
+}
+
+}  // namespace dist

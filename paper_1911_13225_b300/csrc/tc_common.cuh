@@ -26,7 +26,8 @@ constexpr int SMEM_BYTES =
 constexpr unsigned long long kTimeoutNs = 1000000000ull;
 // Forward kernels: 16 epilogue warps, four per TMEM lane quadrant.
 constexpr int FWD_EPI = 16;
-constexpr int FWD_THREADS = 64 + FWD_EPI * 32;
+constexpr int FWD_STEP_WARPS = 2;   // march step update of a tile's rows
+constexpr int FWD_THREADS = 64 + FWD_EPI * 32 + FWD_STEP_WARPS * 32;
 constexpr int FWD_GRPS = FWD_EPI / 4;
 constexpr int FWD_SMEM_BYTES =
     1024 + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES + (FWD_GRPS - 1) * BM * 4;

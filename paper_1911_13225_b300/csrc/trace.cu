@@ -4,27 +4,11 @@
 #include <cmath>
 #include <cstring>
 
-#include "common.cuh"
+#include "step.cuh"
 
 namespace dist {
 
 namespace {
-
-constexpr float kInf = __builtin_huge_valf();
-
-__device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
-
-// Warp-aggregated append: lanes with `pred` get consecutive slots of `list`
-// (one atomic per warp).  Must be called by all 32 lanes.
-__device__ __forceinline__ int warp_append(bool pred, int* counter) {
-  const unsigned m = __ballot_sync(0xffffffffu, pred);
-  if (m == 0) return -1;
-  const int leader = __ffs(m) - 1;
-  int base = 0;
-  if (lane_id() == leader) base = atomicAdd(counter, __popc(m));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  return pred ? base + __popc(m & ((1u << lane_id()) - 1u)) : -1;
-}
 
 // Warp-aggregated append of `k` consecutive slots per lane (k may be 0).
 __device__ __forceinline__ int warp_append_n(int k, int* counter) {
@@ -122,26 +106,6 @@ __global__ void fold_bias_kernel(DecoderF32 d, const float* __restrict__ z, int 
 
 // -------------------------------------------------------------- ray setup
 
-struct TraceArgs {
-  const CamDev* cams;
-  int n_cams;
-  long long n_pix;
-  long long pix0;       // first pixel index handled (0 for a whole batch)
-  int cam_fixed;        // >= 0: every pixel belongs to this camera
-  float radius;
-  int K;
-  float eps, alpha, eps_bf16;
-  int max_steps;
-  float alpha_fp32;     // step factor of FP32-list rays
-  int refine;           // refine_steps for a tensor-core march, else 0
-  int secant;           // secant rule for FP32-list rays of a tensor-core march
-  dist_trace_out o;
-  float4* st;
-  float4* dir;
-  int* fq;              // FP32 queries per ray after the low-precision phase
-  float* fprev;         // previous low-precision sample (then FP32-class, secant)
-  float* dprev;         // distance of the previous FP32-class sample (secant)
-};
 
 // One thread per pixel (Sec. 3.2 "Initialization"): the ray through the
 // pixel centre, its entry/exit distances into the bounding sphere, and the
@@ -241,84 +205,7 @@ __global__ void __launch_bounds__(kStepThreads) step_kernel(TraceArgs a, StepLis
       const int i = L.in[list][jj];
       const float f = L.f[list][jj];
       ray = i;
-      float4 s = a.st[i];
-      const float d = s.x;
-      const int steps = a.o.steps[i] + 1;
-      a.o.steps[i] = steps;
-      const float af = fabsf(f);
-      const float track = list == 0 ? fmaxf(af, a.eps) : af;
-      // k smallest |f|, ascending
-      float* fm = a.o.f_min + (size_t)i * a.K;
-      float* dm = a.o.d_min + (size_t)i * a.K;
-      {
-        float cf = copysignf(track, f), cd = d;
-        for (int k = 0; k < a.K; ++k) {
-          const float ok = fm[k];
-          if (fabsf(cf) < fabsf(ok)) {
-            const float od = dm[k];
-            fm[k] = cf; dm[k] = cd;
-            cf = ok; cd = od;
-          }
-        }
-      }
-      int outcome = -1;   // -1 keep marching
-      float dn = d;
-      bool accepted = false;
-      int q = 0;
-      if (list == 1 && (a.refine > 0 || a.secant)) {
-        // FP32 refinement after a tensor-core march: after `refine` FP32
-        // queries a ray within 4 eps_bf16 of the surface is accepted
-        q = a.fq[i] + 1;
-        a.fq[i] = q;
-        accepted = a.refine > 0 && q >= a.refine && af >= a.eps && af < 4.f * a.eps_bf16;
-      }
-      bool crossed = false;
-      if (list == 0) {
-        // a low-precision march that steps across the surface close to it
-        // hands over to FP32 even if its noisy |f| never drops below eps_bf16
-        const float fp = a.fprev[i];
-        a.fprev[i] = f;
-        crossed = fp != 0.f && ((fp > 0.f) != (f > 0.f)) && af < 16.f * a.eps_bf16;
-      }
-      if (list == 1 && (af < a.eps || accepted)) {
-        outcome = DIST_RAY_HIT;
-      } else if (list == 0 && (af < a.eps_bf16 || crossed)) {
-        keep = 1;       // switch to FP32 queries at the same point
-      } else {
-        dn = fmaf(list == 1 ? a.alpha_fp32 : a.alpha, f, d);
-        if (list == 1 && a.secant) {
-          // unit step first, then secant steps through the last two samples
-          if (q == 1) {
-            dn = d + f;
-          } else {
-            const float dd = d - a.dprev[i];
-            const float sl = dd != 0.f ? (f - a.fprev[i]) / dd : 0.f;
-            const float stp = sl < -1e-3f ? -f / sl : 0.f;
-            if (sl < -1e-3f && fabsf(stp) <= 8.f * af) dn = d + stp;
-          }
-          a.dprev[i] = d;
-          a.fprev[i] = f;
-        }
-        if (dn > s.z || dn < s.y) outcome = DIST_RAY_LEFT;
-        else keep = list;
-      }
-      if (outcome < 0 && steps >= a.max_steps) { outcome = DIST_RAY_MAX_STEPS; keep = -1; }
-      if (outcome == DIST_RAY_HIT) {
-        const float dh = d + f;
-        a.o.d_hit[i] = dh;
-        a.o.depth[i] = dh * a.dir[i].w;
-        a.o.mask[i] = 1;
-        a.o.sil[i] = accepted ? af - 4.f * a.eps_bf16 : fabsf(fm[0]) - a.eps;
-      } else if (outcome >= 0) {
-        a.o.d_hit[i] = kInf;
-        a.o.depth[i] = kInf;
-        a.o.mask[i] = 0;
-        a.o.sil[i] = fabsf(fm[0]) - a.eps;
-      } else if (keep == list) {
-        s.x = dn;
-        a.st[i] = s;
-      }
-      if (outcome >= 0 && a.o.status) a.o.status[i] = outcome;
+      keep = step_ray(a, list, i, f);
     }
     int s0, s1;
     block_append2<kStepThreads / 32>(keep == 0, keep == 1, L.cnt_out[0], L.cnt_out[1], s0, s1);
@@ -856,6 +743,12 @@ cudaError_t pool_step(const RayPool& P, const int* cnt_in, int* cnt_out, int* co
   return cudaGetLastError();
 }
 
+void pool_step_fuse(const RayPool& P, int* cnt_out, int* const out[2], StepFuse* sf) {
+  sf->t = pool_args(P);
+  for (int k = 0; k < 2; ++k) { sf->out[k] = out[k]; sf->cnt_out[k] = cnt_out + k; }
+  sf->queries = P.o.queries;
+}
+
 cudaError_t pool_probes_depth(const RayPool& P, int cam, long long pix0, long long n,
                               const float* g_depth, float4* pp, float4* pq, int* pix, int* count,
                               cudaStream_t st) {
@@ -938,18 +831,16 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
       src.idx = ws->act[par][0];
       sx.count = cB + s;
       sx.idx = ws->act[par][1];
+      // the decoder kernel applies the step update itself
+      StepFuse sf;
+      sf.t = a;
+      sf.out[0] = ws->act[par ^ 1][0]; sf.out[1] = ws->act[par ^ 1][1];
+      sf.cnt_out[0] = cA + s + 1; sf.cnt_out[1] = cB + s + 1;
+      sf.queries = o->queries;
       prof_mlp_begin(st, 0);
       DIST_CUDA_TRY(mlp_tc_fused(dec, src, ws->fbuf[0], sx, ws->fbuf[1], b0, bs, st,
-                                 p->precision == DIST_PREC_FP16));
+                                 p->precision == DIST_PREC_FP16, &sf));
       prof_mlp_end(st);
-      StepLists L;
-      L.cnt_in[0] = cA + s; L.cnt_in[1] = cB + s;
-      L.cnt_out[0] = cA + s + 1; L.cnt_out[1] = cB + s + 1;
-      L.in[0] = ws->act[par][0]; L.in[1] = ws->act[par][1];
-      L.f[0] = ws->fbuf[0]; L.f[1] = ws->fbuf[1];
-      L.out[0] = ws->act[par ^ 1][0]; L.out[1] = ws->act[par ^ 1][1];
-      step_kernel<<<step_grid, kStepThreads, 0, st>>>(a, L, o->queries);
-      DIST_LAUNCH_CHECK();
     }
     if (o->normal) return normals_impl(dec, p, o, o->normal, ws, n_cams, n_pix, st);
     return DIST_OK;
