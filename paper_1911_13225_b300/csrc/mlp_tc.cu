@@ -121,6 +121,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   const int rank = PAIR ? (int)cluster_rank() : 0;          // 0: issues the pair's MMAs
   const int pid = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int npid = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  // launched early behind the previous grid (programmatic dependent
+  // launch): nothing it writes is read before this wait
+  grid_dep_wait();
+  grid_dep_launch();
   const int n0 = rowsrc_count(a.src[0]);
   const int n1 = rowsrc_count(a.src[1]);
   const int t1 = (n1 + MUL * QPT_X - 1) / (MUL * QPT_X);   // FP32-class tiles: [0, t1)
@@ -276,6 +280,17 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         const int j0 = xt ? (t * MUL + rank) * QPT_X : ((t - t1) * MUL + rank) * BM;
         const int rows = xt ? QPT_X : BM;
         const int n = xt ? n1 : n0;
+        // the rows' ray state is read while the tile is being decoded
+        int ray[RPT];
+        bool valid[RPT];
+        RayState rs[RPT];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k) {
+          const int r = s + k * SW;
+          valid[k] = r < rows && j0 + r < n;
+          ray[k] = valid[k] ? a.src[list].idx[j0 + r] : 0;
+          if (valid[k]) load_ray(a.step.t, list, ray[k], rs[k]);
+        }
         if (!mbar_wait(step_full, sphase, abort_flag)) {
           *abort_flag = 1;
           atomicOr(a.err, 4);
@@ -289,17 +304,11 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         if (lane == 0) mbar_arrive(step_empty);
 #pragma unroll
         for (int k = 0; k < RPT; ++k) {
-          const int r = s + k * SW;
-          const int j = j0 + r;
-          int keep = -1, ray = 0;
-          if (r < rows && j < n) {
-            ray = a.src[list].idx[j];
-            keep = step_ray(a.step.t, list, ray, f[k]);
-          }
+          const int keep = valid[k] ? apply_step(a.step.t, list, ray[k], f[k], rs[k]) : -1;
           const int s0 = warp_append(keep == 0, a.step.cnt_out[0]);
           const int s1 = warp_append(keep == 1, a.step.cnt_out[1]);
-          if (s0 >= 0) a.step.out[0][s0] = ray;
-          if (s1 >= 0) a.step.out[1][s1] = ray;
+          if (s0 >= 0) a.step.out[0][s0] = ray[k];
+          if (s1 >= 0) a.step.out[1][s1] = ray[k];
         }
       }
     }
@@ -1157,13 +1166,15 @@ cudaError_t launch_fused(const dist_decoder* dec, const TCArgs& a, cudaStream_t 
   cfg.blockDim = dim3(FWD_THREADS);
   cfg.dynamicSmemBytes = FWD_SMEM_BYTES;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = PAIR ? 2 : 1;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   cudaError_t e = cudaLaunchKernelEx(&cfg, mlp_tc_kernel<F16, PAIR>, maps, xmaps, a);
   count_launch(1);
   if (e != cudaSuccess) return e;

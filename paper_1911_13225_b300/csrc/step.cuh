@@ -52,30 +52,61 @@ __device__ __forceinline__ int warp_append(bool pred, int* counter,
   return pred ? base + __popc(m & ((1u << lane_id()) - 1u)) : -1;
 }
 
+// The per-ray state a step reads: loaded ahead of the query result where
+// the caller can (the fused step), right before it otherwise.
+struct RayState {
+  float4 s;                // (d, t_in, t_out, camera bits)
+  int steps;
+  float fm[kMaxK], dm[kMaxK];
+  int fq;
+  float fprev, dprev, dirw;
+};
+
+__device__ __forceinline__ void load_ray(const TraceArgs& a, int list, int i, RayState& r) {
+  r.s = a.st[i];
+  r.steps = a.o.steps[i];
+  const float* fm = a.o.f_min + (size_t)i * a.K;
+  const float* dm = a.o.d_min + (size_t)i * a.K;
+#pragma unroll
+  for (int k = 0; k < kMaxK; ++k) {
+    r.fm[k] = k < a.K ? fm[k] : kInf;
+    r.dm[k] = k < a.K ? dm[k] : 0.f;
+  }
+  const bool ref = list == 1 && (a.refine > 0 || a.secant);
+  r.fq = ref ? a.fq[i] : 0;
+  r.fprev = (list == 0 || (list == 1 && a.secant)) ? a.fprev[i] : 0.f;
+  r.dprev = (list == 1 && a.secant) ? a.dprev[i] : 0.f;
+  r.dirw = a.dir[i].w;
+}
+
 // One query's update of ray i (list 0: low-precision, 1: FP32 / FP32-class)
-// with decoder value f: step count, the k smallest |f| (silhouette and the
-// paper's gradient), hand-over, convergence (|f| < eps: hit at the unit final
-// step d + f), the aggressive step d += alpha f, leaving the bounding sphere
-// and the step budget.  Returns the list the ray continues in, or -1.
-__device__ __forceinline__ int step_ray(const TraceArgs& a, int list, int i, float f) {
+// with decoder value f and its state r: step count, the k smallest |f|
+// (silhouette and the paper's gradient), hand-over, convergence (|f| < eps:
+// hit at the unit final step d + f), the aggressive step d += alpha f,
+// leaving the bounding sphere and the step budget.  Returns the list the ray
+// continues in, or -1.
+__device__ __forceinline__ int apply_step(const TraceArgs& a, int list, int i, float f,
+                                          const RayState& r) {
   int keep = -1;
-  float4 s = a.st[i];
+  float4 s = r.s;
   const float d = s.x;
-  const int steps = a.o.steps[i] + 1;
+  const int steps = r.steps + 1;
   a.o.steps[i] = steps;
   const float af = fabsf(f);
   const float track = list == 0 ? fmaxf(af, a.eps) : af;
-  // k smallest |f|, ascending
-  float* fm = a.o.f_min + (size_t)i * a.K;
-  float* dm = a.o.d_min + (size_t)i * a.K;
+  // k smallest |f|, ascending; changed entries are written back
+  float fm0 = r.fm[0];
   {
+    float* fm = a.o.f_min + (size_t)i * a.K;
+    float* dm = a.o.d_min + (size_t)i * a.K;
     float cf = copysignf(track, f), cd = d;
-    for (int k = 0; k < a.K; ++k) {
-      const float ok = fm[k];
-      if (fabsf(cf) < fabsf(ok)) {
-        const float od = dm[k];
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) {
+      if (k < a.K && fabsf(cf) < fabsf(r.fm[k])) {
+        const float of = r.fm[k], od = r.dm[k];
+        if (k == 0) fm0 = cf;
         fm[k] = cf; dm[k] = cd;
-        cf = ok; cd = od;
+        cf = of; cd = od;
       }
     }
   }
@@ -86,7 +117,7 @@ __device__ __forceinline__ int step_ray(const TraceArgs& a, int list, int i, flo
   if (list == 1 && (a.refine > 0 || a.secant)) {
     // FP32 refinement after a tensor-core march: after `refine` FP32
     // queries a ray within 4 eps_bf16 of the surface is accepted
-    q = a.fq[i] + 1;
+    q = r.fq + 1;
     a.fq[i] = q;
     accepted = a.refine > 0 && q >= a.refine && af >= a.eps && af < 4.f * a.eps_bf16;
   }
@@ -94,7 +125,7 @@ __device__ __forceinline__ int step_ray(const TraceArgs& a, int list, int i, flo
   if (list == 0) {
     // a low-precision march that steps across the surface close to it
     // hands over to FP32 even if its noisy |f| never drops below eps_bf16
-    const float fp = a.fprev[i];
+    const float fp = r.fprev;
     a.fprev[i] = f;
     crossed = fp != 0.f && ((fp > 0.f) != (f > 0.f)) && af < 16.f * a.eps_bf16;
   }
@@ -109,8 +140,8 @@ __device__ __forceinline__ int step_ray(const TraceArgs& a, int list, int i, flo
       if (q == 1) {
         dn = d + f;
       } else {
-        const float dd = d - a.dprev[i];
-        const float sl = dd != 0.f ? (f - a.fprev[i]) / dd : 0.f;
+        const float dd = d - r.dprev;
+        const float sl = dd != 0.f ? (f - r.fprev) / dd : 0.f;
         const float stp = sl < -1e-3f ? -f / sl : 0.f;
         if (sl < -1e-3f && fabsf(stp) <= 8.f * af) dn = d + stp;
       }
@@ -124,20 +155,26 @@ __device__ __forceinline__ int step_ray(const TraceArgs& a, int list, int i, flo
   if (outcome == DIST_RAY_HIT) {
     const float dh = d + f;
     a.o.d_hit[i] = dh;
-    a.o.depth[i] = dh * a.dir[i].w;
+    a.o.depth[i] = dh * r.dirw;
     a.o.mask[i] = 1;
-    a.o.sil[i] = accepted ? af - 4.f * a.eps_bf16 : fabsf(fm[0]) - a.eps;
+    a.o.sil[i] = accepted ? af - 4.f * a.eps_bf16 : fabsf(fm0) - a.eps;
   } else if (outcome >= 0) {
     a.o.d_hit[i] = kInf;
     a.o.depth[i] = kInf;
     a.o.mask[i] = 0;
-    a.o.sil[i] = fabsf(fm[0]) - a.eps;
+    a.o.sil[i] = fabsf(fm0) - a.eps;
   } else if (keep == list) {
     s.x = dn;
     a.st[i] = s;
   }
   if (outcome >= 0 && a.o.status) a.o.status[i] = outcome;
   return keep;
+}
+
+__device__ __forceinline__ int step_ray(const TraceArgs& a, int list, int i, float f) {
+  RayState r;
+  load_ray(a, list, i, r);
+  return apply_step(a, list, i, f, r);
 }
 
 }  // namespace dist

@@ -33,6 +33,15 @@ constexpr int FWD_SMEM_BYTES =
     1024 + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES + (FWD_GRPS - 1) * BM * 4;
 static_assert(FWD_SMEM_BYTES <= 232448, "forward kernel shared memory");
 
+// Programmatic dependent launch: wait for the previous grid in the stream
+// (complete, its writes visible); let the next grid start launching.
+__device__ __forceinline__ void grid_dep_wait() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void grid_dep_launch() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Instruction descriptor, kind::f16: D fp32 (bits 4-5 = 1), A bf16 (7-9 = 1),
 // B bf16 (10-12 = 1), both K-major (bits 15, 16 = 0), N >> 3 at bits 17-22,
 // M >> 4 at bits 24-28.
