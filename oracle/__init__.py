@@ -14,7 +14,7 @@ of the paper it follows:
 * ``camera``  -- pixel-centre rays and the depth formula (Sec. 3.3, Sec. A.4).
 * ``tracer``  -- unit-sphere initialisation, aggressive sphere tracing,
                  convergence and outputs (Alg. 1, Sec. 3.2, Eq. 1, Sec. 3.3,
-                 Sec. A.3).
+                 Sec. A.3), and coarse-to-fine tracing (Sec. 3.2).
 * ``grad``    -- latent gradients: exact implicit form and the paper's
                  first-term approximation (Eq. 2, Sec. 3.4, Sec. B.2).
 * ``loss``    -- depth / normal / silhouette losses (Sec. 4.2.1, Eq. 4 of the
@@ -25,5 +25,9 @@ of the paper it follows:
 Parity status: every function is pinned by ``tests/test_oracle_*.py`` except
 the paper's approximated gradient (``grad.paper_depth_grad``), whose value as
 an approximation of the true gradient has no reference to compare against:
-parity unpinned (its arithmetic is pinned on an analytic SDF only).
+parity unpinned (its arithmetic is pinned on an analytic SDF only); and
+what a child ray inherits in coarse-to-fine tracing
+(``tracer.render_coarse_to_fine``), which the paper does not state: parity
+unpinned as a reading of the paper (the code is pinned against a scalar
+restatement of the reading, an exact sphere and the plain tracer).
 """

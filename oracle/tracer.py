@@ -58,6 +58,74 @@ def unit_sphere_init(c, v, radius=1.0):
     return enters, t_in, t_out, dist
 
 
+def _new_state(n, t_in, enters, k_min, max_steps, record):
+    """Per-ray march state before the first query (Sec. 3.2 initialisation)."""
+    return {
+        "d": np.where(enters, t_in, 0.0).astype(np.float64),
+        "active": enters.copy(),
+        "status": np.where(enters, MAX_STEPS, INIT_MISS).astype(np.int32),
+        "steps": np.zeros(n, dtype=np.int32),
+        "d_hit": np.full(n, np.inf),
+        "f_last": np.full(n, np.nan),
+        "d_last": np.full(n, np.nan),
+        "topk_f": np.full((n, k_min), np.inf),      # |f| of the k smallest samples
+        "topk_d": np.full((n, k_min), np.nan),      # their ray distances
+        "topk_s": np.full((n, k_min), np.nan),      # their signed f
+        "rec_d": np.full((n, max_steps), np.nan) if record else None,
+        "rec_f": np.full((n, max_steps), np.nan) if record else None,
+    }
+
+
+def _step(S, idx, s, it, t_in, t_out, eps, alpha):
+    """One march iteration for the active rays ``idx`` with SDF values ``s``
+    at their current points (Alg. 1, Sec. 3.2, Eq. 1)."""
+    d = S["d"]
+    if S["rec_d"] is not None:
+        S["rec_d"][idx, it] = d[idx]
+        S["rec_f"][idx, it] = s
+    S["steps"][idx] += 1
+    S["f_last"][idx] = s
+    S["d_last"][idx] = d[idx]
+    a = np.abs(s)
+    topk_f, topk_d, topk_s = S["topk_f"], S["topk_d"], S["topk_s"]
+    # keep the k samples with the smallest |f|, sorted ascending; a new
+    # sample goes before the first kept one it is strictly smaller than
+    # (ties keep the earlier sample)
+    placed = np.zeros(idx.size, dtype=bool)
+    for j in range(topk_f.shape[1]):
+        ins = (~placed) & (a < topk_f[idx, j])
+        bi = idx[ins]
+        if bi.size:
+            topk_f[bi, j + 1:] = topk_f[bi, j:-1].copy()
+            topk_d[bi, j + 1:] = topk_d[bi, j:-1].copy()
+            topk_s[bi, j + 1:] = topk_s[bi, j:-1].copy()
+            topk_f[bi, j] = a[ins]
+            topk_d[bi, j] = d[bi]
+            topk_s[bi, j] = s[ins]
+        placed |= ins
+    conv = np.abs(s) < eps
+    ci = idx[conv]
+    S["d_hit"][ci] = d[ci] + s[conv]          # unit final step (Eq. 1)
+    S["status"][ci] = HIT
+    S["active"][ci] = False
+    ri = idx[~conv]
+    d[ri] = d[ri] + alpha * s[~conv]          # aggressive step (Sec. 3.2)
+    left = (d[ri] > t_out[ri]) | (d[ri] < t_in[ri])
+    S["status"][ri[left]] = LEFT_SPHERE
+    S["active"][ri[left]] = False
+
+
+def _result(S):
+    return {
+        "status": S["status"], "steps": S["steps"], "d_hit": S["d_hit"], "d_end": S["d"],
+        "f_last": S["f_last"], "d_last": S["d_last"],
+        "min_abs_f": S["topk_f"][:, 0], "d_at_min": S["topk_d"][:, 0],
+        "f_at_min": S["topk_s"][:, 0],
+        "topk_f": S["topk_f"], "topk_d": S["topk_d"], "topk_s": S["topk_s"],
+        "rec_d": S["rec_d"], "rec_f": S["rec_f"],
+    }
+
+
 def march(f, c, v, shape, t_in, t_out, enters, max_steps, eps, alpha, k_min=1,
           record=False):
     """Sphere-trace every ray (vectorised over rays, looped over steps).
@@ -67,63 +135,15 @@ def march(f, c, v, shape, t_in, t_out, enters, max_steps, eps, alpha, k_min=1,
     ray distance and f as (n, max_steps) arrays (NaN past the last query)."""
     n = v.shape[0]
     c = np.broadcast_to(np.asarray(c, dtype=np.float64), (n, 3))
-    d = np.where(enters, t_in, 0.0).astype(np.float64)
-    active = enters.copy()
-    status = np.where(enters, MAX_STEPS, INIT_MISS).astype(np.int32)
-    steps = np.zeros(n, dtype=np.int32)
-    d_hit = np.full(n, np.inf)
-    f_last = np.full(n, np.nan)
-    d_last = np.full(n, np.nan)
-    topk_f = np.full((n, k_min), np.inf)      # |f| of the k smallest samples
-    topk_d = np.full((n, k_min), np.nan)      # their ray distances
-    topk_s = np.full((n, k_min), np.nan)      # their signed f
-    rec_d = np.full((n, max_steps), np.nan) if record else None
-    rec_f = np.full((n, max_steps), np.nan) if record else None
+    S = _new_state(n, t_in, enters, k_min, max_steps, record)
     for it in range(max_steps):
-        idx = np.nonzero(active)[0]
+        idx = np.nonzero(S["active"])[0]
         if idx.size == 0:
             break
-        p = c[idx] + d[idx, None] * v[idx]
+        p = c[idx] + S["d"][idx, None] * v[idx]
         s = np.asarray(f(p, shape[idx]), dtype=np.float64)
-        if record:
-            rec_d[idx, it] = d[idx]
-            rec_f[idx, it] = s
-        steps[idx] += 1
-        f_last[idx] = s
-        d_last[idx] = d[idx]
-        a = np.abs(s)
-        # keep the k samples with the smallest |f|, sorted ascending; a new
-        # sample goes before the first kept one it is strictly smaller than
-        # (ties keep the earlier sample)
-        placed = np.zeros(idx.size, dtype=bool)
-        for j in range(k_min):
-            ins = (~placed) & (a < topk_f[idx, j])
-            bi = idx[ins]
-            if bi.size:
-                topk_f[bi, j + 1:] = topk_f[bi, j:-1].copy()
-                topk_d[bi, j + 1:] = topk_d[bi, j:-1].copy()
-                topk_s[bi, j + 1:] = topk_s[bi, j:-1].copy()
-                topk_f[bi, j] = a[ins]
-                topk_d[bi, j] = d[bi]
-                topk_s[bi, j] = s[ins]
-            placed |= ins
-        conv = np.abs(s) < eps
-        ci = idx[conv]
-        d_hit[ci] = d[ci] + s[conv]          # unit final step (Eq. 1)
-        status[ci] = HIT
-        active[ci] = False
-        ri = idx[~conv]
-        d[ri] = d[ri] + alpha * s[~conv]     # aggressive step (Sec. 3.2)
-        left = (d[ri] > t_out[ri]) | (d[ri] < t_in[ri])
-        status[ri[left]] = LEFT_SPHERE
-        active[ri[left]] = False
-    return {
-        "status": status, "steps": steps, "d_hit": d_hit, "d_end": d,
-        "f_last": f_last, "d_last": d_last,
-        "min_abs_f": topk_f[:, 0], "d_at_min": topk_d[:, 0], "f_at_min": topk_s[:, 0],
-        "topk_f": topk_f, "topk_d": topk_d, "topk_s": topk_s,
-        "rec_d": rec_d, "rec_f": rec_f,
-    }
+        _step(S, idx, s, it, t_in, t_out, eps, alpha)
+    return _result(S)
 
 
 def render(sdf, cams, max_steps=50, eps=5e-5, alpha=1.5, normal_delta=0.0,
@@ -181,3 +201,135 @@ def normals(sdf, p, shape, hit, delta=0.0):
             g[:, a] = (sdf(q + e, shape[idx]) - sdf(q - e, shape[idx])) / (2.0 * delta)
     n[idx] = g / np.linalg.norm(g, axis=1, keepdims=True)
     return n
+
+
+# -- coarse-to-fine tracing (Sec. 3.2 "Coarse-to-fine Strategy") ---------------
+#
+# The trace starts on an image 2^levels times coarser per side (the paper's
+# "1/4 of the resolution" read per side: two doublings after six steps reach
+# full resolution) and splits every ray into its four children after every
+# ``split_every`` march iterations.  The paper does not say what a child
+# inherits; the readings applied here (and on the GPU) are:
+#   * coarse ray (X, Y) of level l passes through the image point
+#     ((X + 1/2) 2^l, (Y + 1/2) 2^l), the centre of its 2^l x 2^l pixel block;
+#     its children are (2X + i, 2Y + j), i, j in {0, 1};
+#   * a child has its own direction and its own unit-sphere interval; a child
+#     whose ray misses the sphere is background like any such pixel;
+#   * a child of a parent that missed the sphere starts afresh at its own
+#     entry point;
+#   * otherwise it inherits the parent's ray distance d (raised to its own
+#     t_in; beyond its own t_out it has left the sphere), the parent's query
+#     count, and the parent's k smallest-|f| samples with |f| floored at eps
+#     (a parent's sample is not on the child's ray, so it cannot make the
+#     child's silhouette negative);
+#   * a child of a still-marching or converged parent marches on from d (a
+#     converged parent's d is its converging sample); a child of a parent
+#     that left the sphere or ran out of queries ends the same way.
+
+def _level_camera(cam, level):
+    """The camera of the 2^level-coarser image.  Scaling fx, fy, cx, cy by
+    2^-level is exact in binary floating point, so pixel (X, Y) of it gives
+    x~ = ((X + 1/2) 2^level - cx) / fx as on the full image."""
+    k = float(2 ** level)
+    return {**cam, "H": int(cam["H"]) >> level, "W": int(cam["W"]) >> level,
+            "fx": cam["fx"] / k, "fy": cam["fy"] / k, "cx": cam["cx"] / k,
+            "cy": cam["cy"] / k}
+
+
+def _split(S, Hl, Wl, enters_c, t_in_c, t_out_c, eps):
+    """Children state of the level-l rays S (Hl x Wl, row-major): each ray's
+    four children on the 2 Hl x 2 Wl grid, by the readings above."""
+    def up(a):
+        g = a.reshape((Hl, Wl) + a.shape[1:])
+        return np.repeat(np.repeat(g, 2, axis=0), 2, axis=1).reshape((4 * Hl * Wl,) + a.shape[1:])
+
+    n = 4 * Hl * Wl
+    status_p, active_p = up(S["status"]), up(S["active"])
+    d_p = up(S["d"])
+    fresh = enters_c & (status_p == INIT_MISS)
+    inherit = enters_c & (status_p != INIT_MISS)
+    C = _new_state(n, t_in_c, enters_c, S["topk_f"].shape[1], 0, False)
+    C["rec_d"] = C["rec_f"] = None
+    # inherited steps, samples and last query
+    tf = up(S["topk_f"])
+    C["topk_f"][inherit] = np.maximum(tf[inherit], eps)
+    C["topk_s"][inherit] = np.copysign(C["topk_f"][inherit], up(S["topk_s"])[inherit])
+    C["topk_d"][inherit] = up(S["topk_d"])[inherit]
+    C["steps"][inherit] = up(S["steps"])[inherit]
+    C["f_last"][inherit] = up(S["f_last"])[inherit]
+    C["d_last"][inherit] = up(S["d_last"])[inherit]
+    marching = inherit & (active_p | (status_p == HIT))
+    ended = inherit & ~marching
+    C["status"][ended] = status_p[ended]
+    C["active"][ended] = False
+    d = np.maximum(d_p, t_in_c)
+    out = marching & (d > t_out_c)
+    C["d"][marching] = d[marching]
+    C["status"][marching] = MAX_STEPS
+    C["active"][marching] = True
+    C["status"][out] = LEFT_SPHERE
+    C["active"][out] = False
+    C["d"][fresh] = t_in_c[fresh]
+    return C
+
+
+def render_coarse_to_fine(sdf, cams, levels=2, split_every=3, max_steps=50, eps=5e-5,
+                          alpha=1.5, normal_delta=0.0, k_min=1, radius=1.0,
+                          with_normals=True):
+    """``render`` with the coarse-to-fine strategy of Sec. 3.2 (readings
+    above).  Every camera's H and W must be multiples of 2^levels.  Returns
+    the same per-pixel fields, plus ``queries``: the number of SDF queries
+    made (Tab. 1 counts these)."""
+    parts, queries = [], 0
+    for cam in cams:
+        H, W = int(cam["H"]), int(cam["W"])
+        if H % (1 << levels) or W % (1 << levels):
+            raise ValueError("image size not a multiple of 2^levels")
+        shape_id = int(cam.get("shape", 0))
+        level = levels
+        c, v, inv = pixel_rays(_level_camera(cam, level))
+        if float(c @ c) <= radius * radius:
+            raise ValueError("camera inside the bounding sphere")
+        enters, t_in, t_out, dist = unit_sphere_init(c, v, radius)
+        S = _new_state(v.shape[0], t_in, enters, k_min, 0, False)
+        for it in range(max_steps):
+            if level > 0 and it == split_every * (levels - level + 1):
+                Hl, Wl = H >> level, W >> level
+                level -= 1
+                c, v, inv = pixel_rays(_level_camera(cam, level))
+                enters, t_in, t_out, dist = unit_sphere_init(c, v, radius)
+                S = _split(S, Hl, Wl, enters, t_in, t_out, eps)
+            idx = np.nonzero(S["active"])[0]
+            if idx.size == 0:
+                if level == 0:
+                    break
+                continue
+            p = c + S["d"][idx, None] * v[idx]
+            s = np.asarray(sdf(p, np.full(idx.size, shape_id)), dtype=np.float64)
+            queries += idx.size
+            _step(S, idx, s, it, t_in, t_out, eps, alpha)
+        while level > 0:   # max_steps shorter than the coarse phase
+            Hl, Wl = H >> level, W >> level
+            level -= 1
+            c, v, inv = pixel_rays(_level_camera(cam, level))
+            enters, t_in, t_out, dist = unit_sphere_init(c, v, radius)
+            S = _split(S, Hl, Wl, enters, t_in, t_out, eps)
+            S["status"][S["active"]] = MAX_STEPS
+            S["active"][:] = False
+        out = _result(S)
+        hit = out["status"] == HIT
+        out.update({
+            "mask": hit, "depth": np.where(hit, depth_from_distance(out["d_hit"], inv), np.inf),
+            "sil": np.where(enters, out["min_abs_f"] - eps, dist - radius),
+            "enters": enters, "t_in": t_in, "t_out": t_out,
+            "c": np.broadcast_to(c, v.shape), "v": v, "inv_norm": inv,
+            "shape": np.full(v.shape[0], shape_id),
+            "p_hit": c + np.where(hit, out["d_hit"], 0.0)[:, None] * v,
+        })
+        parts.append(out)
+    keys = [k for k in parts[0] if k not in ("rec_d", "rec_f")]
+    res = {k: np.concatenate([p[k] for p in parts]) for k in keys}
+    res.update({"eps": eps, "alpha": alpha, "queries": queries})
+    if with_normals:
+        res["normal"] = normals(sdf, res["p_hit"], res["shape"], res["mask"], normal_delta)
+    return res
