@@ -73,6 +73,8 @@ def _new_state(n, t_in, enters, k_min, max_steps, record):
         "topk_s": np.full((n, k_min), np.nan),      # their signed f
         "rec_d": np.full((n, max_steps), np.nan) if record else None,
         "rec_f": np.full((n, max_steps), np.nan) if record else None,
+        # distance of each step's new d from t_in / t_out (exit-test margin)
+        "rec_x": np.full((n, max_steps), np.inf) if record else None,
     }
 
 
@@ -113,6 +115,8 @@ def _step(S, idx, s, it, t_in, t_out, eps, alpha):
     left = (d[ri] > t_out[ri]) | (d[ri] < t_in[ri])
     S["status"][ri[left]] = LEFT_SPHERE
     S["active"][ri[left]] = False
+    if S["rec_x"] is not None:
+        S["rec_x"][ri, it] = np.minimum(np.abs(d[ri] - t_out[ri]), np.abs(d[ri] - t_in[ri]))
 
 
 def _result(S):
@@ -122,7 +126,7 @@ def _result(S):
         "min_abs_f": S["topk_f"][:, 0], "d_at_min": S["topk_d"][:, 0],
         "f_at_min": S["topk_s"][:, 0],
         "topk_f": S["topk_f"], "topk_d": S["topk_d"], "topk_s": S["topk_s"],
-        "rec_d": S["rec_d"], "rec_f": S["rec_f"],
+        "rec_d": S["rec_d"], "rec_f": S["rec_f"], "rec_x": S["rec_x"],
     }
 
 
@@ -236,7 +240,7 @@ def _level_camera(cam, level):
             "cy": cam["cy"] / k}
 
 
-def _split(S, Hl, Wl, enters_c, t_in_c, t_out_c, eps):
+def _split(S, Hl, Wl, enters_c, t_in_c, t_out_c, eps, graze_c):
     """Children state of the level-l rays S (Hl x Wl, row-major): each ray's
     four children on the 2 Hl x 2 Wl grid, by the readings above."""
     def up(a):
@@ -249,7 +253,12 @@ def _split(S, Hl, Wl, enters_c, t_in_c, t_out_c, eps):
     fresh = enters_c & (status_p == INIT_MISS)
     inherit = enters_c & (status_p != INIT_MISS)
     C = _new_state(n, t_in_c, enters_c, S["topk_f"].shape[1], 0, False)
-    C["rec_d"] = C["rec_f"] = None
+    for k in ("rec_d", "rec_f", "rec_x"):
+        C[k] = up(S[k]) if S[k] is not None else None
+    # margins of the decisions taken here and by the ancestors (test aid):
+    # entry into the bounding sphere, and the inherited d against t_out
+    C["graze"] = np.minimum(up(S["graze"]), graze_c)
+    C["split_x"] = up(S["split_x"]).copy()
     # inherited steps, samples and last query
     tf = up(S["topk_f"])
     C["topk_f"][inherit] = np.maximum(tf[inherit], eps)
@@ -263,6 +272,8 @@ def _split(S, Hl, Wl, enters_c, t_in_c, t_out_c, eps):
     C["status"][ended] = status_p[ended]
     C["active"][ended] = False
     d = np.maximum(d_p, t_in_c)
+    C["split_x"][marching] = np.minimum(C["split_x"][marching],
+                                        np.abs(d[marching] - t_out_c[marching]))
     out = marching & (d > t_out_c)
     C["d"][marching] = d[marching]
     C["status"][marching] = MAX_STEPS
@@ -273,13 +284,22 @@ def _split(S, Hl, Wl, enters_c, t_in_c, t_out_c, eps):
     return C
 
 
+def _graze(c, v, radius):
+    """| squared distance from the origin to the ray - radius^2 |: where it is
+    tiny, FP32 and FP64 may disagree on entering the bounding sphere."""
+    b = v @ c
+    return np.abs(float(c @ c) - b * b - radius * radius)
+
+
 def render_coarse_to_fine(sdf, cams, levels=2, split_every=3, max_steps=50, eps=5e-5,
                           alpha=1.5, normal_delta=0.0, k_min=1, radius=1.0,
-                          with_normals=True):
+                          with_normals=True, record=False):
     """``render`` with the coarse-to-fine strategy of Sec. 3.2 (readings
     above).  Every camera's H and W must be multiples of 2^levels.  Returns
     the same per-pixel fields, plus ``queries``: the number of SDF queries
-    made (Tab. 1 counts these)."""
+    made (Tab. 1 counts these).  With ``record``, each pixel's samples along
+    its chain of ancestors (``rec_d``, ``rec_f``, ``rec_x``) and the margins
+    of the chain's entry and split decisions (``graze``, ``split_x``)."""
     parts, queries = [], 0
     for cam in cams:
         H, W = int(cam["H"]), int(cam["W"])
@@ -291,14 +311,16 @@ def render_coarse_to_fine(sdf, cams, levels=2, split_every=3, max_steps=50, eps=
         if float(c @ c) <= radius * radius:
             raise ValueError("camera inside the bounding sphere")
         enters, t_in, t_out, dist = unit_sphere_init(c, v, radius)
-        S = _new_state(v.shape[0], t_in, enters, k_min, 0, False)
+        S = _new_state(v.shape[0], t_in, enters, k_min, max_steps, record)
+        S["graze"] = _graze(c, v, radius)
+        S["split_x"] = np.full(v.shape[0], np.inf)
         for it in range(max_steps):
             if level > 0 and it == split_every * (levels - level + 1):
                 Hl, Wl = H >> level, W >> level
                 level -= 1
                 c, v, inv = pixel_rays(_level_camera(cam, level))
                 enters, t_in, t_out, dist = unit_sphere_init(c, v, radius)
-                S = _split(S, Hl, Wl, enters, t_in, t_out, eps)
+                S = _split(S, Hl, Wl, enters, t_in, t_out, eps, _graze(c, v, radius))
             idx = np.nonzero(S["active"])[0]
             if idx.size == 0:
                 if level == 0:
@@ -309,11 +331,14 @@ def render_coarse_to_fine(sdf, cams, levels=2, split_every=3, max_steps=50, eps=
             queries += idx.size
             _step(S, idx, s, it, t_in, t_out, eps, alpha)
         while level > 0:   # max_steps shorter than the coarse phase
+            # rays still marching have run out of queries (status MAX_STEPS):
+            # their children end the same way
+            S["active"][:] = False
             Hl, Wl = H >> level, W >> level
             level -= 1
             c, v, inv = pixel_rays(_level_camera(cam, level))
             enters, t_in, t_out, dist = unit_sphere_init(c, v, radius)
-            S = _split(S, Hl, Wl, enters, t_in, t_out, eps)
+            S = _split(S, Hl, Wl, enters, t_in, t_out, eps, _graze(c, v, radius))
             S["status"][S["active"]] = MAX_STEPS
             S["active"][:] = False
         out = _result(S)
@@ -325,9 +350,10 @@ def render_coarse_to_fine(sdf, cams, levels=2, split_every=3, max_steps=50, eps=
             "c": np.broadcast_to(c, v.shape), "v": v, "inv_norm": inv,
             "shape": np.full(v.shape[0], shape_id),
             "p_hit": c + np.where(hit, out["d_hit"], 0.0)[:, None] * v,
+            "graze": S["graze"], "split_x": S["split_x"],
         })
         parts.append(out)
-    keys = [k for k in parts[0] if k not in ("rec_d", "rec_f")]
+    keys = [k for k in parts[0] if parts[0][k] is not None]
     res = {k: np.concatenate([p[k] for p in parts]) for k in keys}
     res.update({"eps": eps, "alpha": alpha, "queries": queries})
     if with_normals:
