@@ -183,7 +183,8 @@ def run_ours(args, rank, world, local_rank):
         precision = "bf16" if dec.has_bf16 else "fp32"
     params = api.TraceParams(max_steps=MAX_STEPS, precision=precision, eps_bf16=args.eps_lo,
                              refine_steps=args.refine, alpha_refine=args.alpha_refine,
-                             refine_engine=args.refine_engine, refine_rule=args.refine_rule)
+                             refine_engine=args.refine_engine, refine_rule=args.refine_rule,
+                             coarse_levels=args.coarse_levels)
     ws = api.Workspace(SIZE * SIZE, MAX_STEPS)
     z = torch.from_numpy(Z).to(dev)
     # target: depth of the second latent (untimed setup)
@@ -316,6 +317,7 @@ def run_ours(args, rank, world, local_rank):
                    "rays_per_step": rays, "precision": precision,
                    "eps_lo": args.eps_lo, "refine_steps": args.refine,
                    "refine_engine": args.refine_engine, "refine_rule": args.refine_rule,
+                   "coarse_levels": args.coarse_levels,
                    "normals": "rendered (analytic, adjoint at the hits)" if args.normals
                               else "not rendered (unused by the L1 depth loss)",
                    "parallelism": f"replicas x{world}",
@@ -332,6 +334,9 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
     }
     line["fp32_trace"] = fp32_trace_rate(api, dec, cam, z, tgt, stream)
+    if args.coarse_levels == 0 and precision in ("bf16", "fp16"):
+        line["coarse_to_fine"] = coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream,
+                                                     flush, args.steps, args.normals)
     line["roofline"]["large_launch"] = large_launch_rate(api, dec, z, precision, peaks["bf16_tflops"])
     if not args.no_serve:
         line["serving"] = run_serving(args, dec, params, dev)
@@ -341,6 +346,37 @@ def run_ours(args, rank, world, local_rank):
 
 
 # ------------------------------------------------- FP32 trace, large launches
+
+def coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps, normals):
+    """The same fwd+bwd step with the paper's coarse-to-fine tracing (Sec. 3.2:
+    start at 1/4 resolution per side, split every ray into four after every
+    three iterations), timed like the main line."""
+    import dataclasses
+    import torch
+    p2 = dataclasses.replace(params, coarse_levels=2, coarse_every=3)
+    step = Step(api, dec, ws, cam, p2, z, tgt, normals=normals)
+    for _ in range(3):
+        step(stream)
+    torch.cuda.synchronize()
+    step.res.queries.zero_()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        evs[i][0].record(stream)
+        step(stream)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    q = step.res.queries.cpu().numpy().astype(np.float64) / steps
+    return {"value": SIZE * SIZE / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
+            "coarse_levels": 2, "coarse_every": 3,
+            "queries_per_step": {"lowp": float(q[0]), "fp32": float(q[1])},
+            "hits": int(step.res.mask.sum().item()),
+            "note": "same step with coarse-to-fine tracing (Sec. 3.2); child rays inherit by "
+                    "the stated reading, so depths differ from the exact per-pixel trace near "
+                    "silhouettes"}
+
 
 def fp32_trace_rate(api, dec, cam, z, tgt, stream, steps=3):
     """The plain FP32 GPU trace (CUDA-core decoder, FP32 adjoint) on the same
@@ -609,6 +645,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--normals", action="store_true",
                     help="also render analytic normals in the forward pass")
+    ap.add_argument("--coarse-levels", type=int, default=0,
+                    help="coarse-to-fine tracing for the main line (0: exact per-pixel trace; "
+                         "the coarse_to_fine key reports 2 beside it)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-load", type=float, default=0.8,

@@ -154,11 +154,29 @@ typedef struct {
                           SIMT: FP32 CUDA-core kernel)                      */
   int refine_rule;     /* BF16/FP16 path: dist_refine_rule of the queries
                           after the hand-over                               */
+  int coarse_levels;   /* coarse-to-fine tracing (Sec. 3.2): 0 = off; n > 0
+                          = start on an image 2^n times coarser per side
+                          (the paper: 2) and split every ray into its four
+                          children after every `coarse_every` march
+                          iterations.  Every camera's H and W must be
+                          multiples of 2^n; 0..4.  With a BF16/FP16 march
+                          it needs refine_steps 0 and refine_engine TC.
+                          What a child inherits is not stated in the
+                          paper: it has its own direction and bounding-
+                          sphere interval, and takes over its parent's ray
+                          distance (raised to its own entry; past its own
+                          exit it has left the sphere), step count, k
+                          smallest-|f| samples (|f| raised to eps) and
+                          outcome if the parent left the sphere or ran out
+                          of queries; a child of a parent that missed the
+                          sphere starts at its own entry.                   */
+  int coarse_every;    /* march iterations per coarse level (the paper: 3) */
 } dist_trace_params;
 
 /* Fill `p` with the paper's defaults: max_steps 50, eps 5e-5, alpha 1.5,
  * k_min 1, normal_delta 0, exact gradients, FP32, eps_bf16 1e-3, radius 1,
- * refine_steps 0, alpha_refine 0, refine_engine TC, refine_rule MARCH. */
+ * refine_steps 0, alpha_refine 0, refine_engine TC, refine_rule MARCH,
+ * coarse_levels 0 (off), coarse_every 3. */
 void dist_trace_params_default(dist_trace_params* p);
 
 /* -------------------------------------------------------------- workspace */

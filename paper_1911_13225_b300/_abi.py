@@ -52,7 +52,8 @@ class TraceParams(Structure):
     _fields_ = [("max_steps", c_int), ("eps", c_float), ("alpha", c_float), ("k_min", c_int),
                 ("normal_delta", c_float), ("grad_mode", c_int), ("precision", c_int),
                 ("eps_bf16", c_float), ("radius", c_float), ("refine_steps", c_int),
-                ("alpha_refine", c_float), ("refine_engine", c_int), ("refine_rule", c_int)]
+                ("alpha_refine", c_float), ("refine_engine", c_int), ("refine_rule", c_int),
+                ("coarse_levels", c_int), ("coarse_every", c_int)]
 
 
 class TraceOut(Structure):

@@ -45,6 +45,8 @@ class TraceParams:
     alpha_refine: float = 0.0     # step factor of the FP32 phase (0: alpha)
     refine_engine: str = "tc"     # FP32-class queries after the hand-over: "tc" | "simt"
     refine_rule: str = "march"    # their step rule: "march" (alpha) | "secant"
+    coarse_levels: int = 0        # coarse-to-fine tracing (Sec. 3.2): 0 off, 2 the paper's
+    coarse_every: int = 3         # march iterations per coarse level
 
     def c(self) -> _abi.TraceParams:
         return _abi.TraceParams(
@@ -53,7 +55,8 @@ class TraceParams:
             _abi.GRAD_EXACT if self.grad_mode == "exact" else _abi.GRAD_PAPER,
             _abi.PRECISIONS[self.precision], float(self.eps_bf16), float(self.radius),
             int(self.refine_steps), float(self.alpha_refine),
-            _abi.REFINE_ENGINES[self.refine_engine], _abi.REFINE_RULES[self.refine_rule])
+            _abi.REFINE_ENGINES[self.refine_engine], _abi.REFINE_RULES[self.refine_rule],
+            int(self.coarse_levels), int(self.coarse_every))
 
 
 def camera_struct(cam) -> _abi.Camera:

@@ -72,6 +72,8 @@ void dist_trace_params_default(dist_trace_params* p) {
   p->alpha_refine = 0.f;
   p->refine_engine = DIST_REFINE_TC;
   p->refine_rule = DIST_REFINE_MARCH;
+  p->coarse_levels = 0;
+  p->coarse_every = 3;
 }
 
 dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* const* W,
@@ -202,7 +204,8 @@ dist_status dist_workspace_create(int64_t max_rays, int max_steps, dist_workspac
   WS_ALLOC(act[1][1], n * sizeof(int));
   WS_ALLOC(fbuf[0], n * sizeof(float));
   WS_ALLOC(fbuf[1], n * sizeof(float));
-  WS_ALLOC(counts, (size_t)(max_steps + 2) * 2 * sizeof(int));
+  WS_ALLOC(counts, ((size_t)(max_steps + 2) * 2 + 2 * kMaxCoarseLevels) * sizeof(int));
+  WS_ALLOC(rstat, n * sizeof(int));
   WS_ALLOC(cams, (size_t)w->max_cams * sizeof(CamDev));
   WS_ALLOC(bfold, (size_t)2 * kMaxShapes * 512 * sizeof(float));
   WS_ALLOC(gacc, (size_t)2 * kMaxShapes * 512 * sizeof(double));

@@ -63,6 +63,7 @@ inline bool fp32_on_tc(const dist_trace_params& p) {
 
 constexpr int kMaxShapes = 1024;    // folded-bias capacity of a workspace
 constexpr int kMaxK = 3;            // k_min upper bound (Sec. B.4 uses 1 or 3)
+constexpr int kMaxCoarseLevels = 4; // coarse-to-fine: at most 16x coarser per side
 constexpr int kProbesPerRay = 10;   // probe capacity per pixel in a workspace:
                                     // <= 4 depth/silhouette + 6 normal probes
 
@@ -122,6 +123,12 @@ struct DecoderTC {
   TCMaps bmaps16;                // same, fp16
   TCMaps xmaps;                  // [N][2K] fp16 hi | lo split of 2^s_l W_l (FP32-class kernel)
   TCMaps pmaps, pmaps16, pxmaps; // the same three with 128-row boxes (CTA-pair kernel)
+  // The same weights as images of the forward kernel's shared-memory stages:
+  // per GEMM, [N/256][K'/64] blocks of 256 x 64 16-bit values in the 128B-
+  // swizzled K-major layout (32 KB each, K' = K, or 2K for the split), so
+  // that one bulk copy fills a stage
+  const uint8_t* img[2][7];      // bf16, fp16
+  const uint8_t* ximg[7];        // FP32-class split
   bool pair;                     // forward kernel on CTA pairs (cta_group::2)
   float x_inv_scale[7];          // 2^-s_l
   const TCConst* cst;            // epilogue constants (device)
@@ -153,7 +160,9 @@ struct dist_workspace {
   float* dprev;       // distance of the previous FP32-class sample (secant rule)
   int* act[2][2];     // [parity][0 = BF16 list, 1 = FP32 list] active ray ids
   float* fbuf[2];     // MLP outputs for the two lists
-  int* counts;        // [(max_steps + 2) * 2] list lengths per step
+  int* counts;        // [(max_steps + 2) * 2 + 2 kMaxCoarseLevels] list lengths
+                      // per step, then per coarse-to-fine split
+  int* rstat;         // per-ray status when the caller asks for none
   dist::CamDev* cams; // camera table (device)
   int max_cams;
   float* bfold;       // [2][kMaxShapes][512] folded latent biases

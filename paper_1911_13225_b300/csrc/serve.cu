@@ -389,6 +389,8 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
              DIST_E_INVALID, "dist_serve_create: bad refine_rule");
   DIST_CHECK(!(is_tc(p->precision) || fp32_on_tc(*p)) || dec->tc.ok, DIST_E_UNSUPPORTED,
              "the tensor-core decoder covers only the DeepSDF shape");
+  DIST_CHECK(p->coarse_levels == 0, DIST_E_INVALID,
+             "dist_serve_create: coarse-to-fine tracing is not supported by the server");
   dist_server* S = new dist_server();
   S->dec = dec;
   S->p = *p;

@@ -27,6 +27,11 @@ struct TraceArgs {
   int* fq;              // FP32 queries per ray after the low-precision phase
   float* fprev;         // previous low-precision sample (then FP32-class, secant)
   float* dprev;         // distance of the previous FP32-class sample (secant)
+  int c2f;              // coarse-to-fine trace: o.status holds -1 / -2 for a
+                        // ray marching in list 0 / list 1 until it ends
+  int c2f_start;        // the code of a ray that starts marching
+  int last;             // coarse-to-fine: this is the last march iteration, so
+                        // a ray that started late also ends here (MAX_STEPS)
 };
 
 // The step update applied by the decoder kernel itself: the thread that
@@ -133,6 +138,7 @@ __device__ __forceinline__ int apply_step(const TraceArgs& a, int list, int i, f
     outcome = DIST_RAY_HIT;
   } else if (list == 0 && (af < a.eps_bf16 || crossed)) {
     keep = 1;       // switch to FP32 queries at the same point
+    if (a.c2f) a.o.status[i] = -2;
   } else {
     dn = fmaf(list == 1 ? a.alpha_fp32 : a.alpha, f, d);
     if (list == 1 && a.secant) {
@@ -151,7 +157,10 @@ __device__ __forceinline__ int apply_step(const TraceArgs& a, int list, int i, f
     if (dn > s.z || dn < s.y) outcome = DIST_RAY_LEFT;
     else keep = list;
   }
-  if (outcome < 0 && steps >= a.max_steps) { outcome = DIST_RAY_MAX_STEPS; keep = -1; }
+  if (outcome < 0 && (steps >= a.max_steps || a.last)) {
+    outcome = DIST_RAY_MAX_STEPS;
+    keep = -1;
+  }
   if (outcome == DIST_RAY_HIT) {
     const float dh = d + f;
     a.o.d_hit[i] = dh;

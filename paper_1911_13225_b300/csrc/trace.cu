@@ -107,60 +107,216 @@ __global__ void fold_bias_kernel(DecoderF32 d, const float* __restrict__ z, int 
 // -------------------------------------------------------------- ray setup
 
 
-// One thread per pixel (Sec. 3.2 "Initialization"): the ray through the
-// pixel centre, its entry/exit distances into the bounding sphere, and the
-// background outputs of rays that miss it (depth +inf, silhouette =
-// distance from the origin to the ray minus the radius, Sec. A.3).
-__global__ void raygen_kernel(TraceArgs a, int* list0, int* count0) {
+// The ray through image point (u, v) of camera c (Sec. 3.2 "Initialization"):
+// its world direction, 1/sqrt(x~^2 + y~^2 + 1) for the depth (Sec. 3.3), its
+// entry/exit distances into the bounding sphere and, for a ray that misses
+// it, the distance from the origin to the ray (Sec. A.3).
+struct RayGeom {
+  float vx, vy, vz, inv, t_in, t_out, dist;
+  bool enters;
+};
+
+__device__ __forceinline__ RayGeom ray_geom(const CamDev& c, float radius, float u, float v) {
+  RayGeom g;
+  const float xt = (u - c.cx) / c.fx;
+  const float yt = (v - c.cy) / c.fy;
+  const float inv = 1.0f / sqrtf(xt * xt + yt * yt + 1.0f);
+  const float vx0 = xt * inv, vy0 = yt * inv, vz0 = inv;
+  float vx = c.R[0] * vx0 + c.R[1] * vy0 + c.R[2] * vz0;
+  float vy = c.R[3] * vx0 + c.R[4] * vy0 + c.R[5] * vz0;
+  float vz = c.R[6] * vx0 + c.R[7] * vy0 + c.R[8] * vz0;
+  const float vn = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
+  vx *= vn; vy *= vn; vz *= vn;
+  const float b = vx * c.c[0] + vy * c.c[1] + vz * c.c[2];
+  // squared distance from the origin to the line, without cancellation
+  const float qx = c.c[0] - b * vx, qy = c.c[1] - b * vy, qz = c.c[2] - b * vz;
+  const float qq = qx * qx + qy * qy + qz * qz;
+  const float disc = radius * radius - qq;
+  const float sq = sqrtf(fmaxf(disc, 0.f));
+  g.vx = vx; g.vy = vy; g.vz = vz; g.inv = inv;
+  g.t_in = -b - sq;
+  g.t_out = -b + sq;
+  g.enters = disc > 0.f && g.t_out > 0.f;
+  const float cc = c.c[0] * c.c[0] + c.c[1] * c.c[1] + c.c[2] * c.c[2];
+  g.dist = b < 0.f ? sqrtf(qq) : sqrtf(cc);
+  return g;
+}
+
+// Image coordinate of the centre of block X of a 2^level-coarser image:
+// (X + 1/2) 2^level, exact in float (x + 0.5 at level 0).
+__device__ __forceinline__ float block_centre(int X, int level) {
+  return (float)(2 * X + 1) * (float)(1 << level) * 0.5f;
+}
+
+// Ray q of a 2^level-coarser image (coarse-to-fine tracing, Sec. 3.2): its
+// camera, the full-resolution pixel that holds its state (the top-left pixel
+// of its block) and its block coordinates.  Every camera's H and W are
+// multiples of 2^level, so camera offsets are multiples of 4^level.
+__device__ __forceinline__ long long coarse_ray(const TraceArgs& a, long long q, int level,
+                                                int& ci, int& X, int& Y) {
+  ci = find_cam(a.cams, a.n_cams, q << (2 * level));
+  const CamDev& c = a.cams[ci];
+  const long long lq = q - (c.offset >> (2 * level));
+  const int Wl = c.W >> level;
+  X = (int)(lq % Wl);
+  Y = (int)(lq / Wl);
+  return c.offset + ((long long)Y << level) * c.W + ((long long)X << level);
+}
+
+__device__ __forceinline__ void write_miss(const TraceArgs& a, long long i, float sil, int status) {
+  a.o.depth[i] = kInf;
+  a.o.d_hit[i] = kInf;
+  a.o.mask[i] = 0;
+  a.o.sil[i] = sil;
+  if (a.o.status) a.o.status[i] = status;
+}
+
+// A ray that starts marching at its own entry point: no queries, no samples.
+__device__ __forceinline__ void start_ray(const TraceArgs& a, long long i, const RayGeom& g,
+                                          int ci) {
+  a.o.steps[i] = 0;
+  for (int k = 0; k < a.K; ++k) {
+    a.o.d_min[i * a.K + k] = __int_as_float(0x7fc00000);
+    a.o.f_min[i * a.K + k] = kInf;
+  }
+  if (g.enters) {
+    a.st[i] = make_float4(g.t_in, g.t_in, g.t_out, __int_as_float(ci));
+    a.fq[i] = 0;
+    a.fprev[i] = 0.f;
+    if (a.c2f) a.o.status[i] = a.c2f_start;
+  } else {
+    write_miss(a, i, g.dist - a.radius, DIST_RAY_INIT_MISS);
+  }
+}
+
+// One thread per ray (Sec. 3.2 "Initialization"): the ray through the pixel
+// centre (level 0) or through the centre of its block of a 2^level-coarser
+// image (coarse-to-fine tracing), its entry/exit distances into the bounding
+// sphere, and the background outputs of rays that miss it (depth +inf,
+// silhouette = distance from the origin to the ray minus the radius,
+// Sec. A.3).  Rays that enter are appended to `list0`.
+__global__ void raygen_kernel(TraceArgs a, int level, int* list0, int* count0) {
+  const long long n = a.n_pix >> (2 * level);
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
-       base < a.n_pix; base += stride) {
-    const long long i = a.pix0 + base + lane_id();
+       base < n; base += stride) {
+    long long i = 0;
     bool enters = false;
-    if (base + lane_id() < a.n_pix) {
-      const int ci = a.cam_fixed >= 0 ? a.cam_fixed : find_cam(a.cams, a.n_cams, i);
-      const CamDev& c = a.cams[ci];
-      const long long li = i - c.offset;
-      const int x = (int)(li % c.W), y = (int)(li / c.W);
-      const float xt = ((float)x + 0.5f - c.cx) / c.fx;
-      const float yt = ((float)y + 0.5f - c.cy) / c.fy;
-      const float inv = 1.0f / sqrtf(xt * xt + yt * yt + 1.0f);
-      const float vx0 = xt * inv, vy0 = yt * inv, vz0 = inv;
-      float vx = c.R[0] * vx0 + c.R[1] * vy0 + c.R[2] * vz0;
-      float vy = c.R[3] * vx0 + c.R[4] * vy0 + c.R[5] * vz0;
-      float vz = c.R[6] * vx0 + c.R[7] * vy0 + c.R[8] * vz0;
-      const float vn = 1.0f / sqrtf(vx * vx + vy * vy + vz * vz);
-      vx *= vn; vy *= vn; vz *= vn;
-      const float b = vx * c.c[0] + vy * c.c[1] + vz * c.c[2];
-      // squared distance from the origin to the line, without cancellation
-      const float qx = c.c[0] - b * vx, qy = c.c[1] - b * vy, qz = c.c[2] - b * vz;
-      const float qq = qx * qx + qy * qy + qz * qz;
-      const float disc = a.radius * a.radius - qq;
-      const float sq = sqrtf(fmaxf(disc, 0.f));
-      const float t_in = -b - sq, t_out = -b + sq;
-      enters = disc > 0.f && t_out > 0.f;
-      a.dir[i] = make_float4(vx, vy, vz, inv);
-      a.o.steps[i] = 0;
-      for (int k = 0; k < a.K; ++k) {
-        a.o.d_min[i * a.K + k] = __int_as_float(0x7fc00000);
-        a.o.f_min[i * a.K + k] = kInf;
-      }
-      if (enters) {
-        a.st[i] = make_float4(t_in, t_in, t_out, __int_as_float(ci));
-        a.fq[i] = 0;
-        a.fprev[i] = 0.f;
+    if (base + lane_id() < n) {
+      int ci, X, Y;
+      if (level == 0) {
+        i = a.pix0 + base + lane_id();
+        ci = a.cam_fixed >= 0 ? a.cam_fixed : find_cam(a.cams, a.n_cams, i);
+        const long long li = i - a.cams[ci].offset;
+        X = (int)(li % a.cams[ci].W);
+        Y = (int)(li / a.cams[ci].W);
       } else {
-        const float cc = c.c[0] * c.c[0] + c.c[1] * c.c[1] + c.c[2] * c.c[2];
-        const float dist = b < 0.f ? sqrtf(qq) : sqrtf(cc);
-        a.o.depth[i] = kInf;
-        a.o.d_hit[i] = kInf;
-        a.o.mask[i] = 0;
-        a.o.sil[i] = dist - a.radius;
-        if (a.o.status) a.o.status[i] = DIST_RAY_INIT_MISS;
+        i = coarse_ray(a, base + lane_id(), level, ci, X, Y);
       }
+      const RayGeom g = ray_geom(a.cams[ci], a.radius, block_centre(X, level),
+                                 block_centre(Y, level));
+      a.dir[i] = make_float4(g.vx, g.vy, g.vz, g.inv);
+      start_ray(a, i, g, ci);
+      enters = g.enters;
     }
     const int slot = warp_append(enters, count0);
     if (slot >= 0) list0[slot] = (int)i;
+  }
+}
+
+// Coarse-to-fine split (Sec. 3.2): every ray of level `level` becomes its
+// four children of level - 1.  One thread per parent reads the parent's state
+// (held at its block's top-left pixel, which is also its first child's) and
+// writes the children's.  What a child inherits is not stated in the paper;
+// the reading: a child has its own direction and bounding-sphere interval (a
+// child that misses the sphere is background); a child of a parent that
+// missed the sphere starts at its own entry; otherwise it inherits the step
+// count and the k smallest-|f| samples with |f| raised to eps, and
+//  * a marching or converged parent's ray distance d, raised to the child's
+//    t_in (past its t_out the child has left the sphere): the child marches
+//    on from there, in the parent's list (a converged parent's children in
+//    the FP32 list), or ends as MAX_STEPS when no query is left (`final`);
+//  * a parent that left the sphere or ran out of queries: the same outcome.
+__global__ void split_kernel(TraceArgs a, int level, int final, int* list0, int* list1,
+                             int* count0, int* count1) {
+  const long long n = a.n_pix >> (2 * level);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
+       base < n; base += stride) {
+    // per lane: up to 4 children appended to list 0 / list 1
+    int add0[4] = {-1, -1, -1, -1}, add1[4] = {-1, -1, -1, -1};
+    if (base + lane_id() < n) {
+      int ci, X, Y;
+      const long long ip = coarse_ray(a, base + lane_id(), level, ci, X, Y);
+      const CamDev& c = a.cams[ci];
+      const int status = a.o.status[ip];
+      const float4 sp = a.st[ip];
+      const int steps = a.o.steps[ip];
+      float fm[kMaxK], dm[kMaxK];
+      for (int k = 0; k < kMaxK; ++k) {
+        fm[k] = k < a.K ? a.o.f_min[ip * a.K + k] : kInf;
+        dm[k] = k < a.K ? a.o.d_min[ip * a.K + k] : 0.f;
+      }
+      const int fq = a.fq[ip];
+      const float fprev = a.fprev[ip], dprev = a.dprev[ip];
+      const bool marching = status < 0 || status == DIST_RAY_HIT;
+      const int list = status == DIST_RAY_HIT ? 1 : (status == -1 ? 0 : 1);
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) {
+        const int cx = 2 * X + (ch & 1), cy = 2 * Y + (ch >> 1);
+        const long long i = c.offset + ((long long)cy << (level - 1)) * c.W +
+                            ((long long)cx << (level - 1));
+        const RayGeom g = ray_geom(c, a.radius, block_centre(cx, level - 1),
+                                   block_centre(cy, level - 1));
+        a.dir[i] = make_float4(g.vx, g.vy, g.vz, g.inv);
+        if (!g.enters || status == DIST_RAY_INIT_MISS) {
+          start_ray(a, i, g, ci);
+          if (g.enters) {
+            if (final) {
+              write_miss(a, i, kInf, DIST_RAY_MAX_STEPS);
+            } else if (a.c2f_start == -1) {
+              add0[ch] = (int)i;
+            } else {
+              add1[ch] = (int)i;
+            }
+          }
+          continue;
+        }
+        a.o.steps[i] = steps;
+        float fm0 = kInf;
+        for (int k = 0; k < a.K; ++k) {
+          const float f = copysignf(fmaxf(fabsf(fm[k]), a.eps), fm[k]);
+          a.o.f_min[i * a.K + k] = f;
+          a.o.d_min[i * a.K + k] = dm[k];
+          if (k == 0) fm0 = fabsf(f);
+        }
+        if (!marching) {
+          write_miss(a, i, fm0 - a.eps, status);
+          continue;
+        }
+        const float d = fmaxf(sp.x, g.t_in);
+        if (d > g.t_out) {
+          write_miss(a, i, fm0 - a.eps, DIST_RAY_LEFT);
+        } else if (final) {
+          write_miss(a, i, fm0 - a.eps, DIST_RAY_MAX_STEPS);
+        } else {
+          a.st[i] = make_float4(d, g.t_in, g.t_out, __int_as_float(ci));
+          a.fq[i] = fq;
+          a.fprev[i] = fprev;
+          a.dprev[i] = dprev;
+          a.o.status[i] = list == 0 ? -1 : -2;
+          if (list == 0) add0[ch] = (int)i;
+          else add1[ch] = (int)i;
+        }
+      }
+    }
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      const int s0 = warp_append(add0[ch] >= 0, count0);
+      if (s0 >= 0) list0[s0] = add0[ch];
+      const int s1 = warp_append(add1[ch] >= 0, count1);
+      if (s1 >= 0) list1[s1] = add1[ch];
+    }
   }
 }
 
@@ -563,6 +719,14 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
              DIST_E_INVALID, "bad refine_rule");
   DIST_CHECK(p->grad_mode == DIST_GRAD_EXACT || p->grad_mode == DIST_GRAD_PAPER, DIST_E_INVALID,
              "bad grad_mode");
+  DIST_CHECK(p->coarse_levels >= 0 && p->coarse_levels <= kMaxCoarseLevels &&
+                 p->coarse_every >= 1,
+             DIST_E_INVALID, "coarse_levels must be 0..4 and coarse_every >= 1");
+  DIST_CHECK(p->coarse_levels == 0 || !is_tc(p->precision) ||
+                 (fp32_on_tc(*p) && p->refine_steps == 0),
+             DIST_E_INVALID,
+             "coarse-to-fine tracing with a BF16/FP16 march needs refine_steps 0 and the TC "
+             "refine engine");
   DIST_CHECK(!(is_tc(p->precision) || fp32_on_tc(*p)) || dec->tc.ok, DIST_E_UNSUPPORTED,
              "the tensor-core decoder covers only the DeepSDF shape (512 x 8, skip 4, latent 256)");
   DIST_CHECK(o->depth && o->sil && o->mask && o->steps && o->d_hit && o->d_min && o->f_min,
@@ -577,6 +741,9 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
                "camera image size out of range");
     DIST_CHECK(k.shape >= 0 && k.shape < n_shapes, DIST_E_INVALID, "camera shape index out of range");
     DIST_CHECK(k.fx != 0.f && k.fy != 0.f, DIST_E_INVALID, "zero focal length");
+    DIST_CHECK(k.H % (1 << p->coarse_levels) == 0 && k.W % (1 << p->coarse_levels) == 0,
+               DIST_E_INVALID, "coarse-to-fine tracing: H and W must be multiples of "
+               "2^coarse_levels");
     const double cc = (double)k.c[0] * k.c[0] + (double)k.c[1] * k.c[1] + (double)k.c[2] * k.c[2];
     DIST_CHECK(cc > (double)p->radius * p->radius, DIST_E_INVALID,
                "camera inside the bounding sphere");
@@ -615,6 +782,10 @@ TraceArgs make_args(const dist_trace_params* p, const dist_trace_out* o, dist_wo
   a.alpha_fp32 = (is_tc(p->precision) && p->alpha_refine > 0.f) ? p->alpha_refine : p->alpha;
   a.o = *o; a.st = ws->st; a.dir = ws->dir; a.fq = ws->fq; a.fprev = ws->fprev;
   a.dprev = ws->dprev;
+  a.c2f = p->coarse_levels > 0 ? 1 : 0;
+  a.c2f_start = is_tc(p->precision) ? -1 : -2;
+  a.last = 0;
+  if (a.c2f && !a.o.status) a.o.status = ws->rstat;
   return a;
 }
 
@@ -709,6 +880,7 @@ static TraceArgs pool_args(const RayPool& P) {
   a.max_steps = P.max_steps; a.o = P.o; a.st = P.st; a.dir = P.dir;
   a.fq = P.fq; a.fprev = P.fprev; a.dprev = P.dprev; a.refine = P.refine;
   a.secant = P.secant; a.alpha_fp32 = P.alpha_fp32;
+  a.c2f = 0; a.c2f_start = 0; a.last = 0;
   return a;
 }
 
@@ -727,7 +899,7 @@ cudaError_t pool_raygen(const RayPool& P, int cam, long long pix0, long long n, 
                         int* count0, cudaStream_t st) {
   TraceArgs a = pool_args(P);
   a.n_pix = n; a.pix0 = pix0; a.cam_fixed = cam;
-  raygen_kernel<<<grid_for(n, 256), 256, 0, st>>>(a, list0, count0);
+  raygen_kernel<<<grid_for(n, 256), 256, 0, st>>>(a, 0, list0, count0);
   count_launch(1);
   return cudaGetLastError();
 }
@@ -800,17 +972,38 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
   const long long n_pix = pr.n_pix;
   TraceArgs a = make_args(p, o, ws, n_cams, n_pix);
   // list lengths: cA[s] low-precision list at step s, cB[t] FP32 list at
-  // FP32 step t, and a constant zero for a list that is not used
+  // FP32 step t, a constant zero for a list that is not used, and the two
+  // lists made by each coarse-to-fine split
   const int M = p->max_steps;
   int* cA = ws->counts;
   int* cB = ws->counts + (M + 1);
   int* zero = ws->counts + 2 * (M + 1);
-  DIST_CUDA_TRY(cudaMemsetAsync(ws->counts, 0, (size_t)(2 * (M + 1) + 1) * sizeof(int), st));
+  int* cSplit = zero + 1;
+  DIST_CUDA_TRY(cudaMemsetAsync(
+      ws->counts, 0, (size_t)(2 * (M + 1) + 1 + 2 * kMaxCoarseLevels) * sizeof(int), st));
   const bool tc = is_tc(p->precision);
+  const int L = p->coarse_levels;
+  // coarse-to-fine: rays start 2^L coarser per side; before march iteration
+  // `every * k` (k = 1..L) every ray splits into its four children
+  int level = L;
+  auto split_due = [&](int it) { return level > 0 && it == p->coarse_every * (L - level + 1); };
+  int par = 0;
+  auto split = [&](int final, const int*& in0, const int*& in1) -> cudaError_t {
+    int* c0 = cSplit + 2 * (L - level);
+    split_kernel<<<grid_for(n_pix >> (2 * level), 256), 256, 0, st>>>(
+        a, level, final, ws->act[par ^ 1][0], ws->act[par ^ 1][1], c0, c0 + 1);
+    count_launch(1);
+    --level;
+    par ^= 1;
+    in0 = c0;
+    in1 = c0 + 1;
+    return cudaGetLastError();
+  };
+  const long long n0 = n_pix >> (2 * L);
   if (tc)
-    raygen_kernel<<<grid_for(n_pix, 256), 256, 0, st>>>(a, ws->act[0][0], cA);
+    raygen_kernel<<<grid_for(n0, 256), 256, 0, st>>>(a, L, ws->act[0][0], cA);
   else
-    raygen_kernel<<<grid_for(n_pix, 256), 256, 0, st>>>(a, ws->act[0][1], cB);
+    raygen_kernel<<<grid_for(n0, 256), 256, 0, st>>>(a, L, ws->act[0][1], cB);
   DIST_LAUNCH_CHECK();
   const float* b0 = ws->bfold;
   const float* bs = ws->bfold + kMaxShapes * 512;
@@ -824,16 +1017,19 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
     // of steps.  (With refine_steps > 0 a handed-over ray needs only a few
     // FP32-class queries, and one deferred batch of them, below, is
     // cheaper.)
+    const int* in0 = cA;
+    const int* in1 = cB;
     for (int s = 0; s < M; ++s) {
-      const int par = s & 1;
+      if (split_due(s)) DIST_CUDA_TRY(split(0, in0, in1));
       RowSrc sx = src;
-      src.count = cA + s;
+      src.count = in0;
       src.idx = ws->act[par][0];
-      sx.count = cB + s;
+      sx.count = in1;
       sx.idx = ws->act[par][1];
       // the decoder kernel applies the step update itself
       StepFuse sf;
       sf.t = a;
+      sf.t.last = a.c2f && s == M - 1;
       sf.out[0] = ws->act[par ^ 1][0]; sf.out[1] = ws->act[par ^ 1][1];
       sf.cnt_out[0] = cA + s + 1; sf.cnt_out[1] = cB + s + 1;
       sf.queries = o->queries;
@@ -841,7 +1037,11 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
       DIST_CUDA_TRY(mlp_tc_fused(dec, src, ws->fbuf[0], sx, ws->fbuf[1], b0, bs, st,
                                  p->precision == DIST_PREC_FP16, &sf));
       prof_mlp_end(st);
+      in0 = cA + s + 1;
+      in1 = cB + s + 1;
+      par ^= 1;
     }
+    while (level > 0) DIST_CUDA_TRY(split(1, in0, in1));
     if (o->normal) return normals_impl(dec, p, o, o->normal, ws, n_cams, n_pix, st);
     return DIST_OK;
   }
@@ -850,7 +1050,7 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
     // low-precision |f| is small enough move to one FP32 list that grows
     // over all steps: their FP32 queries run together afterwards instead of
     // as a small launch every step.  A ray's result does not depend on when
-    // its queries run.
+    // its queries run.  (No coarse-to-fine here: validated.)
     for (int s = 0; s < M; ++s) {
       const int par = s & 1;
       src.count = cA + s;
@@ -873,9 +1073,11 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
   // After the tensor-core march the first FP32 launch holds every handed-over
   // ray (64-row tiles for throughput); the shrinking tail after it runs in
   // 16-row tiles, whose launch latency is a quarter of a 64-row tile's.
+  const int* in0 = zero;
+  const int* in1 = cB;
   for (int t = 0; t < M; ++t) {
-    const int par = t & 1;
-    src.count = cB + t;
+    if (split_due(t)) DIST_CUDA_TRY(split(0, in0, in1));
+    src.count = in1;
     src.idx = ws->act[par][1];
     prof_mlp_begin(st, 1);
     if (fp32_on_tc(*p))
@@ -884,14 +1086,19 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
       DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->fbuf[1], st, tc && t > 0));
     prof_mlp_end(st);
     StepLists L;
-    L.cnt_in[0] = zero; L.cnt_in[1] = cB + t;
+    L.cnt_in[0] = zero; L.cnt_in[1] = in1;
     L.cnt_out[0] = zero; L.cnt_out[1] = cB + t + 1;
     L.in[0] = ws->act[0][0]; L.in[1] = ws->act[par][1];
     L.f[0] = ws->fbuf[0]; L.f[1] = ws->fbuf[1];
     L.out[0] = ws->act[0][0]; L.out[1] = ws->act[par ^ 1][1];
-    step_kernel<<<step_grid, kStepThreads, 0, st>>>(a, L, o->queries);
+    TraceArgs at = a;
+    at.last = a.c2f && t == M - 1;
+    step_kernel<<<step_grid, kStepThreads, 0, st>>>(at, L, o->queries);
     DIST_LAUNCH_CHECK();
+    in1 = cB + t + 1;
+    par ^= 1;
   }
+  while (level > 0) DIST_CUDA_TRY(split(1, in0, in1));
   if (o->normal) return normals_impl(dec, p, o, o->normal, ws, n_cams, n_pix, st);
   return DIST_OK;
 }
