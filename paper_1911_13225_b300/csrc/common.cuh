@@ -123,12 +123,6 @@ struct DecoderTC {
   TCMaps bmaps16;                // same, fp16
   TCMaps xmaps;                  // [N][2K] fp16 hi | lo split of 2^s_l W_l (FP32-class kernel)
   TCMaps pmaps, pmaps16, pxmaps; // the same three with 128-row boxes (CTA-pair kernel)
-  // The same weights as images of the forward kernel's shared-memory stages:
-  // per GEMM, [N/256][K'/64] blocks of 256 x 64 16-bit values in the 128B-
-  // swizzled K-major layout (32 KB each, K' = K, or 2K for the split), so
-  // that one bulk copy fills a stage
-  const uint8_t* img[2][7];      // bf16, fp16
-  const uint8_t* ximg[7];        // FP32-class split
   bool pair;                     // forward kernel on CTA pairs (cta_group::2)
   float x_inv_scale[7];          // 2^-s_l
   const TCConst* cst;            // epilogue constants (device)

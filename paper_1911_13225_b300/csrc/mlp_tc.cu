@@ -57,8 +57,6 @@ struct TCArgs {
   float* fout[2];
   int* err;
   float inv_scale[NUM_GEMM];     // list 1: 2^-s_l of GEMM layer g
-  const uint8_t* img[NUM_GEMM];  // stage images of the 16-bit weights (this launch's format)
-  const uint8_t* ximg[NUM_GEMM]; // stage images of the FP32-class split
   int fuse_step;                 // apply `step` to each row instead of writing f
   StepFuse step;
 };
@@ -186,10 +184,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
                 tma_load_2d_pair(wst + stage * SB, map, full_lead + 8u * (uint32_t)stage,
                                  xk * BK, nh * BN + 128 * rank);
               } else {
-                // one 32 KB block of the stage image: (nh, xk) of this GEMM
-                const uint8_t* src = (xt ? a.ximg[g] : a.img[g]) +
-                                     (size_t)(nh * (xt ? 2 : 1) * nkc + xk) * SB;
-                bulk_load(wst + stage * SB, src, SB, full + stage);
+                tma_load_2d(wst + stage * SB, map, full + stage, xk * BK, nh * BN);
               }
               issued[stage] = true;
               issued_parity[stage] = phase;
@@ -996,31 +991,6 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
 // epilogue; the transposed copy's extra rows meet a zero ReLU mask.)
 static int skip_col(int l, int k) { return (l == 4 && k >= 253) ? 253 + 256 + (k - 253) : k; }
 
-// Stage image of an [N][K] 16-bit matrix (K contiguous): blocks (nh, kc) of
-// 256 rows x 64 columns in that order, each laid out as the 128B-swizzled
-// K-major tile a TMA copy of the same box writes to shared memory (16-byte
-// group u of row r at r * 128 + ((u ^ (r & 7)) << 4)).  Uploaded; owned by d.
-static dist_status upload_stage_image(dist_decoder* d, const std::vector<uint16_t>& h, int N,
-                                      int K, const uint8_t** out) {
-  std::vector<uint16_t> img((size_t)N * K);
-  const int nkc = K / BK;
-  for (int nh = 0; nh < N / BN; ++nh)
-    for (int kc = 0; kc < nkc; ++kc) {
-      uint16_t* blk = img.data() + (size_t)(nh * nkc + kc) * (BN * BK);
-      for (int r = 0; r < BN; ++r)
-        for (int u = 0; u < BK / 8; ++u)
-          for (int e = 0; e < 8; ++e)
-            blk[(r * 128 + ((u ^ (r & 7)) << 4)) / 2 + e] =
-                h[(size_t)(nh * BN + r) * K + kc * BK + u * 8 + e];
-    }
-  void* p = nullptr;
-  DIST_CUDA_TRY(cudaMalloc(&p, img.size() * sizeof(uint16_t)));
-  d->allocations.push_back(p);
-  DIST_CUDA_TRY(cudaMemcpy(p, img.data(), img.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
-  *out = static_cast<const uint8_t*>(p);
-  return DIST_OK;
-}
-
 // Weights of GEMM layers 1..7 as [N rows][2K cols] fp16: columns 0..K-1 hold
 // W_hi, K..2K-1 hold W_lo, both of W * 2^s_l.
 dist_status pack_tcx(dist_decoder* d, const float* const* W) {
@@ -1056,10 +1026,6 @@ dist_status pack_tcx(dist_decoder* d, const float* const* W) {
     DIST_CUDA_TRY(cudaMalloc(&q, h.size() * sizeof(uint16_t)));
     d->allocations.push_back(q);
     DIST_CUDA_TRY(cudaMemcpy(q, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
-    {
-      dist_status is = upload_stage_image(d, h, N, 2 * K, &d->tc.ximg[g]);
-      if (is != DIST_OK) return is;
-    }
     cuuint64_t dims[2] = {(cuuint64_t)(2 * K), (cuuint64_t)N};
     cuuint64_t strides[1] = {(cuuint64_t)(2 * K) * sizeof(uint16_t)};
     cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BN};
@@ -1132,10 +1098,6 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
       DIST_CUDA_TRY(cudaMalloc(&p, h.size() * sizeof(uint16_t)));
       d->allocations.push_back(p);
       DIST_CUDA_TRY(cudaMemcpy(p, h.data(), h.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
-      {
-        dist_status is = upload_stage_image(d, h, N, K, &d->tc.img[f16][g]);
-        if (is != DIST_OK) return is;
-      }
       cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)N};
       cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(uint16_t)};
       cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)BN};
@@ -1234,11 +1196,7 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
   a.fout[0] = f16out;
   a.fout[1] = fxout;
   a.err = dec->tc.err;
-  for (int g = 0; g < NUM_GEMM; ++g) {
-    a.inv_scale[g] = dec->tc.x_inv_scale[g];
-    a.img[g] = dec->tc.img[f16 ? 1 : 0][g];
-    a.ximg[g] = dec->tc.ximg[g];
-  }
+  for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
   a.fuse_step = step ? 1 : 0;
   if (step) a.step = *step;
   else memset(&a.step, 0, sizeof(a.step));
