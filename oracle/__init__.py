@@ -16,7 +16,9 @@ of the paper it follows:
                  convergence and outputs (Alg. 1, Sec. 3.2, Eq. 1, Sec. 3.3,
                  Sec. A.3), and coarse-to-fine tracing (Sec. 3.2).
 * ``grad``    -- latent gradients: exact implicit form and the paper's
-                 first-term approximation (Eq. 2, Sec. 3.4, Sec. B.2).
+                 first-term approximation (Eq. 2, Sec. 3.4, Sec. B.2);
+                 camera-extrinsic gradients of depth and silhouette
+                 (Sec. 4.2, pose optimisation through the renderer).
 * ``loss``    -- depth / normal / silhouette losses (Sec. 4.2.1, Eq. 4 of the
                  appendix, Sec. B.3).
 * ``sdf``     -- analytic SDFs used as pins (sphere, box, plane, slab).
