@@ -322,6 +322,29 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
                            const float* g_sil, float* dz,
                            dist_workspace* ws, void* stream);
 
+/* Gradients of the loss with respect to each camera's extrinsics (Sec. 4.2:
+ * the pose optimised through the renderer with the shape fixed, from depth
+ * and silhouette).  A camera enters each ray through its centre c and the
+ * direction v = R v_cam / |R v_cam|, v_cam the unit pixel direction in the
+ * camera frame.  Depth: the exact implicit derivative of the converged root,
+ * dd = -(grad_p f . (dc + d dv)) / (grad_p f . v) at the hit (grazing rays
+ * contribute 0, as in dist_trace_bwd), times 1/sqrt(x~^2+y~^2+1).
+ * Silhouette of a ray that entered the bounding sphere: the first-term rule,
+ * sign(f_min) grad_p f(p_min) . (dc + d_min dv) with d_min held fixed; of a
+ * ray that missed it: the exact derivative of the distance from the origin
+ * to the ray.  R is differentiated as a free 3 x 3 matrix (v renormalised).
+ * Output dcam (device, [n_cams][12], OVERWRITTEN): dL/dc (3 floats) then
+ * dL/dR row-major (9 floats) per camera; per-camera sums are reduced in
+ * FP64.  grad_p f comes from the decoder adjoint in the trace's precision.
+ * g_depth [n], g_sil [n] are device arrays or NULL.  Uses the workspace's
+ * probe buffers and reduction scratch. */
+dist_status dist_trace_bwd_camera(const dist_decoder* dec, const float* z, int n_shapes,
+                                  const dist_camera* cams, int n_cams,
+                                  const dist_trace_params* params,
+                                  const dist_trace_out* fwd, const float* g_depth,
+                                  const float* g_sil, float* dcam, dist_workspace* ws,
+                                  void* stream);
+
 /* ---------------------------------------------------------------- serving */
 
 typedef struct dist_server dist_server;

@@ -264,6 +264,20 @@ def backward(dec: Decoder, z: torch.Tensor, cams, params: TraceParams, ws: Works
     return dz
 
 
+def backward_camera(dec: Decoder, z: torch.Tensor, cams, params: TraceParams, ws: Workspace,
+                    fwd: TraceResult, g_depth=None, g_sil=None, stream=None) -> torch.Tensor:
+    """dist_trace_bwd_camera: [n_cams, 12] = dL/dc (3) and dL/dR row-major (9)."""
+    z = z.contiguous()
+    out = torch.empty(len(cams), 12, device=z.device, dtype=torch.float32)
+    p = params.c()
+    o = fwd.c()
+    check(lib().dist_trace_bwd_camera(dec.handle, _ptr(z), int(z.shape[0]), camera_array(cams),
+                                      len(cams), byref(p), byref(o), _ptr(g_depth), _ptr(g_sil),
+                                      _ptr(out), ws.handle, _stream(stream)),
+          "dist_trace_bwd_camera")
+    return out
+
+
 class DistRender(torch.autograd.Function):
     """Differentiable render: z -> (depth, silhouette[, normal]).
 

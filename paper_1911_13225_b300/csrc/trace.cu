@@ -517,6 +517,188 @@ __global__ void probes_bwd_kernel(ProbeArgs a, const float* g_depth, const float
   }
 }
 
+// ------------------------------------------------------ camera gradients
+
+constexpr int kCamSil = 1 << 30;   // probe_pix flag: silhouette probe (else depth)
+
+// Probes for the camera gradient: at the hit of every pixel with a depth
+// gradient, and at the smallest-|f| sample of every pixel with a silhouette
+// gradient whose ray entered the sphere and was queried.
+__global__ void probes_cam_kernel(ProbeArgs a, const float* g_depth, const float* g_sil) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
+       base < a.n_pix; base += stride) {
+    const long long i = base + lane_id();
+    int nd = 0, ns = 0;
+    if (i < a.n_pix) {
+      nd = g_depth && a.o.mask[i] && g_depth[i] != 0.f ? 1 : 0;
+      ns = g_sil && g_sil[i] != 0.f && !isnan(a.o.d_min[i * a.K]) ? 1 : 0;
+    }
+    int slot = warp_append_n(nd + ns, a.count);
+    if (nd + ns > 0) {
+      const CamDev& c = a.cams[find_cam(a.cams, a.n_cams, i)];
+      const float4 v = a.dir[i];
+      if (nd) {
+        a.pp[slot] = ray_point(c, v, a.o.d_hit[i], c.shape);
+        a.pix[slot] = (int)i;
+        ++slot;
+      }
+      if (ns) {
+        a.pp[slot] = ray_point(c, v, a.o.d_min[i * a.K], c.shape);
+        a.pix[slot] = (int)i | kCamSil;
+      }
+    }
+  }
+}
+
+// Adds the 12 values of one ray's dL/d(c, R) to its camera's FP64 sums: one
+// set of atomics per warp when the warp's lanes share a camera.
+__device__ __forceinline__ void cam_accumulate(double* G, int ci, bool have, const double (&v)[12]) {
+  const unsigned act = __activemask();
+  const unsigned peers = __match_any_sync(act, have ? ci : -1);
+  const bool uniform = __all_sync(act, have) && peers == act;
+  if (uniform) {
+    double r[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) {
+      double x = v[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(act, x, o);
+      r[k] = x;
+    }
+    if (lane_id() == __ffs(act) - 1) {
+#pragma unroll
+      for (int k = 0; k < 12; ++k)
+        if (r[k] != 0.0) atomicAdd(G + (size_t)ci * 12 + k, r[k]);
+    }
+  } else if (have) {
+#pragma unroll
+    for (int k = 0; k < 12; ++k)
+      if (v[k] != 0.0) atomicAdd(G + (size_t)ci * 12 + k, v[k]);
+  }
+}
+
+// The camera frame direction of pixel i: v_cam = (x~, y~, 1)/|.|, and
+// u = R v_cam (the world direction before normalisation).
+__device__ __forceinline__ void pixel_frame(const CamDev& c, long long i, double (&vc)[3],
+                                            double (&u)[3]) {
+  const long long li = i - c.offset;
+  const int x = (int)(li % c.W), y = (int)(li / c.W);
+  const double xt = ((double)x + 0.5 - c.cx) / c.fx;
+  const double yt = ((double)y + 0.5 - c.cy) / c.fy;
+  const double inv = 1.0 / sqrt(xt * xt + yt * yt + 1.0);
+  vc[0] = xt * inv; vc[1] = yt * inv; vc[2] = inv;
+  for (int a = 0; a < 3; ++a)
+    u[a] = c.R[3 * a] * vc[0] + c.R[3 * a + 1] * vc[1] + c.R[3 * a + 2] * vc[2];
+}
+
+// dL/dR from dL/dv: v = u/|u|, u = R v_cam.
+__device__ __forceinline__ void cam_pack(const double (&dc)[3], const double (&dv)[3],
+                                         const double (&vc)[3], const double (&u)[3],
+                                         double (&out)[12]) {
+  const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+  const double v[3] = {u[0] / un, u[1] / un, u[2] / un};
+  const double vd = v[0] * dv[0] + v[1] * dv[1] + v[2] * dv[2];
+  for (int a = 0; a < 3; ++a) {
+    out[a] = dc[a];
+    const double du = (dv[a] - v[a] * vd) / un;
+    for (int b = 0; b < 3; ++b) out[3 + 3 * a + b] = du * vc[b];
+  }
+}
+
+// Per probe: the depth (implicit) or entering-silhouette (first-term)
+// contribution to the camera gradient, from grad_p f of the adjoint.
+__global__ void cam_probe_grad_kernel(ProbeArgs a, const float* out4, const float* g_depth,
+                                      const float* g_sil, double* G) {
+  const int n = *a.count;
+  for (int base = (blockIdx.x * blockDim.x + threadIdx.x) & ~31; base < n;
+       base += gridDim.x * blockDim.x) {
+    const int j = base + lane_id();
+    double val[12];
+    for (int k = 0; k < 12; ++k) val[k] = 0.0;
+    bool have = false;
+    int ci = 0;
+    if (j < n) {
+      const int pj = a.pix[j];
+      const bool sil = (pj & kCamSil) != 0;
+      const long long i = pj & (kCamSil - 1);
+      ci = find_cam(a.cams, a.n_cams, i);
+      const CamDev& c = a.cams[ci];
+      double vc[3], u[3];
+      pixel_frame(c, i, vc, u);
+      const float4 g4 = reinterpret_cast<const float4*>(out4)[j];
+      const double gp[3] = {g4.y, g4.z, g4.w};
+      const float4 v4 = a.dir[i];
+      const double v[3] = {v4.x, v4.y, v4.z};
+      double dc[3] = {0.0, 0.0, 0.0}, dv[3] = {0.0, 0.0, 0.0};
+      if (!sil) {
+        const double gv = gp[0] * v[0] + gp[1] * v[1] + gp[2] * v[2];
+        const double gn = sqrt(gp[0] * gp[0] + gp[1] * gp[1] + gp[2] * gp[2]);
+        if (fabs(gv) >= 1e-3 * gn && gv != 0.0) {
+          const double w = (double)g_depth[i] * (double)v4.w / gv;
+          const double d = a.o.d_hit[i];
+          for (int k = 0; k < 3; ++k) { dc[k] = -w * gp[k]; dv[k] = -w * d * gp[k]; }
+          have = true;
+        }
+      } else {
+        const float fm = a.o.f_min[i * a.K];
+        const double s = (fm > 0.f ? 1.0 : (fm < 0.f ? -1.0 : 0.0)) * (double)g_sil[i];
+        const double d = a.o.d_min[i * a.K];
+        for (int k = 0; k < 3; ++k) { dc[k] = s * gp[k]; dv[k] = s * d * gp[k]; }
+        have = true;
+      }
+      if (have) cam_pack(dc, dv, vc, u, val);
+    }
+    cam_accumulate(G, ci, have, val);
+  }
+}
+
+// Rays that missed the bounding sphere: S = dist(origin, ray) - radius
+// (Sec. A.3), differentiated exactly; such a ray made no query (steps 0)
+// and has a finite silhouette.
+__global__ void cam_miss_grad_kernel(ProbeArgs a, const float* g_sil, double* G) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = ((long long)blockIdx.x * blockDim.x + threadIdx.x) & ~31ll;
+       base < a.n_pix; base += stride) {
+    const long long i = base + lane_id();
+    double val[12];
+    for (int k = 0; k < 12; ++k) val[k] = 0.0;
+    bool have = false;
+    int ci = 0;
+    if (i < a.n_pix && g_sil[i] != 0.f && a.o.steps[i] == 0 && isfinite(a.o.sil[i])) {
+      ci = find_cam(a.cams, a.n_cams, i);
+      const CamDev& c = a.cams[ci];
+      double vc[3], u[3];
+      pixel_frame(c, i, vc, u);
+      const float4 v4 = a.dir[i];
+      const double v[3] = {v4.x, v4.y, v4.z};
+      const double cc[3] = {c.c[0], c.c[1], c.c[2]};
+      const double b = v[0] * cc[0] + v[1] * cc[1] + v[2] * cc[2];
+      const double c2 = cc[0] * cc[0] + cc[1] * cc[1] + cc[2] * cc[2];
+      const double g = g_sil[i];
+      double dc[3], dv[3];
+      if (b < 0.0) {
+        const double dist = sqrt(fmax(c2 - b * b, 0.0));
+        for (int k = 0; k < 3; ++k) {
+          dc[k] = g * (cc[k] - b * v[k]) / dist;
+          dv[k] = -g * b * cc[k] / dist;
+        }
+      } else {
+        const double dist = sqrt(c2);
+        for (int k = 0; k < 3; ++k) { dc[k] = g * cc[k] / dist; dv[k] = 0.0; }
+      }
+      cam_pack(dc, dv, vc, u, val);
+      have = true;
+    }
+    cam_accumulate(G, ci, have, val);
+  }
+}
+
+__global__ void cam_finalize_kernel(const double* G, int n, float* out) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    out[k] = (float)G[k];
+}
+
 // Normal-loss coefficients: with g = FD gradient from the six probe values
 // and n = g / |g|, dL/dg = (g_n - n (n . g_n)) / |g|; probe +a gets
 // dL/dg_a / (2 delta), probe -a its negative (hit point held fixed).
@@ -1177,6 +1359,42 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
   }
   dim3 fg((d.latent + 31) / 32, n_shapes);
   latent_finalize_kernel<<<fg, kFinalizeWarps * 32, 0, st>>>(d, G0, Gs, n_shapes, dz);
+  DIST_LAUNCH_CHECK();
+  return DIST_OK;
+}
+
+dist_status dist_trace_bwd_camera(const dist_decoder* dec, const float* z, int n_shapes,
+                                  const dist_camera* cams, int n_cams, const dist_trace_params* p,
+                                  const dist_trace_out* fwd, const float* g_depth,
+                                  const float* g_sil, float* dcam, dist_workspace* ws,
+                                  void* stream) {
+  DIST_CHECK(dcam, DIST_E_INVALID, "dist_trace_bwd_camera: NULL dcam");
+  Prepared pr;
+  dist_status s = validate_and_upload(dec, z, n_shapes, cams, n_cams, p, fwd, ws, stream, &pr);
+  if (s != DIST_OK) return s;
+  cudaStream_t st = pr.st;
+  const long long n_pix = pr.n_pix;
+  const float* b0 = ws->bfold;
+  const float* bs = ws->bfold + kMaxShapes * 512;
+  double* G = ws->gacc;   // [n_cams][12] (the latent accumulators are free here)
+  DIST_CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)n_cams * 12 * sizeof(double), st));
+  DIST_CUDA_TRY(cudaMemsetAsync(ws->probe_count, 0, 8 * sizeof(int), st));
+  const int g = grid_for(n_pix, 256);
+  ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, 0, 0);
+  if (g_depth || g_sil) {
+    probes_cam_kernel<<<g, 256, 0, st>>>(a, g_depth, g_sil);
+    DIST_LAUNCH_CHECK();
+    DIST_CUDA_TRY(adjoint(dec, p, ws, ws->probe_p, nullptr, ws->probe_count, b0, bs,
+                          ws->probe_out, nullptr, nullptr, 0, st));
+    cam_probe_grad_kernel<<<grid_for(2 * n_pix, 256), 256, 0, st>>>(a, ws->probe_out, g_depth,
+                                                                     g_sil, G);
+    DIST_LAUNCH_CHECK();
+  }
+  if (g_sil) {
+    cam_miss_grad_kernel<<<g, 256, 0, st>>>(a, g_sil, G);
+    DIST_LAUNCH_CHECK();
+  }
+  cam_finalize_kernel<<<grid_for(n_cams * 12, 256), 256, 0, st>>>(G, n_cams * 12, dcam);
   DIST_LAUNCH_CHECK();
   return DIST_OK;
 }
