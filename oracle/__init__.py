@@ -21,6 +21,8 @@ of the paper it follows:
                  (Sec. 4.2, pose optimisation through the renderer).
 * ``loss``    -- depth / normal / silhouette losses (Sec. 4.2.1, Eq. 4 of the
                  appendix, Sec. B.3).
+* ``photo``   -- multi-view photometric loss: warp by the rendered depth,
+                 bilinear sampling, visibility test, L1 (Sec. 4.2, Sec. B.3).
 * ``sdf``     -- analytic SDFs used as pins (sphere, box, plane, slab).
 * ``brute``   -- dense fixed-step first-root search used as a pin.
 
