@@ -300,6 +300,26 @@ dist_status dist_loss(int64_t n_pixels, const float* depth, const uint8_t* mask,
                       float* g_depth, float* g_normal, float* g_sil, float* dz,
                       dist_workspace* ws, void* stream);
 
+/* Multi-view photometric loss (Sec. 4.2: each colour image warped into the
+ * other views by the rendered depth; Sec. B.3: visibility by the depth test
+ * (z_j(P) - D_j)^2 < 1e-3).  For each ordered pair (i, j) in `pairs` (host,
+ * [n_pairs][2]), every pixel of view i with a finite depth is lifted to its
+ * world point, projected into view j and image j sampled there bilinearly
+ * between pixel centres; a projection whose four neighbours are not all
+ * inside view j and hit there, or that fails the depth test, is not visible.
+ * loss = w * (sum over visible pixels of all pairs of the channel-summed L1
+ * colour difference) / (number of them), 0 with none.  Inputs (device):
+ * depth [n] (dist_trace_out.depth of the same cameras, +inf background),
+ * images [n][channels] (1..4 channels, pixels in camera order, row-major).
+ * Outputs (device): loss (double), g_depth [n] = dL/d depth OVERWRITTEN (the
+ * visibility decisions and the other view's depth are held fixed), to pass
+ * to dist_trace_bwd.  Uses the workspace's camera table and reduction
+ * scratch; no decoder is involved. */
+dist_status dist_photo_loss(const dist_camera* cams, int n_cams, const float* depth,
+                            const float* images, int channels, const int32_t* pairs,
+                            int n_pairs, float w, double* loss, float* g_depth,
+                            dist_workspace* ws, void* stream);
+
 /* --------------------------------------------------------------- backward */
 
 /* dL/dz += sum over pixels of upstream gradients times the latent Jacobians

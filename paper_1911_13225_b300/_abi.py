@@ -33,7 +33,7 @@ EXPORTS = [
     "dist_profile_read",
     "dist_trace_params_default", "dist_workspace_create", "dist_workspace_destroy",
     "dist_trace_fwd", "dist_render_normals", "dist_sdf_eval", "dist_loss", "dist_trace_bwd",
-    "dist_trace_bwd_camera",
+    "dist_trace_bwd_camera", "dist_photo_loss",
     "dist_serve_create", "dist_serve_submit", "dist_serve_poll", "dist_serve_destroy",
     "dist_last_error", "dist_version", "dist_sdf_eval_static",
 ]
@@ -117,6 +117,8 @@ def lib():
         "dist_trace_bwd_camera": (c_int, [c_void_p, c_void_p, c_int, POINTER(Camera), c_int,
                                           POINTER(TraceParams), POINTER(TraceOut), c_void_p,
                                           c_void_p, c_void_p, c_void_p, c_void_p]),
+        "dist_photo_loss": (c_int, [POINTER(Camera), c_int, c_void_p, c_void_p, c_int, c_void_p,
+                                    c_int, c_float, c_void_p, c_void_p, c_void_p, c_void_p]),
         "dist_serve_create": (c_int, [c_void_p, POINTER(TraceParams), c_int64, c_size_t, c_int,
                                       POINTER(c_void_p)]),
         "dist_serve_submit": (c_int, [c_void_p, POINTER(Request), POINTER(c_uint64)]),

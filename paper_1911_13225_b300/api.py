@@ -278,6 +278,23 @@ def backward_camera(dec: Decoder, z: torch.Tensor, cams, params: TraceParams, ws
     return out
 
 
+def photo_loss(cams, depth: torch.Tensor, images: torch.Tensor, pairs, ws: Workspace,
+               w: float = 1.0, stream=None):
+    """dist_photo_loss: (loss (float64 device scalar), g_depth [n])."""
+    depth = depth.contiguous().float()
+    images = images.contiguous().float()
+    n = depth.shape[0]
+    channels = images.numel() // n
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1, 2))
+    loss = torch.empty(1, device=depth.device, dtype=torch.float64)
+    g = torch.empty(n, device=depth.device, dtype=torch.float32)
+    check(lib().dist_photo_loss(camera_array(cams), len(cams), _ptr(depth), _ptr(images),
+                                int(channels), pr.ctypes.data_as(ctypes.c_void_p), int(pr.shape[0]),
+                                float(w), _ptr(loss), _ptr(g), ws.handle, _stream(stream)),
+          "dist_photo_loss")
+    return loss, g
+
+
 class DistRender(torch.autograd.Function):
     """Differentiable render: z -> (depth, silhouette[, normal]).
 

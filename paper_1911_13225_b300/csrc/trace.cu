@@ -699,6 +699,120 @@ __global__ void cam_finalize_kernel(const double* G, int n, float* out) {
     out[k] = (float)G[k];
 }
 
+// ------------------------------------------------- photometric warp loss
+
+struct PhotoArgs {
+  const CamDev* cams;
+  int vi, vj;            // warp view vj onto view vi
+  const float* depth;    // [n_pix] rendered depth of all views (inf = background)
+  const float* img;      // [n_pix][C] colour images of all views
+  int C;
+  double vis_thresh;
+  double* sums;          // [0] sum of |I_i - I_{j->i}|, [1] visible pixels
+  float* g_depth;        // += d(sum)/d depth_i (normalised afterwards)
+};
+
+// One thread per pixel of view vi (Sec. 4.2 multi-view loss, Sec. B.3
+// visibility): lift the hit to P = c_i + d v, project into view vj, sample
+// its image and depth bilinearly between pixel centres, test visibility
+// ((z_j(P) - D_j)^2 below the threshold, all four neighbours hit and inside)
+// and add the L1 colour difference and its derivative with respect to the
+// rendered depth of view vi.  Double precision (a small kernel; it keeps the
+// cell and visibility decisions those of the reference arithmetic).
+__global__ void photo_pair_kernel(PhotoArgs a) {
+  const CamDev& ci = a.cams[a.vi];
+  const CamDev& cj = a.cams[a.vj];
+  const long long n = (long long)ci.H * ci.W;
+  double lsum = 0.0, lcnt = 0.0;
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n;
+       x += (long long)gridDim.x * blockDim.x) {
+    const long long gi = ci.offset + x;
+    const float Di = a.depth[gi];
+    if (!isfinite(Di)) continue;
+    const int px = (int)(x % ci.W), py = (int)(x / ci.W);
+    const double xt = ((double)px + 0.5 - ci.cx) / ci.fx;
+    const double yt = ((double)py + 0.5 - ci.cy) / ci.fy;
+    const double nrm = sqrt(xt * xt + yt * yt + 1.0);
+    const double vc[3] = {xt / nrm, yt / nrm, 1.0 / nrm};
+    double v[3];
+    for (int r = 0; r < 3; ++r)
+      v[r] = ci.R[3 * r] * vc[0] + ci.R[3 * r + 1] * vc[1] + ci.R[3 * r + 2] * vc[2];
+    const double vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    for (int r = 0; r < 3; ++r) v[r] /= vn;
+    const double inv = 1.0 / nrm;
+    const double d = (double)Di / inv;
+    double w3[3], pc[3] = {0.0, 0.0, 0.0}, q[3] = {0.0, 0.0, 0.0};
+    for (int r = 0; r < 3; ++r) w3[r] = ci.c[r] + d * v[r] - cj.c[r];
+    // R_j^T (P - c_j) and R_j^T v
+    for (int k = 0; k < 3; ++k)
+      for (int r = 0; r < 3; ++r) {
+        pc[k] += cj.R[3 * r + k] * w3[r];
+        q[k] += cj.R[3 * r + k] * v[r];
+      }
+    if (!(pc[2] > 1e-9)) continue;
+    const double pz = pc[2];
+    const double u = cj.fx * pc[0] / pz + cj.cx;
+    const double vv = cj.fy * pc[1] / pz + cj.cy;
+    const double sx = u - 0.5, sy = vv - 0.5;
+    const double fx0 = floor(sx), fy0 = floor(sy);
+    if (!(fx0 >= 0.0 && fy0 >= 0.0 && fx0 <= (double)(cj.W - 2) && fy0 <= (double)(cj.H - 2)))
+      continue;
+    const int x0 = (int)fx0, y0 = (int)fy0;
+    const double fx = sx - fx0, fy = sy - fy0;
+    const long long b00 = cj.offset + (long long)y0 * cj.W + x0;
+    const long long b01 = b00 + 1, b10 = b00 + cj.W, b11 = b10 + 1;
+    const float d00 = a.depth[b00], d01 = a.depth[b01], d10 = a.depth[b10], d11 = a.depth[b11];
+    if (!(isfinite(d00) && isfinite(d01) && isfinite(d10) && isfinite(d11))) continue;
+    const double Dj = (1 - fy) * ((1 - fx) * d00 + fx * d01) + fy * ((1 - fx) * d10 + fx * d11);
+    if (!((pz - Dj) * (pz - Dj) < a.vis_thresh)) continue;
+    const double dudd = cj.fx * (q[0] * pz - pc[0] * q[2]) / (pz * pz);
+    const double dvdd = cj.fy * (q[1] * pz - pc[1] * q[2]) / (pz * pz);
+    double term = 0.0, dterm = 0.0;
+    for (int c = 0; c < a.C; ++c) {
+      const double i00 = a.img[b00 * a.C + c], i01 = a.img[b01 * a.C + c];
+      const double i10 = a.img[b10 * a.C + c], i11 = a.img[b11 * a.C + c];
+      const double val = (1 - fy) * ((1 - fx) * i00 + fx * i01) + fy * ((1 - fx) * i10 + fx * i11);
+      const double du = (1 - fy) * (i01 - i00) + fy * (i11 - i10);
+      const double dv = (1 - fx) * (i10 - i00) + fx * (i11 - i01);
+      const double r = (double)a.img[gi * a.C + c] - val;
+      term += fabs(r);
+      const double sg = r > 0.0 ? 1.0 : (r < 0.0 ? -1.0 : 0.0);
+      dterm -= sg * (du * dudd + dv * dvdd);
+    }
+    lsum += term;
+    lcnt += 1.0;
+    a.g_depth[gi] += (float)(dterm / inv);
+  }
+  // block sums, one atomic pair per block
+  __shared__ double s_sum[8], s_cnt[8];
+  for (int o = 16; o > 0; o >>= 1) {
+    lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    lcnt += __shfl_xor_sync(0xffffffffu, lcnt, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if (lane_id() == 0) { s_sum[w] = lsum; s_cnt[w] = lcnt; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ts = 0.0, tc = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) { ts += s_sum[k]; tc += s_cnt[k]; }
+    if (tc > 0.0) {
+      atomicAdd(a.sums, ts);
+      atomicAdd(a.sums + 1, tc);
+    }
+  }
+}
+
+// loss = w sum / count and g_depth *= w / count (0 without visible pixels).
+__global__ void photo_finalize_kernel(const double* sums, double w, long long n, float* g_depth,
+                                      double* loss) {
+  const double cnt = sums[1];
+  const double s = cnt > 0.0 ? w / cnt : 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) *loss = sums[0] * s;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x)
+    g_depth[k] = (float)((double)g_depth[k] * s);
+}
+
 // Normal-loss coefficients: with g = FD gradient from the six probe values
 // and n = g / |g|, dL/dg = (g_n - n (n . g_n)) / |g|; probe +a gets
 // dL/dg_a / (2 delta), probe -a its negative (hit point held fixed).
@@ -881,6 +995,41 @@ struct Prepared {
   cudaStream_t st;
 };
 
+// Validates the cameras and writes the workspace's camera table; *n_pix is
+// the total pixel count (cameras' pixels concatenated in order).
+dist_status upload_cameras(const dist_camera* cams, int n_cams, float radius, dist_workspace* ws,
+                           cudaStream_t st, long long* n_pix_out) {
+  DIST_CHECK(cams && ws, DIST_E_INVALID, "NULL argument");
+  DIST_CHECK(n_cams >= 1 && n_cams <= ws->max_cams, DIST_E_INVALID, "n_cams out of range");
+  long long n_pix = 0;
+  CamChunk ch;
+  std::memset(&ch, 0, sizeof(ch));
+  for (int c = 0; c < n_cams; ++c) {
+    const dist_camera& k = cams[c];
+    DIST_CHECK(k.H > 0 && k.W > 0 && (long long)k.H * k.W <= (1ll << 31), DIST_E_INVALID,
+               "camera image size out of range");
+    DIST_CHECK(k.fx != 0.f && k.fy != 0.f, DIST_E_INVALID, "zero focal length");
+    const double cc = (double)k.c[0] * k.c[0] + (double)k.c[1] * k.c[1] + (double)k.c[2] * k.c[2];
+    DIST_CHECK(cc > (double)radius * radius, DIST_E_INVALID, "camera inside the bounding sphere");
+    CamDev& d = ch.c[c % kCamChunk];
+    std::memcpy(d.c, k.c, sizeof(d.c));
+    std::memcpy(d.R, k.R, sizeof(d.R));
+    d.fx = k.fx; d.fy = k.fy; d.cx = k.cx; d.cy = k.cy;
+    d.H = k.H; d.W = k.W; d.shape = k.shape; d.pad = 0;
+    d.offset = n_pix;
+    n_pix += (long long)k.H * k.W;
+    if (c % kCamChunk == kCamChunk - 1 || c == n_cams - 1) {
+      ch.n = c % kCamChunk + 1;
+      ch.first = c - (c % kCamChunk);
+      write_cams_kernel<<<1, 64, 0, st>>>(ch, ws->cams);
+      DIST_LAUNCH_CHECK();
+    }
+  }
+  DIST_CHECK(n_pix <= ws->max_rays, DIST_E_INVALID, "more pixels than the workspace holds");
+  *n_pix_out = n_pix;
+  return DIST_OK;
+}
+
 dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_shapes,
                                 const dist_camera* cams, int n_cams,
                                 const dist_trace_params* p, const dist_trace_out* o,
@@ -913,35 +1062,18 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
              "the tensor-core decoder covers only the DeepSDF shape (512 x 8, skip 4, latent 256)");
   DIST_CHECK(o->depth && o->sil && o->mask && o->steps && o->d_hit && o->d_min && o->f_min,
              DIST_E_INVALID, "dist_trace_out: NULL required buffer");
-  long long n_pix = 0;
-  CamChunk ch;
-  std::memset(&ch, 0, sizeof(ch));
   cudaStream_t st = (cudaStream_t)stream;
   for (int c = 0; c < n_cams; ++c) {
-    const dist_camera& k = cams[c];
-    DIST_CHECK(k.H > 0 && k.W > 0 && (long long)k.H * k.W <= (1ll << 31), DIST_E_INVALID,
-               "camera image size out of range");
-    DIST_CHECK(k.shape >= 0 && k.shape < n_shapes, DIST_E_INVALID, "camera shape index out of range");
-    DIST_CHECK(k.fx != 0.f && k.fy != 0.f, DIST_E_INVALID, "zero focal length");
-    DIST_CHECK(k.H % (1 << p->coarse_levels) == 0 && k.W % (1 << p->coarse_levels) == 0,
+    DIST_CHECK(cams[c].shape >= 0 && cams[c].shape < n_shapes, DIST_E_INVALID,
+               "camera shape index out of range");
+    DIST_CHECK(cams[c].H % (1 << p->coarse_levels) == 0 && cams[c].W % (1 << p->coarse_levels) == 0,
                DIST_E_INVALID, "coarse-to-fine tracing: H and W must be multiples of "
                "2^coarse_levels");
-    const double cc = (double)k.c[0] * k.c[0] + (double)k.c[1] * k.c[1] + (double)k.c[2] * k.c[2];
-    DIST_CHECK(cc > (double)p->radius * p->radius, DIST_E_INVALID,
-               "camera inside the bounding sphere");
-    CamDev& d = ch.c[c % kCamChunk];
-    std::memcpy(d.c, k.c, sizeof(d.c));
-    std::memcpy(d.R, k.R, sizeof(d.R));
-    d.fx = k.fx; d.fy = k.fy; d.cx = k.cx; d.cy = k.cy;
-    d.H = k.H; d.W = k.W; d.shape = k.shape; d.pad = 0;
-    d.offset = n_pix;
-    n_pix += (long long)k.H * k.W;
-    if (c % kCamChunk == kCamChunk - 1 || c == n_cams - 1) {
-      ch.n = c % kCamChunk + 1;
-      ch.first = c - (c % kCamChunk);
-      write_cams_kernel<<<1, 64, 0, st>>>(ch, ws->cams);
-      DIST_LAUNCH_CHECK();
-    }
+  }
+  long long n_pix = 0;
+  {
+    dist_status cs = upload_cameras(cams, n_cams, p->radius, ws, st, &n_pix);
+    if (cs != DIST_OK) return cs;
   }
   DIST_CHECK(n_pix <= ws->max_rays, DIST_E_INVALID, "more pixels than the workspace holds");
   const DecoderF32& d = dec->f32;
@@ -1395,6 +1527,46 @@ dist_status dist_trace_bwd_camera(const dist_decoder* dec, const float* z, int n
     DIST_LAUNCH_CHECK();
   }
   cam_finalize_kernel<<<grid_for(n_cams * 12, 256), 256, 0, st>>>(G, n_cams * 12, dcam);
+  DIST_LAUNCH_CHECK();
+  return DIST_OK;
+}
+
+dist_status dist_photo_loss(const dist_camera* cams, int n_cams, const float* depth,
+                           const float* images, int channels, const int32_t* pairs, int n_pairs,
+                           float w, double* loss, float* g_depth, dist_workspace* ws,
+                           void* stream) {
+  DIST_CHECK(cams && depth && images && pairs && loss && g_depth && ws, DIST_E_INVALID,
+             "dist_photo_loss: NULL argument");
+  DIST_CHECK(channels >= 1 && channels <= 4, DIST_E_INVALID, "dist_photo_loss: channels 1..4");
+  DIST_CHECK(n_pairs >= 1, DIST_E_INVALID, "dist_photo_loss: no pair");
+  for (int k = 0; k < n_pairs; ++k)
+    DIST_CHECK(pairs[2 * k] >= 0 && pairs[2 * k] < n_cams && pairs[2 * k + 1] >= 0 &&
+                   pairs[2 * k + 1] < n_cams,
+               DIST_E_INVALID, "dist_photo_loss: view index out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  long long n_pix = 0;
+  {
+    dist_status cs = upload_cameras(cams, n_cams, 0.f, ws, st, &n_pix);
+    if (cs != DIST_OK) return cs;
+  }
+  DIST_CUDA_TRY(cudaMemsetAsync(g_depth, 0, (size_t)n_pix * sizeof(float), st));
+  DIST_CUDA_TRY(cudaMemsetAsync(ws->red, 0, 2 * sizeof(double), st));
+  for (int k = 0; k < n_pairs; ++k) {
+    PhotoArgs a;
+    a.cams = ws->cams;
+    a.vi = pairs[2 * k];
+    a.vj = pairs[2 * k + 1];
+    a.depth = depth;
+    a.img = images;
+    a.C = channels;
+    a.vis_thresh = 1e-3;
+    a.sums = ws->red;
+    a.g_depth = g_depth;
+    photo_pair_kernel<<<grid_for((long long)cams[a.vi].H * cams[a.vi].W, 256), 256, 0, st>>>(a);
+    DIST_LAUNCH_CHECK();
+  }
+  photo_finalize_kernel<<<grid_for(n_pix, 256), 256, 0, st>>>(ws->red, (double)w, n_pix, g_depth,
+                                                              loss);
   DIST_LAUNCH_CHECK();
   return DIST_OK;
 }
