@@ -15,12 +15,20 @@ import numpy as np
 
 
 class OracleDecoder:
-    """f(p, z) for weights ``Ws[l]`` ([out, in]) and biases ``bs[l]``."""
+    """f(p, z) for weights ``Ws[l]`` ([out, in]) and biases ``bs[l]``.
 
-    def __init__(self, Ws, bs, latent_dim: int, skip: int):
+    ``latent_dim0`` > ``latent_dim`` gives the texture network of Sec. B.1
+    (reading: layer 0 reads the whole code, e.g. [shape code, texture code],
+    and the skip layer its last ``latent_dim`` entries, the texture code);
+    ``out_dim`` > 1 gives that many tanh outputs (colour)."""
+
+    def __init__(self, Ws, bs, latent_dim: int, skip: int, latent_dim0: int = 0,
+                 out_dim: int = 1):
         self.Ws = [np.asarray(W, dtype=np.float64) for W in Ws]
         self.bs = [np.asarray(b, dtype=np.float64) for b in bs]
         self.L = int(latent_dim)
+        self.L0 = int(latent_dim0) if latent_dim0 else self.L
+        self.out_dim = int(out_dim)
         self.skip = int(skip)
         self.n_hidden = len(self.Ws) - 1
 
@@ -33,17 +41,22 @@ class OracleDecoder:
         return np.concatenate([z, p], axis=1)
 
     def forward(self, p, z, keep=False):
-        """Return f (n,) and, with ``keep``, the per-layer pre-activations."""
+        """Return f (n,) (or (n, out_dim) for out_dim > 1) and, with ``keep``,
+        the per-layer pre-activations."""
         x_in = self._inputs(p, z)
+        # the skip layer's input tail: [last latent_dim code entries, p]
+        x_skip = x_in[:, self.L0 - self.L:]
         h = x_in
         pre = []
         for l in range(self.n_hidden):
             if l == self.skip:
-                h = np.concatenate([h, x_in], axis=1)
+                h = np.concatenate([h, x_skip], axis=1)
             a = h @ self.Ws[l].T + self.bs[l]
             pre.append(a)
             h = np.maximum(a, 0.0)
         s = h @ self.Ws[-1].T + self.bs[-1]
+        if self.out_dim > 1:
+            return np.tanh(s)
         f = np.tanh(s[:, 0])
         if keep:
             return f, (x_in, pre, s[:, 0])
@@ -59,6 +72,7 @@ class OracleDecoder:
         passes g -> (W^T g) * 1[a > 0]; the skip concatenation splits the
         gradient between the previous layer's output and the input [z, p].
         """
+        assert self.out_dim == 1 and self.L0 == self.L, "gradients of the SDF decoder only"
         f, (x_in, pre, s) = self.forward(p, z, keep=True)
         n = x_in.shape[0]
         g_x = np.zeros_like(x_in)               # gradient w.r.t. [z, p]

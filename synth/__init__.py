@@ -12,13 +12,15 @@ CVPR 2020) plus a seeded perturbation, with the DeepSDF layer shapes
 of [latent, xyz] at layer 4; Sec. B.1 "Network Architecture").
 """
 
-from .decoder import DecoderSpec, DEEPSDF_SPEC, SMALL_SPEC, make_decoder, make_latents
+from .decoder import (DecoderSpec, DEEPSDF_SPEC, SMALL_SPEC, make_color_decoder, make_decoder,
+                      make_latents)
 from .camera import look_at_camera, random_viewpoints, ring_viewpoints
 
 __all__ = [
     "DecoderSpec",
     "DEEPSDF_SPEC",
     "SMALL_SPEC",
+    "make_color_decoder",
     "make_decoder",
     "make_latents",
     "look_at_camera",

@@ -89,3 +89,26 @@ def make_latents(spec: DecoderSpec, n: int, seed: int = 0, sigma: float = 0.01):
     rng = np.random.Generator(np.random.PCG64(10_000 + seed))
     return np.ascontiguousarray(
         rng.normal(0.0, sigma, size=(n, spec.latent_dim)), dtype=np.float32)
+
+
+def make_color_decoder(spec: DecoderSpec, latent_dim0: int, out_dim: int = 3, seed: int = 0):
+    """Weights of a texture network with the layer widths of ``spec``: layer 0
+    reads ``[code (latent_dim0), xyz]``, the skip layer ``[h, last
+    spec.latent_dim code entries, xyz]``, the head has ``out_dim`` rows
+    (tanh outputs).  Hidden weights ~ N(0, 2/out); head ~ N(0, 1/in)."""
+    rng = np.random.Generator(np.random.PCG64(50_000 + seed))
+    Ws, bs = [], []
+    for l in range(spec.n_layers):
+        fan_in = latent_dim0 + 3 if l == 0 else spec.in_dim(l)
+        fan_out = out_dim if l == spec.n_hidden else spec.out_dim(l)
+        if l < spec.n_hidden:
+            W = rng.normal(0.0, np.sqrt(2.0 / fan_out), size=(fan_out, fan_in))
+            if l == spec.skip:
+                W *= 1.0 / np.sqrt(2.0)
+            b = 0.002 * rng.standard_normal(size=fan_out)
+        else:
+            W = rng.normal(0.0, np.sqrt(1.0 / fan_in), size=(fan_out, fan_in))
+            b = np.zeros(fan_out)
+        Ws.append(np.ascontiguousarray(W, dtype=np.float32))
+        bs.append(np.ascontiguousarray(b, dtype=np.float32))
+    return Ws, bs
