@@ -79,12 +79,20 @@ enum { DIST_RAY_INIT_MISS = 0, DIST_RAY_HIT = 1, DIST_RAY_LEFT = 2, DIST_RAY_MAX
  * 256, DeepSDF's skip concatenation).  Layer 0 reads [z (latent_dim), x, y, z];
  * layer `skip` reads [h, z, x, y, z] where h is the output of layer skip-1
  * (width - latent_dim - 3 values); hidden layers use ReLU; layer n_hidden is
- * the head (width -> 1) followed by tanh.  skip = -1: no skip layer. */
+ * the head (width -> 1) followed by tanh.  skip = -1: no skip layer.
+ * The texture network of Sec. B.1 (colour for texture re-rendering) has the
+ * same layers with a longer code at layer 0 and three outputs (reading: layer
+ * 0 reads [code (latent_dim0), x, y, z], e.g. [shape code, texture code]; the
+ * skip layer reads the code's last latent_dim entries, the texture code;
+ * the head is width -> out_dim, each output followed by tanh).  Such a
+ * decoder is used by dist_render_color only. */
 typedef struct {
   int latent_dim;
   int width;       /* 128, 256, 384 or 512 */
   int n_hidden;    /* 2..16 */
   int skip;        /* -1 or 1..n_hidden-1 */
+  int latent_dim0; /* layer-0 code length, latent_dim..1024; 0 = latent_dim */
+  int out_dim;     /* 1 (SDF) or 3 (colour); 0 = 1 */
 } dist_decoder_desc;
 
 typedef struct dist_decoder dist_decoder;
@@ -364,6 +372,19 @@ dist_status dist_trace_bwd_camera(const dist_decoder* dec, const float* z, int n
                                   const dist_trace_out* fwd, const float* g_depth,
                                   const float* g_sil, float* dcam, dist_workspace* ws,
                                   void* stream);
+
+/* Texture re-rendering (Sec. B.1): the colour of every hit pixel of a trace
+ * from a colour decoder (out_dim 3, see dist_decoder_desc) at the hit point
+ * p = c + d_hit v, rgb = tanh(head) per channel; background pixels get 0.
+ * codes (device, [n_shapes][latent_dim0]): the colour decoder's code per
+ * shape (the paper: [shape code, texture code]); each camera's `shape` picks
+ * it.  fwd and ws must come from the dist_trace_fwd of the same cameras (the
+ * workspace holds the rays).  precision: DIST_PREC_FP32 (CUDA cores) or
+ * BF16 / FP16 (tensor cores; the head in FP32).  Output rgb (device,
+ * [n][3]) OVERWRITTEN. */
+dist_status dist_render_color(const dist_decoder* tex, const float* codes, int n_shapes,
+                              const dist_camera* cams, int n_cams, const dist_trace_out* fwd,
+                              int precision, float* rgb, dist_workspace* ws, void* stream);
 
 /* ---------------------------------------------------------------- serving */
 

@@ -33,14 +33,15 @@ EXPORTS = [
     "dist_profile_read",
     "dist_trace_params_default", "dist_workspace_create", "dist_workspace_destroy",
     "dist_trace_fwd", "dist_render_normals", "dist_sdf_eval", "dist_loss", "dist_trace_bwd",
-    "dist_trace_bwd_camera", "dist_photo_loss",
+    "dist_trace_bwd_camera", "dist_photo_loss", "dist_render_color",
     "dist_serve_create", "dist_serve_submit", "dist_serve_poll", "dist_serve_destroy",
     "dist_last_error", "dist_version", "dist_sdf_eval_static",
 ]
 
 
 class DecoderDesc(Structure):
-    _fields_ = [("latent_dim", c_int), ("width", c_int), ("n_hidden", c_int), ("skip", c_int)]
+    _fields_ = [("latent_dim", c_int), ("width", c_int), ("n_hidden", c_int), ("skip", c_int),
+                ("latent_dim0", c_int), ("out_dim", c_int)]
 
 
 class Camera(Structure):
@@ -117,6 +118,8 @@ def lib():
         "dist_trace_bwd_camera": (c_int, [c_void_p, c_void_p, c_int, POINTER(Camera), c_int,
                                           POINTER(TraceParams), POINTER(TraceOut), c_void_p,
                                           c_void_p, c_void_p, c_void_p, c_void_p]),
+        "dist_render_color": (c_int, [c_void_p, c_void_p, c_int, POINTER(Camera), c_int,
+                                      POINTER(TraceOut), c_int, c_void_p, c_void_p, c_void_p]),
         "dist_photo_loss": (c_int, [POINTER(Camera), c_int, c_void_p, c_void_p, c_int, c_void_p,
                                     c_int, c_float, c_void_p, c_void_p, c_void_p, c_void_p]),
         "dist_serve_create": (c_int, [c_void_p, POINTER(TraceParams), c_int64, c_size_t, c_int,

@@ -78,14 +78,18 @@ def camera_array(cams: Sequence[dict]):
 class Decoder:
     """Decoder weights uploaded to the device (dist_decoder_create)."""
 
-    def __init__(self, Ws, bs, latent_dim: int, skip: int):
+    def __init__(self, Ws, bs, latent_dim: int, skip: int, latent_dim0: int = 0,
+                 out_dim: int = 1):
         Ws = [np.ascontiguousarray(W, dtype=np.float32) for W in Ws]
         bs = [np.ascontiguousarray(b, dtype=np.float32) for b in bs]
         self.latent_dim = int(latent_dim)
+        self.latent_dim0 = int(latent_dim0) if latent_dim0 else self.latent_dim
+        self.out_dim = int(out_dim)
         self.width = int(Ws[0].shape[0])
         self.n_hidden = len(Ws) - 1
         self.skip = int(skip)
-        desc = _abi.DecoderDesc(self.latent_dim, self.width, self.n_hidden, self.skip)
+        desc = _abi.DecoderDesc(self.latent_dim, self.width, self.n_hidden, self.skip,
+                                self.latent_dim0, self.out_dim)
         Wp = (c_void_p * len(Ws))(*[W.ctypes.data for W in Ws])
         bp = (c_void_p * len(bs))(*[b.ctypes.data for b in bs])
         h = c_void_p()
@@ -293,6 +297,20 @@ def photo_loss(cams, depth: torch.Tensor, images: torch.Tensor, pairs, ws: Works
                                 float(w), _ptr(loss), _ptr(g), ws.handle, _stream(stream)),
           "dist_photo_loss")
     return loss, g
+
+
+def render_color(tex: Decoder, codes: torch.Tensor, cams, fwd: "TraceResult", ws: Workspace,
+                 precision: str = "bf16", stream=None) -> torch.Tensor:
+    """dist_render_color: [n, 3] colour of the hit pixels of ``fwd`` (0 elsewhere)."""
+    codes = codes.contiguous().float()
+    n = fwd.depth.shape[0]
+    rgb = torch.empty(n, 3, device=codes.device, dtype=torch.float32)
+    o = fwd.c()
+    check(lib().dist_render_color(tex.handle, _ptr(codes), int(codes.shape[0]), camera_array(cams),
+                                  len(cams), byref(o), _abi.PRECISIONS[precision], _ptr(rgb),
+                                  ws.handle, _stream(stream)),
+          "dist_render_color")
+    return rgb
 
 
 class DistRender(torch.autograd.Function):

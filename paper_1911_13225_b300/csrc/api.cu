@@ -80,6 +80,11 @@ dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* cons
                                 const float* const* b, dist_decoder** out) {
   DIST_CHECK(desc && W && b && out, DIST_E_INVALID, "dist_decoder_create: NULL argument");
   const int L = desc->latent_dim, Wd = desc->width, H = desc->n_hidden, S = desc->skip;
+  const int L0 = desc->latent_dim0 ? desc->latent_dim0 : L;
+  const int OD = desc->out_dim ? desc->out_dim : 1;
+  DIST_CHECK(OD == 1 || OD == 3, DIST_E_INVALID, "dist_decoder_create: out_dim must be 1 or 3");
+  DIST_CHECK(L0 >= L && L0 <= 1024, DIST_E_INVALID,
+             "dist_decoder_create: latent_dim0 must be latent_dim..1024");
   DIST_CHECK(Wd == 128 || Wd == 256 || Wd == 384 || Wd == 512, DIST_E_INVALID,
              "dist_decoder_create: width must be 128, 256, 384 or 512");
   DIST_CHECK(H >= 2 && H <= 16, DIST_E_INVALID, "dist_decoder_create: n_hidden must be 2..16");
@@ -95,10 +100,11 @@ dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* cons
   DecoderF32& f = d->f32;
   std::memset(&f, 0, sizeof(f));
   f.width = Wd; f.n_hidden = H; f.skip = S; f.latent = L;
-  auto in_dim = [&](int l) { return (l == 0) ? L + 3 : Wd; };
+  f.latent0 = L0; f.out_dim = OD;
+  auto in_dim = [&](int l) { return (l == 0) ? L0 + 3 : Wd; };
   auto out_dim = [&](int l) { return (S > 0 && l == S - 1) ? Wd - L - 3 : Wd; };
   dist_status st = DIST_OK;
-  std::vector<float> Wx0(Wd * 4, 0.f), Wxs(Wd * 4, 0.f), Wz0((size_t)Wd * L, 0.f),
+  std::vector<float> Wx0(Wd * 4, 0.f), Wxs(Wd * 4, 0.f), Wz0((size_t)Wd * L0, 0.f),
       Wzs((size_t)Wd * L, 0.f);
   for (int l = 0; l < H && st == DIST_OK; ++l) {
     const int K = in_dim(l), N = out_dim(l);
@@ -119,8 +125,9 @@ dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* cons
         const int zc = kh;          // latent columns start after the h part
         std::vector<float>& Wx = (l == 0) ? Wx0 : Wxs;
         std::vector<float>& Wz = (l == 0) ? Wz0 : Wzs;
-        for (int k = 0; k < L; ++k) Wz[(size_t)j * L + k] = W[l][(size_t)j * K + zc + k];
-        for (int a = 0; a < 3; ++a) Wx[j * 4 + a] = W[l][(size_t)j * K + zc + L + a];
+        const int Lz = (l == 0) ? L0 : L;   // code columns of this layer
+        for (int k = 0; k < Lz; ++k) Wz[(size_t)j * Lz + k] = W[l][(size_t)j * K + zc + k];
+        for (int a = 0; a < 3; ++a) Wx[j * 4 + a] = W[l][(size_t)j * K + zc + Lz + a];
       }
     }
     if (st == DIST_OK) st = upload(d->allocations, &f.Wt[l], Wt);
@@ -132,10 +139,12 @@ dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* cons
   if (st == DIST_OK) st = upload(d->allocations, &f.Wz0, Wz0);
   if (st == DIST_OK) st = upload(d->allocations, &f.Wzs, Wzs);
   if (st == DIST_OK) {
-    std::vector<float> wh(Wd, 0.f);
-    for (int k = 0; k < Wd; ++k) wh[k] = W[H][k];
+    std::vector<float> wh((size_t)OD * Wd, 0.f);
+    for (int o = 0; o < OD; ++o)
+      for (int k = 0; k < Wd; ++k) wh[(size_t)o * Wd + k] = W[H][(size_t)o * Wd + k];
     st = upload(d->allocations, &f.w_head, wh);
     f.b_head = b[H][0];
+    for (int o = 0; o < OD; ++o) f.b_out[o] = b[H][o];
   }
   d->tc.ok = false;
   if (st == DIST_OK && Wd == 512 && H == 8 && S == 4 && L == 256) st = pack_tc(d, W, b);

@@ -45,6 +45,11 @@ void prof_mlp_end(cudaStream_t st);
     }                                                                         \
   } while (0)
 
+// A decoder of the SDF (one output, one code): what tracing needs.
+inline bool is_sdf_decoder(const dist_decoder_desc& d) {
+  return (d.out_dim == 0 || d.out_dim == 1) && (d.latent_dim0 == 0 || d.latent_dim0 == d.latent_dim);
+}
+
 // Precisions whose march runs on the tensor cores.
 inline bool is_tc(int precision) {
   return precision == DIST_PREC_BF16 || precision == DIST_PREC_FP16;
@@ -96,8 +101,11 @@ struct DecoderF32 {
   const float* Wxs;      // [WIDTH][4]  xyz columns of the skip layer (or null)
   const float* Wz0;      // [WIDTH][latent] latent columns of layer 0
   const float* Wzs;      // [WIDTH][latent] latent columns of the skip layer
-  const float* w_head;   // [WIDTH]
-  float b_head;
+  const float* w_head;   // [out_dim][WIDTH] (row 0: the SDF head)
+  float b_head;          // b of output 0
+  int latent0;           // layer-0 code length (the skip layer reads its last `latent`)
+  int out_dim;           // 1 (SDF) or 3 (colour)
+  float b_out[4];        // head biases
 };
 
 // BF16 tensor-core packing of the DeepSDF shape (width 512, 8 hidden, skip 4):
@@ -113,8 +121,13 @@ struct TCConst {
   float wx0[3][512];             // xyz columns of layer 0, by axis
   float wx4[3][512];             // xyz columns of the skip layer 4, by axis
   float w_head[512];
+  float w_c[3][512];             // colour decoder: the three head rows (read as float4)
   float b_head;
+  float b_c[3];
 };
+static_assert(offsetof(TCConst, w_c) % 16 == 0 && offsetof(TCConst, w_head) % 16 == 0 &&
+                  offsetof(TCConst, wx0) % 16 == 0 && offsetof(TCConst, wx4) % 16 == 0,
+              "TCConst rows are read as float4");
 struct DecoderTC {
   bool ok;
   TCMaps maps;                   // bf16 operands
@@ -288,6 +301,14 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
                          const RowSrc& srcx, float* fxout, const float* bfold0,
                          const float* bfolds, cudaStream_t st, bool f16,
                          const StepFuse* step = nullptr);
+
+// Colour decoder on the tensor cores (16-bit rows only): per row the three
+// head dot products of its last hidden layer in four partial sums (one per
+// 32-column group, each over the four quarters in order),
+// cpart[row][4][3]; bias and tanh are applied afterwards.
+cudaError_t mlp_tc_color(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
+                         const float* bfolds, float* scratch, float* cpart, cudaStream_t st,
+                         bool f16);
 
 // tcgen05 decoder adjoint over probes (same contract as mlp_fp32_adjoint;
 // `scratch` holds num_sms() * kTcAdjScratchPerCta bytes).

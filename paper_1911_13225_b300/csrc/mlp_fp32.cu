@@ -200,19 +200,22 @@ mlp_fp32_fwd_kernel(DecoderF32 d, RowSrc src, const float* bfold0, const float* 
       store_rows<WIDTH, RPT>(A, row0, acc, lane);
       __syncthreads();
     }
-    // head: s = w . h + b, f = tanh(s)
+    // head: s = w . h + b, f = tanh(s) (out_dim outputs per row: fout[j][o])
 #pragma unroll
     for (int r = 0; r < RPT; ++r) {
-      float s = 0.f;
+      for (int o = 0; o < d.out_dim; ++o) {
+        const float* wo = d.w_head + (size_t)o * WIDTH;
+        float s = 0.f;
 #pragma unroll
-      for (int q = 0; q < WIDTH / 128; ++q) {
-        const float4 h = *reinterpret_cast<const float4*>(A + (row0 + r) * WIDTH + 4 * lane + 128 * q);
-        const float4 w = __ldg(reinterpret_cast<const float4*>(d.w_head) + lane + 32 * q);
-        s = fmaf(h.x, w.x, fmaf(h.y, w.y, fmaf(h.z, w.z, fmaf(h.w, w.w, s))));
+        for (int q = 0; q < WIDTH / 128; ++q) {
+          const float4 h = *reinterpret_cast<const float4*>(A + (row0 + r) * WIDTH + 4 * lane + 128 * q);
+          const float4 w = __ldg(reinterpret_cast<const float4*>(wo) + lane + 32 * q);
+          s = fmaf(h.x, w.x, fmaf(h.y, w.y, fmaf(h.z, w.z, fmaf(h.w, w.w, s))));
+        }
+        s = warp_sum(s);
+        const int j = base + row0 + r;
+        if (lane == 0 && j < n) fout[(size_t)j * d.out_dim + o] = tanhf(s + d.b_out[o]);
       }
-      s = warp_sum(s);
-      const int j = base + row0 + r;
-      if (lane == 0 && j < n) fout[j] = tanhf(s + d.b_head);
     }
     __syncthreads();
   }

@@ -57,6 +57,7 @@ struct TCArgs {
   float* fout[2];
   int* err;
   float inv_scale[NUM_GEMM];     // list 1: 2^-s_l of GEMM layer g
+  float* cpart;                  // colour decoder: [row][4 column groups][3] head partials
   int fuse_step;                 // apply `step` to each row instead of writing f
   StepFuse step;
 };
@@ -90,7 +91,7 @@ constexpr int QPT_X = 64;        // FP32-class queries per tile
 // every weight tile.  Both CTAs load their half of each stage (completing on
 // the even CTA's full barrier), commits arrive on both CTAs' barriers, and
 // every epilogue warp of both CTAs arrives on the even CTA's act_full.
-template <bool F16, bool PAIR>
+template <bool F16, bool PAIR, bool COLOR>
 __global__ void __launch_bounds__(FWD_THREADS, 1)
 mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMaps xmaps,
               const TCArgs a) {
@@ -496,9 +497,32 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       const bool cur_valid = valid;
       const float3 cur_p = p;
       float head = 0.f;
+      // colour decoder (16-bit rows): the three head rows' partial dot
+      // products over this thread's 32 columns of each quarter, in order
+      float cacc[3] = {0.f, 0.f, 0.f};
+      auto color_q = [&](int q) {
+        if constexpr (COLOR) {
+          uint32_t r[32];
+          tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
+          float v[32];
+          bias32(K, NUM_GEMM - 1, bf4, 128 * q + cg, cur_p, r, v);
+#pragma unroll
+          for (int o = 0; o < 3; ++o)
+#pragma unroll
+            for (int i = 0; i < 32; i += 4) {
+              const float4 w = ldg4(K->w_c[o] + 128 * q + cg + i);
+              cacc[o] = fmaf(fmaxf(v[i], 0.f), w.x,
+                             fmaf(fmaxf(v[i + 1], 0.f), w.y,
+                                  fmaf(fmaxf(v[i + 2], 0.f), w.z,
+                                       fmaf(fmaxf(v[i + 3], 0.f), w.w, cacc[o]))));
+            }
+        }
+      };
       if (!wait_acc(0)) { ok = false; break; }
       head += head_q(cur_xt, bf4, cur_p, 0);
+      color_q(0);
       head += head_q(cur_xt, bf4, cur_p, 1);
+      color_q(1);
       // from here on xt/j/p/shape describe the next tile's rows (layer 0 in
       // its format): quarters 0 and 1 of it are computed while the tensor
       // core finishes this layer; quarter q is released once this tile's
@@ -518,6 +542,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       }
       for (int q = 2; q < 4; ++q) {
         head += head_q(cur_xt, bf4, cur_p, q);
+        color_q(q);
         if (has_next) {
           uint32_t h[16];
           layer0(q, h);
@@ -526,6 +551,11 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         }
       }
       if (!has_next) tc_fence_before();
+      if constexpr (COLOR) {
+        if (cur_valid && !cur_xt)
+#pragma unroll
+          for (int o = 0; o < 3; ++o) a.cpart[((size_t)cur_j * 4 + grp) * 3 + o] = cacc[o];
+      }
       // head: f = tanh(w . h7 + b); column groups 1..3 hand their partial
       // sums to group 0 (head_part is rewritten only after the next tile's
       // layers, which group 0 takes part in, so one phase per tile suffices)
@@ -1048,6 +1078,7 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
   auto enc = tensor_map_encoder();
   DIST_CHECK(enc != nullptr, DIST_E_CUDA, "cuTensorMapEncodeTiled entry point not available");
   const int L = 256, Hh = 253;   // latent, h-part of the skip input
+  const int L0 = d->f32.latent0; // layer-0 code length (L, or longer for a colour decoder)
   {
     // epilogue constants; layer 3 has Hh real outputs, the rest stay 0
     TCConst* c = new TCConst();
@@ -1057,11 +1088,17 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
     }
     for (int j = 0; j < 512; ++j)
       for (int ax = 0; ax < 3; ++ax) {
-        c->wx0[ax][j] = W[0][(size_t)j * (L + 3) + L + ax];
+        c->wx0[ax][j] = W[0][(size_t)j * (L0 + 3) + L0 + ax];
         c->wx4[ax][j] = W[4][(size_t)j * 512 + Hh + L + ax];
       }
     for (int j = 0; j < 512; ++j) c->w_head[j] = W[8][j];
     c->b_head = b[8][0];
+    if (d->f32.out_dim == 3) {
+      for (int o = 0; o < 3; ++o) {
+        for (int j = 0; j < 512; ++j) c->w_c[o][j] = W[8][(size_t)o * 512 + j];
+        c->b_c[o] = b[8][o];
+      }
+    }
     void* q = nullptr;
     cudaError_t e = cudaMalloc(&q, sizeof(TCConst));
     if (e == cudaSuccess) {
@@ -1149,11 +1186,11 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
   return DIST_OK;
 }
 
-template <bool F16, bool PAIR>
+template <bool F16, bool PAIR, bool COLOR = false>
 cudaError_t launch_fused(const dist_decoder* dec, const TCArgs& a, cudaStream_t st) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<F16, PAIR>,
+    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<F16, PAIR, COLOR>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          FWD_SMEM_BYTES);
     if (e != cudaSuccess) return e;
@@ -1176,7 +1213,7 @@ cudaError_t launch_fused(const dist_decoder* dec, const TCArgs& a, cudaStream_t 
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, mlp_tc_kernel<F16, PAIR>, maps, xmaps, a);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, mlp_tc_kernel<F16, PAIR, COLOR>, maps, xmaps, a);
   count_launch(1);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -1197,12 +1234,31 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
   a.fout[1] = fxout;
   a.err = dec->tc.err;
   for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
+  a.cpart = nullptr;
   a.fuse_step = step ? 1 : 0;
   if (step) a.step = *step;
   else memset(&a.step, 0, sizeof(a.step));
   if (dec->tc.pair)
     return f16 ? launch_fused<true, true>(dec, a, st) : launch_fused<false, true>(dec, a, st);
   return f16 ? launch_fused<true, false>(dec, a, st) : launch_fused<false, false>(dec, a, st);
+}
+
+cudaError_t mlp_tc_color(const dist_decoder* dec, const RowSrc& src, const float* bfold0,
+                         const float* bfolds, float* scratch, float* cpart, cudaStream_t st,
+                         bool f16) {
+  if (!dec->tc.ok) return cudaErrorNotSupported;
+  TCArgs a;
+  memset(&a, 0, sizeof(a));
+  a.K = dec->tc.cst;
+  a.bfold0 = bfold0;
+  a.bfold4 = bfolds;
+  a.src[0] = src;
+  a.fout[0] = scratch;
+  a.err = dec->tc.err;
+  for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
+  a.cpart = cpart;
+  return f16 ? launch_fused<true, false, true>(dec, a, st)
+             : launch_fused<false, false, true>(dec, a, st);
 }
 
 cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,

@@ -55,6 +55,8 @@ extern "C" dist_status dist_sdf_eval_static(const dist_decoder* dec, const float
                                             int precision, float* f, float* grad, void* stream) {
   DIST_CHECK(dec && z && pts && shape && f, DIST_E_INVALID,
              "dist_sdf_eval_static: NULL argument");
+  DIST_CHECK(is_sdf_decoder(dec->desc), DIST_E_INVALID,
+             "dist_sdf_eval_static needs an SDF decoder (out_dim 1, latent_dim0 = latent_dim)");
   DIST_CHECK(n >= 1 && n <= kStaticMaxPoints, DIST_E_INVALID,
              "dist_sdf_eval_static: n must be 1..65536 (size of the built-in scratch)");
   DIST_CHECK(n_shapes >= 1 && n_shapes <= kStaticMaxShapes, DIST_E_INVALID,

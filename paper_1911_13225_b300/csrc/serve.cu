@@ -375,6 +375,8 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
                               int64_t max_rays, size_t mem_budget, int max_requests,
                               dist_server** out) {
   DIST_CHECK(dec && p && out, DIST_E_INVALID, "dist_serve_create: NULL argument");
+  DIST_CHECK(is_sdf_decoder(dec->desc), DIST_E_INVALID,
+             "dist_serve_create needs an SDF decoder (out_dim 1, latent_dim0 = latent_dim)");
   DIST_CHECK(max_rays >= 1 && max_rays <= (1ll << 28), DIST_E_INVALID,
              "dist_serve_create: max_rays out of range");
   DIST_CHECK(max_requests >= 1 && max_requests <= kMaxShapes, DIST_E_INVALID,

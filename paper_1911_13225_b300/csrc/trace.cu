@@ -93,11 +93,14 @@ __global__ void fold_bias_kernel(DecoderF32 d, const float* __restrict__ z, int 
   const float* Wz = which == 0 ? d.Wz0 : d.Wzs;
   const float* b = which == 0 ? d.b[0] : d.b[d.skip];
   float* out = (which == 0 ? bfold0 : bfolds) + (size_t)s * d.width;
+  // layer 0 reads the whole code, the skip layer its last `latent` entries
+  const int Lz = which == 0 ? d.latent0 : d.latent;
+  const float* zs = z + (size_t)s * d.latent0 + (which == 0 ? 0 : d.latent0 - d.latent);
   const int warp = threadIdx.x >> 5, lane = lane_id();
   for (int j = blockIdx.z * 8 + warp; j < d.width; j += gridDim.z * 8) {
     double acc = 0.0;
-    for (int k = lane; k < d.latent; k += 32)
-      acc += (double)Wz[(size_t)j * d.latent + k] * (double)z[(size_t)s * d.latent + k];
+    for (int k = lane; k < Lz; k += 32)
+      acc += (double)Wz[(size_t)j * Lz + k] * (double)zs[k];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) out[j] = (float)(acc + (double)b[j]);
@@ -813,6 +816,34 @@ __global__ void photo_finalize_kernel(const double* sums, double w, long long n,
     g_depth[k] = (float)((double)g_depth[k] * s);
 }
 
+// ------------------------------------------------------- texture colour
+
+// rgb of hit pixels from the FP32 colour rows (tanh applied).
+__global__ void color_scatter_kernel(const float* rows, const int* pix, const int* count,
+                                     float* rgb) {
+  const int n = *count;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int i = pix[j];
+    for (int o = 0; o < 3; ++o) rgb[3 * (size_t)i + o] = rows[3 * (size_t)j + o];
+  }
+}
+
+// rgb = tanh(sum of the four column-group partials, in order, + b) from the
+// tensor-core colour decoder.
+__global__ void color_finalize_kernel(const float* cpart, const int* pix, const int* count,
+                                      float b0, float b1, float b2, float* rgb) {
+  const int n = *count;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+    const int i = pix[j];
+    const float b[3] = {b0, b1, b2};
+    for (int o = 0; o < 3; ++o) {
+      float s = 0.f;
+      for (int g = 0; g < 4; ++g) s += cpart[((size_t)j * 4 + g) * 3 + o];
+      rgb[3 * (size_t)i + o] = tanhf(s + b[o]);
+    }
+  }
+}
+
 // Normal-loss coefficients: with g = FD gradient from the six probe values
 // and n = g / |g|, dL/dg = (g_n - n (n . g_n)) / |g|; probe +a gets
 // dL/dg_a / (2 delta), probe -a its negative (hit point held fixed).
@@ -1035,6 +1066,8 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
                                 const dist_trace_params* p, const dist_trace_out* o,
                                 dist_workspace* ws, void* stream, Prepared* out) {
   DIST_CHECK(dec && z && cams && p && o && ws, DIST_E_INVALID, "NULL argument");
+  DIST_CHECK(is_sdf_decoder(dec->desc), DIST_E_INVALID,
+             "tracing needs an SDF decoder (out_dim 1, latent_dim0 = latent_dim)");
   DIST_CHECK(n_cams >= 1 && n_cams <= ws->max_cams, DIST_E_INVALID, "n_cams out of range");
   DIST_CHECK(n_shapes >= 1 && n_shapes <= kMaxShapes, DIST_E_INVALID, "n_shapes out of range");
   DIST_CHECK(p->max_steps >= 1 && p->max_steps <= ws->max_steps, DIST_E_INVALID,
@@ -1571,10 +1604,63 @@ dist_status dist_photo_loss(const dist_camera* cams, int n_cams, const float* de
   return DIST_OK;
 }
 
+dist_status dist_render_color(const dist_decoder* tex, const float* codes, int n_shapes,
+                              const dist_camera* cams, int n_cams, const dist_trace_out* fwd,
+                              int precision, float* rgb, dist_workspace* ws, void* stream) {
+  DIST_CHECK(tex && codes && cams && fwd && rgb && ws, DIST_E_INVALID,
+             "dist_render_color: NULL argument");
+  DIST_CHECK(tex->f32.out_dim == 3, DIST_E_INVALID, "dist_render_color: decoder out_dim must be 3");
+  DIST_CHECK(fwd->mask && fwd->d_hit, DIST_E_INVALID, "dist_render_color: NULL trace output");
+  DIST_CHECK(n_shapes >= 1 && n_shapes <= kMaxShapes, DIST_E_INVALID, "n_shapes out of range");
+  DIST_CHECK(precision == DIST_PREC_FP32 || is_tc(precision), DIST_E_INVALID,
+             "dist_render_color: precision must be FP32, BF16 or FP16");
+  DIST_CHECK(precision == DIST_PREC_FP32 || tex->tc.ok, DIST_E_UNSUPPORTED,
+             "the tensor-core decoder covers only the DeepSDF layer shape");
+  for (int c = 0; c < n_cams; ++c)
+    DIST_CHECK(cams[c].shape >= 0 && cams[c].shape < n_shapes, DIST_E_INVALID,
+               "camera shape index out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  long long n_pix = 0;
+  {
+    dist_status cs = upload_cameras(cams, n_cams, 0.f, ws, st, &n_pix);
+    if (cs != DIST_OK) return cs;
+  }
+  float* b0 = ws->bfold;
+  float* bs = ws->bfold + kMaxShapes * 512;
+  DIST_CUDA_TRY(launch_fold_bias(tex->f32, codes, n_shapes, b0, bs, st));
+  DIST_CUDA_TRY(cudaMemsetAsync(rgb, 0, (size_t)n_pix * 3 * sizeof(float), st));
+  DIST_CUDA_TRY(cudaMemsetAsync(ws->probe_count, 0, 8 * sizeof(int), st));
+  ProbeArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.cams = ws->cams; a.st = ws->st; a.dir = ws->dir; a.n_pix = n_pix; a.n_cams = n_cams;
+  a.cam_fixed = -1; a.K = 1; a.o = *fwd;
+  a.pp = ws->probe_p; a.pq = ws->probe_q; a.pix = ws->probe_pix; a.count = ws->probe_count;
+  const int g = grid_for(n_pix, 256);
+  probes_hits_kernel<<<g, 256, 0, st>>>(a);
+  DIST_LAUNCH_CHECK();
+  RowSrc src{};
+  src.count = ws->probe_count;
+  src.pts = ws->probe_p;
+  if (precision == DIST_PREC_FP32) {
+    DIST_CUDA_TRY(mlp_fp32_forward(tex->f32, src, b0, bs, ws->probe_out, st));
+    color_scatter_kernel<<<g, 256, 0, st>>>(ws->probe_out, ws->probe_pix, ws->probe_count, rgb);
+  } else {
+    DIST_CUDA_TRY(mlp_tc_color(tex, src, b0, bs, ws->fbuf[0], ws->probe_out, st,
+                               precision == DIST_PREC_FP16));
+    color_finalize_kernel<<<g, 256, 0, st>>>(ws->probe_out, ws->probe_pix, ws->probe_count,
+                                             tex->f32.b_out[0], tex->f32.b_out[1],
+                                             tex->f32.b_out[2], rgb);
+  }
+  DIST_LAUNCH_CHECK();
+  return DIST_OK;
+}
+
 dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
                           const float* pts, const int32_t* shape, int64_t n, int precision,
                           float* f, float* grad, dist_workspace* ws, void* stream) {
   DIST_CHECK(dec && z && pts && shape && f && ws, DIST_E_INVALID, "dist_sdf_eval: NULL argument");
+  DIST_CHECK(is_sdf_decoder(dec->desc), DIST_E_INVALID,
+             "dist_sdf_eval needs an SDF decoder (out_dim 1, latent_dim0 = latent_dim)");
   DIST_CHECK(n >= 1 && n <= ws->max_rays * kProbesPerRay, DIST_E_INVALID,
              "dist_sdf_eval: n must be 1..10 * workspace max_rays");
   DIST_CHECK(n_shapes >= 1 && n_shapes <= kMaxShapes, DIST_E_INVALID, "n_shapes out of range");
