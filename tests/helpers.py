@@ -43,6 +43,42 @@ def fp16_round(x):
     return np.asarray(x, dtype=np.float32).astype(np.float16).astype(np.float64)
 
 
+def e4m3_round(x):
+    """Round to the nearest FP8 E4M3 value (3 mantissa bits, ties to even;
+    saturating at 448, subnormals down to 2^-9), returned as float64."""
+    x = np.asarray(x, dtype=np.float64)
+    a = np.minimum(np.abs(x), 448.0)
+    e = np.maximum(np.floor(np.log2(np.maximum(a, 2.0 ** -9))), -6.0)
+    q = 2.0 ** (e - 3)
+    return np.sign(x) * np.minimum(np.round(a / q) * q, 448.0)
+
+
+def fp8_decoder_reference(Ws, bs, Z, pts, shape, act_scale, latent=256, skip=4):
+    """The DeepSDF decoder as an FP8 (E4M3) tensor-core kernel would run it:
+    GEMM layers 1..7 with E4M3 activations (per-layer scale ``act_scale[l]``)
+    and E4M3 weights (per-output-row scale), exact accumulation; layer 0, the
+    folded latent biases, the skip layer's xyz term and the head in full
+    precision."""
+    W = [np.asarray(w, dtype=np.float64) for w in Ws]
+    b = [np.asarray(v, dtype=np.float64) for v in bs]
+    z = np.asarray(Z, dtype=np.float64)[shape]
+    p = np.asarray(pts, dtype=np.float64)
+    hk = W[skip].shape[1] - latent - 3
+    b0 = z @ W[0][:, :latent].T + b[0]
+    bsk = z @ W[skip][:, hk:hk + latent].T + b[skip]
+    h = np.maximum(p @ W[0][:, latent:].T + b0, 0.0)
+    maxima = []
+    for l in range(1, len(W) - 1):
+        Wl = W[l][:, :hk] if l == skip else W[l]
+        maxima.append(float(np.max(h)))
+        sa = act_scale[l - 1] if act_scale is not None else max(np.max(h), 1e-30) / 448.0
+        sw = np.maximum(np.max(np.abs(Wl), axis=1, keepdims=True), 1e-30) / 448.0
+        a = (e4m3_round(h / sa) * sa) @ (e4m3_round(Wl / sw) * sw).T
+        a = a + (p @ W[l][:, hk + latent:].T + bsk if l == skip else b[l])
+        h = np.maximum(a, 0.0)
+    return np.tanh(h @ W[-1].T + b[-1])[:, 0], maxima
+
+
 def lowp_decoder_reference(Ws, bs, Z, pts, shape, precision, latent=256, skip=4):
     rnd = bf16_round if precision == "bf16" else fp16_round
     return bf16_decoder_reference(Ws, bs, Z, pts, shape, latent, skip, rnd=rnd)
