@@ -185,7 +185,8 @@ def run_ours(args, rank, world, local_rank):
     params = api.TraceParams(max_steps=MAX_STEPS, precision=precision, eps_bf16=args.eps_lo,
                              refine_steps=args.refine, alpha_refine=args.alpha_refine,
                              refine_engine=args.refine_engine, refine_rule=args.refine_rule,
-                             coarse_levels=args.coarse_levels)
+                             coarse_levels=args.coarse_levels,
+                             latency_mode=args.latency_mode)
     ws = api.Workspace(SIZE * SIZE, MAX_STEPS)
     z = torch.from_numpy(Z).to(dev)
     # target: depth of the second latent (untimed setup)
@@ -318,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
                    "rays_per_step": rays, "precision": precision,
                    "eps_lo": args.eps_lo, "refine_steps": args.refine,
                    "refine_engine": args.refine_engine, "refine_rule": args.refine_rule,
-                   "coarse_levels": args.coarse_levels,
+                   "coarse_levels": args.coarse_levels, "latency_mode": args.latency_mode,
                    "normals": "rendered (analytic, adjoint at the hits)" if args.normals
                               else "not rendered (unused by the L1 depth loss)",
                    "parallelism": f"replicas x{world}",
@@ -649,6 +650,8 @@ def main():
     ap.add_argument("--coarse-levels", type=int, default=0,
                     help="coarse-to-fine tracing for the main line (0: exact per-pixel trace; "
                          "the coarse_to_fine key reports 2 beside it)")
+    ap.add_argument("--latency-mode", type=int, default=1, choices=[0, 1],
+                    help="1: steps with few tiles spread each tile over a four-SM cluster")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-load", type=float, default=0.8,

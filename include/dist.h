@@ -179,6 +179,14 @@ typedef struct {
                           of queries; a child of a parent that missed the
                           sphere starts at its own entry.                   */
   int coarse_every;    /* march iterations per coarse level (the paper: 3) */
+  int latency_mode;    /* tensor-core march with FP32-class TC queries
+                          (refine_steps 0): 1 (default) = a step whose
+                          lists fit in as many tiles (128 16-bit rays or
+                          64 FP32-class rays each) as four-SM clusters fit
+                          on the GPU at once (at most 37) spreads each tile over
+                          four SMs, a quarter of every layer's columns per
+                          SM; 0 = one tile per SM (pair) throughout.  Both
+                          give the same f for every query.                   */
 } dist_trace_params;
 
 /* Fill `p` with the paper's defaults: max_steps 50, eps 5e-5, alpha 1.5,

@@ -47,6 +47,7 @@ class TraceParams:
     refine_rule: str = "march"    # their step rule: "march" (alpha) | "secant"
     coarse_levels: int = 0        # coarse-to-fine tracing (Sec. 3.2): 0 off, 2 the paper's
     coarse_every: int = 3         # march iterations per coarse level
+    latency_mode: int = 1         # 1: small steps spread each tile over a four-SM cluster
 
     def c(self) -> _abi.TraceParams:
         return _abi.TraceParams(
@@ -56,7 +57,7 @@ class TraceParams:
             _abi.PRECISIONS[self.precision], float(self.eps_bf16), float(self.radius),
             int(self.refine_steps), float(self.alpha_refine),
             _abi.REFINE_ENGINES[self.refine_engine], _abi.REFINE_RULES[self.refine_rule],
-            int(self.coarse_levels), int(self.coarse_every))
+            int(self.coarse_levels), int(self.coarse_every), int(self.latency_mode))
 
 
 def camera_struct(cam) -> _abi.Camera:

@@ -74,6 +74,7 @@ void dist_trace_params_default(dist_trace_params* p) {
   p->refine_rule = DIST_REFINE_MARCH;
   p->coarse_levels = 0;
   p->coarse_every = 3;
+  p->latency_mode = 1;
 }
 
 dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* const* W,
@@ -226,6 +227,7 @@ dist_status dist_workspace_create(int64_t max_rays, int max_steps, dist_workspac
   WS_ALLOC(red, 8 * sizeof(double));
   WS_ALLOC(ired, 8 * sizeof(int));
   WS_ALLOC(tc_scratch, (size_t)num_sms() * kTcAdjScratchPerCta);
+  WS_ALLOC(wide_scratch, tc_wide_scratch_bytes());
 #undef WS_ALLOC
   if (s != DIST_OK) {
     dist_workspace_destroy(w);

@@ -182,6 +182,7 @@ struct dist_workspace {
   double* red;        // [8] small FP64 reduction scratch
   int* ired;          // [8] small integer scratch
   void* tc_scratch;   // num_sms() * kTcAdjScratchPerCta bytes (tensor-core adjoint)
+  void* wide_scratch; // tc_wide_scratch_bytes(): latency-mode operand images
   std::vector<void*> allocations;
 };
 
@@ -301,6 +302,18 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
                          const RowSrc& srcx, float* fxout, const float* bfold0,
                          const float* bfolds, cudaStream_t st, bool f16,
                          const StepFuse* step = nullptr);
+
+// Latency mode of the fused decoder (a launch of at most tc_wide_max_tiles()
+// tiles of 128 16-bit rows or 64 FP32-class queries): each tile on a cluster
+// of four CTAs, one quarter of every layer's output columns each.  Same
+// arguments as mlp_tc_fused plus `scratch` (tc_wide_scratch_bytes() of
+// device memory); the kernel does nothing when the lists are longer.
+cudaError_t mlp_tc_wide(const dist_decoder* dec, const RowSrc& src16, float* f16out,
+                        const RowSrc& srcx, float* fxout, const float* bfold0,
+                        const float* bfolds, cudaStream_t st, bool f16, const StepFuse* step,
+                        void* scratch);
+int tc_wide_max_tiles();
+size_t tc_wide_scratch_bytes();
 
 // Colour decoder on the tensor cores (16-bit rows only): per row the three
 // head dot products of its last hidden layer in four partial sums (one per

@@ -60,6 +60,8 @@ struct TCArgs {
   float* cpart;                  // colour decoder: [row][4 column groups][3] head partials
   int fuse_step;                 // apply `step` to each row instead of writing f
   StepFuse step;
+  int wide_tiles;                // > 0: launches of at most this many latency-mode tiles
+                                 // are left to mlp_tc_wide_kernel
 };
 
 constexpr int QPT_X = 64;        // FP32-class queries per tile
@@ -131,6 +133,9 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   const int t1 = (n1 + MUL * QPT_X - 1) / (MUL * QPT_X);   // FP32-class tiles: [0, t1)
   const int n_tiles = t1 + (n0 + MUL * BM - 1) / (MUL * BM);
   if (pid >= n_tiles) return;                               // uniform over a pair
+  // a launch small enough for the latency mode (its tiles: 128 16-bit rows
+  // or 64 FP32-class queries) runs there instead, launched right behind this
+  if (a.wide_tiles > 0 && (n1 + 63) / 64 + (n0 + BM - 1) / BM <= a.wide_tiles) return;
   if (a.fuse_step && a.step.queries && pid == 0 && rank == 0 && threadIdx.x == 0) {
     atomicAdd(a.step.queries + 0, (unsigned long long)n0);
     atomicAdd(a.step.queries + 1, (unsigned long long)n1);
@@ -442,7 +447,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     };
     // head term of the 32-column chunk of quarter q of the last layer (tile
     // kind `kx`): its own sum, so that the per-row total is the same fixed-
-    // order sum of 16 chunk sums as in the cluster latency mode
+    // order sum of 16 chunk sums as in the latency mode (mlp_tc_wide_kernel)
     auto head_q = [&](bool kx, const float* bf4, const float3& pp, int q) -> float {
       uint32_t r[32];
       tmem_ld32(t_row + (uint32_t)(128 * q + cg), r);
@@ -1238,9 +1243,16 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
   a.fuse_step = step ? 1 : 0;
   if (step) a.step = *step;
   else memset(&a.step, 0, sizeof(a.step));
+  // with a fused step and latency-mode scratch, both kernels are launched;
+  // each decides from the list lengths on the device which one decodes
+  a.wide_tiles = (step && step->wide) ? tc_wide_max_tiles() : 0;
+  cudaError_t e;
   if (dec->tc.pair)
-    return f16 ? launch_fused<true, true>(dec, a, st) : launch_fused<false, true>(dec, a, st);
-  return f16 ? launch_fused<true, false>(dec, a, st) : launch_fused<false, false>(dec, a, st);
+    e = f16 ? launch_fused<true, true>(dec, a, st) : launch_fused<false, true>(dec, a, st);
+  else
+    e = f16 ? launch_fused<true, false>(dec, a, st) : launch_fused<false, false>(dec, a, st);
+  if (e != cudaSuccess || a.wide_tiles <= 0) return e;
+  return mlp_tc_wide(dec, src16, f16out, srcx, fxout, bfold0, bfolds, st, f16, step, step->wide);
 }
 
 cudaError_t mlp_tc_color(const dist_decoder* dec, const RowSrc& src, const float* bfold0,

@@ -100,6 +100,7 @@ struct dist_server {
   double* loss = nullptr;
   unsigned long long* queries = nullptr;
   void* tc_scratch = nullptr;
+  void* wide_scratch = nullptr;
   std::vector<void*> allocs;
   // host state
   std::mutex mu;
@@ -222,6 +223,7 @@ struct dist_server {
       src.idx = act[par][0];
       StepFuse sf;
       pool_step_fuse(P, cnt + 2 * (par ^ 1), out, &sf);
+      if (p.latency_mode) sf.wide = static_cast<uint8_t*>(wide_scratch);
       DIST_CUDA_TRY(mlp_tc_fused(dec, src, fbuf[0], sx, fbuf[1], b0, bs, st,
                                  p.precision == DIST_PREC_FP16, &sf));
     } else {
@@ -446,6 +448,7 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
   SV_ALLOC(loss, max_requests * sizeof(double));
   SV_ALLOC(queries, 2 * sizeof(unsigned long long));
   SV_ALLOC(tc_scratch, (size_t)num_sms() * kTcAdjScratchPerCta);
+  SV_ALLOC(wide_scratch, tc_wide_scratch_bytes());
 #undef SV_ALLOC
   if (s == DIST_OK && cudaMallocHost(&S->slot_active_host, max_requests * sizeof(int)) != cudaSuccess) {
     S->slot_active_host = nullptr;

@@ -41,6 +41,8 @@ struct StepFuse {
   int* out[2];                   // next step's lists (0: 16-bit, 1: FP32-class)
   int* cnt_out[2];               // their append counters
   unsigned long long* queries;   // per-list query counters, or null
+  uint8_t* wide;                 // latency-mode scratch (tc_wide_scratch_bytes()), or
+                                 // null: every launch on the one-tile-per-SM kernel
 };
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }

@@ -1086,6 +1086,8 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
   DIST_CHECK(p->coarse_levels >= 0 && p->coarse_levels <= kMaxCoarseLevels &&
                  p->coarse_every >= 1,
              DIST_E_INVALID, "coarse_levels must be 0..4 and coarse_every >= 1");
+  DIST_CHECK(p->latency_mode == 0 || p->latency_mode == 1, DIST_E_INVALID,
+             "latency_mode must be 0 or 1");
   DIST_CHECK(p->coarse_levels == 0 || !is_tc(p->precision) ||
                  (fp32_on_tc(*p) && p->refine_steps == 0),
              DIST_E_INVALID,
@@ -1266,6 +1268,7 @@ void pool_step_fuse(const RayPool& P, int* cnt_out, int* const out[2], StepFuse*
   sf->t = pool_args(P);
   for (int k = 0; k < 2; ++k) { sf->out[k] = out[k]; sf->cnt_out[k] = cnt_out + k; }
   sf->queries = P.o.queries;
+  sf->wide = nullptr;
 }
 
 cudaError_t pool_probes_depth(const RayPool& P, int cam, long long pix0, long long n,
@@ -1380,6 +1383,7 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
       sf.out[0] = ws->act[par ^ 1][0]; sf.out[1] = ws->act[par ^ 1][1];
       sf.cnt_out[0] = cA + s + 1; sf.cnt_out[1] = cB + s + 1;
       sf.queries = o->queries;
+      sf.wide = p->latency_mode ? static_cast<uint8_t*>(ws->wide_scratch) : nullptr;
       prof_mlp_begin(st, 0);
       DIST_CUDA_TRY(mlp_tc_fused(dec, src, ws->fbuf[0], sx, ws->fbuf[1], b0, bs, st,
                                  p->precision == DIST_PREC_FP16, &sf));
