@@ -3,16 +3,17 @@
 // CTA r computing output columns [r N/WC, (r+1) N/WC) of every layer for all
 // of the tile's rows.  The per-layer tensor-core work of one SM drops by WC;
 // the CTAs exchange the next layer's operand through an L2-resident staging
-// image (each writes its column slice, then loads the others').  Every output
+// image (each stores its column slice there with one bulk copy, then bulk-
+// loads the others').  Every output
 // column is accumulated over K in the same order and through the same
 // epilogue arithmetic as in mlp_tc_kernel, and the head adds the same 32-column
 // chunk sums in the same order, so a row's f is the same in either kernel.
 //
-// Roles per CTA (6 warps): warp 0 streams this CTA's weight rows through a
+// Roles per CTA (10 warps): warp 0 streams this CTA's weight rows through a
 // TMA ring, warp 1 issues the MMAs (N = 128, or 64 for the 256-wide layer),
-// warps 2..5 are the epilogue (one TMEM lane quadrant each); lane 0 of warp 2
-// also loads the peers' operand slices.  Waits are bounded like the main
-// kernel's.
+// warps 2..9 are the epilogue (TMEM lane quadrant warp & 3, one half of the
+// CTA's columns each); lane 0 of warp 2 also loads the peers' operand
+// slices.  Waits are bounded like the main kernel's.
 #include <cmath>
 #include <cstring>
 
@@ -28,7 +29,8 @@ constexpr int WT_MAX = 37;                     // clusters per launch: 148 SMs /
 constexpr int W_BN = 128;                      // weight rows per stage (= 512 / WC)
 constexpr int W_STAGE = W_BN * BK * 2;         // 16 KB
 constexpr int W_NST = 5;
-constexpr int W_THREADS = 6 * 32;
+constexpr int W_EPI = 8;                       // epilogue warps: two per TMEM lane quadrant
+constexpr int W_THREADS = (2 + W_EPI) * 32;
 constexpr int W_BAR_BYTES = 256;
 constexpr int W_SMEM = 1024 + ACT_BYTES + W_NST * W_STAGE + W_BAR_BYTES;
 static_assert(W_SMEM <= 232448, "wide kernel shared memory");
@@ -53,11 +55,27 @@ __device__ __forceinline__ uint32_t wide_idesc(bool f16, int n) {
          ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
 }
 
-__device__ __forceinline__ void st_global_v4(uint8_t* p, uint32_t a, uint32_t b, uint32_t c,
-                                             uint32_t d) {
-  asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c),
-               "r"(d)
+__device__ __forceinline__ void prefetch_l1(const float* q) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
+}
+
+// Named barrier 1 over the epilogue warps: warp 2 waits for the others.
+__device__ __forceinline__ void epi_bar_sync() {
+  asm volatile("bar.sync 1, %0;" ::"n"(W_EPI * 32) : "memory");
+}
+__device__ __forceinline__ void epi_bar_arrive() {
+  asm volatile("bar.arrive 1, %0;" ::"n"(W_EPI * 32) : "memory");
+}
+
+// Shared -> global bulk copy (16-byte aligned, size a multiple of 16),
+// waited for to completion.
+__device__ __forceinline__ void bulk_store(uint8_t* dst, uint32_t src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(
+                   reinterpret_cast<uint64_t>(dst)),
+               "r"(src), "r"(bytes)
                : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 template <bool F16>
@@ -112,10 +130,10 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
     }
     mbar_init(acc_full, 1);
     mbar_init(act_full, 1);
-    mbar_init(slice_ready + 0, 4 * WC);
-    mbar_init(slice_ready + 1, 4 * WC);
+    mbar_init(slice_ready + 0, WC);   // one arrival per CTA (its loader)
+    mbar_init(slice_ready + 1, WC);
     mbar_init(a_loaded, 1);
-    mbar_init(head_ready, 4 * WC);
+    mbar_init(head_ready, W_EPI * WC);
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -205,6 +223,7 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
   } else {
     // ------------------------------------------------------------- epilogue
     const int quad = warp & 3;
+    const int half = (warp - 2) >> 2;            // 0: first half of each column range
     const int row = quad * 32 + lane;            // 16-bit tiles
     const int part = lane >> 4;                  // FP32-class tiles
     const int jr = quad * 16 + (lane & 15);
@@ -222,11 +241,9 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
     float3 p = make_float3(0.f, 0.f, 0.f);
     uint8_t* stage_base = nullptr;
 
-    // operand words at column c (8-aligned) of this thread's row(s): to the
-    // local operand tile and to the staging image, at the same offsets
+    // operand words at column c (8-aligned) of this thread's row(s)
     auto put4 = [&](uint32_t off, uint32_t w0, uint32_t w1, uint32_t w2, uint32_t w3) {
       st_shared_v4(smem_u32(act) + off, w0, w1, w2, w3);
-      st_global_v4(stage_base + off, w0, w1, w2, w3);
     };
     auto put = [&](int c, const uint32_t (&h)[16]) {
       if (!xt) {
@@ -303,38 +320,46 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
     };
     // this CTA's slice of the next operand is in place: make it visible to
     // the tensor core and to the other CTAs, then (loader) bring in theirs
+    // this CTA's slice of the next operand is in place: make it visible to
+    // the tensor core; then (loader) store it to the staging image with one
+    // bulk copy, tell the peers, and bring in theirs
     auto exchange = [&](int width) -> bool {
       uint64_t* ready = slice_ready + (xs & 1);
+      const uint32_t slice = (uint32_t)(width / WC) * 2u * BM;   // bytes per CTA slice
       fence_async_shared();
-      asm volatile("fence.proxy.async.global;" ::: "memory");
-      __threadfence();
-      __syncwarp();
-      if (lane == 0)
-        for (int d = 0; d < WC; ++d) mbar_arrive_remote(map_rank(smem_u32(ready), (uint32_t)d));
       bool good = true;
-      if (loader) {
-        good = mbar_wait_cl(ready, (uint32_t)(xs >> 1) & 1u, abort_flag);
-        if (good) {
+      if (warp != 2) {
+        epi_bar_arrive();
+      } else {
+        epi_bar_sync();   // every epilogue warp's part of the slice is in act
+        if (lane == 0) {
+          bulk_store(stage_base + (size_t)slice * rank, smem_u32(act) + slice * rank, slice);
+          // the store is complete before the peers hear of it
           asm volatile("fence.proxy.async.global;" ::: "memory");
-          const uint32_t slice = (uint32_t)(width / WC) * 2u * BM;   // bytes per CTA slice
-          mbar_expect_tx(a_loaded, slice * (WC - 1));
-          for (int d = 0; d < WC; ++d) {
-            if (d == rank) continue;
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
-                "%2, [%3];" ::"r"(smem_u32(act) + slice * d),
-                "l"(reinterpret_cast<uint64_t>(stage_base + (size_t)slice * d)), "r"(slice),
-                "r"(smem_u32(a_loaded))
-                : "memory");
+          for (int d = 0; d < WC; ++d) mbar_arrive_remote(map_rank(smem_u32(ready), (uint32_t)d));
+          good = mbar_wait_cl(ready, (uint32_t)(xs >> 1) & 1u, abort_flag);
+          if (good) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            mbar_expect_tx(a_loaded, slice * (WC - 1));
+            for (int d = 0; d < WC; ++d) {
+              if (d == rank) continue;
+              asm volatile(
+                  "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], "
+                  "%2, [%3];" ::"r"(smem_u32(act) + slice * d),
+                  "l"(reinterpret_cast<uint64_t>(stage_base + (size_t)slice * d)), "r"(slice),
+                  "r"(smem_u32(a_loaded))
+                  : "memory");
+            }
+            good = mbar_wait(a_loaded, load_phase, abort_flag);
+            load_phase ^= 1u;
+            if (good) mbar_arrive(act_full);
           }
-          good = mbar_wait(a_loaded, load_phase, abort_flag);
-          load_phase ^= 1u;
-          if (good) mbar_arrive(act_full);
         }
+        good = __shfl_sync(0xffffffffu, good ? 1 : 0, 0) != 0;
       }
       ++xs;
       stage_base = a.stage_g + ((size_t)cid * 2 + (xs & 1)) * ACT_BYTES;
-      return __shfl_sync(0xffffffffu, good ? 1 : 0, 0) != 0;
+      return good;
     };
     auto wait_acc = [&]() -> bool {
       if (!mbar_wait(acc_full, acc_phase, abort_flag)) return false;
@@ -354,7 +379,7 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
       const float* bf4 = a.bfold4 + (size_t)shape * 512;
       // layer 0: this CTA's 128 columns
 #pragma unroll 1
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 2 * half; k < 2 * half + 2; ++k) {
         uint32_t h[16];
         layer0(W_BN * rank + 32 * k, h);
         put(W_BN * rank + 32 * k, h);
@@ -362,12 +387,17 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
       if (!exchange(512)) { ok = false; break; }
       float hc[4] = {0.f, 0.f, 0.f, 0.f};
       for (int g = 0; g < NUM_GEMM; ++g) {
-        if (!wait_acc()) { ok = false; break; }
         const int nr = gemm_n(g) / WC;
         const int c0 = nr * rank;
+        // this layer's epilogue constants into L1 while its MMAs run
+        for (int k = half * nr / 64; k < (half + 1) * nr / 64; ++k) {
+          prefetch_l1((g == 3 ? bf4 : K->bias[g]) + c0 + 32 * k);
+          if (g == NUM_GEMM - 1) prefetch_l1(K->w_head + c0 + 32 * k);
+        }
+        if (!wait_acc()) { ok = false; break; }
         if (g < NUM_GEMM - 1) {
 #pragma unroll 1
-          for (int k = 0; k < nr / 32; ++k) {
+          for (int k = half * nr / 64; k < (half + 1) * nr / 64; ++k) {
             uint32_t h[16];
             hold(g, bf4, 32 * k, c0 + 32 * k, h);
             put(c0 + 32 * k, h);
@@ -377,7 +407,7 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
         } else {
           // head chunk sums of this CTA's quarter (q = rank, groups k)
 #pragma unroll 1
-          for (int k = 0; k < 4; ++k) {
+          for (int k = 2 * half; k < 2 * half + 2; ++k) {
             uint32_t r[32];
             tmem_ld32(t_row + (uint32_t)(32 * k), r);
             hc[k] = head_chunk_sum<F16>(K, xt, bf4, p, c0 + 32 * k, part,
@@ -392,11 +422,11 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
       const int hr = xt ? jr : row;
       float* hg = a.head_g + ((size_t)cid * BM + hr) * 16;
       if (!xt || part == 0)
-        for (int k = 0; k < 4; ++k) hg[rank * 4 + k] = hc[k];
+        for (int k = 2 * half; k < 2 * half + 2; ++k) hg[rank * 4 + k] = hc[k];
       __threadfence();
       __syncwarp();
       if (lane == 0) mbar_arrive_remote(map_rank(smem_u32(head_ready), 0u));
-      if (rank == 0) {
+      if (rank == 0 && half == 0) {
         if (!mbar_wait_cl(head_ready, head_phase, abort_flag)) { ok = false; break; }
         head_phase ^= 1u;
         float total = 0.f;
