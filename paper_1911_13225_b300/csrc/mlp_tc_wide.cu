@@ -28,7 +28,7 @@ constexpr int WC = 4;                          // CTAs per tile
 constexpr int WT_MAX = 37;                     // clusters per launch: 148 SMs / WC
 constexpr int W_BN = 128;                      // weight rows per stage (= 512 / WC)
 constexpr int W_STAGE = W_BN * BK * 2;         // 16 KB
-constexpr int W_NST = 5;
+constexpr int W_NST = 6;
 constexpr int W_EPI = 8;                       // epilogue warps: two per TMEM lane quadrant
 constexpr int W_THREADS = (2 + W_EPI) * 32;
 constexpr int W_BAR_BYTES = 256;
