@@ -271,7 +271,10 @@ def run_ours(args, rank, world, local_rank):
         roof = {"bound": "tensor",
                 "kernel": f"mlp_tc_kernel ({precision.upper()} tcgen05 decoder"
                           + (" + FP32-class rows in the same launch" if fused else "")
-                          + "; fp16 and bf16 share the dense tensor rate)",
+                          + "; fp16 and bf16 share the dense tensor rate)"
+                          + (" with mlp_tc_wide_kernel on the march's small steps"
+                             " (latency mode); achieved = per-step average over both"
+                             if fused and args.latency_mode else ""),
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "peak_source": f"{peak_src} bf16 burst",
                 "traffic": TC_TRAFFIC_BYTES,
@@ -285,7 +288,7 @@ def run_ours(args, rank, world, local_rank):
         achieved = k_q * FLOP_PER_QUERY / (k_ms * 1e-3) / 1e12 if k_ms > 0 else 0.0
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor",
-                "kernel": "mlp_tcx_kernel (FP32-class tcgen05 decoder: two-term FP16 split, "
+                "kernel": "mlp_tc_kernel, FP32-class rows only (two-term FP16 split, "
                           "4 tensor FLOP per algorithmic FLOP, so frac <= 0.25)",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "peak_source": f"{peak_src} bf16 burst",

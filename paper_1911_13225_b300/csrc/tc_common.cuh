@@ -1,5 +1,5 @@
 // Internal: tcgen05 / TMA / mbarrier helpers and epilogue pieces shared by the
-// tensor-core decoder kernels (mlp_tc.cu, mlp_tcx.cu).
+// tensor-core decoder kernels (mlp_tc.cu, mlp_tc_wide.cu).
 #pragma once
 
 #include <cudaTypedefs.h>
