@@ -231,7 +231,6 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
     const int rlo = rhi + 16;
     const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
     const TCConst* K = a.K;
-    const bool loader = warp == 2 && lane == 0;
     uint32_t acc_phase = 0, load_phase = 0, head_phase = 0;
     int xs = 0;                                   // exchanges so far
     bool ok = true;
@@ -319,10 +318,8 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
       }
     };
     // this CTA's slice of the next operand is in place: make it visible to
-    // the tensor core and to the other CTAs, then (loader) bring in theirs
-    // this CTA's slice of the next operand is in place: make it visible to
-    // the tensor core; then (loader) store it to the staging image with one
-    // bulk copy, tell the peers, and bring in theirs
+    // the tensor core; then (loader: lane 0 of warp 2) store it to the
+    // staging image with one bulk copy, tell the peers, and bring in theirs
     auto exchange = [&](int width) -> bool {
       uint64_t* ready = slice_ready + (xs & 1);
       const uint32_t slice = (uint32_t)(width / WC) * 2u * BM;   // bytes per CTA slice
