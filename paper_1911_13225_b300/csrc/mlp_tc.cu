@@ -1074,6 +1074,18 @@ dist_status pack_tcx(dist_decoder* d, const float* const* W) {
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (split, half box)");
+    // 3D view for the latency mode: one copy brings two 64-column chunks of
+    // 128 rows (a TMA copy costs ~160 ns whether it moves 16 or 32 KB)
+    {
+      cuuint64_t d3[3] = {(cuuint64_t)BK, (cuuint64_t)N, (cuuint64_t)(2 * K / BK)};
+      cuuint64_t s3[2] = {(cuuint64_t)(2 * K) * sizeof(uint16_t), (cuuint64_t)BK * sizeof(uint16_t)};
+      cuuint32_t b3[3] = {(cuuint32_t)BK, (cuuint32_t)(BN / 2), 2};
+      cuuint32_t e3[3] = {1, 1, 1};
+      r = enc(&d->tc.wxmaps.m[g], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, q, d3, s3, b3, e3,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (split, 3D)");
+    }
   }
   return DIST_OK;
 }
@@ -1157,6 +1169,17 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (half box)");
+      {
+        cuuint64_t d3[3] = {(cuuint64_t)BK, (cuuint64_t)N, (cuuint64_t)(K / BK)};
+        cuuint64_t s3[2] = {(cuuint64_t)K * sizeof(uint16_t), (cuuint64_t)BK * sizeof(uint16_t)};
+        cuuint32_t b3[3] = {(cuuint32_t)BK, (cuuint32_t)(BN / 2), 2};
+        cuuint32_t e3[3] = {1, 1, 1};
+        CUtensorMap* mw = f16 ? &d->tc.wmaps16.m[g] : &d->tc.wmaps.m[g];
+        r = enc(mw, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, p,
+                d3, s3, b3, e3, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (3D)");
+      }
       // the transpose [K rows][N cols] for the adjoint's backward GEMM
       std::vector<uint16_t> t((size_t)K * N, 0);
       for (int nn = 0; nn < N; ++nn)

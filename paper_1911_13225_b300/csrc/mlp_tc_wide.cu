@@ -27,8 +27,8 @@ namespace {
 constexpr int WC = 4;                          // CTAs per tile
 constexpr int WT_MAX = 37;                     // clusters per launch: 148 SMs / WC
 constexpr int W_BN = 128;                      // weight rows per stage (= 512 / WC)
-constexpr int W_STAGE = W_BN * BK * 2;         // 16 KB
-constexpr int W_NST = 6;
+constexpr int W_STAGE = 2 * W_BN * BK * 2;     // 32 KB: two 64-column chunks, one TMA copy
+constexpr int W_NST = 3;
 constexpr int W_EPI = 8;                       // epilogue warps: two per TMEM lane quadrant
 constexpr int W_THREADS = (2 + W_EPI) * 32;
 constexpr int W_BAR_BYTES = 256;
@@ -53,6 +53,16 @@ struct WideArgs {
 __device__ __forceinline__ uint32_t wide_idesc(bool f16, int n) {
   return (1u << 4) | ((f16 ? 0u : 1u) << 7) | ((f16 ? 0u : 1u) << 10) |
          ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+// Two [128 x 64] chunks (z, z + 1) of a 3D weight view, rows from y.
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int y,
+                                            int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(0), "r"(y), "r"(z)
+      : "memory");
 }
 
 __device__ __forceinline__ void prefetch_l1(const float* q) {
@@ -80,7 +90,7 @@ __device__ __forceinline__ void bulk_store(uint8_t* dst, uint32_t src, uint32_t 
 
 template <bool F16>
 __global__ void __launch_bounds__(W_THREADS, 1)
-mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__ TCMaps pxmaps,
+mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__ TCMaps wxmaps,
                    const WideArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -157,14 +167,16 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
       for (int tile = cid; ok && tile < n_tiles; tile += ncl) {
         const bool xt = tile < t1;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
-          const CUtensorMap* map = xt ? &pxmaps.m[g] : &pmaps.m[g];
+          const CUtensorMap* map = xt ? &wxmaps.m[g] : &wmaps.m[g];
           const int nkc = gemm_k(g) / BK;
           const int row0 = (gemm_n(g) / WC) * rank;
-          for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
+          // stages of two K chunks (nkc is even, so a pair never straddles
+          // the FP32-class tiles' W_lo / W_hi passes)
+          for (int kc = 0; kc < (xt ? 2 : 1) * nkc; kc += 2) {
             if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) { ok = false; break; }
             mbar_expect_tx(full + stage, W_STAGE);
             const int xk = !xt ? kc : (kc < nkc ? nkc + kc : kc - nkc);
-            tma_load_2d(wst + stage * W_STAGE, map, full + stage, xk * BK, row0);
+            tma_load_3d(wst + stage * W_STAGE, map, full + stage, row0, xk);
             issued[stage] = true;
             issued_parity[stage] = phase;
             if (++stage == W_NST) { stage = 0; phase ^= 1u; }
@@ -196,15 +208,18 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps pmaps, const __grid_constant__
           if (!mbar_wait(act_full, act_phase, abort_flag)) { ok = false; break; }
           act_phase ^= 1u;
           tc_fence_after();
-          for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
+          for (int kc = 0; kc < (xt ? 2 : 1) * nkc; kc += 2) {
             if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
             tc_fence_after();
             const uint32_t a_base = smem_u32(act + (kc < nkc ? kc : kc - nkc) * CHUNK_BYTES);
             const uint32_t b_base = smem_u32(wst + stage * W_STAGE);
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k)
-              mma_bf16(tmem, sw128_desc(a_base + 32 * k), sw128_desc(b_base + 32 * k), idesc,
-                       (kc | k) != 0);
+            for (int c = 0; c < 2; ++c)
+#pragma unroll
+              for (int k = 0; k < BK / 16; ++k)
+                mma_bf16(tmem, sw128_desc(a_base + c * CHUNK_BYTES + 32 * k),
+                         sw128_desc(b_base + c * (W_BN * BK * 2) + 32 * k), idesc,
+                         (kc | c | k) != 0);
             mma_commit(empty + stage);
             if (++stage == W_NST) { stage = 0; phase ^= 1u; }
           }
@@ -523,7 +538,7 @@ cudaError_t mlp_tc_wide(const dist_decoder* dec, const RowSrc& src16, float* f16
   const int wt = tc_wide_max_tiles();
   if (wt <= 0) return cudaErrorNotSupported;
   auto kern = f16 ? mlp_tc_wide_kernel<true> : mlp_tc_wide_kernel<false>;
-  const TCMaps& maps = f16 ? dec->tc.pmaps16 : dec->tc.pmaps;
+  const TCMaps& maps = f16 ? dec->tc.wmaps16 : dec->tc.wmaps;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(WC * wt);
   cfg.blockDim = dim3(W_THREADS);
@@ -538,7 +553,7 @@ cudaError_t mlp_tc_wide(const dist_decoder* dec, const RowSrc& src16, float* f16
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, dec->tc.pxmaps, a);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, dec->tc.wxmaps, a);
   count_launch(1);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
