@@ -31,19 +31,23 @@ def _target(api, dec, cam, z_tgt, ws, params, dev):
     return to_np(api.trace(dec, z, [dict(cam, shape=0)], params, ws).depth)
 
 
-@pytest.mark.parametrize("precision", ["fp32", "bf16"])
-def test_mixed_load_equals_alone_and_direct_calls(cuda_device, precision):
+@pytest.mark.parametrize("precision,latency_mode", [("fp32", 1), ("bf16", 1), ("bf16", 0)])
+def test_mixed_load_equals_alone_and_direct_calls(cuda_device, precision, latency_mode):
+    """(With latency_mode 0 the server decodes every step one tile per SM, the
+    direct calls use the default latency mode: the results still agree bit
+    for bit.)"""
     from paper_1911_13225_b300 import api
     from paper_1911_13225_b300.serve import Server
     spec = synth.DEEPSDF_SPEC if precision == "bf16" else synth.SMALL_SPEC
     Ws, bs, _ = workload(spec)
     dec = gpu_decoder(spec, Ws, bs)
     params = api.TraceParams(precision=precision)
+    srv_params = api.TraceParams(precision=precision, latency_mode=latency_mode)
     reqs, z_tgt = _requests(spec, 12)
     ws = api.Workspace(48 * 48, 50)
     tgts = [_target(api, dec, c, z_tgt, ws, params, cuda_device) if k == "backward" else None
             for c, _, k in reqs]
-    srv = Server(dec, params, max_rays=8192, mem_budget=1 << 30, max_requests=8)
+    srv = Server(dec, srv_params, max_rays=8192, mem_budget=1 << 30, max_requests=8)
     # all at once: requests join and leave the running batch
     mixed = [srv.submit(c, z, k, t) for (c, z, k), t in zip(reqs, tgts)]
     for t in mixed:
