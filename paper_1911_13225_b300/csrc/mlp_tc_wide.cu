@@ -69,14 +69,6 @@ __device__ __forceinline__ void prefetch_l1(const float* q) {
   asm volatile("prefetch.global.L1 [%0];" ::"l"(q));
 }
 
-// Named barrier 1 over the epilogue warps: warp 2 waits for the others.
-__device__ __forceinline__ void epi_bar_sync() {
-  asm volatile("bar.sync 1, %0;" ::"n"(W_EPI * 32) : "memory");
-}
-__device__ __forceinline__ void epi_bar_arrive() {
-  asm volatile("bar.arrive 1, %0;" ::"n"(W_EPI * 32) : "memory");
-}
-
 // Shared -> global bulk copy (16-byte aligned, size a multiple of 16),
 // waited for to completion.
 __device__ __forceinline__ void bulk_store(uint8_t* dst, uint32_t src, uint32_t bytes) {
@@ -109,9 +101,12 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
   uint64_t* a_loaded = bars + 2 * W_NST + 4;    // peers' slices copied in
   uint64_t* head_ready = bars + 2 * W_NST + 5;  // (rank 0) every CTA's head chunk sums
   uint64_t* drain = bars + 2 * W_NST + 6;       // every issued MMA complete
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * W_NST + 7);
+  // the other epilogue warps' parts of an operand slice are written -> warp 2
+  // (an mbarrier, so that warp 2's wait is bounded like every other)
+  uint64_t* epi_done = bars + 2 * W_NST + 7;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * W_NST + 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  static_assert((2 * W_NST + 7) * 8 + 8 <= W_BAR_BYTES, "barrier block");
+  static_assert((2 * W_NST + 8) * 8 + 8 <= W_BAR_BYTES, "barrier block");
 
   // launched behind the previous grid (programmatic dependent launch)
   grid_dep_wait();
@@ -145,6 +140,7 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
     mbar_init(a_loaded, 1);
     mbar_init(head_ready, W_EPI * WC);
     mbar_init(drain, 1);
+    mbar_init(epi_done, W_EPI - 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -246,7 +242,7 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
     const int rlo = rhi + 16;
     const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
     const TCConst* K = a.K;
-    uint32_t acc_phase = 0, load_phase = 0, head_phase = 0;
+    uint32_t acc_phase = 0, load_phase = 0, head_phase = 0, epi_phase = 0;
     int xs = 0;                                   // exchanges so far
     bool ok = true;
     float vmax = 0.f;
@@ -340,11 +336,14 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
       const uint32_t slice = (uint32_t)(width / WC) * 2u * BM;   // bytes per CTA slice
       fence_async_shared();
       bool good = true;
+      __syncwarp();
       if (warp != 2) {
-        epi_bar_arrive();
+        if (lane == 0) mbar_arrive(epi_done);
       } else {
-        epi_bar_sync();   // every epilogue warp's part of the slice is in act
-        if (lane == 0) {
+        // every epilogue warp's part of the slice is in act
+        good = mbar_wait(epi_done, epi_phase, abort_flag);
+        epi_phase ^= 1u;
+        if (good && lane == 0) {
           bulk_store(stage_base + (size_t)slice * rank, smem_u32(act) + slice * rank, slice);
           // the store is complete before the peers hear of it
           asm volatile("fence.proxy.async.global;" ::: "memory");
