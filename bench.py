@@ -339,7 +339,9 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clk,
     }
     line["fp32_trace"] = fp32_trace_rate(api, dec, cam, z, tgt, stream)
-    if args.coarse_levels == 0 and precision in ("bf16", "fp16"):
+    # (coarse-to-fine needs the fused tensor-core march: refine_steps 0, TC engine)
+    if args.coarse_levels == 0 and precision in ("bf16", "fp16") and args.refine == 0 \
+            and args.refine_engine == "tc":
         line["coarse_to_fine"] = coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream,
                                                      flush, args.steps, args.normals)
     line["roofline"]["large_launch"] = large_launch_rate(api, dec, z, precision, peaks["bf16_tflops"])
