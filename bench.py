@@ -504,10 +504,16 @@ def run_serving(args, dec, params, dev):
     drive(np.zeros(min(16, len(reqs))))                      # warm-up
     _, t_sat = drive(np.zeros(len(reqs)))
     sat_req_s = len(reqs) / t_sat
-    rng = np.random.default_rng(4242)
-    arr = np.cumsum(rng.exponential(1.0 / (args.serve_load * sat_req_s), len(reqs)))
-    arr -= arr[0]
-    lat, t_run = drive(arr)
+    # Poisson arrivals at each load (fraction of the saturated request rate)
+    loads = sorted(set([float(x) for x in args.serve_loads.split(",") if x] + [args.serve_load]))
+    by_load = {}
+    for load in loads:
+        rng = np.random.default_rng(4242)
+        arr = np.cumsum(rng.exponential(1.0 / (load * sat_req_s), len(reqs)))
+        arr -= arr[0]
+        lat_l, t_l = drive(arr)
+        by_load[load] = (lat_l, t_l)
+    lat, t_run = by_load[args.serve_load]
     srv.close()
 
     # the plain per-request FP32 CUDA-core trace (+ backward), one at a time
@@ -535,6 +541,10 @@ def run_serving(args, dec, params, dev):
         "poisson_rays_per_s": float(rays.sum() / t_run),
         "p50_ms": float(np.percentile(lat, 50) * 1e3),
         "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "by_load": {f"{load:g}": {"poisson_rays_per_s": float(rays.sum() / t_l),
+                                   "p50_ms": float(np.percentile(lat_l, 50) * 1e3),
+                                   "p99_ms": float(np.percentile(lat_l, 99) * 1e3)}
+                    for load, (lat_l, t_l) in by_load.items()},
         "fp32_per_request_rays_per_s": float(rays[sample].sum() / t32),
         "fp32_sample_requests": len(sample),
     }
@@ -659,6 +669,8 @@ def main():
                     help="1: steps with few tiles spread each tile over a four-SM cluster")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-loads", default="0.5,0.95",
+                    help="further Poisson loads reported under serving.by_load")
     ap.add_argument("--serve-load", type=float, default=0.8,
                     help="Poisson arrival rate as a fraction of the saturated request rate")
     ap.add_argument("--serve-fp32-sample", type=int, default=12)
