@@ -328,6 +328,11 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"replicas x{world}",
                    "l2": "flushed between timed steps (256 MB write, untimed)"},
         "sdf_queries_per_s": float(queries.sum()) * world / (total_ms * 1e-3),
+        # the same queries over the decoder launches' own time (forward march only)
+        "march_sdf_queries_per_s": (float(queries.sum()) / args.steps * world /
+                                    ((breakdown["march_tc_ms"] + breakdown["march_fp32_list_ms"])
+                                     * 1e-3)) if (breakdown["march_tc_ms"] +
+                                                  breakdown["march_fp32_list_ms"]) > 0 else None,
         "queries_per_step": {"lowp": float(queries[0]) / args.steps,
                              "fp32": float(queries[1]) / args.steps},
         "hits": hits,

@@ -180,7 +180,7 @@ typedef struct {
                           sphere starts at its own entry.                   */
   int coarse_every;    /* march iterations per coarse level (the paper: 3) */
   int latency_mode;    /* tensor-core march with FP32-class TC queries
-                          (refine_steps 0): 1 (default) = a step whose
+                          (refine_engine TC): 1 (default) = a step whose
                           lists fit in as many tiles (128 16-bit rays or
                           64 FP32-class rays each) as four-SM clusters fit
                           on the GPU at once (at most 37) spreads each tile over

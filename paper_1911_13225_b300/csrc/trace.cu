@@ -1360,13 +1360,13 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
   const int step_grid = num_sms() * 4;
   RowSrc src{};
   src.st = ws->st; src.dir = ws->dir; src.cams = ws->cams;
-  if (tc && fp32_on_tc(*p) && p->refine_steps == 0) {
-    // Tensor-core march with FP32-class tensor-core queries that run to
-    // convergence: one launch per step decodes both lists (16-bit rows and
-    // handed-over rays), so the two share the latency of the shrinking tail
-    // of steps.  (With refine_steps > 0 a handed-over ray needs only a few
-    // FP32-class queries, and one deferred batch of them, below, is
-    // cheaper.)
+  if (tc && fp32_on_tc(*p)) {
+    // Tensor-core march with FP32-class tensor-core queries (to convergence,
+    // or refine_steps of them): one launch per step decodes both lists
+    // (16-bit rows and handed-over rays), so the two share the latency of
+    // the shrinking tail of steps, which the latency mode shortens.  (With
+    // refine_steps > 0 this measured faster than one deferred batch of the
+    // FP32-class queries after the 16-bit march.)
     const int* in0 = cA;
     const int* in1 = cB;
     for (int s = 0; s < M; ++s) {
