@@ -1360,9 +1360,10 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
   const int step_grid = num_sms() * 4;
   RowSrc src{};
   src.st = ws->st; src.dir = ws->dir; src.cams = ws->cams;
-  if (tc && fp32_on_tc(*p)) {
+  if (fp32_on_tc(*p)) {
     // Tensor-core march with FP32-class tensor-core queries (to convergence,
-    // or refine_steps of them): one launch per step decodes both lists
+    // or refine_steps of them; FP32_TC: every query, the 16-bit list stays
+    // empty): one launch per step decodes both lists
     // (16-bit rows and handed-over rays), so the two share the latency of
     // the shrinking tail of steps, which the latency mode shortens.  (With
     // refine_steps > 0 this measured faster than one deferred batch of the
