@@ -1432,10 +1432,8 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
     src.count = in1;
     src.idx = ws->act[par][1];
     prof_mlp_begin(st, 1);
-    if (fp32_on_tc(*p))
-      DIST_CUDA_TRY(mlp_tcx_forward(dec, src, b0, bs, ws->fbuf[1], st));
-    else
-      DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->fbuf[1], st, tc && t > 0));
+    // (FP32-class queries on the tensor cores take the fused march above)
+    DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->fbuf[1], st, tc && t > 0));
     prof_mlp_end(st);
     StepLists L;
     L.cnt_in[0] = zero; L.cnt_in[1] = in1;
