@@ -349,6 +349,9 @@ def run_ours(args, rank, world, local_rank):
             and args.refine_engine == "tc":
         line["coarse_to_fine"] = coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream,
                                                      flush, args.steps, args.normals)
+        if precision == "bf16" and args.refine == 0:
+            line["fp16_one_step"] = fp16_one_step_rate(api, dec, ws, cam, params, z, tgt, stream,
+                                                       flush, args.steps, args.normals)
     line["roofline"]["large_launch"] = large_launch_rate(api, dec, z, precision, peaks["bf16_tflops"])
     if not args.no_serve:
         line["serving"] = run_serving(args, dec, params, dev)
@@ -359,13 +362,10 @@ def run_ours(args, rank, world, local_rank):
 
 # ------------------------------------------------- FP32 trace, large launches
 
-def coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps, normals):
-    """The same fwd+bwd step with the paper's coarse-to-fine tracing (Sec. 3.2:
-    start at 1/4 resolution per side, split every ray into four after every
-    three iterations), timed like the main line."""
-    import dataclasses
+def variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals):
+    """The same fwd+bwd step with trace parameters p2, timed like the main
+    line: (ms per step, queries per step, hits)."""
     import torch
-    p2 = dataclasses.replace(params, coarse_levels=2, coarse_every=3)
     step = Step(api, dec, ws, cam, p2, z, tgt, normals=normals)
     for _ in range(3):
         step(stream)
@@ -381,13 +381,39 @@ def coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps,
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     q = step.res.queries.cpu().numpy().astype(np.float64) / steps
+    return ms, q, int(step.res.mask.sum().item())
+
+
+def coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps, normals):
+    """The same fwd+bwd step with the paper's coarse-to-fine tracing (Sec. 3.2:
+    start at 1/4 resolution per side, split every ray into four after every
+    three iterations), timed like the main line."""
+    import dataclasses
+    p2 = dataclasses.replace(params, coarse_levels=2, coarse_every=3)
+    ms, q, hits = variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals)
     return {"value": SIZE * SIZE / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
             "coarse_levels": 2, "coarse_every": 3,
             "queries_per_step": {"lowp": float(q[0]), "fp32": float(q[1])},
-            "hits": int(step.res.mask.sum().item()),
+            "hits": hits,
             "note": "same step with coarse-to-fine tracing (Sec. 3.2); child rays inherit by "
                     "the stated reading, so depths differ from the exact per-pixel trace near "
                     "silhouettes"}
+
+
+def fp16_one_step_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps, normals):
+    """The same fwd+bwd step with FP16 operands, hand-over at |f| < 1e-4 and
+    one FP32-class query after it (the one-step refinement mode)."""
+    import dataclasses
+    p2 = dataclasses.replace(params, precision="fp16", eps_bf16=1e-4, refine_steps=1,
+                             coarse_levels=0)
+    ms, q, hits = variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals)
+    return {"value": SIZE * SIZE / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
+            "dtype": "fp16", "eps_lo": 1e-4, "refine_steps": 1,
+            "queries_per_step": {"lowp": float(q[0]), "fp32": float(q[1])},
+            "hits": hits,
+            "note": "FP16 GEMM operands (same tensor rate as BF16), one FP32-class query after "
+                    "the hand-over; depth within 2e-3 of the oracle away from the silhouette "
+                    "(tests)"}
 
 
 def fp32_trace_rate(api, dec, cam, z, tgt, stream, steps=3):
