@@ -141,3 +141,48 @@ def ambiguous_rays(orc, tol_f, tol_d=1e-5, max_steps=50, grazing=0.05, near_miss
     qq = np.einsum("ij,ij->i", orc["c"], orc["c"]) - b * b
     amb |= np.abs(qq - 1.0) < 1e-5
     return amb
+
+
+# -------------------------------------------- silhouette rays at an |SDF| margin
+
+SDF_MARGIN = 1e-3       # the |SDF| margin of the mask contract (hit/miss bit-exact beyond it)
+FP32_CLASS_TOL = 5e-6   # bound on |f| error of the GPU's FP32 / FP32-class queries vs FP64
+
+
+class ShiftedSDF:
+    """f + delta: the zero level set moved by about delta along the normal
+    (outwards for delta < 0).  Same gradient as f."""
+
+    def __init__(self, sdf, delta):
+        self.sdf, self.delta = sdf, float(delta)
+
+    def __call__(self, p, shape=None):
+        return self.sdf(p, shape) + self.delta
+
+    def grad(self, p, shape=None):
+        f, gp, gz = self.sdf.grad(p, shape)
+        return f + self.delta, gp, gz
+
+
+def shifted_traces(trace, sdf, margin=SDF_MARGIN):
+    """The oracle trace ``trace(sdf')`` of the decoder shifted by -margin and
+    +margin (trace is a function of an SDF, e.g. a partial of tracer.render)."""
+    return [trace(ShiftedSDF(sdf, d)) for d in (-margin, margin)]
+
+
+def silhouette_rays(orc, shifted, max_steps=50, tol_f=FP32_CLASS_TOL):
+    """Rays excluded from the bit-exact hit/miss comparison of a 16-bit march
+    against the oracle: rays within the |SDF| margin of the silhouette, read
+    as "the oracle's hit/miss outcome changes when f is shifted by -margin
+    or +margin" (the surface moved out or in by the margin: near-miss rays
+    and barely-penetrating grazing hits); rays that use (almost) their whole
+    step budget in any of the three traces (the budget is a count of
+    queries, not a distance); rays whose convergence test the oracle passed
+    or failed within the FP32-class query error (tol_f) of eps; and rays
+    grazing the bounding sphere.  ``orc`` is the recorded oracle trace and
+    ``shifted`` its two shifted traces (shifted_traces)."""
+    amb = ambiguous_rays(orc, tol_f=tol_f, tol_d=0.0, max_steps=max_steps)
+    for o in shifted:
+        amb |= o["mask"] != orc["mask"]
+        amb |= o["steps"] >= max_steps - 2
+    return amb

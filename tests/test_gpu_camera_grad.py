@@ -14,7 +14,8 @@ import torch
 import synth
 from oracle import tracer
 from oracle.grad import camera_vjp
-from tests.helpers import ambiguous_rays, gpu_decoder, oracle_sdf, to_np, workload
+from tests.helpers import (ambiguous_rays, gpu_decoder, oracle_sdf, shifted_traces,
+                           silhouette_rays, to_np, workload)
 
 pytestmark = pytest.mark.gpu
 
@@ -47,14 +48,27 @@ def test_camera_gradient_matches_oracle(cuda_device, precision, tol):
                                w_sil=1.0)
     amb = ambiguous_rays(orc, tol_f=1e-5, max_steps=60, normals=orc["normal"], near_miss=1e-3)
     if precision != "fp32":
-        # BF16 samples move by ~1e-3: silhouette-adjacent rays may change outcome
-        amb |= ambiguous_rays(orc, tol_f=0.0, tol_d=0.0, normals=orc["normal"], grazing=0.15,
-                              near_miss=2e-2)
+        # 16-bit samples move the march: silhouette rays at the 1e-3 |SDF|
+        # margin may change outcome (and the first-term silhouette gradient
+        # of a near-miss ray depends on where its smallest |f| was sampled)
+        shifted = shifted_traces(lambda f: tracer.render(f, cams, max_steps=60,
+                                                         with_normals=False), sdf)
+        amb |= silhouette_rays(orc, shifted, max_steps=60)
         amb |= to_np(res.mask).astype(bool) != orc["mask"]
     g_d = to_np(gd).astype(np.float64)
     g_s = to_np(gs).astype(np.float64)
     g_d[amb] = 0.0
     g_s[amb] = 0.0
+    if precision != "fp32":
+        # not a mask question but where the gradient is evaluated: the depth
+        # term divides by grad f . v, which amplifies the 16-bit march's
+        # ~1e-4 hit displacement at grazing hits (|n . v| < 0.15), and the
+        # silhouette term of a near miss is taken at its smallest-|f| sample,
+        # which a 16-bit march places elsewhere along the ray (misses with
+        # min |f| < 2e-2); both are left out of the comparison
+        nv = np.abs(np.einsum("ij,ij->i", orc["normal"], orc["v"]))
+        g_d[orc["mask"] & (nv < 0.15)] = 0.0
+        g_s[orc["enters"] & ~orc["mask"] & (orc["min_abs_f"] < 2e-2)] = 0.0
     for name, kw, okw in (("depth", {"g_depth": g_d}, {"g_depth": g_d}),
                           ("sil", {"g_sil": g_s}, {"g_sil": g_s}),
                           ("both", {"g_depth": g_d, "g_sil": g_s}, {"g_depth": g_d, "g_sil": g_s})):

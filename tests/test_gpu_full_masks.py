@@ -1,0 +1,60 @@
+"""Hit masks of whole images against the FP64 oracle: the 512 x 512
+benchmark view and the five 256 x 256 views, every pixel.
+
+The oracle's masks and exclusion sets are stored in tests/golden/
+full_masks.npz, written by tests/golden/make_full_masks.py from the oracle
+alone.  A 16-bit march (BF16 or FP16 operands, FP32-class convergence) must
+give the oracle's hit/miss on every ray outside the silhouette rays at the
+1e-3 |SDF| margin; the FP32 trace on every ray outside its threshold-
+ambiguous set.  Zero mismatches are allowed there."""
+
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from tests.helpers import gpu_decoder, to_np, workload
+
+pytestmark = pytest.mark.gpu
+
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_masks.npz")
+
+
+def _golden(tag):
+    with np.load(GOLD) as g:
+        n = int(g[f"{tag}/n"])
+        return {k: np.unpackbits(g[f"{tag}/{k}"])[:n].astype(bool) for k in ("mask", "sil", "amb32")}
+
+
+def _view(tag):
+    spec = synth.DEEPSDF_SPEC
+    if tag == "b512":
+        Ws, bs, Z = workload(spec, seed=0, n_shapes=2)
+        cams = [synth.look_at_camera(synth.random_viewpoints(5, seed=0)[0], 512, 512, shape=0)]
+    else:
+        Ws, bs, Z = workload(spec, seed=0, n_shapes=1)
+        cams = [synth.look_at_camera(vp, 256, 256) for vp in synth.random_viewpoints(5, seed=0)]
+    return spec, Ws, bs, Z, cams
+
+
+@pytest.mark.parametrize("tag,precision", [("b512", "bf16"), ("b512", "fp16"), ("b512", "fp32"),
+                                           ("v5", "bf16"), ("v5", "fp32")])
+def test_whole_image_hit_masks(cuda_device, tag, precision):
+    from paper_1911_13225_b300 import api
+    spec, Ws, bs, Z, cams = _view(tag)
+    dec = gpu_decoder(spec, Ws, bs)
+    ws = api.Workspace(api.n_pixels(cams), 50)
+    res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), cams,
+                    api.TraceParams(precision=precision), ws)
+    assert dec.device_error() == 0
+    g = _golden(tag)
+    mask = to_np(res.mask).astype(bool)
+    assert mask.size == g["mask"].size
+    excluded = g["amb32"] if precision == "fp32" else g["sil"]
+    assert excluded.mean() < (0.1 if precision == "fp32" else 0.06)
+    diff = mask != g["mask"]
+    outside = np.nonzero(diff & ~excluded)[0]
+    assert outside.size == 0, (outside[:10], int(diff.sum()))
+    assert diff.sum() < 1e-3 * mask.size

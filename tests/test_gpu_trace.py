@@ -5,13 +5,16 @@ Away from rays whose discrete decisions sit within rounding of a threshold
 (tests/helpers.ambiguous_rays), masks, step counts and outcome codes must be
 identical and depth / silhouette within 1e-5 in scene units."""
 
+import functools
+
 import numpy as np
 import pytest
 import torch
 
 import synth
 from oracle import tracer
-from tests.helpers import ambiguous_rays, gpu_decoder, oracle_sdf, to_np, workload
+from tests.helpers import (ambiguous_rays, gpu_decoder, oracle_sdf, shifted_traces,
+                           silhouette_rays, to_np, workload)
 
 pytestmark = pytest.mark.gpu
 
@@ -121,6 +124,19 @@ def test_normals_at_gpu_hits(cuda_device, delta):
     assert np.all(to_np(res.normal)[~m] == 0)
 
 
+@functools.lru_cache(maxsize=None)
+def _oracle_view(size, vp_seed):
+    """The oracle's trace of the DeepSDF decoder (seed 0) from viewpoint
+    vp_seed, and its traces shifted by -1e-3 and +1e-3 (cached: every
+    precision mode compares against the same oracle)."""
+    spec = synth.DEEPSDF_SPEC
+    Ws, bs, Z = workload(spec, seed=0, n_shapes=1)
+    cam = synth.look_at_camera(synth.random_viewpoints(1, seed=vp_seed)[0], size, size)
+    sdf = oracle_sdf(spec, Ws, bs, Z)
+    orc = tracer.render(sdf, [cam], record=True)
+    return orc, shifted_traces(lambda f: tracer.render(f, [cam], with_normals=False), sdf)
+
+
 @pytest.mark.parametrize("precision,eps_lo,refine,alpha_r,engine,rule", [
     ("bf16", 1e-3, 0, 0.0, "tc", "march"), ("fp16", 1e-3, 0, 0.0, "tc", "march"),
     ("fp16", 1e-4, 1, 0.0, "tc", "march"), ("fp16", 2e-4, 1, 0.0, "tc", "march"),
@@ -137,7 +153,7 @@ def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precisio
     secant steps): converge to eps = 5e-5 (refine = 0) or accept after
     `refine` FP32 queries within 4 eps_lo (unit final step).  Depth within
     2e-3 of the FP64 oracle on hits away from the silhouette; masks agree
-    except near-silhouette rays."""
+    except on silhouette rays at the 1e-3 |SDF| margin."""
     from paper_1911_13225_b300 import api
     spec = synth.DEEPSDF_SPEC
     Ws, bs, Z = workload(spec, seed=0, n_shapes=1)
@@ -148,13 +164,12 @@ def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precisio
                              alpha_refine=alpha_r, refine_engine=engine, refine_rule=rule)
     res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), [cam], params, ws)
     assert dec.device_error() == 0
-    orc = tracer.render(oracle_sdf(spec, Ws, bs, Z), [cam], record=True)
-    # BF16 queries move every sample by ~1e-3, so hit/miss can differ near the
-    # silhouette (near-miss rays, grazing hits, rays at the step budget); the
-    # final convergence test is FP32, so no per-sample threshold criterion
-    amb = ambiguous_rays(orc, tol_f=0.0, tol_d=0.0, normals=orc["normal"], grazing=0.15,
-                         near_miss=2e-2)
-    ok = ~amb
+    orc, shifted = _oracle_view(size, vp_seed)
+    # 16-bit queries move the march's samples, so hit/miss may differ only on
+    # silhouette rays at the 1e-3 |SDF| margin (tests/helpers.silhouette_rays);
+    # everywhere else the masks are identical
+    ok = ~silhouette_rays(orc, shifted)
+    assert ok.mean() > 0.9
     mask = to_np(res.mask).astype(bool)
     assert (mask == orc["mask"]).mean() > 0.99
     assert np.array_equal(mask[ok], orc["mask"][ok])
