@@ -239,16 +239,21 @@ def run_ours(args, rank, world, local_rank):
     loss_host = torch.zeros(1, dtype=torch.float64).pin_memory()
     dz_host = torch.zeros_like(z_host).pin_memory()
     e2e_steps = max(3, args.steps // 2)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    e2e_total = 0.0
     for _ in range(e2e_steps):
+        # L2 flushed before every step as in the device-timed loop, outside
+        # the timed region (each step is timed on the host from here)
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         step.z.copy_(z_host, non_blocking=True)
         step.tgt.copy_(tgt_host, non_blocking=True)
         step(stream)
         loss_host.copy_(step.loss, non_blocking=True)
         dz_host.copy_(step.dz, non_blocking=True)
         stream.synchronize()
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
+        e2e_total += time.perf_counter() - t0
+    e2e_s = e2e_total / e2e_steps
 
     if world > 1:
         total_ms, e2e_s = max_over_ranks([total_ms, e2e_s], dev)
@@ -337,7 +342,10 @@ def run_ours(args, rank, world, local_rank):
                              "fp32": float(queries[1]) / args.steps},
         "hits": hits,
         "e2e": {"value": rays * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": bi,
-                "d2h_bytes_per_step": bo},
+                "d2h_bytes_per_step": bo,
+                "note": "host-timed per step (pinned copies in, loss and dz out, stream "
+                        "synchronised); L2 flushed before each step outside the timed region, "
+                        "as for value"},
         "gpu_launches": int(all_launches.value),
         "step_breakdown_ms": breakdown,
         "roofline": roof,
@@ -353,6 +361,9 @@ def run_ours(args, rank, world, local_rank):
             line["fp16"] = fp16_rate(api, dec, ws, cam, params, z, tgt, stream, flush,
                                      args.steps, args.normals)
     line["roofline"]["large_launch"] = large_launch_rate(api, dec, z, precision, peaks["bf16_tflops"])
+    if not args.no_side_configs and SIZE == 512:
+        line["five_views_256"] = five_views_rate(api, dec, z, stream, flush)
+        line["inverse_32x8_224"] = inverse_rate(api, dec, spec, dev, args.inverse_steps)
     if not args.no_serve:
         line["serving"] = run_serving(args, dec, params, dev)
     if not args.no_cpu_baseline:
@@ -461,6 +472,89 @@ def large_launch_rate(api, dec, z, precision, peak, n=262144 * 2, reps=5):
     tf = n * FLOP_PER_QUERY / (ms * 1e-3) / 1e12
     return {"rows": n, "ms": ms, "achieved": tf, "peak": peak, "frac": tf / peak,
             "note": "dist_sdf_eval of one launch (fold + pack + decoder), algorithmic FLOPs"}
+
+
+# ------------------------------------------ the other configurations' lines
+
+def five_views_rate(api, dec, z, stream, flush, steps=5):
+    """Forward trace of 5 seeded viewpoints (radius 2.5) at 256x256 in one
+    call (327,680 rays), latent 0 of the benchmark's, 50 steps: BF16 tcgen05
+    march with FP32-class convergence against the plain FP32 trace, both
+    device-timed with L2 flushed between steps."""
+    import torch
+    import synth
+    cams = [synth.look_at_camera(vp, 256, 256) for vp in synth.random_viewpoints(5, seed=0)]
+    n = api.n_pixels(cams)
+    ws = api.Workspace(n, MAX_STEPS)
+    cam_c = api.camera_array(cams)
+    out = {"rays_per_step": n, "note": "5 views x 256x256 in one dist_trace_fwd call, forward "
+           "only (depth, silhouette, mask), 50 steps, eps 5e-5, alpha 1.5"}
+    for prec in ("bf16", "fp32"):
+        p = api.TraceParams(max_steps=MAX_STEPS, precision=prec)
+        res = api.alloc_result(n, 1, z.device, normals=False)
+        for _ in range(2):
+            api.trace(dec, z, cams, p, ws, out=res, cam_c=cam_c, stream=stream)
+        torch.cuda.synchronize()
+        res.queries.zero_()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for i in range(steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            api.trace(dec, z, cams, p, ws, out=res, cam_c=cam_c, stream=stream)
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+        q = res.queries.cpu().numpy().astype(np.float64) / steps
+        out[prec] = {"value": n / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
+                     "queries_per_step": {"lowp": float(q[0]), "fp32": float(q[1])},
+                     "hits": int(res.mask.sum().item())}
+    out["bf16_over_fp32"] = out["bf16"]["value"] / out["fp32"]["value"]
+    return out
+
+
+def inverse_rate(api, dec, spec, dev, steps=3):
+    """The inverse-optimisation batch: 32 shapes (seeded target latents) x 8
+    ring views (elevation 20 deg, radius 2.5) at 224x224 = 12,845,056 rays,
+    all in one call per library entry point.  One Adam step = trace (BF16
+    march, central-difference normals, delta 1e-3) + depth and normal losses
+    (weights 10 and 1) + latent gradient + Adam (lr 1e-2, z0 = 0), device-timed
+    after one warm-up step (the ray state alone is 411 MB, far above L2)."""
+    import torch
+    import synth
+    from paper_1911_13225_b300.inverse import InverseProblem
+    ring = synth.ring_viewpoints(8)
+    cams = [synth.look_at_camera(ring[v], 224, 224, shape=s) for s in range(32) for v in range(8)]
+    n = api.n_pixels(cams)
+    params = api.TraceParams(max_steps=MAX_STEPS, precision="bf16", normal_delta=1e-3)
+    ws = api.Workspace(n, MAX_STEPS)
+    z_true = torch.from_numpy(synth.make_latents(spec, 32, seed=3)).to(dev)
+    tgt = api.trace(dec, z_true, cams, params, ws, normals=True)
+    prob = InverseProblem(dec, cams, 32, tgt.depth.clone(), tgt.normal.clone(), params=params,
+                          ws=ws, lr=1e-2, w_depth=10.0, w_normal=1.0)
+    del tgt
+    stream = torch.cuda.current_stream()
+    loss0 = float(prob.step(stream))
+    torch.cuda.synchronize()
+    prob.res.queries.zero_()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    for i in range(steps):
+        evs[i][0].record(stream)
+        prob.step(stream)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / steps
+    q = prob.res.queries.cpu().numpy().astype(np.float64) / steps
+    assert dec.device_error() == 0
+    return {"value": n / (ms * 1e-3), "unit": "rays/s", "s_per_adam_step": ms * 1e-3,
+            "rays_per_step": n, "steps": steps,
+            "march_queries_per_step": {"lowp": float(q[0]), "fp32": float(q[1])},
+            "loss_step1": loss0, "loss_last": float(prob.loss.item()),
+            "note": "32 shapes x 8 views x 224x224 per Adam step, one call per entry point "
+                    "(dist_trace_fwd with central-difference normals, dist_loss, "
+                    "dist_trace_bwd, dist_adam_step); the paper's Tab. 1 unit is the time "
+                    "of one such optimisation step"}
 
 
 # ----------------------------------------------------------------- serving
@@ -625,21 +719,60 @@ def oracle_step(spec, sdf, cam, tgt_depth):
     return L, G
 
 
-def cpu_baseline(crop):
-    import synth
-    spec = synth.DEEPSDF_SPEC
-    Ws, bs, Z, cam = make_workload(spec)
+def _cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def _oracle_crop_rate(spec, sdf, cam, crop):
     c = _crop_camera(cam, crop)
-    sdf = oracle_sdf(spec, Ws, bs, Z)
     tgt = oracle_target(sdf, c)
     t0 = time.perf_counter()
     oracle_step(spec, sdf, c, tgt)
     dt = time.perf_counter() - t0
-    return {"value": crop * crop / dt, "unit": "rays/s", "cores": _blas_threads(),
-            "kind": "oracle",
+    return crop * crop / dt, dt
+
+
+def _oracle_one_thread(crop):
+    """The oracle's crop rate in a child process whose BLAS runs one thread."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-crop-rate", str(crop)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode != 0:
+        return None, None
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["rate"], d["s"]
+
+
+def cpu_baseline(crop, crop_1t=32):
+    """The FP64 oracle's step on central crops of the benchmark view, on all
+    host threads (numpy/BLAS) and on one; the full 512x512 step time is
+    extrapolated from the all-thread per-ray rate (the crop is the image's
+    centre, where more rays hit and march longer than at the border, so the
+    extrapolation overstates the full image's time)."""
+    import synth
+    spec = synth.DEEPSDF_SPEC
+    Ws, bs, Z, cam = make_workload(spec)
+    sdf = oracle_sdf(spec, Ws, bs, Z)
+    rate, dt = _oracle_crop_rate(spec, sdf, cam, crop)
+    rate1, dt1 = _oracle_one_thread(crop_1t)
+    return {"value": rate, "unit": "rays/s", "cores": _blas_threads(),
+            "kind": "oracle", "cpu_model": _cpu_model(), "host_cpus": os.cpu_count(),
             "sample": f"central {crop}x{crop} crop of the 512x512 view (same decoder, latents, "
                       f"camera, target rendered beforehand); forward + L1 loss + exact latent "
-                      f"gradient; {dt:.1f} s wall"}
+                      f"gradient; {dt:.1f} s wall",
+            "one_thread": ({"value": rate1, "unit": "rays/s", "cores": 1,
+                            "sample": f"central {crop_1t}x{crop_1t} crop, {dt1:.1f} s wall "
+                                      f"(BLAS limited to one thread)"}
+                           if rate1 is not None else None),
+            "extrapolated_512x512_step_s": SIZE * SIZE / rate,
+            "extrapolation": "512x512 rays / the all-thread crop rate (labelled extrapolated; "
+                             "not measured)"}
 
 
 def run_reference(args):
@@ -700,13 +833,26 @@ def main():
     ap.add_argument("--latency-mode", type=int, default=1, choices=[0, 1],
                     help="1: steps with few tiles spread each tile over a four-SM cluster")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-side-configs", action="store_true",
+                    help="skip the 5-view 256x256 and the 32x8x224^2 inverse-step lines")
+    ap.add_argument("--inverse-steps", type=int, default=3,
+                    help="timed Adam steps of the 32x8x224^2 inverse-step line")
     ap.add_argument("--serve-requests", type=int, default=400)
     ap.add_argument("--serve-loads", default="0.5,0.95",
                     help="further Poisson loads reported under serving.by_load")
     ap.add_argument("--serve-load", type=float, default=0.8,
                     help="Poisson arrival rate as a fraction of the saturated request rate")
     ap.add_argument("--serve-fp32-sample", type=int, default=12)
+    ap.add_argument("--oracle-crop-rate", type=int, default=0, help=argparse.SUPPRESS)
     args = ap.parse_args()
+    if args.oracle_crop_rate:
+        # (child of cpu_baseline: the oracle's rate on one crop, printed as JSON)
+        import synth
+        spec = synth.DEEPSDF_SPEC
+        Ws, bs, Z, cam = make_workload(spec)
+        rate, dt = _oracle_crop_rate(spec, oracle_sdf(spec, Ws, bs, Z), cam, args.oracle_crop_rate)
+        print(json.dumps({"rate": rate, "s": dt}), flush=True)
+        return
     global SIZE
     SIZE = args.size
     world = int(os.environ.get("WORLD_SIZE", "1"))

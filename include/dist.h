@@ -22,6 +22,9 @@
  *    pixels row-major (index = offset + y * W + x).  Cameras use OpenCV axes:
  *    x right, y down, z forward (the depth formula of Sec. 3.3).
  *  - Background pixels have depth +inf (Sec. 3.2, "Initialization").
+ *  - One device per process: the library sizes its grids and sets its
+ *    kernels' shared-memory limits for the device that is current at its
+ *    first launch, and every later call must run with that device current.
  */
 #ifndef DIST_H
 #define DIST_H
@@ -109,12 +112,27 @@ dist_status dist_decoder_create(const dist_decoder_desc* desc,
 dist_status dist_decoder_destroy(dist_decoder* dec);
 /* 1 if the BF16 tensor-core MLP covers this decoder, else 0. */
 int dist_decoder_has_bf16(const dist_decoder* dec);
-/* Not from the paper: every device-side wait of the tensor-core kernel is
- * bounded (1 s).  A launch that gives up sets bits in a device error word of
- * the decoder and returns early (its outputs are then invalid).  This call
- * synchronises the device, returns the word in *code (0 = no timeout since
- * the last call) and clears it. */
+/* Not from the paper: every device-side wait of the tensor-core kernels is
+ * bounded (1 s by default).  A launch that gives up sets bits in a device
+ * error word of the decoder (1: weight loader, 2: MMA issuer, 4: epilogue or
+ * step update of a forward kernel, 8/16/32: the adjoint's roles; 64: an
+ * FP32-class activation beyond the FP16 range), drains its copies and MMAs,
+ * frees its tensor memory and returns early (its outputs, and those of the
+ * launches that depend on them, are then invalid).  This call synchronises
+ * the device, returns the word in *code (0 = nothing since the last call)
+ * and clears it.  Returns DIST_E_TIMEOUT if a wait ran out (bits 1..32),
+ * else DIST_OK. */
 dist_status dist_decoder_device_error(const dist_decoder* dec, int32_t* code);
+/* Not from the paper: failure-detection settings of the tensor-core forward
+ * kernel (the march, dist_sdf_eval, colour).  wait_ns: the limit of each of
+ * its device-side waits, 1e4..1e10 ns (default 1e9).  withhold_copies = 1 is
+ * for tests of the failure path: the kernel's weight loader issues no copies,
+ * so the MMA issuer's first wait for a weight stage runs out after wait_ns;
+ * the kernel then takes its abort path (error bits 2 and 4, see
+ * dist_decoder_device_error) without faulting, and the decoder works
+ * normally again once withhold_copies is 0.  Host-side state; set it only
+ * while no call of this decoder is running. */
+dist_status dist_decoder_set_wait_limit(dist_decoder* dec, uint64_t wait_ns, int withhold_copies);
 /* Not from the paper: kernel variant of the tensor-core forward.  enable = 1
  * runs it on CTA pairs that share each MMA (2-SM tensor core instructions,
  * each SM streaming half of every weight tile); 0 (the default, faster on
@@ -275,9 +293,11 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
  * biases, packed points, gradient staging) is a built-in device array of
  * 2,359,552 bytes that every GPU which loads the library keeps until the
  * process exits.  Limits: 1 <= n <= 65536 points and 1 <= n_shapes <= 64;
- * larger sizes return DIST_E_INVALID.  Arguments and results are those of
- * dist_sdf_eval (no workspace).  The first call on a device, made with that
- * device current, looks up the array's device address (cudaGetSymbolAddress);
+ * larger sizes return DIST_E_INVALID.  Arguments, precisions (FP32 with or
+ * without grad; BF16, FP16 and FP32_TC without) and results are those of
+ * dist_sdf_eval, bit for bit (the same kernels; no workspace).  The first
+ * call on a device, made with that device current, looks up the array's
+ * device address (cudaGetSymbolAddress);
  * make that first call before any stream capture.  All calls share the one
  * array, so calls whose work overlaps on the GPU (different streams, or
  * threads without ordering) race and corrupt each other's results; a call
@@ -357,6 +377,20 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
                            const float* g_depth, const float* g_normal,
                            const float* g_sil, float* dz,
                            dist_workspace* ws, void* stream);
+
+/* One Adam step on the latent codes, the optimiser of the inverse problem
+ * (Sec. 4.2: shape from depth by optimising z through the renderer; Sec.
+ * B.4: Adam, lr 1e-2; the update is Adam as published, Kingma & Ba 2015):
+ *   m = beta1 m + (1 - beta1) dz,  v = beta2 v + (1 - beta2) dz^2,
+ *   z -= lr / (1 - beta1^t) * m / (sqrt(v / (1 - beta2^t)) + eps).
+ * z, m, v: device float [n], updated in place (m and v start at 0); dz:
+ * device float [n], the gradient (e.g. of dist_loss + dist_trace_bwd);
+ * t: the step number, from 1.  Element-wise FP32, so (z, m, v, t) fully
+ * determine the result (a checkpoint of them resumes bit for bit).
+ * Errors: DIST_E_INVALID (NULL, n < 1, t < 1, lr <= 0, beta outside [0, 1),
+ * eps <= 0), DIST_E_CUDA. */
+dist_status dist_adam_step(float* z, const float* dz, float* m, float* v, int64_t n, int t,
+                           float lr, float beta1, float beta2, float eps, void* stream);
 
 /* Gradients of the loss with respect to each camera's extrinsics (Sec. 4.2:
  * the pose optimised through the renderer with the shape fixed, from depth

@@ -35,7 +35,8 @@ EXPORTS = [
     "dist_trace_fwd", "dist_render_normals", "dist_sdf_eval", "dist_loss", "dist_trace_bwd",
     "dist_trace_bwd_camera", "dist_photo_loss", "dist_render_color",
     "dist_serve_create", "dist_serve_submit", "dist_serve_poll", "dist_serve_destroy",
-    "dist_last_error", "dist_version", "dist_sdf_eval_static",
+    "dist_last_error", "dist_version", "dist_sdf_eval_static", "dist_adam_step",
+    "dist_decoder_set_wait_limit",
 ]
 
 
@@ -96,6 +97,7 @@ def lib():
         "dist_decoder_has_bf16": (c_int, [c_void_p]),
         "dist_decoder_device_error": (c_int, [c_void_p, POINTER(ctypes.c_int32)]),
         "dist_decoder_set_tc_pair": (c_int, [c_void_p, c_int]),
+        "dist_decoder_set_wait_limit": (c_int, [c_void_p, c_uint64, c_int]),
         "dist_profile_enable": (c_int, [c_int]),
         "dist_profile_read": (c_int, [POINTER(c_double), POINTER(c_int64), POINTER(c_int64)]),
         "dist_trace_params_default": (None, [POINTER(TraceParams)]),
@@ -131,6 +133,8 @@ def lib():
         "dist_version": (c_char_p, []),
         "dist_sdf_eval_static": (c_int, [c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_int64,
                                          c_int, c_void_p, c_void_p, c_void_p]),
+        "dist_adam_step": (c_int, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int,
+                                   c_float, c_float, c_float, c_float, c_void_p]),
     }
     for name, (res, args) in sig.items():
         if not hasattr(L, name):

@@ -107,10 +107,19 @@ class Decoder:
         return bool(lib().dist_decoder_has_bf16(self.handle))
 
     def device_error(self) -> int:
-        """Synchronise and return (then clear) the tensor-core kernel's timeout word."""
+        """Synchronise and return (then clear) the tensor-core kernels' error
+        word (0: no wait ran out and no FP16 overflow since the last call)."""
         code = ctypes.c_int32(0)
-        check(lib().dist_decoder_device_error(self.handle, byref(code)), "dist_decoder_device_error")
+        st = lib().dist_decoder_device_error(self.handle, byref(code))
+        if st != _abi.DIST_E_TIMEOUT:
+            check(st, "dist_decoder_device_error")
         return int(code.value)
+
+    def set_wait_limit(self, wait_ns: int = 1_000_000_000, withhold_copies: bool = False) -> None:
+        """Limit of the tensor-core forward kernel's waits; withhold_copies
+        (tests of the failure path) makes its weight loader issue nothing."""
+        check(lib().dist_decoder_set_wait_limit(self.handle, int(wait_ns), int(bool(withhold_copies))),
+              "dist_decoder_set_wait_limit")
 
     def set_tc_pair(self, enable: bool) -> None:
         """Tensor-core forward on CTA pairs (2-SM MMAs) or one CTA per tile (default)."""

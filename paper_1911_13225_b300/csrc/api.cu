@@ -10,14 +10,15 @@ static thread_local std::string g_last_error;
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+// SM count of the device current at the first call (the library drives one
+// device per process); the static's initialisation is thread-safe.
 int num_sms() {
-  static int n = 0;
-  if (n == 0) {
-    int dev = 0;
+  static const int n = [] {
+    int dev = 0, v = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (n <= 0) n = 148;
-  }
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 148;
+  }();
   return n;
 }
 
@@ -182,6 +183,19 @@ dist_status dist_decoder_device_error(const dist_decoder* d, int32_t* code) {
   DIST_CUDA_TRY(cudaMemcpy(&v, d->tc.err, sizeof(int), cudaMemcpyDeviceToHost));
   DIST_CUDA_TRY(cudaMemset(d->tc.err, 0, sizeof(int)));
   *code = v;
+  DIST_CHECK((v & 63) == 0, DIST_E_TIMEOUT,
+             "a bounded wait of a tensor-core kernel ran out (outputs since the last check "
+             "are invalid)");
+  return DIST_OK;
+}
+
+dist_status dist_decoder_set_wait_limit(dist_decoder* d, uint64_t wait_ns, int withhold_copies) {
+  DIST_CHECK(d, DIST_E_INVALID, "dist_decoder_set_wait_limit: NULL decoder");
+  DIST_CHECK(d->tc.ok, DIST_E_UNSUPPORTED, "dist_decoder_set_wait_limit: no tensor-core path");
+  DIST_CHECK(wait_ns >= 10000ull && wait_ns <= 10000000000ull, DIST_E_INVALID,
+             "dist_decoder_set_wait_limit: wait_ns must be 1e4..1e10");
+  d->tc.wait_ns = wait_ns;
+  d->tc.withhold = withhold_copies != 0;
   return DIST_OK;
 }
 
@@ -216,6 +230,7 @@ dist_status dist_workspace_create(int64_t max_rays, int max_steps, dist_workspac
   WS_ALLOC(fbuf[1], n * sizeof(float));
   WS_ALLOC(counts, ((size_t)(max_steps + 2) * 2 + 2 * kMaxCoarseLevels) * sizeof(int));
   WS_ALLOC(rstat, n * sizeof(int));
+  WS_ALLOC(chunk, ((n + 31) / 32) * sizeof(int));
   WS_ALLOC(cams, (size_t)w->max_cams * sizeof(CamDev));
   WS_ALLOC(bfold, (size_t)2 * kMaxShapes * 512 * sizeof(float));
   WS_ALLOC(gacc, (size_t)2 * kMaxShapes * 512 * sizeof(double));

@@ -142,6 +142,8 @@ struct DecoderTC {
   float x_inv_scale[7];          // 2^-s_l
   const TCConst* cst;            // epilogue constants (device)
   int* err;                      // device error word of the bounded waits
+  unsigned long long wait_ns;    // limit of the forward kernel's waits (default 1 s)
+  int withhold;                  // tests: the forward kernel's loader issues no copies
 };
 
 // Per-CTA global scratch of the tensor-core adjoint: ReLU masks and the
@@ -172,6 +174,7 @@ struct dist_workspace {
   int* counts;        // [(max_steps + 2) * 2 + 2 kMaxCoarseLevels] list lengths
                       // per step, then per coarse-to-fine split
   int* rstat;         // per-ray status when the caller asks for none
+  int* chunk;         // (max_rays + 31) / 32 probe counts / offsets (ordered append)
   dist::CamDev* cams; // camera table (device)
   int max_cams;
   float* bfold;       // [2][kMaxShapes][512] folded latent biases

@@ -424,13 +424,10 @@ template <int WIDTH, int TM>
 cudaError_t launch_fwd(const DecoderF32& d, const RowSrc& src, const float* b0, const float* bs,
                        float* fout, cudaStream_t st) {
   const size_t sm = fwd_smem<WIDTH, TM>();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_fp32_fwd_kernel<WIDTH, TM>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // set once per process (thread-safe static initialisation)
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      mlp_fp32_fwd_kernel<WIDTH, TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (configured != cudaSuccess) return configured;
   const int grid = num_sms() * (TM >= 64 ? 1 : 4);
   mlp_fp32_fwd_kernel<WIDTH, TM><<<grid, fwd_threads<TM>(), sm, st>>>(d, src, b0, bs, fout);
   count_launch(1);
@@ -442,13 +439,9 @@ cudaError_t launch_adj(const DecoderF32& d, const float4* pp, const float4* pq, 
                        const float* b0, const float* bs, float* out4, double* g0, double* gs,
                        int acc, cudaStream_t st) {
   const size_t sm = adj_smem<WIDTH>();
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_fp32_adj_kernel<WIDTH>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      mlp_fp32_adj_kernel<WIDTH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (configured != cudaSuccess) return configured;
   prof_mlp_begin(st, 2);
   mlp_fp32_adj_kernel<WIDTH><<<num_sms(), kAdjRows * 8, sm, st>>>(d, pp, pq, count, b0, bs, out4,
                                                                     g0, gs, acc);

@@ -62,6 +62,9 @@ struct TCArgs {
   StepFuse step;
   int wide_tiles;                // > 0: launches of at most this many latency-mode tiles
                                  // are left to mlp_tc_wide_kernel
+  unsigned long long wait_ns;    // limit of every wait of the decoding loop
+  int withhold;                  // tests: the TMA producer issues no weight copies, so
+                                 // the MMA warp's first wait runs out
 };
 
 constexpr int QPT_X = 64;        // FP32-class queries per tile
@@ -121,6 +124,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  const unsigned long long wlim = a.wait_ns;
   const int rank = PAIR ? (int)cluster_rank() : 0;          // 0: issues the pair's MMAs
   const int pid = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
   const int npid = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
@@ -175,14 +179,16 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       for (int s = 0; s < NST; ++s) issued[s] = false;
       bool ok = true;
       const uint32_t full_lead = PAIR ? map_rank(smem_u32(full), 0u) : 0u;
-      for (int tile = pid; ok && tile < n_tiles; tile += npid) {
+      // (a.withhold, tests only: no copy is issued, so the MMA warp's first
+      // wait for a weight stage runs out and the CTA takes its abort path)
+      for (int tile = pid; ok && !a.withhold && tile < n_tiles; tile += npid) {
         const bool xt = tile < t1;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
           const CUtensorMap* map = xt ? &xmaps.m[g] : &maps.m[g];
           const int nkc = gemm_k(g) / BK;
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
             for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
-              if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) { ok = false; break; }
+              if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag, wlim)) { ok = false; break; }
               if (rank == 0) mbar_expect_tx(full + stage, MUL * SB);
               // FP32-class: the W_lo pass (columns K..2K-1) first, then W_hi
               const int xk = !xt ? kc : (kc < nkc ? nkc + kc : kc - nkc);
@@ -233,13 +239,13 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
             for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
               if (nh == 0 && kc < nkc && (kc & 1) == 0) {
                 const int q = kc >> 1;
-                const bool got = PAIR ? mbar_wait_cl(act_full + q, act_phase[q], abort_flag)
-                                      : mbar_wait(act_full + q, act_phase[q], abort_flag);
+                const bool got = PAIR ? mbar_wait_cl(act_full + q, act_phase[q], abort_flag, wlim)
+                                      : mbar_wait(act_full + q, act_phase[q], abort_flag, wlim);
                 if (!got) { ok = false; break; }
                 act_phase[q] ^= 1u;
                 tc_fence_after();
               }
-              if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
+              if (!mbar_wait(full + stage, phase, abort_flag, wlim)) { ok = false; break; }
               tc_fence_after();
               const uint32_t a_base = smem_u32(act + (kc < nkc ? kc : kc - nkc) * CHUNK_BYTES);
               const uint32_t b_base = smem_u32(wst + stage * SB);
@@ -298,7 +304,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
           ray[k] = valid[k] ? a.src[list].idx[j0 + r] : 0;
           if (valid[k]) load_ray(a.step.t, list, ray[k], rs[k]);
         }
-        if (!mbar_wait(step_full, sphase, abort_flag)) {
+        if (!mbar_wait(step_full, sphase, abort_flag, wlim)) {
           *abort_flag = 1;
           atomicOr(a.err, 4);
           break;
@@ -354,7 +360,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       if (valid) rowsrc_load(a.src[xt ? 1 : 0], j, p, shape);
     };
     auto wait_acc = [&](int h) -> bool {
-      if (!mbar_wait(acc_full + h, acc_phase[h], abort_flag)) return false;
+      if (!mbar_wait(acc_full + h, acc_phase[h], abort_flag, wlim)) return false;
       acc_phase[h] ^= 1u;
       tc_fence_after();
       return true;
@@ -569,13 +575,13 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         // with a fused step, head_part[0..BM) carries the previous tile's f
         // to the step warps: group 1 overwrites it once they have read it
         if (a.fuse_step && grp == 1 && tile != pid) {
-          if (!mbar_wait(step_empty, step_phase, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(step_empty, step_phase, abort_flag, wlim)) { ok = false; break; }
           step_phase ^= 1u;
         }
         head_part[(grp - 1) * BM + hr] = head;
         mbar_arrive(head_bar);
       } else {
-        if (!mbar_wait(head_bar, head_phase, abort_flag)) { ok = false; break; }
+        if (!mbar_wait(head_bar, head_phase, abort_flag, wlim)) { ok = false; break; }
 #pragma unroll
         for (int q = 0; q < FWD_GRPS - 1; ++q) head += head_part[q * BM + hr];
         const bool mine = cur_valid && (!cur_xt || part == 0);
@@ -1210,20 +1216,18 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
   // measured on B300: the CTA-pair variant is slower (973 vs 1183 TFLOP/s on
   // large launches, 92 vs 78 us for one tile), so one CTA per tile is the default
   d->tc.pair = false;
+  d->tc.wait_ns = kTimeoutNs;
+  d->tc.withhold = 0;
   d->tc.ok = true;
   return DIST_OK;
 }
 
 template <bool F16, bool PAIR, bool COLOR = false>
 cudaError_t launch_fused(const dist_decoder* dec, const TCArgs& a, cudaStream_t st) {
-  static bool configured = false;
-  if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(mlp_tc_kernel<F16, PAIR, COLOR>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         FWD_SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+  // set once per process (thread-safe static initialisation)
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      mlp_tc_kernel<F16, PAIR, COLOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, FWD_SMEM_BYTES);
+  if (configured != cudaSuccess) return configured;
   const TCMaps& maps = PAIR ? (F16 ? dec->tc.pmaps16 : dec->tc.pmaps)
                             : (F16 ? dec->tc.maps16 : dec->tc.maps);
   const TCMaps& xmaps = PAIR ? dec->tc.pxmaps : dec->tc.xmaps;
@@ -1269,6 +1273,8 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
   // with a fused step and latency-mode scratch, both kernels are launched;
   // each decides from the list lengths on the device which one decodes
   a.wide_tiles = (step && step->wide) ? tc_wide_max_tiles() : 0;
+  a.wait_ns = dec->tc.wait_ns;
+  a.withhold = dec->tc.withhold;
   cudaError_t e;
   if (dec->tc.pair)
     e = f16 ? launch_fused<true, true>(dec, a, st) : launch_fused<false, true>(dec, a, st);
@@ -1292,6 +1298,8 @@ cudaError_t mlp_tc_color(const dist_decoder* dec, const RowSrc& src, const float
   a.err = dec->tc.err;
   for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
   a.cpart = cpart;
+  a.wait_ns = dec->tc.wait_ns;
+  a.withhold = dec->tc.withhold;
   return f16 ? launch_fused<true, false, true>(dec, a, st)
              : launch_fused<false, false, true>(dec, a, st);
 }
@@ -1313,17 +1321,16 @@ cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const floa
                            float* out4, double* gacc0, double* gaccs, int accumulate,
                            void* scratch, cudaStream_t st, bool f16) {
   if (!dec->tc.ok) return cudaErrorNotSupported;
-  static bool configured = false;
-  if (!configured) {
+  static const cudaError_t configured = [] {
     cudaError_t e = cudaFuncSetAttribute(mlp_tc_adj_kernel<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          ADJ_SMEM_BYTES);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mlp_tc_adj_kernel<true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    configured = true;
-  }
+    return e;
+  }();
+  if (configured != cudaSuccess) return configured;
   TCAdjArgs a;
   a.K = dec->tc.cst;
   a.bfold0 = bfold0;

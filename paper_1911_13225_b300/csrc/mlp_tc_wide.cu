@@ -484,15 +484,14 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
 // Clusters of WC CTAs that can be resident at once (at most WT_MAX): the
 // largest tile count the latency mode takes.
 int tc_wide_max_tiles() {
-  static int n = -1;
-  if (n < 0) {
-    n = 0;
+  // computed once per process (thread-safe static initialisation)
+  static const int n = [] {
     if (cudaFuncSetAttribute(mlp_tc_wide_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              W_SMEM) != cudaSuccess ||
         cudaFuncSetAttribute(mlp_tc_wide_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              W_SMEM) != cudaSuccess) {
       (void)cudaGetLastError();
-      return n;
+      return 0;
     }
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(WC * WT_MAX);
@@ -510,8 +509,8 @@ int tc_wide_max_tiles() {
       (void)cudaGetLastError();
       c = 0;
     }
-    n = c < WT_MAX ? c : WT_MAX;
-  }
+    return c < WT_MAX ? c : WT_MAX;
+  }();
   return n;
 }
 

@@ -61,9 +61,10 @@ extern "C" dist_status dist_sdf_eval_static(const dist_decoder* dec, const float
              "dist_sdf_eval_static: n must be 1..65536 (size of the built-in scratch)");
   DIST_CHECK(n_shapes >= 1 && n_shapes <= kStaticMaxShapes, DIST_E_INVALID,
              "dist_sdf_eval_static: n_shapes must be 1..64 (size of the built-in scratch)");
-  DIST_CHECK(precision == DIST_PREC_FP32 || (is_tc(precision) && !grad),
-             DIST_E_INVALID, "dist_sdf_eval_static: bad precision (BF16/FP16 have no gradient)");
-  DIST_CHECK(!is_tc(precision) || dec->tc.ok, DIST_E_UNSUPPORTED,
+  DIST_CHECK(precision == DIST_PREC_FP32 || (valid_precision(precision) && !grad),
+             DIST_E_INVALID,
+             "dist_sdf_eval_static: bad precision (the tensor-core kernels have no gradient)");
+  DIST_CHECK(precision == DIST_PREC_FP32 || dec->tc.ok, DIST_E_UNSUPPORTED,
              "BF16 tensor-core MLP covers only the DeepSDF decoder shape");
   unsigned char* base = nullptr;
   dist_status s = scratch_on_current_device(&base);
@@ -85,6 +86,8 @@ extern "C" dist_status dist_sdf_eval_static(const dist_decoder* dec, const float
   src.pts = pts4;
   if (is_tc(precision)) {
     DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, f, st, precision == DIST_PREC_FP16));
+  } else if (precision == DIST_PREC_FP32_TC) {
+    DIST_CUDA_TRY(mlp_tcx_forward(dec, src, b0, bs, f, st));
   } else if (!grad) {
     DIST_CUDA_TRY(mlp_fp32_forward(d, src, b0, bs, f, st));
   } else {

@@ -93,16 +93,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait for the phase with `parity` to complete; false on timeout or
-// when another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait for the phase with `parity` to complete; false after
+// `limit_ns` or when another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit_ns = kTimeoutNs) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 63) == 0) {
       if (*abort_flag) return false;
-      if (globaltimer() - t0 > kTimeoutNs) return false;
+      if (globaltimer() - t0 > limit_ns) return false;
     }
   }
 }
@@ -226,14 +227,15 @@ __device__ __forceinline__ bool mbar_try_wait_acq_cluster(uint64_t* bar, uint32_
 }
 // Bounded wait with cluster-scope acquire (barriers other CTAs arrive on).
 __device__ __forceinline__ bool mbar_wait_cl(uint64_t* bar, uint32_t parity,
-                                             volatile int* abort_flag) {
+                                             volatile int* abort_flag,
+                                             unsigned long long limit_ns = kTimeoutNs) {
   if (mbar_try_wait_acq_cluster(bar, parity)) return true;
   const unsigned long long t0 = globaltimer();
   for (uint32_t it = 1;; ++it) {
     if (mbar_try_wait_acq_cluster(bar, parity)) return true;
     if ((it & 63) == 0) {
       if (*abort_flag) return false;
-      if (globaltimer() - t0 > kTimeoutNs) return false;
+      if (globaltimer() - t0 > limit_ns) return false;
     }
   }
 }

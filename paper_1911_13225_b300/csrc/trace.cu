@@ -389,7 +389,57 @@ struct ProbeArgs {
   float4* pq;
   int* pix;
   int* count;
+  // Ordered append (pixel order, so the backward pass sums its probes in the
+  // same grouping on every run): null = atomic append in arrival order; else
+  // phase 0 writes each 32-pixel chunk's probe count to chunk[base / 32],
+  // chunk_scan_kernel turns the counts into offsets, and phase 1 writes the
+  // probes at them.
+  int* chunk;
+  int phase;
 };
+
+// Slot of the first of this lane's k probes for the 32-pixel chunk at
+// `base` (all lanes of the warp call it), or -1 when nothing is written
+// (the counting phase of an ordered append).
+__device__ __forceinline__ int probe_slot(const ProbeArgs& a, long long base, int k) {
+  if (!a.chunk) return warp_append_n(k, a.count);
+  int incl = k;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane_id() >= o) incl += y;
+  }
+  if (a.phase == 0) {
+    if (lane_id() == 31) a.chunk[base >> 5] = incl;
+    return -1;
+  }
+  return a.chunk[base >> 5] + incl - k;
+}
+
+// In-place exclusive scan of the per-chunk probe counts of an ordered append
+// (one block); *total = their sum, the probe count the adjoint reads.
+__global__ void __launch_bounds__(1024) chunk_scan_kernel(int* c, long long n, int* total) {
+  __shared__ int part[1024];
+  const long long per = (n + blockDim.x - 1) / blockDim.x;
+  const long long lo = min(n, per * threadIdx.x), hi = min(n, lo + per);
+  int s = 0;
+  for (long long i = lo; i < hi; ++i) s += c[i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < (int)blockDim.x; o <<= 1) {
+    const int v = threadIdx.x >= (unsigned)o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;      // exclusive prefix of this thread's range
+  for (long long i = lo; i < hi; ++i) {
+    const int v = c[i];
+    c[i] = run;
+    run += v;
+  }
+  if (threadIdx.x == blockDim.x - 1) *total = part[threadIdx.x];
+}
 
 __device__ __forceinline__ float4 ray_point(const CamDev& c, const float4& v, float d, int shape) {
   return make_float4(fmaf(d, v.x, c.c[0]), fmaf(d, v.y, c.c[1]), fmaf(d, v.z, c.c[2]),
@@ -424,8 +474,8 @@ __global__ void probes_fd_kernel(ProbeArgs a, float delta, const float* g_normal
     bool take = i < a.n_pix && a.o.mask[i];
     if (take && g_normal)
       take = g_normal[3 * i] != 0.f || g_normal[3 * i + 1] != 0.f || g_normal[3 * i + 2] != 0.f;
-    const int slot = warp_append_n(take ? 6 : 0, a.count);
-    if (take) {
+    const int slot = probe_slot(a, base, take ? 6 : 0);
+    if (take && slot >= 0) {
       const CamDev& c = a.cams[find_cam(a.cams, a.n_cams, i)];
       const float4 p = ray_point(c, a.dir[i], a.o.d_hit[i], c.shape);
       for (int e = 0; e < 6; ++e) {
@@ -491,8 +541,8 @@ __global__ void probes_bwd_kernel(ProbeArgs a, const float* g_depth, const float
       const float fm0 = a.o.f_min[i * a.K];
       if (gs != 0.f && !isnan(a.o.d_min[i * a.K]) && fm0 != 0.f) ns = 1;
     }
-    int slot = warp_append_n(nd + ns, a.count);
-    if (nd + ns > 0) {
+    int slot = probe_slot(a, base, nd + ns);
+    if (nd + ns > 0 && slot >= 0) {
       const CamDev& c = a.cams[a.cam_fixed >= 0 ? a.cam_fixed : find_cam(a.cams, a.n_cams, i)];
       const float4 v = a.dir[i];
       if (nd > 0 && !paper) {
@@ -537,8 +587,8 @@ __global__ void probes_cam_kernel(ProbeArgs a, const float* g_depth, const float
       nd = g_depth && a.o.mask[i] && g_depth[i] != 0.f ? 1 : 0;
       ns = g_sil && g_sil[i] != 0.f && !isnan(a.o.d_min[i * a.K]) ? 1 : 0;
     }
-    int slot = warp_append_n(nd + ns, a.count);
-    if (nd + ns > 0) {
+    int slot = probe_slot(a, base, nd + ns);
+    if (nd + ns > 0 && slot >= 0) {
       const CamDev& c = a.cams[find_cam(a.cams, a.n_cams, i)];
       const float4 v = a.dir[i];
       if (nd) {
@@ -1146,7 +1196,27 @@ ProbeArgs make_probe_args(const dist_trace_params* p, const dist_trace_out* o, d
   a.K = p->k_min; a.o = *o;
   a.pp = ws->probe_p + offset; a.pq = ws->probe_q + offset; a.pix = ws->probe_pix + offset;
   a.count = ws->probe_count + count_slot;
+  a.chunk = nullptr;
+  a.phase = 0;
   return a;
+}
+
+// An ordered append of probes: the kernel's counting phase, the scan of the
+// chunk counts (in ws->chunk) and the writing phase.
+template <class Launch>
+cudaError_t ordered_probes(ProbeArgs a, dist_workspace* ws, long long n_pix, cudaStream_t st,
+                           Launch launch) {
+  a.chunk = ws->chunk;
+  a.phase = 0;
+  launch(a);
+  count_launch(1);
+  const long long n_chunks = (n_pix + 31) / 32;
+  chunk_scan_kernel<<<1, 1024, 0, st>>>(a.chunk, n_chunks, a.count);
+  count_launch(1);
+  a.phase = 1;
+  launch(a);
+  count_launch(1);
+  return cudaGetLastError();
 }
 
 // The decoder adjoint in the trace's precision: tcgen05 (BF16 / FP16
@@ -1277,6 +1347,7 @@ cudaError_t pool_probes_depth(const RayPool& P, int cam, long long pix0, long lo
   ProbeArgs a;
   a.cams = P.cams; a.st = P.st; a.dir = P.dir; a.n_pix = n; a.pix0 = pix0; a.cam_fixed = cam;
   a.n_cams = 0; a.K = P.K; a.o = P.o; a.pp = pp; a.pq = pq; a.pix = pix; a.count = count;
+  a.chunk = nullptr; a.phase = 0;
   probes_bwd_kernel<<<grid_for(n, 256), 256, 0, st>>>(a, g_depth, nullptr, 0, P.alpha);
   count_launch(1);
   return cudaGetLastError();
@@ -1490,9 +1561,11 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
   if (g_depth) {
     // depth probes (<= k_min per pixel) in [0, 3 max_rays), in the trace's precision
     ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, 0, 0);
-    probes_bwd_kernel<<<g, 256, 0, st>>>(a, g_depth, nullptr, p->grad_mode == DIST_GRAD_PAPER,
-                                         p->alpha);
-    DIST_LAUNCH_CHECK();
+    const int paper = p->grad_mode == DIST_GRAD_PAPER;
+    const float alpha = p->alpha;
+    DIST_CUDA_TRY(ordered_probes(a, ws, n_pix, st, [&](const ProbeArgs& b) {
+      probes_bwd_kernel<<<g, 256, 0, st>>>(b, g_depth, nullptr, paper, alpha);
+    }));
     DIST_CUDA_TRY(adjoint(dec, p, ws, ws->probe_p, ws->probe_q, ws->probe_count, b0, bs, nullptr,
                           G0, Gs, 1, st));
   }
@@ -1502,8 +1575,10 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
     // 16-bit rounding errors to average out, so the FP32 adjoint
     const long long off = 3 * (long long)ws->max_rays;
     ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, off, 2);
-    probes_bwd_kernel<<<g, 256, 0, st>>>(a, nullptr, g_sil, 0, p->alpha);
-    DIST_LAUNCH_CHECK();
+    const float alpha = p->alpha;
+    DIST_CUDA_TRY(ordered_probes(a, ws, n_pix, st, [&](const ProbeArgs& b) {
+      probes_bwd_kernel<<<g, 256, 0, st>>>(b, nullptr, g_sil, 0, alpha);
+    }));
     DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p + off, ws->probe_q + off, ws->probe_count + 2,
                                    b0, bs, nullptr, G0, Gs, 1, st));
   }
@@ -1512,8 +1587,10 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
     // FP32 adjoint whatever the march precision
     const long long off = 4 * (long long)ws->max_rays;
     ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, off, 1);
-    probes_fd_kernel<<<g, 256, 0, st>>>(a, p->normal_delta, g_normal);
-    DIST_LAUNCH_CHECK();
+    const float delta = p->normal_delta;
+    DIST_CUDA_TRY(ordered_probes(a, ws, n_pix, st, [&](const ProbeArgs& b) {
+      probes_fd_kernel<<<g, 256, 0, st>>>(b, delta, g_normal);
+    }));
     RowSrc src{};
     src.count = ws->probe_count + 1;
     src.pts = ws->probe_p + off;
