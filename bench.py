@@ -537,6 +537,10 @@ def inverse_rate(api, dec, spec, dev, steps=3):
     loss0 = float(prob.step(stream))
     torch.cuda.synchronize()
     prob.res.queries.zero_()
+    from ctypes import byref, c_double, c_int64
+    from paper_1911_13225_b300 import _abi
+    L = _abi.lib()
+    L.dist_profile_enable(1)
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
            for _ in range(steps)]
     for i in range(steps):
@@ -544,13 +548,24 @@ def inverse_rate(api, dec, spec, dev, steps=3):
         prob.step(stream)
         evs[i][1].record(stream)
     torch.cuda.synchronize()
+    L.dist_profile_enable(0)
+    ms_arr, cnt_arr, all_l = (c_double * 3)(), (c_int64 * 3)(), c_int64()
+    _abi.check(L.dist_profile_read(ms_arr, cnt_arr, byref(all_l)), "dist_profile_read")
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     q = prob.res.queries.cpu().numpy().astype(np.float64) / steps
     assert dec.device_error() == 0
+    brk = {"march_decoder_s": (ms_arr[0] + ms_arr[1]) / steps * 1e-3,
+           "adjoint_s": ms_arr[2] / steps * 1e-3,
+           "rest_s": ms * 1e-3 - (ms_arr[0] + ms_arr[1] + ms_arr[2]) / steps * 1e-3,
+           "note": "adjoint: the BF16 depth adjoint plus the FP32 adjoint of the six "
+                   "central-difference probes per hit (the normal term's latent gradient "
+                   "subtracts Jacobians 2e-3 apart, so it runs in FP32); rest: mostly the "
+                   "FP32 queries of those probes (normals and their coefficients)"}
     return {"value": n / (ms * 1e-3), "unit": "rays/s", "s_per_adam_step": ms * 1e-3,
             "rays_per_step": n, "steps": steps,
             "march_queries_per_step": {"lowp": float(q[0]), "fp32": float(q[1])},
             "loss_step1": loss0, "loss_last": float(prob.loss.item()),
+            "breakdown": brk,
             "note": "32 shapes x 8 views x 224x224 per Adam step, one call per entry point "
                     "(dist_trace_fwd with central-difference normals, dist_loss, "
                     "dist_trace_bwd, dist_adam_step); the paper's Tab. 1 unit is the time "

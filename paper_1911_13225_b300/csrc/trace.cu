@@ -1231,6 +1231,17 @@ cudaError_t adjoint(const dist_decoder* dec, const dist_trace_params* p, dist_wo
   return mlp_fp32_adjoint(dec->f32, pp, pq, count, b0, bs, out4, G0, Gs, acc, st);
 }
 
+// Queries of the central-difference probes (normals and their gradient):
+// differences of nearby values, so FP32-class precision whatever the march's:
+// the FP32_TC tensor-core kernel (two-term FP16 split; its ~2e-6 error in f
+// is mostly a common offset that cancels in the differences) when the trace
+// runs its FP32-class queries there, else the FP32 CUDA-core kernel.
+cudaError_t fd_forward(const dist_decoder* dec, const dist_trace_params* p, const RowSrc& src,
+                       const float* b0, const float* bs, float* out, cudaStream_t st) {
+  if (fp32_on_tc(*p) && dec->tc.ok) return mlp_tcx_forward(dec, src, b0, bs, out, st);
+  return mlp_fp32_forward(dec->f32, src, b0, bs, out, st);
+}
+
 dist_status normals_impl(const dist_decoder* dec, const dist_trace_params* p,
                          const dist_trace_out* o, float* normal, dist_workspace* ws,
                          int n_cams, long long n_pix, cudaStream_t st) {
@@ -1255,7 +1266,7 @@ dist_status normals_impl(const dist_decoder* dec, const dist_trace_params* p,
     RowSrc src{};
     src.count = ws->probe_count;
     src.pts = ws->probe_p;
-    DIST_CUDA_TRY(mlp_fp32_forward(dec->f32, src, b0, bs, ws->probe_out, st));
+    DIST_CUDA_TRY(fd_forward(dec, p, src, b0, bs, ws->probe_out, st));
     normals_from_fd_kernel<<<g, 256, 0, st>>>(ws->probe_out, ws->probe_pix, ws->probe_count,
                                                p->normal_delta, normal);
     DIST_LAUNCH_CHECK();
@@ -1583,8 +1594,8 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
                                    b0, bs, nullptr, G0, Gs, 1, st));
   }
   if (g_normal) {
-    // central-difference normals difference nearby values: FP32 queries and
-    // FP32 adjoint whatever the march precision
+    // central-difference normals difference nearby values: FP32-class
+    // queries (fd_forward) and the FP32 adjoint whatever the march precision
     const long long off = 4 * (long long)ws->max_rays;
     ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, off, 1);
     const float delta = p->normal_delta;
@@ -1595,7 +1606,7 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
     src.count = ws->probe_count + 1;
     src.pts = ws->probe_p + off;
     float* f6 = ws->probe_out + off * 4;
-    DIST_CUDA_TRY(mlp_fp32_forward(d, src, b0, bs, f6, st));
+    DIST_CUDA_TRY(fd_forward(dec, p, src, b0, bs, f6, st));
     fd_coef_kernel<<<g, 256, 0, st>>>(f6, ws->probe_pix + off, ws->probe_count + 1,
                                       p->normal_delta, g_normal, ws->probe_q + off);
     DIST_LAUNCH_CHECK();

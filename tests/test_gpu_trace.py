@@ -109,11 +109,16 @@ def test_multi_camera_multi_shape_topk(cuda_device):
     assert np.max(np.abs(fmin[ent][have] - orc["topk_s"][ent][have])) < DEPTH_TOL
 
 
-@pytest.mark.parametrize("delta", [0.0, 1e-3])
-def test_normals_at_gpu_hits(cuda_device, delta):
+@pytest.mark.parametrize("delta,precision", [(0.0, "fp32"), (1e-3, "fp32"), (1e-3, "bf16"),
+                                             (1e-3, "fp32_tc")])
+def test_normals_at_gpu_hits(cuda_device, delta, precision):
+    """Normals at the GPU's hits against the oracle's at the same points:
+    analytic (FP32 adjoint) or the paper's central differences with step
+    delta, whose queries are FP32 (CUDA cores) or FP32-class (tensor cores,
+    after a tensor-core march)."""
     cam = synth.look_at_camera((0.4, 0.7, 2.3), 40, 40)
     spec = synth.DEEPSDF_SPEC
-    res, orc, sdf = _run(cuda_device, spec, [cam], normals=True, delta=delta)
+    res, orc, sdf = _run(cuda_device, spec, [cam], normals=True, delta=delta, precision=precision)
     m = to_np(res.mask).astype(bool)
     c, v = orc["c"], orc["v"]
     p = c[m] + to_np(res.d_hit)[m].astype(np.float64)[:, None] * v[m]
