@@ -232,6 +232,7 @@ def run_ours(args, rank, world, local_rank):
     _abi.check(L.dist_profile_read(ms_arr, cnt_arr, byref(all_launches)), "dist_profile_read")
     queries = step.res.queries.cpu().numpy().astype(np.int64)
     hits = int(step.res.mask.sum().item())
+    accuracy = accuracy_vs_oracle(step.res, precision)
 
     # end to end through the C ABI: pinned host inputs in, loss and dz out
     z_host = torch.from_numpy(Z).pin_memory()
@@ -341,6 +342,12 @@ def run_ours(args, rank, world, local_rank):
         "queries_per_step": {"lowp": float(queries[0]) / args.steps,
                              "fp32": float(queries[1]) / args.steps},
         "hits": hits,
+        "accuracy_vs_oracle": accuracy,
+        "fp32_class_queries": ({"tc": "tensor cores, every operand a sum of two FP16 numbers "
+                                      "(FP32-class; the accumulator truncates: f within 5e-6 "
+                                      "of FP64)",
+                                "simt": "FP32 CUDA cores"}[args.refine_engine]
+                               if precision in ("bf16", "fp16") else None),
         "e2e": {"value": rays * world / e2e_s, "unit": "rays/s", "h2d_bytes_per_step": bi,
                 "d2h_bytes_per_step": bo,
                 "note": "host-timed per step (pinned copies in, loss and dz out, stream "
@@ -371,6 +378,41 @@ def run_ours(args, rank, world, local_rank):
     return line
 
 
+# ------------------------------------------------- accuracy against the oracle
+
+GOLDEN = os.path.join(ROOT, "tests", "golden", "full_masks.npz")
+
+
+def accuracy_vs_oracle(res, precision):
+    """The benchmark view's hit mask and depth against the FP64 oracle's,
+    stored by tests/golden/make_full_masks.py (an oracle-only script): mask
+    mismatches in all and outside the excluded rays (16-bit march: silhouette
+    rays at the 1e-3 |SDF| margin; FP32: threshold-ambiguous rays), and the
+    depth error on the hits both share outside them."""
+    if SIZE != 512 or not os.path.exists(GOLDEN):
+        return None
+    with np.load(GOLDEN) as g:
+        n = int(g["b512/n"])
+        gm = np.unpackbits(g["b512/mask"])[:n].astype(bool)
+        ex = np.unpackbits(g["b512/sil" if precision != "fp32" else "b512/amb32"])[:n].astype(bool)
+        if "b512/depth_hits" not in g.files:
+            return None
+        gd = np.full(n, np.inf)
+        gd[gm] = g["b512/depth_hits"].astype(np.float64)
+    m = res.mask.cpu().numpy().astype(bool)
+    d = res.depth.cpu().numpy().astype(np.float64)
+    both = m & gm & ~ex
+    err = np.abs(d[both] - gd[both])
+    return {"mask_mismatches": int((m != gm).sum()),
+            "mask_mismatches_outside_excluded": int(((m != gm) & ~ex).sum()),
+            "excluded": "silhouette rays at the 1e-3 |SDF| margin" if precision != "fp32"
+                        else "threshold-ambiguous rays (FP32 vs FP64 branch)",
+            "excluded_frac": float(ex.mean()),
+            "depth_err_q50": float(np.quantile(err, 0.5)), "depth_err_q99": float(np.quantile(err, 0.99)),
+            "depth_err_max": float(err.max()), "hits_compared": int(both.sum()),
+            "reference": "FP64 oracle, stored by tests/golden/make_full_masks.py"}
+
+
 # ------------------------------------------------- FP32 trace, large launches
 
 def variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals):
@@ -392,7 +434,7 @@ def variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals):
     torch.cuda.synchronize()
     ms = sum(a.elapsed_time(b) for a, b in evs) / steps
     q = step.res.queries.cpu().numpy().astype(np.float64) / steps
-    return ms, q, int(step.res.mask.sum().item())
+    return ms, q, int(step.res.mask.sum().item()), accuracy_vs_oracle(step.res, p2.precision)
 
 
 def coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps, normals):
@@ -401,7 +443,7 @@ def coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps,
     three iterations), timed like the main line."""
     import dataclasses
     p2 = dataclasses.replace(params, coarse_levels=2, coarse_every=3)
-    ms, q, hits = variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals)
+    ms, q, hits, _ = variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals)
     return {"value": SIZE * SIZE / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
             "coarse_levels": 2, "coarse_every": 3,
             "queries_per_step": {"lowp": float(q[0]), "fp32": float(q[1])},
@@ -418,11 +460,11 @@ def fp16_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps, normals):
     import dataclasses
     p2 = dataclasses.replace(params, precision="fp16", eps_bf16=2e-4, refine_steps=0,
                              coarse_levels=0)
-    ms, q, hits = variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals)
+    ms, q, hits, acc = variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals)
     return {"value": SIZE * SIZE / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
             "dtype": "fp16", "eps_lo": 2e-4, "refine_steps": 0,
             "queries_per_step": {"lowp": float(q[0]), "fp32": float(q[1])},
-            "hits": hits,
+            "hits": hits, "accuracy_vs_oracle": acc,
             "note": "FP16 GEMM operands (same tensor rate as BF16), FP32-class convergence after "
                     "the hand-over; on this view depth vs the FP32 trace q99 7.8e-5 (BF16 "
                     "default: 1.2e-4)"}
@@ -445,7 +487,8 @@ def fp32_trace_rate(api, dec, cam, z, tgt, stream, steps=3):
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
     return {"value": SIZE * SIZE / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
-            "steps": steps, "note": "precision fp32: mlp_fp32_fwd_kernel + FP32 adjoint"}
+            "steps": steps, "note": "precision fp32: mlp_fp32_fwd_kernel + FP32 adjoint",
+            "accuracy_vs_oracle": accuracy_vs_oracle(step.res, "fp32")}
 
 
 def large_launch_rate(api, dec, z, precision, peak, n=262144 * 2, reps=5):

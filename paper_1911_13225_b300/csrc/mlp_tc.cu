@@ -69,6 +69,14 @@ struct TCArgs {
 
 constexpr int QPT_X = 64;        // FP32-class queries per tile
 
+// Tile of round r for CTA (pair) pid in a launch of npid: serpentine order.
+// The FP32-class tiles (twice a 16-bit tile's work) come first in the tile
+// list, so odd rounds run backwards and hand their tiles to the CTAs that took
+// the cheaper tiles of the round before.  Increasing in r for a fixed pid.
+__device__ __forceinline__ int tile_of(int r, int pid, int npid) {
+  return r * npid + ((r & 1) ? npid - 1 - pid : pid);
+}
+
 
 // Forward pipeline.  A tile is one of the two kinds; the FP32-class tiles
 // come first in tile order (they take twice as long).  A tile's K loop runs
@@ -181,7 +189,8 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       const uint32_t full_lead = PAIR ? map_rank(smem_u32(full), 0u) : 0u;
       // (a.withhold, tests only: no copy is issued, so the MMA warp's first
       // wait for a weight stage runs out and the CTA takes its abort path)
-      for (int tile = pid; ok && !a.withhold && tile < n_tiles; tile += npid) {
+      for (int r = 0, tile = pid; ok && !a.withhold && tile < n_tiles;
+           tile = tile_of(++r, pid, npid)) {
         const bool xt = tile < t1;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
           const CUtensorMap* map = xt ? &xmaps.m[g] : &maps.m[g];
@@ -230,7 +239,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         if (PAIR) mma_commit_pair(bar);
         else mma_commit(bar);
       };
-      for (int tile = pid; ok && tile < n_tiles; tile += npid) {
+      for (int r = 0, tile = pid; ok && tile < n_tiles; tile = tile_of(++r, pid, npid)) {
         const bool xt = tile < t1;
         const uint32_t idesc = instr_desc_m(xt || F16, MUL * BM);
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
@@ -287,7 +296,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       constexpr int RPT = BM / SW;   // rows per step thread
       const int s = threadIdx.x - (2 + FWD_EPI) * 32;
       uint32_t sphase = 0;
-      for (int t = pid; t < n_tiles; t += npid) {
+      for (int r = 0, t = pid; t < n_tiles; t = tile_of(++r, pid, npid)) {
         const bool xt = t < t1;
         const int list = xt ? 1 : 0;
         const int j0 = xt ? (t * MUL + rank) * QPT_X : ((t - t1) * MUL + rank) * BM;
@@ -462,6 +471,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
 
     uint32_t step_phase = 0;   // column group 1: step_empty parity
     int tile = pid;
+    int rnd = 0;
     load_rows(tile);
     for (int q = 0; q < 4; ++q) {
       uint32_t h[16];
@@ -469,9 +479,9 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       put(q, h);
       release(q);
     }
-    for (; tile < n_tiles; tile += npid) {
+    for (; tile < n_tiles; tile = tile_of(++rnd, pid, npid)) {
       const float* bf4 = a.bfold4 + (size_t)shape * 512;
-      const int next = tile + npid;
+      const int next = tile_of(rnd + 1, pid, npid);
       const bool has_next = next < n_tiles;
       for (int g = 0; g < NUM_GEMM - 1; ++g) {
         if (!wait_acc(0)) { ok = false; break; }
@@ -574,7 +584,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       if (grp > 0) {
         // with a fused step, head_part[0..BM) carries the previous tile's f
         // to the step warps: group 1 overwrites it once they have read it
-        if (a.fuse_step && grp == 1 && tile != pid) {
+        if (a.fuse_step && grp == 1 && rnd > 0) {
           if (!mbar_wait(step_empty, step_phase, abort_flag, wlim)) { ok = false; break; }
           step_phase ^= 1u;
         }

@@ -1,7 +1,8 @@
 """Writes tests/golden/full_masks.npz from the FP64 oracle alone (no CUDA):
 for the 512 x 512 benchmark view (DeepSDF decoder seed 0, latent 0 of seed
 0, first of five seeded viewpoints) and the five 256 x 256 views of seed 0,
-every pixel's oracle hit mask and two exclusion sets, bit-packed:
+every pixel's oracle hit mask and two exclusion sets, bit-packed, and the
+oracle's depth at its hits (float32, ``depth_hits``):
 
 * ``sil``: silhouette rays at the 1e-3 |SDF| margin (tests/helpers.
   silhouette_rays: the outcome changes when f is shifted by -/+1e-3, a ray
@@ -49,6 +50,8 @@ def main():
         out[f"{tag}/n"] = np.int64(orc["mask"].size)
         for k, v in (("mask", orc["mask"]), ("sil", sil), ("amb32", amb32)):
             out[f"{tag}/{k}"] = np.packbits(v.astype(bool))
+        # the oracle's depth at its hits (pixel order), rounded to float32
+        out[f"{tag}/depth_hits"] = orc["depth"][orc["mask"]].astype(np.float32)
         print(tag, orc["mask"].size, int(orc["mask"].sum()), float(sil.mean()), float(amb32.mean()))
     np.savez_compressed(os.path.join(ROOT, "tests", "golden", "full_masks.npz"), **out)
 

@@ -6,7 +6,9 @@ full_masks.npz, written by tests/golden/make_full_masks.py from the oracle
 alone.  A 16-bit march (BF16 or FP16 operands, FP32-class convergence) must
 give the oracle's hit/miss on every ray outside the silhouette rays at the
 1e-3 |SDF| margin; the FP32 trace on every ray outside its threshold-
-ambiguous set.  Zero mismatches are allowed there."""
+ambiguous set.  Zero mismatches are allowed there.  On the hits both share
+outside those sets, the depth is within the stated bars (1e-5 FP32, 2e-3
+16-bit) of the oracle's stored depth."""
 
 import os
 
@@ -25,7 +27,10 @@ GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_
 def _golden(tag):
     with np.load(GOLD) as g:
         n = int(g[f"{tag}/n"])
-        return {k: np.unpackbits(g[f"{tag}/{k}"])[:n].astype(bool) for k in ("mask", "sil", "amb32")}
+        out = {k: np.unpackbits(g[f"{tag}/{k}"])[:n].astype(bool) for k in ("mask", "sil", "amb32")}
+        out["depth"] = np.full(n, np.inf)
+        out["depth"][out["mask"]] = g[f"{tag}/depth_hits"].astype(np.float64)
+        return out
 
 
 def _view(tag):
@@ -58,3 +63,9 @@ def test_whole_image_hit_masks(cuda_device, tag, precision):
     outside = np.nonzero(diff & ~excluded)[0]
     assert outside.size == 0, (outside[:10], int(diff.sum()))
     assert diff.sum() < 1e-3 * mask.size
+    # depth on every shared hit outside the excluded rays: 1e-5 (FP32) or
+    # 2e-3 (16-bit march; its FP32-class convergence lands far closer)
+    both = mask & g["mask"] & ~excluded
+    err = np.abs(to_np(res.depth).astype(np.float64)[both] - g["depth"][both])
+    assert both.sum() > 0.9 * (g["mask"] & ~excluded).sum()
+    assert err.max() < (1e-5 if precision == "fp32" else 2e-3), float(err.max())
