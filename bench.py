@@ -31,7 +31,7 @@ FLOP_PER_QUERY = 3_146_752          # 8x512 decoder, latent folded into per-shap
 # dram__bytes_read.sum + dram__bytes_write.sum of one mlp_tc_kernel launch (ncu, the
 # first march launch of a 256x256 trace: 65,536 rows); the weights dominate it, so it
 # is not scaled by rows.  Taken on the current kernel; None once the kernel changes.
-TC_TRAFFIC_BYTES = 6298368 + 3072
+TC_TRAFFIC_BYTES = 6298112 + 3072
 TC_TRAFFIC_NOTE = ("ncu dram read+write, first march launch of a 256x256 BF16 trace "
                    "(65,536 rows; weights once + ray state read and written by the step "
                    "warps), not scaled")

@@ -4,6 +4,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <string>
@@ -36,6 +37,17 @@ void prof_mlp_end(cudaStream_t st);
     ::dist::count_launch(1);                                                  \
     DIST_CUDA_TRY(cudaGetLastError());                                        \
   } while (0)
+
+// NVTX range over a scope: each entry point and march step shows up by name
+// in Nsight Systems and under `ncu --nvtx`; without a tool attached the
+// push/pop are no-ops (NVTX v3 is header-only, nothing to link).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define DIST_NVTX(name) ::dist::NvtxRange dist_nvtx_range_(name)
 
 #define DIST_CHECK(cond, code, msg)                                           \
   do {                                                                        \

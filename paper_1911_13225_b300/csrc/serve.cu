@@ -327,6 +327,7 @@ struct dist_server {
         have_work = run || !pending.empty();
       }
       if (!have_work) continue;
+      DIST_NVTX("serve iteration");
       bool any = false;
       dist_status e = admit(&any);
       bool run = false;

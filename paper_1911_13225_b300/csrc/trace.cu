@@ -1397,6 +1397,7 @@ extern "C" {
 dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes,
                            const dist_camera* cams, int n_cams, const dist_trace_params* p,
                            const dist_trace_out* o, dist_workspace* ws, void* stream) {
+  DIST_NVTX("dist_trace_fwd");
   Prepared pr;
   dist_status s = validate_and_upload(dec, z, n_shapes, cams, n_cams, p, o, ws, stream, &pr);
   if (s != DIST_OK) return s;
@@ -1453,6 +1454,7 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
     const int* in0 = cA;
     const int* in1 = cB;
     for (int s = 0; s < M; ++s) {
+      DIST_NVTX("march step");
       if (split_due(s)) DIST_CUDA_TRY(split(0, in0, in1));
       RowSrc sx = src;
       src.count = in0;
@@ -1510,6 +1512,7 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
   const int* in0 = zero;
   const int* in1 = cB;
   for (int t = 0; t < M; ++t) {
+    DIST_NVTX("march step (FP32 list)");
     if (split_due(t)) DIST_CUDA_TRY(split(0, in0, in1));
     src.count = in1;
     src.idx = ws->act[par][1];
@@ -1539,6 +1542,7 @@ dist_status dist_render_normals(const dist_decoder* dec, const float* z, int n_s
                                 const dist_camera* cams, int n_cams, const dist_trace_params* p,
                                 const dist_trace_out* fwd, float* normal, dist_workspace* ws,
                                 void* stream) {
+  DIST_NVTX("dist_render_normals");
   DIST_CHECK(normal, DIST_E_INVALID, "dist_render_normals: NULL normal");
   Prepared pr;
   dist_status s = validate_and_upload(dec, z, n_shapes, cams, n_cams, p, fwd, ws, stream, &pr);
@@ -1551,6 +1555,7 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
                            const dist_trace_out* fwd, const float* g_depth,
                            const float* g_normal, const float* g_sil, float* dz,
                            dist_workspace* ws, void* stream) {
+  DIST_NVTX("dist_trace_bwd");
   DIST_CHECK(dz, DIST_E_INVALID, "dist_trace_bwd: NULL dz");
   DIST_CHECK(!g_normal || p == nullptr || p->normal_delta > 0.f, DIST_E_INVALID,
              "dist_trace_bwd: a normal gradient needs normal_delta > 0 (the analytic normal of a "
@@ -1624,6 +1629,7 @@ dist_status dist_trace_bwd_camera(const dist_decoder* dec, const float* z, int n
                                   const dist_trace_out* fwd, const float* g_depth,
                                   const float* g_sil, float* dcam, dist_workspace* ws,
                                   void* stream) {
+  DIST_NVTX("dist_trace_bwd_camera");
   DIST_CHECK(dcam, DIST_E_INVALID, "dist_trace_bwd_camera: NULL dcam");
   Prepared pr;
   dist_status s = validate_and_upload(dec, z, n_shapes, cams, n_cams, p, fwd, ws, stream, &pr);
@@ -1659,6 +1665,7 @@ dist_status dist_photo_loss(const dist_camera* cams, int n_cams, const float* de
                            const float* images, int channels, const int32_t* pairs, int n_pairs,
                            float w, double* loss, float* g_depth, dist_workspace* ws,
                            void* stream) {
+  DIST_NVTX("dist_photo_loss");
   DIST_CHECK(cams && depth && images && pairs && loss && g_depth && ws, DIST_E_INVALID,
              "dist_photo_loss: NULL argument");
   DIST_CHECK(channels >= 1 && channels <= 4, DIST_E_INVALID, "dist_photo_loss: channels 1..4");
@@ -1698,6 +1705,7 @@ dist_status dist_photo_loss(const dist_camera* cams, int n_cams, const float* de
 dist_status dist_render_color(const dist_decoder* tex, const float* codes, int n_shapes,
                               const dist_camera* cams, int n_cams, const dist_trace_out* fwd,
                               int precision, float* rgb, dist_workspace* ws, void* stream) {
+  DIST_NVTX("dist_render_color");
   DIST_CHECK(tex && codes && cams && fwd && rgb && ws, DIST_E_INVALID,
              "dist_render_color: NULL argument");
   DIST_CHECK(tex->f32.out_dim == 3, DIST_E_INVALID, "dist_render_color: decoder out_dim must be 3");
@@ -1749,6 +1757,7 @@ dist_status dist_render_color(const dist_decoder* tex, const float* codes, int n
 dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
                           const float* pts, const int32_t* shape, int64_t n, int precision,
                           float* f, float* grad, dist_workspace* ws, void* stream) {
+  DIST_NVTX("dist_sdf_eval");
   DIST_CHECK(dec && z && pts && shape && f && ws, DIST_E_INVALID, "dist_sdf_eval: NULL argument");
   DIST_CHECK(is_sdf_decoder(dec->desc), DIST_E_INVALID,
              "dist_sdf_eval needs an SDF decoder (out_dim 1, latent_dim0 = latent_dim)");
@@ -1792,6 +1801,7 @@ dist_status dist_loss(int64_t n, const float* depth, const uint8_t* mask, const 
                       const float* tgt_sil, const float* z, int n_shapes, int latent_dim,
                       const dist_loss_weights* w, double* loss, float* g_depth, float* g_normal,
                       float* g_sil, float* dz, dist_workspace* ws, void* stream) {
+  DIST_NVTX("dist_loss");
   DIST_CHECK(n >= 1 && depth && mask && tgt_depth && w && loss && ws, DIST_E_INVALID,
              "dist_loss: NULL argument or empty batch");
   DIST_CHECK(w->w_depth == 0.f || g_depth, DIST_E_INVALID, "dist_loss: g_depth required");
