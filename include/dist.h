@@ -205,12 +205,23 @@ typedef struct {
                           four SMs, a quarter of every layer's columns per
                           SM; 0 = one tile per SM (pair) throughout.  Both
                           give the same f for every query.                   */
+  float eps_mid;       /* BF16 march only: 0 (default) = a ray whose BF16
+                          |f| < eps_bf16 goes straight to FP32-class
+                          queries; in (0, eps_bf16) = it goes to FP16
+                          queries first (same tensor rate, 3 more mantissa
+                          bits) and from there to FP32-class queries once
+                          its FP16 |f| < eps_mid (or its FP16 samples change
+                          sign with |f| < 16 eps_mid), so fewer queries pay
+                          the FP32-class cost.  Needs refine_engine TC,
+                          refine_steps 0, refine_rule MARCH, coarse_levels
+                          0; ignored for other precisions; the server
+                          rejects it.                                        */
 } dist_trace_params;
 
 /* Fill `p` with the paper's defaults: max_steps 50, eps 5e-5, alpha 1.5,
  * k_min 1, normal_delta 0, exact gradients, FP32, eps_bf16 1e-3, radius 1,
  * refine_steps 0, alpha_refine 0, refine_engine TC, refine_rule MARCH,
- * coarse_levels 0 (off), coarse_every 3. */
+ * coarse_levels 0 (off), coarse_every 3, latency_mode 1, eps_mid 0. */
 void dist_trace_params_default(dist_trace_params* p);
 
 /* -------------------------------------------------------------- workspace */
@@ -245,7 +256,8 @@ typedef struct {
   float* normal;     /* [n_pixels][3] (optional): filled by dist_trace_fwd
                         when non-NULL, else by dist_render_normals          */
   unsigned long long* queries;  /* optional, device [2]: += MLP queries made
-                        while marching, [0] BF16, [1] FP32                  */
+                        while marching, [0] 16-bit (BF16 or FP16), [1] FP32
+                        or FP32-class                                       */
 } dist_trace_out;
 
 /* Forward render: unit-sphere initialisation (Sec. 3.2), then up to

@@ -56,7 +56,8 @@ class TraceParams(Structure):
                 ("normal_delta", c_float), ("grad_mode", c_int), ("precision", c_int),
                 ("eps_bf16", c_float), ("radius", c_float), ("refine_steps", c_int),
                 ("alpha_refine", c_float), ("refine_engine", c_int), ("refine_rule", c_int),
-                ("coarse_levels", c_int), ("coarse_every", c_int), ("latency_mode", c_int)]
+                ("coarse_levels", c_int), ("coarse_every", c_int), ("latency_mode", c_int),
+                ("eps_mid", c_float)]
 
 
 class TraceOut(Structure):

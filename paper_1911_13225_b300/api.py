@@ -48,6 +48,7 @@ class TraceParams:
     coarse_levels: int = 0        # coarse-to-fine tracing (Sec. 3.2): 0 off, 2 the paper's
     coarse_every: int = 3         # march iterations per coarse level
     latency_mode: int = 1         # 1: small steps spread each tile over a four-SM cluster
+    eps_mid: float = 0.0          # BF16 march: > 0 = an FP16 stage before the FP32-class queries
 
     def c(self) -> _abi.TraceParams:
         return _abi.TraceParams(
@@ -57,7 +58,8 @@ class TraceParams:
             _abi.PRECISIONS[self.precision], float(self.eps_bf16), float(self.radius),
             int(self.refine_steps), float(self.alpha_refine),
             _abi.REFINE_ENGINES[self.refine_engine], _abi.REFINE_RULES[self.refine_rule],
-            int(self.coarse_levels), int(self.coarse_every), int(self.latency_mode))
+            int(self.coarse_levels), int(self.coarse_every), int(self.latency_mode),
+            float(self.eps_mid))
 
 
 def camera_struct(cam) -> _abi.Camera:

@@ -76,6 +76,7 @@ void dist_trace_params_default(dist_trace_params* p) {
   p->coarse_levels = 0;
   p->coarse_every = 3;
   p->latency_mode = 1;
+  p->eps_mid = 0.f;
 }
 
 dist_status dist_decoder_create(const dist_decoder_desc* desc, const float* const* W,
@@ -226,9 +227,12 @@ dist_status dist_workspace_create(int64_t max_rays, int max_steps, dist_workspac
   WS_ALLOC(act[0][1], n * sizeof(int));
   WS_ALLOC(act[1][0], n * sizeof(int));
   WS_ALLOC(act[1][1], n * sizeof(int));
+  WS_ALLOC(act[0][2], n * sizeof(int));
+  WS_ALLOC(act[1][2], n * sizeof(int));
   WS_ALLOC(fbuf[0], n * sizeof(float));
   WS_ALLOC(fbuf[1], n * sizeof(float));
-  WS_ALLOC(counts, ((size_t)(max_steps + 2) * 2 + 2 * kMaxCoarseLevels) * sizeof(int));
+  WS_ALLOC(fbuf[2], n * sizeof(float));
+  WS_ALLOC(counts, ((size_t)(max_steps + 2) * 3 + 2 * kMaxCoarseLevels) * sizeof(int));
   WS_ALLOC(rstat, n * sizeof(int));
   WS_ALLOC(chunk, ((n + 31) / 32) * sizeof(int));
   WS_ALLOC(cams, (size_t)w->max_cams * sizeof(CamDev));

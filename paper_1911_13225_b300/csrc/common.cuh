@@ -181,9 +181,9 @@ struct dist_workspace {
   float* fprev;       // previous low-precision sample of each ray (its FP32-class
                       // sample after the hand-over, secant rule)
   float* dprev;       // distance of the previous FP32-class sample (secant rule)
-  int* act[2][2];     // [parity][0 = BF16 list, 1 = FP32 list] active ray ids
-  float* fbuf[2];     // MLP outputs for the two lists
-  int* counts;        // [(max_steps + 2) * 2 + 2 kMaxCoarseLevels] list lengths
+  int* act[2][3];     // [parity][0 = BF16 list, 1 = FP32 list, 2 = FP16 stage] ray ids
+  float* fbuf[3];     // MLP outputs for the three lists
+  int* counts;        // [(max_steps + 2) * 3 + 2 kMaxCoarseLevels] list lengths
                       // per step, then per coarse-to-fine split
   int* rstat;         // per-ray status when the caller asks for none
   int* chunk;         // (max_rays + 31) / 32 probe counts / offsets (ordered append)
@@ -318,7 +318,8 @@ cudaError_t mlp_tcx_forward(const dist_decoder* dec, const RowSrc& src, const fl
 cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f16out,
                          const RowSrc& srcx, float* fxout, const float* bfold0,
                          const float* bfolds, cudaStream_t st, bool f16,
-                         const StepFuse* step = nullptr);
+                         const StepFuse* step = nullptr, const RowSrc* srcm = nullptr,
+                         float* fmout = nullptr);
 
 // Latency mode of the fused decoder (a launch of at most tc_wide_max_tiles()
 // tiles of 128 16-bit rows or 64 FP32-class queries): each tile on a cluster
@@ -328,7 +329,7 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
 cudaError_t mlp_tc_wide(const dist_decoder* dec, const RowSrc& src16, float* f16out,
                         const RowSrc& srcx, float* fxout, const float* bfold0,
                         const float* bfolds, cudaStream_t st, bool f16, const StepFuse* step,
-                        void* scratch);
+                        void* scratch, const RowSrc* srcm = nullptr, float* fmout = nullptr);
 int tc_wide_max_tiles();
 size_t tc_wide_scratch_bytes();
 

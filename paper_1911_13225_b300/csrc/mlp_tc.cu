@@ -45,16 +45,18 @@ namespace dist {
 
 namespace {
 
-// Forward arguments: two row lists decoded in one launch.  List 0 runs with
-// 16-bit operands (BF16, or FP16 with the F16 variant), 128 rows per tile;
-// list 1 is FP32-class: every operand a sum of two FP16 numbers (hi + lo,
-// weights scaled by 2^s_l), 64 queries per tile, see tc_common.cuh.
+// Forward arguments: three row lists decoded in one launch.  List 0 runs
+// with 16-bit operands (BF16, or FP16 with the F16 variant), 128 rows per
+// tile; list 1 is FP32-class: every operand a sum of two FP16 numbers (hi +
+// lo, weights scaled by 2^s_l), 64 queries per tile, see tc_common.cuh; list
+// 2 runs with FP16 operands, 128 rows per tile (the FP16 stage between a
+// BF16 march and its FP32-class queries; empty otherwise).
 struct TCArgs {
   const TCConst* K;              // epilogue constants (device)
   const float* bfold0;           // [shape][512] folded bias of layer 0
   const float* bfold4;           // [shape][512] folded bias of the skip layer 4
-  RowSrc src[2];
-  float* fout[2];
+  RowSrc src[3];
+  float* fout[3];
   int* err;
   float inv_scale[NUM_GEMM];     // list 1: 2^-s_l of GEMM layer g
   float* cpart;                  // colour decoder: [row][4 column groups][3] head partials
@@ -107,7 +109,7 @@ __device__ __forceinline__ int tile_of(int r, int pid, int npid) {
 template <bool F16, bool PAIR, bool COLOR>
 __global__ void __launch_bounds__(FWD_THREADS, 1)
 mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMaps xmaps,
-              const TCArgs a) {
+              const __grid_constant__ TCMaps maps16, const TCArgs a) {
   constexpr int NST = PAIR ? 2 * STAGES : STAGES;            // weight ring stages
   constexpr int SB = PAIR ? STAGE_BYTES / 2 : STAGE_BYTES;   // bytes per stage per CTA
   constexpr int MUL = PAIR ? 2 : 1;                          // CTAs per tile
@@ -142,16 +144,26 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   grid_dep_launch();
   const int n0 = rowsrc_count(a.src[0]);
   const int n1 = rowsrc_count(a.src[1]);
+  const int n2 = rowsrc_count(a.src[2]);
   const int t1 = (n1 + MUL * QPT_X - 1) / (MUL * QPT_X);   // FP32-class tiles: [0, t1)
-  const int n_tiles = t1 + (n0 + MUL * BM - 1) / (MUL * BM);
+  const int t2 = t1 + (n2 + MUL * BM - 1) / (MUL * BM);     // FP16-stage tiles: [t1, t2)
+  const int n_tiles = t2 + (n0 + MUL * BM - 1) / (MUL * BM);
   if (pid >= n_tiles) return;                               // uniform over a pair
   // a launch small enough for the latency mode (its tiles: 128 16-bit rows
   // or 64 FP32-class queries) runs there instead, launched right behind this
-  if (a.wide_tiles > 0 && (n1 + 63) / 64 + (n0 + BM - 1) / BM <= a.wide_tiles) return;
+  if (a.wide_tiles > 0 &&
+      (n1 + 63) / 64 + (n2 + BM - 1) / BM + (n0 + BM - 1) / BM <= a.wide_tiles)
+    return;
   if (a.fuse_step && a.step.queries && pid == 0 && rank == 0 && threadIdx.x == 0) {
-    atomicAdd(a.step.queries + 0, (unsigned long long)n0);
+    atomicAdd(a.step.queries + 0, (unsigned long long)(n0 + n2));
     atomicAdd(a.step.queries + 1, (unsigned long long)n1);
   }
+  // row list of tile t, and the first row of its list in this CTA
+  auto tile_list = [&](int t) { return t < t1 ? 1 : (t < t2 ? 2 : 0); };
+  auto tile_row0 = [&](int t) {
+    return t < t1 ? (t * MUL + rank) * QPT_X
+                  : ((t - (t < t2 ? t1 : t2)) * MUL + rank) * BM;
+  };
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NST; ++s) {
@@ -192,8 +204,9 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       for (int r = 0, tile = pid; ok && !a.withhold && tile < n_tiles;
            tile = tile_of(++r, pid, npid)) {
         const bool xt = tile < t1;
+        const bool mid = tile_list(tile) == 2;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
-          const CUtensorMap* map = xt ? &xmaps.m[g] : &maps.m[g];
+          const CUtensorMap* map = xt ? &xmaps.m[g] : (mid ? &maps16.m[g] : &maps.m[g]);
           const int nkc = gemm_k(g) / BK;
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
             for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
@@ -241,7 +254,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       };
       for (int r = 0, tile = pid; ok && tile < n_tiles; tile = tile_of(++r, pid, npid)) {
         const bool xt = tile < t1;
-        const uint32_t idesc = instr_desc_m(xt || F16, MUL * BM);
+        const uint32_t idesc = instr_desc_m(xt || F16 || tile_list(tile) == 2, MUL * BM);
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
           const int nkc = gemm_k(g) / BK;
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
@@ -298,10 +311,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       uint32_t sphase = 0;
       for (int r = 0, t = pid; t < n_tiles; t = tile_of(++r, pid, npid)) {
         const bool xt = t < t1;
-        const int list = xt ? 1 : 0;
-        const int j0 = xt ? (t * MUL + rank) * QPT_X : ((t - t1) * MUL + rank) * BM;
+        const int list = tile_list(t);
+        const int j0 = tile_row0(t);
         const int rows = xt ? QPT_X : BM;
-        const int n = xt ? n1 : n0;
+        const int n = list == 1 ? n1 : (list == 2 ? n2 : n0);
         // the rows' ray state is read while the tile is being decoded
         int ray[RPT];
         bool valid[RPT];
@@ -329,8 +342,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
           const int keep = valid[k] ? apply_step(a.step.t, list, ray[k], f[k], rs[k]) : -1;
           const int s0 = warp_append(keep == 0, a.step.cnt_out[0]);
           const int s1 = warp_append(keep == 1, a.step.cnt_out[1]);
+          const int s2 = warp_append(keep == 2, a.step.cnt_out[2]);
           if (s0 >= 0) a.step.out[0][s0] = ray[k];
           if (s1 >= 0) a.step.out[1][s1] = ray[k];
+          if (s2 >= 0) a.step.out[2][s2] = ray[k];
         }
       }
     }
@@ -356,17 +371,20 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     bool ok = true;
     float vmax = 0.f;
 
-    // rows of tile t for this thread
-    bool xt = false, valid = false;
-    int j = 0, shape = 0;
+    // rows of tile t for this thread (list, operand format: f16 for the
+    // FP16 stage, or for every 16-bit tile of the F16 variant)
+    bool xt = false, valid = false, f16 = F16;
+    int list = 0, j = 0, shape = 0;
     float3 p = make_float3(0.f, 0.f, 0.f);
     auto load_rows = [&](int t) {
-      xt = t < t1;
-      j = xt ? (t * MUL + rank) * QPT_X + jr : ((t - t1) * MUL + rank) * BM + row;
-      valid = j < (xt ? n1 : n0);
+      list = tile_list(t);
+      xt = list == 1;
+      f16 = F16 || list == 2;
+      j = tile_row0(t) + (xt ? jr : row);
+      valid = j < (list == 1 ? n1 : (list == 2 ? n2 : n0));
       p = make_float3(0.f, 0.f, 0.f);
       shape = 0;
-      if (valid) rowsrc_load(a.src[xt ? 1 : 0], j, p, shape);
+      if (valid) rowsrc_load(a.src[list], j, p, shape);
     };
     auto wait_acc = [&](int h) -> bool {
       if (!mbar_wait(acc_full + h, acc_phase[h], abort_flag, wlim)) return false;
@@ -417,7 +435,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         float v[32];
         layer0_32(K, bf0, 128 * q + cg, p, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) h[i] = pack16<F16>(v[2 * i], v[2 * i + 1]);
+        for (int i = 0; i < 16; ++i) h[i] = pack16r(f16, v[2 * i], v[2 * i + 1]);
       } else {
         float v[16];
         layer0_16(K, bf0, 128 * q + cg + 16 * part, p, v);
@@ -438,15 +456,15 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
 #pragma unroll
         for (int i = 0; i < 32; i += 4) {
           const float4 b = ldg4(bias + 128 * q + cg + i);
-          h[i / 2] = pack16<F16>(fmaxf(__uint_as_float(r[i]) + b.x, 0.f),
+          h[i / 2] = pack16r(f16, fmaxf(__uint_as_float(r[i]) + b.x, 0.f),
                                  fmaxf(__uint_as_float(r[i + 1]) + b.y, 0.f));
-          h[i / 2 + 1] = pack16<F16>(fmaxf(__uint_as_float(r[i + 2]) + b.z, 0.f),
+          h[i / 2 + 1] = pack16r(f16, fmaxf(__uint_as_float(r[i + 2]) + b.z, 0.f),
                                      fmaxf(__uint_as_float(r[i + 3]) + b.w, 0.f));
         }
         if (point) {
           const float b28 = __ldg(K->bias[g] + 252);
-          h[14] = pack16<F16>(fmaxf(__uint_as_float(r[28]) + b28, 0.f), pp.x);
-          h[15] = pack16<F16>(pp.y, pp.z);
+          h[14] = pack16r(f16, fmaxf(__uint_as_float(r[28]) + b28, 0.f), pp.x);
+          h[15] = pack16r(f16, pp.y, pp.z);
         }
       } else {
         float m[16], v[16];
@@ -514,6 +532,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       // ---- last layer: head partial sums; the operand tile takes the next
       // tile's layer 0 once this layer's MMAs are done
       const bool cur_xt = xt;
+      const int cur_list = list;
       const int cur_j = j;
       const bool cur_valid = valid;
       const float3 cur_p = p;
@@ -603,7 +622,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
           __syncwarp();
           if (lane == 0) mbar_arrive(step_full);
         } else if (mine) {
-          a.fout[cur_xt ? 1 : 0][cur_j] = tanhf(head + __ldg(&K->b_head));
+          a.fout[cur_list][cur_j] = tanhf(head + __ldg(&K->b_head));
         }
       }
       head_phase ^= 1u;
@@ -1241,6 +1260,7 @@ cudaError_t launch_fused(const dist_decoder* dec, const TCArgs& a, cudaStream_t 
   const TCMaps& maps = PAIR ? (F16 ? dec->tc.pmaps16 : dec->tc.pmaps)
                             : (F16 ? dec->tc.maps16 : dec->tc.maps);
   const TCMaps& xmaps = PAIR ? dec->tc.pxmaps : dec->tc.xmaps;
+  const TCMaps& maps16 = PAIR ? dec->tc.pmaps16 : dec->tc.maps16;   // FP16-stage tiles
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(PAIR ? (num_sms() / 2) * 2 : num_sms());
   cfg.blockDim = dim3(FWD_THREADS);
@@ -1255,7 +1275,8 @@ cudaError_t launch_fused(const dist_decoder* dec, const TCArgs& a, cudaStream_t 
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, mlp_tc_kernel<F16, PAIR, COLOR>, maps, xmaps, a);
+  cudaError_t e =
+      cudaLaunchKernelEx(&cfg, mlp_tc_kernel<F16, PAIR, COLOR>, maps, xmaps, maps16, a);
   count_launch(1);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -1264,7 +1285,7 @@ cudaError_t launch_fused(const dist_decoder* dec, const TCArgs& a, cudaStream_t 
 cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f16out,
                          const RowSrc& srcx, float* fxout, const float* bfold0,
                          const float* bfolds, cudaStream_t st, bool f16,
-                         const StepFuse* step) {
+                         const StepFuse* step, const RowSrc* srcm, float* fmout) {
   if (!dec->tc.ok) return cudaErrorNotSupported;
   TCArgs a;
   a.K = dec->tc.cst;
@@ -1272,8 +1293,10 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
   a.bfold4 = bfolds;
   a.src[0] = src16;
   a.src[1] = srcx;
+  a.src[2] = srcm ? *srcm : RowSrc{};     // no FP16-stage list: count 0
   a.fout[0] = f16out;
   a.fout[1] = fxout;
+  a.fout[2] = fmout;
   a.err = dec->tc.err;
   for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
   a.cpart = nullptr;
@@ -1291,7 +1314,8 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
   else
     e = f16 ? launch_fused<true, false>(dec, a, st) : launch_fused<false, false>(dec, a, st);
   if (e != cudaSuccess || a.wide_tiles <= 0) return e;
-  return mlp_tc_wide(dec, src16, f16out, srcx, fxout, bfold0, bfolds, st, f16, step, step->wide);
+  return mlp_tc_wide(dec, src16, f16out, srcx, fxout, bfold0, bfolds, st, f16, step, step->wide,
+                     srcm, fmout);
 }
 
 cudaError_t mlp_tc_color(const dist_decoder* dec, const RowSrc& src, const float* bfold0,

@@ -40,8 +40,8 @@ struct WideArgs {
   const TCConst* K;
   const float* bfold0;
   const float* bfold4;
-  RowSrc src[2];
-  float* fout[2];
+  RowSrc src[3];       // lists as in mlp_tc_kernel: 16-bit, FP32-class, FP16 stage
+  float* fout[3];
   int* err;
   float inv_scale[NUM_GEMM];
   int fuse_step;
@@ -83,7 +83,7 @@ __device__ __forceinline__ void bulk_store(uint8_t* dst, uint32_t src, uint32_t 
 template <bool F16>
 __global__ void __launch_bounds__(W_THREADS, 1)
 mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__ TCMaps wxmaps,
-                   const WideArgs a) {
+                   const __grid_constant__ TCMaps wmaps16, const WideArgs a) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -119,15 +119,20 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
   const int ncl = (int)(gridDim.x / WC);
   const int n0 = rowsrc_count(a.src[0]);
   const int n1 = rowsrc_count(a.src[1]);
-  const int t1 = (n1 + QPT_XW - 1) / QPT_XW;
-  const int n_tiles = t1 + (n0 + BM - 1) / BM;
+  const int n2 = rowsrc_count(a.src[2]);
+  const int t1 = (n1 + QPT_XW - 1) / QPT_XW;         // FP32-class tiles: [0, t1)
+  const int t2 = t1 + (n2 + BM - 1) / BM;            // FP16-stage tiles: [t1, t2)
+  const int n_tiles = t2 + (n0 + BM - 1) / BM;
   // launches with more tiles than clusters go to mlp_tc_kernel, which makes
   // the same decision from the same counts; uniform over a cluster
   if (n_tiles == 0 || n_tiles > ncl || cid >= n_tiles) return;
   if (a.fuse_step && a.step.queries && cid == 0 && rank == 0 && threadIdx.x == 0) {
-    atomicAdd(a.step.queries + 0, (unsigned long long)n0);
+    atomicAdd(a.step.queries + 0, (unsigned long long)(n0 + n2));
     atomicAdd(a.step.queries + 1, (unsigned long long)n1);
   }
+  // row list of tile t and its first row in the list
+  auto tile_list = [&](int t) { return t < t1 ? 1 : (t < t2 ? 2 : 0); };
+  auto tile_row0 = [&](int t) { return t < t1 ? t * QPT_XW : (t - (t < t2 ? t1 : t2)) * BM; };
   if (threadIdx.x == 0) {
     for (int s = 0; s < W_NST; ++s) {
       mbar_init(full + s, 1);
@@ -162,8 +167,9 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
       bool ok = true;
       for (int tile = cid; ok && tile < n_tiles; tile += ncl) {
         const bool xt = tile < t1;
+        const bool mid = tile_list(tile) == 2;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
-          const CUtensorMap* map = xt ? &wxmaps.m[g] : &wmaps.m[g];
+          const CUtensorMap* map = xt ? &wxmaps.m[g] : (mid ? &wmaps16.m[g] : &wmaps.m[g]);
           const int nkc = gemm_k(g) / BK;
           const int row0 = (gemm_n(g) / WC) * rank;
           // stages of two K chunks (nkc is even, so a pair never straddles
@@ -198,9 +204,10 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
       bool ok = true;
       for (int tile = cid; ok && tile < n_tiles; tile += ncl) {
         const bool xt = tile < t1;
+        const bool f16 = xt || F16 || tile_list(tile) == 2;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
           const int nkc = gemm_k(g) / BK;
-          const uint32_t idesc = wide_idesc(xt || F16, gemm_n(g) / WC);
+          const uint32_t idesc = wide_idesc(f16, gemm_n(g) / WC);
           if (!mbar_wait(act_full, act_phase, abort_flag)) { ok = false; break; }
           act_phase ^= 1u;
           tc_fence_after();
@@ -246,8 +253,8 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
     int xs = 0;                                   // exchanges so far
     bool ok = true;
     float vmax = 0.f;
-    bool xt = false, valid = false;
-    int j = 0, shape = 0;
+    bool xt = false, valid = false, f16 = F16;
+    int list = 0, j = 0, shape = 0;
     float3 p = make_float3(0.f, 0.f, 0.f);
     uint8_t* stage_base = nullptr;
 
@@ -289,7 +296,7 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
         float v[32];
         layer0_32(K, bf0, c, p, v);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) h[i] = pack16<F16>(v[2 * i], v[2 * i + 1]);
+        for (int i = 0; i < 16; ++i) h[i] = pack16r(f16, v[2 * i], v[2 * i + 1]);
       } else {
         float v[16];
         layer0_16(K, bf0, c + 16 * part, p, v);
@@ -306,15 +313,15 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
 #pragma unroll
         for (int i = 0; i < 32; i += 4) {
           const float4 b = ldg4(bias + c + i);
-          h[i / 2] = pack16<F16>(fmaxf(__uint_as_float(r[i]) + b.x, 0.f),
+          h[i / 2] = pack16r(f16, fmaxf(__uint_as_float(r[i]) + b.x, 0.f),
                                  fmaxf(__uint_as_float(r[i + 1]) + b.y, 0.f));
-          h[i / 2 + 1] = pack16<F16>(fmaxf(__uint_as_float(r[i + 2]) + b.z, 0.f),
+          h[i / 2 + 1] = pack16r(f16, fmaxf(__uint_as_float(r[i + 2]) + b.z, 0.f),
                                      fmaxf(__uint_as_float(r[i + 3]) + b.w, 0.f));
         }
         if (point) {
           const float b28 = __ldg(K->bias[g] + 252);
-          h[14] = pack16<F16>(fmaxf(__uint_as_float(r[28]) + b28, 0.f), p.x);
-          h[15] = pack16<F16>(p.y, p.z);
+          h[14] = pack16r(f16, fmaxf(__uint_as_float(r[28]) + b28, 0.f), p.x);
+          h[15] = pack16r(f16, p.y, p.z);
         }
       } else {
         float m[16], v[16];
@@ -381,12 +388,14 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
 
     stage_base = a.stage_g + ((size_t)cid * 2 + (xs & 1)) * ACT_BYTES;
     for (int tile = cid; ok && tile < n_tiles; tile += ncl) {
-      xt = tile < t1;
-      j = xt ? tile * QPT_XW + jr : (tile - t1) * BM + row;
-      valid = j < (xt ? n1 : n0);
+      list = tile_list(tile);
+      xt = list == 1;
+      f16 = F16 || list == 2;
+      j = tile_row0(tile) + (xt ? jr : row);
+      valid = j < (list == 1 ? n1 : (list == 2 ? n2 : n0));
       p = make_float3(0.f, 0.f, 0.f);
       shape = 0;
-      if (valid) rowsrc_load(a.src[xt ? 1 : 0], j, p, shape);
+      if (valid) rowsrc_load(a.src[list], j, p, shape);
       const float* bf4 = a.bfold4 + (size_t)shape * 512;
       // layer 0: this CTA's 128 columns
 #pragma unroll 1
@@ -451,16 +460,17 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
         if (a.fuse_step) {
           int keep = -1, ray = 0;
           if (mine) {
-            const int list = xt ? 1 : 0;
             ray = a.src[list].idx[j];
             keep = step_ray(a.step.t, list, ray, f);
           }
           const int s0 = warp_append(keep == 0, a.step.cnt_out[0]);
           const int s1 = warp_append(keep == 1, a.step.cnt_out[1]);
+          const int s2 = warp_append(keep == 2, a.step.cnt_out[2]);
           if (s0 >= 0) a.step.out[0][s0] = ray;
           if (s1 >= 0) a.step.out[1][s1] = ray;
+          if (s2 >= 0) a.step.out[2][s2] = ray;
         } else if (mine) {
-          a.fout[xt ? 1 : 0][j] = f;
+          a.fout[list][j] = f;
         }
       }
     }
@@ -517,7 +527,7 @@ int tc_wide_max_tiles() {
 cudaError_t mlp_tc_wide(const dist_decoder* dec, const RowSrc& src16, float* f16out,
                         const RowSrc& srcx, float* fxout, const float* bfold0,
                         const float* bfolds, cudaStream_t st, bool f16, const StepFuse* step,
-                        void* scratch) {
+                        void* scratch, const RowSrc* srcm, float* fmout) {
   WideArgs a;
   memset(&a, 0, sizeof(a));
   a.K = dec->tc.cst;
@@ -525,8 +535,10 @@ cudaError_t mlp_tc_wide(const dist_decoder* dec, const RowSrc& src16, float* f16
   a.bfold4 = bfolds;
   a.src[0] = src16;
   a.src[1] = srcx;
+  if (srcm) a.src[2] = *srcm;       // else count 0 (zeroed above)
   a.fout[0] = f16out;
   a.fout[1] = fxout;
+  a.fout[2] = fmout;
   a.err = dec->tc.err;
   for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
   a.fuse_step = step ? 1 : 0;
@@ -551,7 +563,7 @@ cudaError_t mlp_tc_wide(const dist_decoder* dec, const RowSrc& src16, float* f16
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, dec->tc.wxmaps, a);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kern, maps, dec->tc.wxmaps, dec->tc.wmaps16, a);
   count_launch(1);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();

@@ -396,6 +396,8 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
              "the tensor-core decoder covers only the DeepSDF shape");
   DIST_CHECK(p->coarse_levels == 0, DIST_E_INVALID,
              "dist_serve_create: coarse-to-fine tracing is not supported by the server");
+  DIST_CHECK(p->eps_mid == 0.f || p->precision != DIST_PREC_BF16, DIST_E_INVALID,
+             "dist_serve_create: the server's march has no FP16 stage (eps_mid must be 0)");
   dist_server* S = new dist_server();
   S->dec = dec;
   S->p = *p;

@@ -17,6 +17,9 @@ struct TraceArgs {
   float radius;
   int K;
   float eps, alpha, eps_bf16;
+  float eps_mid;        // BF16 march: > 0 = rays hand over to FP16 queries (list 2)
+                        // at |f| < eps_bf16, and from there to FP32-class queries
+                        // at |f| < eps_mid; 0 = straight to FP32-class
   int max_steps;
   float alpha_fp32;     // step factor of FP32-list rays
   int refine;           // refine_steps for a tensor-core march, else 0
@@ -38,8 +41,9 @@ struct TraceArgs {
 // computes a ray's f updates the ray and appends it to the next step's list.
 struct StepFuse {
   TraceArgs t;
-  int* out[2];                   // next step's lists (0: 16-bit, 1: FP32-class)
-  int* cnt_out[2];               // their append counters
+  int* out[3];                   // next step's lists (0: 16-bit, 1: FP32-class,
+                                 // 2: FP16 stage of a BF16 march)
+  int* cnt_out[3];               // their append counters
   unsigned long long* queries;   // per-list query counters, or null
   uint8_t* wide;                 // latency-mode scratch (tc_wide_scratch_bytes()), or
                                  // null: every launch on the one-tile-per-SM kernel
@@ -81,17 +85,17 @@ __device__ __forceinline__ void load_ray(const TraceArgs& a, int list, int i, Ra
   }
   const bool ref = list == 1 && (a.refine > 0 || a.secant);
   r.fq = ref ? a.fq[i] : 0;
-  r.fprev = (list == 0 || (list == 1 && a.secant)) ? a.fprev[i] : 0.f;
+  r.fprev = (list != 1 || a.secant) ? a.fprev[i] : 0.f;
   r.dprev = (list == 1 && a.secant) ? a.dprev[i] : 0.f;
   r.dirw = a.dir[i].w;
 }
 
-// One query's update of ray i (list 0: low-precision, 1: FP32 / FP32-class)
-// with decoder value f and its state r: step count, the k smallest |f|
-// (silhouette and the paper's gradient), hand-over, convergence (|f| < eps:
-// hit at the unit final step d + f), the aggressive step d += alpha f,
-// leaving the bounding sphere and the step budget.  Returns the list the ray
-// continues in, or -1.
+// One query's update of ray i (list 0: low-precision, 1: FP32 / FP32-class,
+// 2: the FP16 stage of a BF16 march) with decoder value f and its state r:
+// step count, the k smallest |f| (silhouette and the paper's gradient),
+// hand-over, convergence (|f| < eps: hit at the unit final step d + f), the
+// aggressive step d += alpha f, leaving the bounding sphere and the step
+// budget.  Returns the list the ray continues in, or -1.
 __device__ __forceinline__ int apply_step(const TraceArgs& a, int list, int i, float f,
                                           const RayState& r) {
   int keep = -1;
@@ -100,7 +104,8 @@ __device__ __forceinline__ int apply_step(const TraceArgs& a, int list, int i, f
   const int steps = r.steps + 1;
   a.o.steps[i] = steps;
   const float af = fabsf(f);
-  const float track = list == 0 ? fmaxf(af, a.eps) : af;
+  const bool low = list != 1;             // a 16-bit sample (BF16, or FP16)
+  const float track = low ? fmaxf(af, a.eps) : af;
   // k smallest |f|, ascending; changed entries are written back
   float fm0 = r.fm[0];
   {
@@ -129,17 +134,21 @@ __device__ __forceinline__ int apply_step(const TraceArgs& a, int list, int i, f
     accepted = a.refine > 0 && q >= a.refine && af >= a.eps && af < 4.f * a.eps_bf16;
   }
   bool crossed = false;
-  if (list == 0) {
+  const float eps_lo = list == 2 ? a.eps_mid : a.eps_bf16;
+  if (low) {
     // a low-precision march that steps across the surface close to it
-    // hands over to FP32 even if its noisy |f| never drops below eps_bf16
+    // hands over to FP32 even if its noisy |f| never drops below its
+    // threshold
     const float fp = r.fprev;
     a.fprev[i] = f;
-    crossed = fp != 0.f && ((fp > 0.f) != (f > 0.f)) && af < 16.f * a.eps_bf16;
+    crossed = fp != 0.f && ((fp > 0.f) != (f > 0.f)) && af < 16.f * eps_lo;
   }
   if (list == 1 && (af < a.eps || accepted)) {
     outcome = DIST_RAY_HIT;
-  } else if (list == 0 && (af < a.eps_bf16 || crossed)) {
-    keep = 1;       // switch to FP32 queries at the same point
+  } else if (low && (af < eps_lo || crossed)) {
+    // switch to FP32-class queries at the same point (from a BF16 march with
+    // an FP16 stage: BF16 samples close to the surface go to FP16 first)
+    keep = (list == 0 && a.eps_mid > 0.f && !crossed) ? 2 : 1;
     if (a.c2f) a.o.status[i] = -2;
   } else {
     dn = fmaf(list == 1 ? a.alpha_fp32 : a.alpha, f, d);

@@ -314,6 +314,11 @@ __device__ __forceinline__ uint32_t pack16(float a, float b) {
   }
 }
 
+// pack16 with the operand type chosen at run time (uniform over a warp).
+__device__ __forceinline__ uint32_t pack16r(bool f16, float a, float b) {
+  return f16 ? pack16<true>(a, b) : pack16<false>(a, b);
+}
+
 // Store 32 consecutive activations (columns c..c+31, c % 32 == 0) of row r.
 template <bool F16>
 __device__ __forceinline__ void store_act32(uint8_t* act, int r, int c, const float (&v)[32]) {

@@ -1143,6 +1143,13 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
              DIST_E_INVALID,
              "coarse-to-fine tracing with a BF16/FP16 march needs refine_steps 0 and the TC "
              "refine engine");
+  DIST_CHECK(p->precision != DIST_PREC_BF16 || p->eps_mid == 0.f ||
+                 (p->eps_mid > 0.f && p->eps_mid < p->eps_bf16 && fp32_on_tc(*p) &&
+                  p->refine_steps == 0 && p->refine_rule == DIST_REFINE_MARCH &&
+                  p->coarse_levels == 0),
+             DIST_E_INVALID,
+             "eps_mid (the FP16 stage of a BF16 march) must be 0, or in (0, eps_bf16) with the "
+             "TC refine engine, refine_steps 0, the MARCH rule and no coarse-to-fine levels");
   DIST_CHECK(!(is_tc(p->precision) || fp32_on_tc(*p)) || dec->tc.ok, DIST_E_UNSUPPORTED,
              "the tensor-core decoder covers only the DeepSDF shape (512 x 8, skip 4, latent 256)");
   DIST_CHECK(o->depth && o->sil && o->mask && o->steps && o->d_hit && o->d_min && o->f_min,
@@ -1176,6 +1183,7 @@ TraceArgs make_args(const dist_trace_params* p, const dist_trace_out* o, dist_wo
   a.cams = ws->cams; a.n_cams = n_cams; a.n_pix = n_pix; a.radius = p->radius; a.K = p->k_min;
   a.pix0 = 0; a.cam_fixed = -1;
   a.eps = p->eps; a.alpha = p->alpha; a.eps_bf16 = p->eps_bf16; a.max_steps = p->max_steps;
+  a.eps_mid = p->precision == DIST_PREC_BF16 ? p->eps_mid : 0.f;
   a.refine = is_tc(p->precision) ? p->refine_steps : 0;
   a.secant = is_tc(p->precision) && p->refine_rule == DIST_REFINE_SECANT ? 1 : 0;
   a.alpha_fp32 = (is_tc(p->precision) && p->alpha_refine > 0.f) ? p->alpha_refine : p->alpha;
@@ -1310,6 +1318,7 @@ static TraceArgs pool_args(const RayPool& P) {
   a.max_steps = P.max_steps; a.o = P.o; a.st = P.st; a.dir = P.dir;
   a.fq = P.fq; a.fprev = P.fprev; a.dprev = P.dprev; a.refine = P.refine;
   a.secant = P.secant; a.alpha_fp32 = P.alpha_fp32;
+  a.eps_mid = 0.f;      // the server's march has no FP16 stage
   a.c2f = 0; a.c2f_start = 0; a.last = 0;
   return a;
 }
@@ -1348,6 +1357,8 @@ cudaError_t pool_step(const RayPool& P, const int* cnt_in, int* cnt_out, int* co
 void pool_step_fuse(const RayPool& P, int* cnt_out, int* const out[2], StepFuse* sf) {
   sf->t = pool_args(P);
   for (int k = 0; k < 2; ++k) { sf->out[k] = out[k]; sf->cnt_out[k] = cnt_out + k; }
+  sf->out[2] = nullptr;   // no FP16 stage (eps_mid 0): nothing goes to list 2
+  sf->cnt_out[2] = nullptr;
   sf->queries = P.o.queries;
   sf->wide = nullptr;
 }
@@ -1412,8 +1423,9 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
   int* cB = ws->counts + (M + 1);
   int* zero = ws->counts + 2 * (M + 1);
   int* cSplit = zero + 1;
+  int* cC = cSplit + 2 * kMaxCoarseLevels;   // FP16-stage list of a BF16 march
   DIST_CUDA_TRY(cudaMemsetAsync(
-      ws->counts, 0, (size_t)(2 * (M + 1) + 1 + 2 * kMaxCoarseLevels) * sizeof(int), st));
+      ws->counts, 0, (size_t)(3 * (M + 1) + 1 + 2 * kMaxCoarseLevels) * sizeof(int), st));
   const bool tc = is_tc(p->precision);
   const int L = p->coarse_levels;
   // coarse-to-fine: rays start 2^L coarser per side; before march iteration
@@ -1453,28 +1465,35 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
     // FP32-class queries after the 16-bit march.)
     const int* in0 = cA;
     const int* in1 = cB;
+    const int* in2 = cC;
+    const bool mid = a.eps_mid > 0.f;
     for (int s = 0; s < M; ++s) {
       DIST_NVTX("march step");
       if (split_due(s)) DIST_CUDA_TRY(split(0, in0, in1));
       RowSrc sx = src;
+      RowSrc sm = src;
       src.count = in0;
       src.idx = ws->act[par][0];
       sx.count = in1;
       sx.idx = ws->act[par][1];
+      sm.count = in2;
+      sm.idx = ws->act[par][2];
       // the decoder kernel applies the step update itself
       StepFuse sf;
       sf.t = a;
       sf.t.last = a.c2f && s == M - 1;
-      sf.out[0] = ws->act[par ^ 1][0]; sf.out[1] = ws->act[par ^ 1][1];
-      sf.cnt_out[0] = cA + s + 1; sf.cnt_out[1] = cB + s + 1;
+      for (int k = 0; k < 3; ++k) sf.out[k] = ws->act[par ^ 1][k];
+      sf.cnt_out[0] = cA + s + 1; sf.cnt_out[1] = cB + s + 1; sf.cnt_out[2] = cC + s + 1;
       sf.queries = o->queries;
       sf.wide = p->latency_mode ? static_cast<uint8_t*>(ws->wide_scratch) : nullptr;
       prof_mlp_begin(st, 0);
       DIST_CUDA_TRY(mlp_tc_fused(dec, src, ws->fbuf[0], sx, ws->fbuf[1], b0, bs, st,
-                                 p->precision == DIST_PREC_FP16, &sf));
+                                 p->precision == DIST_PREC_FP16, &sf, mid ? &sm : nullptr,
+                                 ws->fbuf[2]));
       prof_mlp_end(st);
       in0 = cA + s + 1;
       in1 = cB + s + 1;
+      in2 = cC + s + 1;
       par ^= 1;
     }
     while (level > 0) DIST_CUDA_TRY(split(1, in0, in1));

@@ -45,14 +45,17 @@ def _view(tag):
 
 
 @pytest.mark.parametrize("tag,precision", [("b512", "bf16"), ("b512", "fp16"), ("b512", "fp32"),
-                                           ("v5", "bf16"), ("v5", "fp32")])
+                                           ("b512", "bf16+fp16"), ("v5", "bf16"), ("v5", "fp32"),
+                                           ("v5", "bf16+fp16")])
 def test_whole_image_hit_masks(cuda_device, tag, precision):
     from paper_1911_13225_b300 import api
     spec, Ws, bs, Z, cams = _view(tag)
     dec = gpu_decoder(spec, Ws, bs)
     ws = api.Workspace(api.n_pixels(cams), 50)
-    res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), cams,
-                    api.TraceParams(precision=precision), ws)
+    # "bf16+fp16": the BF16 march with its FP16 stage (eps_mid 2e-4)
+    params = (api.TraceParams(precision="bf16", eps_mid=2e-4) if precision == "bf16+fp16"
+              else api.TraceParams(precision=precision))
+    res = api.trace(dec, torch.from_numpy(Z).to(cuda_device), cams, params, ws)
     assert dec.device_error() == 0
     g = _golden(tag)
     mask = to_np(res.mask).astype(bool)

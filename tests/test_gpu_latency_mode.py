@@ -44,6 +44,18 @@ def _assert_identical(out):
         assert np.array_equal(a.view(np.uint8), b.view(np.uint8)), f
 
 
+def test_bitwise_same_trace_with_fp16_stage(cuda_device):
+    """The BF16 march with an FP16 stage (three row lists in both decoder
+    kernels): identical results with and without the latency mode."""
+    vps = synth.random_viewpoints(2, seed=17)
+    cams = [synth.look_at_camera(vps[0], 96, 96, shape=0),
+            synth.look_at_camera(vps[1], 64, 48, shape=1)]
+    out, _ = _run(cuda_device, synth.DEEPSDF_SPEC, cams, n_shapes=2, precision="bf16",
+                  eps_mid=2e-4, k_min=3)
+    assert out[1]["mask"].sum() > 500
+    _assert_identical(out)
+
+
 @pytest.mark.parametrize("precision", ["bf16", "fp16", "fp32_tc"])
 @pytest.mark.parametrize("levels", [0, 2])
 def test_bitwise_same_trace_with_and_without(cuda_device, precision, levels):

@@ -187,6 +187,55 @@ def test_tensor_core_trace_depth_within_2e3(cuda_device, size, vp_seed, precisio
     assert q[0] > 0 and q[1] > 0
 
 
+@pytest.mark.parametrize("eps_mid", [2e-4, 4e-4])
+@pytest.mark.parametrize("size,vp_seed", [(64, 3), (96, 8)])
+def test_bf16_march_with_fp16_stage(cuda_device, size, vp_seed, eps_mid):
+    """BF16 march, FP16 queries once the BF16 |f| < 1e-3, FP32-class
+    queries once the FP16 |f| < eps_mid, convergence at eps = 5e-5: the same
+    bars as the two-stage march (masks bit-exact away from the silhouette
+    rays at the 1e-3 |SDF| margin, depth within 2e-3), with fewer
+    FP32-class queries than without the FP16 stage."""
+    from paper_1911_13225_b300 import api
+    spec = synth.DEEPSDF_SPEC
+    Ws, bs, Z = workload(spec, seed=0, n_shapes=1)
+    dec = gpu_decoder(spec, Ws, bs)
+    cam = synth.look_at_camera(synth.random_viewpoints(1, seed=vp_seed)[0], size, size)
+    ws = api.Workspace(size * size, 50)
+    z = torch.from_numpy(Z).to(cuda_device)
+    res = api.trace(dec, z, [cam], api.TraceParams(precision="bf16", eps_mid=eps_mid), ws)
+    two = api.trace(dec, z, [cam], api.TraceParams(precision="bf16"), ws)
+    assert dec.device_error() == 0
+    orc, shifted = _oracle_view(size, vp_seed)
+    ok = ~silhouette_rays(orc, shifted)
+    mask = to_np(res.mask).astype(bool)
+    assert np.array_equal(mask[ok], orc["mask"][ok])
+    hit = ok & orc["mask"]
+    assert hit.sum() > 100
+    assert np.max(np.abs(to_np(res.depth)[hit] - orc["depth"][hit])) < 2e-3
+    assert np.array_equal(to_np(res.sil) < 0, mask)
+    q, q2 = to_np(res.queries), to_np(two.queries)
+    assert q[1] < q2[1], (q, q2)
+
+
+def test_fp16_stage_arguments(cuda_device):
+    from paper_1911_13225_b300 import api
+    from paper_1911_13225_b300._abi import DistError
+    spec = synth.DEEPSDF_SPEC
+    Ws, bs, Z = workload(spec)
+    dec = gpu_decoder(spec, Ws, bs)
+    ws = api.Workspace(64 * 64, 50)
+    z = torch.from_numpy(Z).to(cuda_device)
+    cam = synth.look_at_camera((0.0, 0.0, 2.5), 64, 64)
+    for kw in (dict(eps_mid=1e-3), dict(eps_mid=2e-3), dict(eps_mid=-1e-4),
+               dict(eps_mid=2e-4, coarse_levels=2), dict(eps_mid=2e-4, refine_steps=1),
+               dict(eps_mid=2e-4, refine_engine="simt"), dict(eps_mid=2e-4, refine_rule="secant")):
+        with pytest.raises(DistError):
+            api.trace(dec, z, [cam], api.TraceParams(precision="bf16", **kw), ws)
+    # other precisions ignore it
+    api.trace(dec, z, [cam], api.TraceParams(precision="fp16", eps_mid=2e-4), ws)
+    assert dec.device_error() == 0
+
+
 def test_all_rays_miss_the_sphere(cuda_device):
     from paper_1911_13225_b300 import api
     spec = synth.SMALL_SPEC
