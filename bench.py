@@ -186,7 +186,8 @@ def run_ours(args, rank, world, local_rank):
                              refine_steps=args.refine, alpha_refine=args.alpha_refine,
                              refine_engine=args.refine_engine, refine_rule=args.refine_rule,
                              coarse_levels=args.coarse_levels,
-                             latency_mode=args.latency_mode)
+                             latency_mode=args.latency_mode,
+                             eps_mid=args.eps_mid if precision == "bf16" else 0.0)
     ws = api.Workspace(SIZE * SIZE, MAX_STEPS)
     z = torch.from_numpy(Z).to(dev)
     # target: depth of the second latent (untimed setup)
@@ -276,6 +277,7 @@ def run_ours(args, rank, world, local_rank):
         peak = peaks["bf16_tflops"]
         roof = {"bound": "tensor",
                 "kernel": f"mlp_tc_kernel ({precision.upper()} tcgen05 decoder"
+                          + (" + FP16-stage rows" if fused and params.eps_mid > 0 else "")
                           + (" + FP32-class rows in the same launch" if fused else "")
                           + "; fp16 and bf16 share the dense tensor rate)"
                           + (" with mlp_tc_wide_kernel on the march's small steps"
@@ -326,7 +328,8 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic (seeded decoder, latents and camera; no DeepSDF weights)",
         "config": {"workload": WORKLOAD.replace("512x512", f"{SIZE}x{SIZE}"),
                    "rays_per_step": rays, "precision": precision,
-                   "eps_lo": args.eps_lo, "refine_steps": args.refine,
+                   "eps_lo": args.eps_lo, "eps_mid": args.eps_mid if precision == "bf16" else 0.0,
+                   "refine_steps": args.refine,
                    "refine_engine": args.refine_engine, "refine_rule": args.refine_rule,
                    "coarse_levels": args.coarse_levels, "latency_mode": args.latency_mode,
                    "normals": "rendered (analytic, adjoint at the hits)" if args.normals
@@ -367,12 +370,18 @@ def run_ours(args, rank, world, local_rank):
         if precision == "bf16" and args.refine == 0:
             line["fp16"] = fp16_rate(api, dec, ws, cam, params, z, tgt, stream, flush,
                                      args.steps, args.normals)
+            if params.eps_mid > 0:
+                line["bf16_without_fp16_stage"] = two_stage_rate(api, dec, ws, cam, params, z, tgt,
+                                                                 stream, flush, args.steps,
+                                                                 args.normals)
     line["roofline"]["large_launch"] = large_launch_rate(api, dec, z, precision, peaks["bf16_tflops"])
     if not args.no_side_configs and SIZE == 512:
         line["five_views_256"] = five_views_rate(api, dec, z, stream, flush)
         line["inverse_32x8_224"] = inverse_rate(api, dec, spec, dev, args.inverse_steps)
     if not args.no_serve:
-        line["serving"] = run_serving(args, dec, params, dev)
+        import dataclasses
+        # (the server's march is the two-stage one: no FP16 stage)
+        line["serving"] = run_serving(args, dec, dataclasses.replace(params, eps_mid=0.0), dev)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.cpu_crop)
     return line
@@ -442,7 +451,8 @@ def coarse_to_fine_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps,
     start at 1/4 resolution per side, split every ray into four after every
     three iterations), timed like the main line."""
     import dataclasses
-    p2 = dataclasses.replace(params, coarse_levels=2, coarse_every=3)
+    # (coarse-to-fine runs the two-stage march: no FP16 stage)
+    p2 = dataclasses.replace(params, coarse_levels=2, coarse_every=3, eps_mid=0.0)
     ms, q, hits, _ = variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals)
     return {"value": SIZE * SIZE / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
             "coarse_levels": 2, "coarse_every": 3,
@@ -468,6 +478,18 @@ def fp16_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps, normals):
             "note": "FP16 GEMM operands (same tensor rate as BF16), FP32-class convergence after "
                     "the hand-over; on this view depth vs the FP32 trace q99 7.8e-5 (BF16 "
                     "default: 1.2e-4)"}
+
+
+def two_stage_rate(api, dec, ws, cam, params, z, tgt, stream, flush, steps, normals):
+    """The same fwd+bwd step with the BF16 march handing over straight to the
+    FP32-class queries (no FP16 stage), timed like the main line."""
+    import dataclasses
+    p2 = dataclasses.replace(params, eps_mid=0.0)
+    ms, q, hits, acc = variant_rate(api, dec, ws, cam, p2, z, tgt, stream, flush, steps, normals)
+    return {"value": SIZE * SIZE / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
+            "eps_mid": 0.0, "queries_per_step": {"lowp": float(q[0]), "fp32": float(q[1])},
+            "hits": hits, "accuracy_vs_oracle": acc,
+            "note": "BF16 march, FP32-class queries from |f| < eps_lo on (the FP16 stage off)"}
 
 
 def fp32_trace_rate(api, dec, cam, z, tgt, stream, steps=3):
@@ -874,6 +896,9 @@ def main():
                     help="step rule of the FP32-class queries after a BF16/FP16 hand-over")
     ap.add_argument("--eps-lo", type=float, default=1e-3,
                     help="|f| below which a BF16/FP16 ray switches to FP32 queries")
+    ap.add_argument("--eps-mid", type=float, default=2e-4,
+                    help="BF16 march: > 0 = FP16 queries between the BF16 march and the "
+                         "FP32-class queries, handing over at this |f|")
     ap.add_argument("--refine", type=int, default=0,
                     help="0: FP32 convergence to eps; n: accept after n FP32 queries")
     ap.add_argument("--alpha-refine", type=float, default=0.0,
