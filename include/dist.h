@@ -133,12 +133,6 @@ dist_status dist_decoder_device_error(const dist_decoder* dec, int32_t* code);
  * normally again once withhold_copies is 0.  Host-side state; set it only
  * while no call of this decoder is running. */
 dist_status dist_decoder_set_wait_limit(dist_decoder* dec, uint64_t wait_ns, int withhold_copies);
-/* Not from the paper: kernel variant of the tensor-core forward.  enable = 1
- * runs it on CTA pairs that share each MMA (2-SM tensor core instructions,
- * each SM streaming half of every weight tile); 0 (the default, faster on
- * B300) runs one CTA per tile.  Results are bitwise identical.
- * DIST_E_UNSUPPORTED for a decoder without the tensor-core path. */
-dist_status dist_decoder_set_tc_pair(dist_decoder* dec, int enable);
 
 /* ----------------------------------------------------------------- camera */
 
@@ -203,7 +197,7 @@ typedef struct {
                           64 FP32-class rays each) as four-SM clusters fit
                           on the GPU at once (at most 37) spreads each tile over
                           four SMs, a quarter of every layer's columns per
-                          SM; 0 = one tile per SM (pair) throughout.  Both
+                          SM; 0 = one tile per SM throughout.  Both
                           give the same f for every query.                   */
   float eps_mid;       /* BF16 march only: 0 (default) = a ray whose BF16
                           |f| < eps_bf16 goes straight to FP32-class

@@ -29,7 +29,7 @@ REQ_RENDER, REQ_RENDER_BACKWARD = 0, 1
 # every entry point include/dist.h declares
 EXPORTS = [
     "dist_decoder_create", "dist_decoder_destroy", "dist_decoder_has_bf16",
-    "dist_decoder_device_error", "dist_decoder_set_tc_pair", "dist_profile_enable",
+    "dist_decoder_device_error", "dist_profile_enable",
     "dist_profile_read",
     "dist_trace_params_default", "dist_workspace_create", "dist_workspace_destroy",
     "dist_trace_fwd", "dist_render_normals", "dist_sdf_eval", "dist_loss", "dist_trace_bwd",
@@ -97,7 +97,6 @@ def lib():
         "dist_decoder_destroy": (c_int, [c_void_p]),
         "dist_decoder_has_bf16": (c_int, [c_void_p]),
         "dist_decoder_device_error": (c_int, [c_void_p, POINTER(ctypes.c_int32)]),
-        "dist_decoder_set_tc_pair": (c_int, [c_void_p, c_int]),
         "dist_decoder_set_wait_limit": (c_int, [c_void_p, c_uint64, c_int]),
         "dist_profile_enable": (c_int, [c_int]),
         "dist_profile_read": (c_int, [POINTER(c_double), POINTER(c_int64), POINTER(c_int64)]),

@@ -123,11 +123,6 @@ class Decoder:
         check(lib().dist_decoder_set_wait_limit(self.handle, int(wait_ns), int(bool(withhold_copies))),
               "dist_decoder_set_wait_limit")
 
-    def set_tc_pair(self, enable: bool) -> None:
-        """Tensor-core forward on CTA pairs (2-SM MMAs) or one CTA per tile (default)."""
-        check(lib().dist_decoder_set_tc_pair(self.handle, int(bool(enable))),
-              "dist_decoder_set_tc_pair")
-
     def close(self):
         if self.handle:
             lib().dist_decoder_destroy(self.handle)

@@ -168,13 +168,6 @@ dist_status dist_decoder_destroy(dist_decoder* d) {
 
 int dist_decoder_has_bf16(const dist_decoder* d) { return d && d->tc.ok ? 1 : 0; }
 
-dist_status dist_decoder_set_tc_pair(dist_decoder* d, int enable) {
-  DIST_CHECK(d, DIST_E_INVALID, "dist_decoder_set_tc_pair: NULL decoder");
-  DIST_CHECK(d->tc.ok, DIST_E_UNSUPPORTED, "dist_decoder_set_tc_pair: no tensor-core path");
-  d->tc.pair = enable != 0;
-  return DIST_OK;
-}
-
 dist_status dist_decoder_device_error(const dist_decoder* d, int32_t* code) {
   DIST_CHECK(d && code, DIST_E_INVALID, "dist_decoder_device_error: NULL argument");
   *code = 0;

@@ -147,10 +147,8 @@ struct DecoderTC {
   TCMaps bmaps;                  // W_l^T for the adjoint's backward GEMMs (bf16)
   TCMaps bmaps16;                // same, fp16
   TCMaps xmaps;                  // [N][2K] fp16 hi | lo split of 2^s_l W_l (FP32-class kernel)
-  TCMaps pmaps, pmaps16, pxmaps; // the same three with 128-row boxes (CTA-pair kernel)
   TCMaps wmaps, wmaps16, wxmaps; // the same three as 3D views [K/64][N][64] with boxes of
                                  // two 128-row x 64-column chunks (latency-mode kernel)
-  bool pair;                     // forward kernel on CTA pairs (cta_group::2)
   float x_inv_scale[7];          // 2^-s_l
   const TCConst* cst;            // epilogue constants (device)
   int* err;                      // device error word of the bounded waits

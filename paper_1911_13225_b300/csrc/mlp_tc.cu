@@ -71,7 +71,7 @@ struct TCArgs {
 
 constexpr int QPT_X = 64;        // FP32-class queries per tile
 
-// Tile of round r for CTA (pair) pid in a launch of npid: serpentine order.
+// Tile of round r for CTA pid in a launch of npid: serpentine order.
 // The FP32-class tiles (twice a 16-bit tile's work) come first in the tile
 // list, so odd rounds run backwards and hand their tiles to the CTAs that took
 // the cheaper tiles of the round before.  Increasing in r for a fixed pid.
@@ -99,20 +99,16 @@ __device__ __forceinline__ int tile_of(int r, int pid, int npid) {
 // (in the next tile's format), so the next tile's GEMMs overlap this tile's
 // head.
 //
-// PAIR: the CTAs run as clusters of two on the 2-SM tensor core path
-// (cta_group::2): a tile is 256 rows (128 FP32-class queries), 128 per CTA;
-// the even CTA issues M = 256 MMAs whose B operand (the weight stage, N =
-// 256) is split by rows between the two CTAs, so each SM streams half of
-// every weight tile.  Both CTAs load their half of each stage (completing on
-// the even CTA's full barrier), commits arrive on both CTAs' barriers, and
-// every epilogue warp of both CTAs arrives on the even CTA's act_full.
-template <bool F16, bool PAIR, bool COLOR>
+// (A CTA-pair variant -- cta_group::2, M = 256, each SM streaming half of
+// every weight stage -- measured slower on B300, 973 against 1,183 TFLOP/s
+// on large launches and 92 against 78 us for one tile: the cross-CTA
+// hand-offs cost more than the halved weight stream saves.  Not kept.)
+template <bool F16, bool COLOR>
 __global__ void __launch_bounds__(FWD_THREADS, 1)
 mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMaps xmaps,
               const __grid_constant__ TCMaps maps16, const TCArgs a) {
-  constexpr int NST = PAIR ? 2 * STAGES : STAGES;            // weight ring stages
-  constexpr int SB = PAIR ? STAGE_BYTES / 2 : STAGE_BYTES;   // bytes per stage per CTA
-  constexpr int MUL = PAIR ? 2 : 1;                          // CTAs per tile
+  constexpr int NST = STAGES;          // weight ring stages
+  constexpr int SB = STAGE_BYTES;      // bytes per stage
   static_assert((2 * NST + 10) * 8 + 8 <= BAR_BYTES, "barrier block");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -135,9 +131,8 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const unsigned long long wlim = a.wait_ns;
-  const int rank = PAIR ? (int)cluster_rank() : 0;          // 0: issues the pair's MMAs
-  const int pid = PAIR ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-  const int npid = PAIR ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+  const int pid = (int)blockIdx.x;
+  const int npid = (int)gridDim.x;
   // launched early behind the previous grid (programmatic dependent
   // launch): nothing it writes is read before this wait
   grid_dep_wait();
@@ -145,24 +140,23 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   const int n0 = rowsrc_count(a.src[0]);
   const int n1 = rowsrc_count(a.src[1]);
   const int n2 = rowsrc_count(a.src[2]);
-  const int t1 = (n1 + MUL * QPT_X - 1) / (MUL * QPT_X);   // FP32-class tiles: [0, t1)
-  const int t2 = t1 + (n2 + MUL * BM - 1) / (MUL * BM);     // FP16-stage tiles: [t1, t2)
-  const int n_tiles = t2 + (n0 + MUL * BM - 1) / (MUL * BM);
-  if (pid >= n_tiles) return;                               // uniform over a pair
+  const int t1 = (n1 + QPT_X - 1) / QPT_X;   // FP32-class tiles: [0, t1)
+  const int t2 = t1 + (n2 + BM - 1) / BM;     // FP16-stage tiles: [t1, t2)
+  const int n_tiles = t2 + (n0 + BM - 1) / BM;
+  if (pid >= n_tiles) return;
   // a launch small enough for the latency mode (its tiles: 128 16-bit rows
   // or 64 FP32-class queries) runs there instead, launched right behind this
   if (a.wide_tiles > 0 &&
       (n1 + 63) / 64 + (n2 + BM - 1) / BM + (n0 + BM - 1) / BM <= a.wide_tiles)
     return;
-  if (a.fuse_step && a.step.queries && pid == 0 && rank == 0 && threadIdx.x == 0) {
+  if (a.fuse_step && a.step.queries && pid == 0 && threadIdx.x == 0) {
     atomicAdd(a.step.queries + 0, (unsigned long long)(n0 + n2));
     atomicAdd(a.step.queries + 1, (unsigned long long)n1);
   }
   // row list of tile t, and the first row of its list in this CTA
   auto tile_list = [&](int t) { return t < t1 ? 1 : (t < t2 ? 2 : 0); };
   auto tile_row0 = [&](int t) {
-    return t < t1 ? (t * MUL + rank) * QPT_X
-                  : ((t - (t < t2 ? t1 : t2)) * MUL + rank) * BM;
+    return t < t1 ? t * QPT_X : (t - (t < t2 ? t1 : t2)) * BM;
   };
 
   if (threadIdx.x == 0) {
@@ -171,7 +165,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       mbar_init(empty + s, 1);
     }
     for (int h = 0; h < 2; ++h) mbar_init(acc_full + h, 1);
-    for (int q = 0; q < 4; ++q) mbar_init(act_full + q, MUL * FWD_EPI);
+    for (int q = 0; q < 4; ++q) mbar_init(act_full + q, FWD_EPI);
     mbar_init(drain, 1);
     mbar_init(head_bar, (FWD_EPI - 4) * 32);
     mbar_init(step_full, 4);
@@ -179,13 +173,9 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) {
-    if (PAIR) tmem_alloc_pair(tmem_slot, 512);
-    else tmem_alloc(tmem_slot, 512);
-  }
+  if (warp == 1) tmem_alloc(tmem_slot, 512);
   tc_fence_before();
   __syncthreads();
-  if (PAIR) cluster_sync_all();   // the even CTA's barriers exist before the odd one uses them
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
@@ -198,7 +188,6 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       bool issued[NST];
       for (int s = 0; s < NST; ++s) issued[s] = false;
       bool ok = true;
-      const uint32_t full_lead = PAIR ? map_rank(smem_u32(full), 0u) : 0u;
       // (a.withhold, tests only: no copy is issued, so the MMA warp's first
       // wait for a weight stage runs out and the CTA takes its abort path)
       for (int r = 0, tile = pid; ok && !a.withhold && tile < n_tiles;
@@ -211,15 +200,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
             for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
               if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag, wlim)) { ok = false; break; }
-              if (rank == 0) mbar_expect_tx(full + stage, MUL * SB);
+              mbar_expect_tx(full + stage, SB);
               // FP32-class: the W_lo pass (columns K..2K-1) first, then W_hi
               const int xk = !xt ? kc : (kc < nkc ? nkc + kc : kc - nkc);
-              if (PAIR) {
-                tma_load_2d_pair(wst + stage * SB, map, full_lead + 8u * (uint32_t)stage,
-                                 xk * BK, nh * BN + 128 * rank);
-              } else {
-                tma_load_2d(wst + stage * SB, map, full + stage, xk * BK, nh * BN);
-              }
+              tma_load_2d(wst + stage * SB, map, full + stage, xk * BK, nh * BN);
               issued[stage] = true;
               issued_parity[stage] = phase;
               if (++stage == NST) { stage = 0; phase ^= 1u; }
@@ -231,10 +215,8 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
         *abort_flag = 1;
         atomicOr(a.err, 1);
       }
-      // every issued copy must land before the CTA exits (the odd CTA of a
-      // pair cannot see its copies land: the even one waits for both halves
-      // and the pair synchronises before exit)
-      for (int s = 0; s < NST && rank == 0; ++s) {
+      // every issued copy must land before the CTA exits
+      for (int s = 0; s < NST; ++s) {
         if (!issued[s]) continue;
         const unsigned long long t0 = globaltimer();
         while (!mbar_try_wait(full + s, issued_parity[s]) && globaltimer() - t0 < kTimeoutNs) {
@@ -243,27 +225,22 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     }
   } else if (warp == 1) {
     // ------------------------------------------------------- MMA issuer
-    if (lane == 0 && rank == 0) {
+    if (lane == 0) {
       int stage = 0;
       uint32_t phase = 0;
       uint32_t act_phase[4] = {0u, 0u, 0u, 0u};
       bool ok = true;
-      auto commit = [&](uint64_t* bar) {
-        if (PAIR) mma_commit_pair(bar);
-        else mma_commit(bar);
-      };
+      auto commit = [&](uint64_t* bar) { mma_commit(bar); };
       for (int r = 0, tile = pid; ok && tile < n_tiles; tile = tile_of(++r, pid, npid)) {
         const bool xt = tile < t1;
-        const uint32_t idesc = instr_desc_m(xt || F16 || tile_list(tile) == 2, MUL * BM);
+        const uint32_t idesc = instr_desc_m(xt || F16 || tile_list(tile) == 2, BM);
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
           const int nkc = gemm_k(g) / BK;
           for (int nh = 0; ok && nh < gemm_n(g) / BN; ++nh) {
             for (int kc = 0; kc < (xt ? 2 : 1) * nkc; ++kc) {
               if (nh == 0 && kc < nkc && (kc & 1) == 0) {
                 const int q = kc >> 1;
-                const bool got = PAIR ? mbar_wait_cl(act_full + q, act_phase[q], abort_flag, wlim)
-                                      : mbar_wait(act_full + q, act_phase[q], abort_flag, wlim);
-                if (!got) { ok = false; break; }
+                if (!mbar_wait(act_full + q, act_phase[q], abort_flag, wlim)) { ok = false; break; }
                 act_phase[q] ^= 1u;
                 tc_fence_after();
               }
@@ -272,14 +249,9 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
               const uint32_t a_base = smem_u32(act + (kc < nkc ? kc : kc - nkc) * CHUNK_BYTES);
               const uint32_t b_base = smem_u32(wst + stage * SB);
 #pragma unroll
-              for (int k = 0; k < BK / 16; ++k) {
-                if (PAIR)
-                  mma_pair(tmem + (uint32_t)(nh * BN), sw128_desc(a_base + 32 * k),
-                           sw128_desc(b_base + 32 * k), idesc, (kc | k) != 0);
-                else
-                  mma_bf16(tmem + (uint32_t)(nh * BN), sw128_desc(a_base + 32 * k),
-                           sw128_desc(b_base + 32 * k), idesc, (kc | k) != 0);
-              }
+              for (int k = 0; k < BK / 16; ++k)
+                mma_bf16(tmem + (uint32_t)(nh * BN), sw128_desc(a_base + 32 * k),
+                         sw128_desc(b_base + 32 * k), idesc, (kc | k) != 0);
               commit(empty + stage);
               if (++stage == NST) { stage = 0; phase ^= 1u; }
             }
@@ -392,16 +364,12 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       tc_fence_after();
       return true;
     };
-    // one arrival per warp on act_full[q] (in a pair, the even CTA's)
-    const uint32_t act_full_lead = PAIR ? map_rank(smem_u32(act_full), 0u) : 0u;
+    // one arrival per warp on act_full[q]
     auto release = [&](int q) {
       fence_async_shared();
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) {
-        if (PAIR) mbar_arrive_remote(act_full_lead + 8u * (uint32_t)q);
-        else mbar_arrive(act_full + q);
-      }
+      if (lane == 0) mbar_arrive(act_full + q);
     };
     // operand words of quarter q: 16 packed pairs (16-bit tile) or 8 hi + 8
     // lo pairs (FP32-class tile), written to the operand tile by put()
@@ -637,10 +605,8 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
-    if (PAIR) tmem_dealloc_pair(tmem, 512);
-    else tmem_dealloc(tmem, 512);
+    tmem_dealloc(tmem, 512);
   }
-  if (PAIR) cluster_sync_all();   // neither CTA leaves while its peer may still use it
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -1104,11 +1070,6 @@ dist_status pack_tcx(dist_decoder* d, const float* const* W) {
                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (split weights)");
-    cuuint32_t pbox[2] = {(cuuint32_t)BK, (cuuint32_t)(BN / 2)};
-    r = enc(&d->tc.pxmaps.m[g], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, q, dims, strides, pbox, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (split, half box)");
     // 3D view for the latency mode: one copy brings two 64-column chunks of
     // 128 rows (a TMA copy costs ~160 ns whether it moves 16 or 32 KB)
     {
@@ -1197,13 +1158,6 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed");
-      cuuint32_t pbox[2] = {(cuuint32_t)BK, (cuuint32_t)(BN / 2)};
-      CUtensorMap* mp = f16 ? &d->tc.pmaps16.m[g] : &d->tc.pmaps.m[g];
-      r = enc(mp, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, p,
-              dims, strides, pbox, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-      DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (half box)");
       {
         cuuint64_t d3[3] = {(cuuint64_t)BK, (cuuint64_t)N, (cuuint64_t)(K / BK)};
         cuuint64_t s3[2] = {(cuuint64_t)K * sizeof(uint16_t), (cuuint64_t)BK * sizeof(uint16_t)};
@@ -1242,41 +1196,32 @@ dist_status pack_tc(dist_decoder* d, const float* const* W, const float* const* 
   d->allocations.push_back(e);
   DIST_CUDA_TRY(cudaMemset(e, 0, sizeof(int)));
   d->tc.err = static_cast<int*>(e);
-  // measured on B300: the CTA-pair variant is slower (973 vs 1183 TFLOP/s on
-  // large launches, 92 vs 78 us for one tile), so one CTA per tile is the default
-  d->tc.pair = false;
   d->tc.wait_ns = kTimeoutNs;
   d->tc.withhold = 0;
   d->tc.ok = true;
   return DIST_OK;
 }
 
-template <bool F16, bool PAIR, bool COLOR = false>
+template <bool F16, bool COLOR = false>
 cudaError_t launch_fused(const dist_decoder* dec, const TCArgs& a, cudaStream_t st) {
   // set once per process (thread-safe static initialisation)
   static const cudaError_t configured = cudaFuncSetAttribute(
-      mlp_tc_kernel<F16, PAIR, COLOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, FWD_SMEM_BYTES);
+      mlp_tc_kernel<F16, COLOR>, cudaFuncAttributeMaxDynamicSharedMemorySize, FWD_SMEM_BYTES);
   if (configured != cudaSuccess) return configured;
-  const TCMaps& maps = PAIR ? (F16 ? dec->tc.pmaps16 : dec->tc.pmaps)
-                            : (F16 ? dec->tc.maps16 : dec->tc.maps);
-  const TCMaps& xmaps = PAIR ? dec->tc.pxmaps : dec->tc.xmaps;
-  const TCMaps& maps16 = PAIR ? dec->tc.pmaps16 : dec->tc.maps16;   // FP16-stage tiles
+  const TCMaps& maps = F16 ? dec->tc.maps16 : dec->tc.maps;
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(PAIR ? (num_sms() / 2) * 2 : num_sms());
+  cfg.gridDim = dim3(num_sms());
   cfg.blockDim = dim3(FWD_THREADS);
   cfg.dynamicSmemBytes = FWD_SMEM_BYTES;
   cfg.stream = st;
-  cudaLaunchAttribute attr[2];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = PAIR ? 2 : 1;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[1].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 2;
-  cudaError_t e =
-      cudaLaunchKernelEx(&cfg, mlp_tc_kernel<F16, PAIR, COLOR>, maps, xmaps, maps16, a);
+  cfg.numAttrs = 1;
+  // (dec->tc.maps16 also serves the FP16-stage tiles of a BF16 march)
+  cudaError_t e = cudaLaunchKernelEx(&cfg, mlp_tc_kernel<F16, COLOR>, maps, dec->tc.xmaps,
+                                     dec->tc.maps16, a);
   count_launch(1);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -1308,11 +1253,7 @@ cudaError_t mlp_tc_fused(const dist_decoder* dec, const RowSrc& src16, float* f1
   a.wide_tiles = (step && step->wide) ? tc_wide_max_tiles() : 0;
   a.wait_ns = dec->tc.wait_ns;
   a.withhold = dec->tc.withhold;
-  cudaError_t e;
-  if (dec->tc.pair)
-    e = f16 ? launch_fused<true, true>(dec, a, st) : launch_fused<false, true>(dec, a, st);
-  else
-    e = f16 ? launch_fused<true, false>(dec, a, st) : launch_fused<false, false>(dec, a, st);
+  cudaError_t e = f16 ? launch_fused<true>(dec, a, st) : launch_fused<false>(dec, a, st);
   if (e != cudaSuccess || a.wide_tiles <= 0) return e;
   return mlp_tc_wide(dec, src16, f16out, srcx, fxout, bfold0, bfolds, st, f16, step, step->wide,
                      srcm, fmout);
@@ -1334,8 +1275,7 @@ cudaError_t mlp_tc_color(const dist_decoder* dec, const RowSrc& src, const float
   a.cpart = cpart;
   a.wait_ns = dec->tc.wait_ns;
   a.withhold = dec->tc.withhold;
-  return f16 ? launch_fused<true, false, true>(dec, a, st)
-             : launch_fused<false, false, true>(dec, a, st);
+  return f16 ? launch_fused<true, true>(dec, a, st) : launch_fused<false, true>(dec, a, st);
 }
 
 cudaError_t mlp_tc_forward(const dist_decoder* dec, const RowSrc& src, const float* bfold0,

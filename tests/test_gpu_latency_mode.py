@@ -128,31 +128,3 @@ def test_invalid_latency_mode(cuda_device):
     cam = synth.look_at_camera((0.0, 0.0, 2.5), 8, 8)
     with pytest.raises(DistError):
         api.trace(dec, z, [cam], api.TraceParams(precision="bf16", latency_mode=2), ws)
-
-
-@pytest.mark.parametrize("precision", ["bf16", "fp32_tc"])
-def test_cta_pair_kernel_with_latency_mode(cuda_device, precision):
-    """With the opt-in CTA-pair variant of the one-tile-per-SM kernel the
-    latency mode's tiles (128 rows, 64 FP32-class queries) differ from the
-    pair's (256 rows, 128 queries): the hand-over between the two kernels
-    uses the latency mode's tile count on both sides, and the trace is still
-    the same bit for bit as with the latency mode off (and as without pairs)."""
-    from paper_1911_13225_b300 import api
-    spec = synth.DEEPSDF_SPEC
-    Ws, bs, Z = workload(spec)
-    dec = gpu_decoder(spec, Ws, bs)
-    z = torch.from_numpy(Z).to(cuda_device)
-    cam = synth.look_at_camera(synth.random_viewpoints(1, seed=9)[0], 96, 96)
-    ws = api.Workspace(96 * 96, 50)
-    out = {}
-    for pair in (True, False):
-        dec.set_tc_pair(pair)
-        for mode in (1, 0):
-            res = api.trace(dec, z, [cam], api.TraceParams(precision=precision, latency_mode=mode),
-                            ws)
-            torch.cuda.synchronize()
-            assert dec.device_error() == 0
-            out[(pair, mode)] = {f: to_np(getattr(res, f)) for f in FIELDS}
-    dec.set_tc_pair(False)
-    for key in out:
-        _assert_identical({1: out[key], 0: out[(False, 0)]})
