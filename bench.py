@@ -376,6 +376,7 @@ def run_ours(args, rank, world, local_rank):
                                                                  args.normals)
     line["roofline"]["large_launch"] = large_launch_rate(api, dec, z, precision, peaks["bf16_tflops"])
     if not args.no_side_configs and SIZE == 512:
+        line["small_32x32"] = small_rate(dev, stream)
         line["five_views_256"] = five_views_rate(api, dec, z, stream, flush)
         line["inverse_32x8_224"] = inverse_rate(api, dec, spec, dev, args.inverse_steps)
     if not args.no_serve:
@@ -540,6 +541,39 @@ def large_launch_rate(api, dec, z, precision, peak, n=262144 * 2, reps=5):
 
 
 # ------------------------------------------ the other configurations' lines
+
+def small_rate(dev, stream, steps=20):
+    """The small configuration: a 4 x 128 decoder (latent 64, no skip),
+    32 x 32 image from (0, 0, 2.5), FP32 forward trace (depth, normals, mask),
+    50 steps -- latency-bound: a few tiles per step."""
+    import torch
+    import synth
+    from paper_1911_13225_b300 import api
+    spec = synth.SMALL_SPEC
+    Ws, bs = synth.make_decoder(spec, seed=0)
+    Z = synth.make_latents(spec, 1, seed=0)
+    dec = api.Decoder.from_spec(spec, Ws, bs)
+    cam = synth.look_at_camera((0.0, 0.0, 2.5), 32, 32)
+    ws = api.Workspace(32 * 32, MAX_STEPS)
+    z = torch.from_numpy(Z).to(dev)
+    p = api.TraceParams(max_steps=MAX_STEPS)
+    res = api.alloc_result(32 * 32, 1, dev, normals=True)
+    cam_c = api.camera_array([cam])
+    for _ in range(3):
+        api.trace(dec, z, [cam], p, ws, normals=True, out=res, cam_c=cam_c, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        api.trace(dec, z, [cam], p, ws, normals=True, out=res, cam_c=cam_c, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"value": 32 * 32 / (ms * 1e-3), "unit": "rays/s", "ms_per_step": ms,
+            "hits": int(res.mask.sum().item()),
+            "note": "4x128 decoder, latent 64, 32x32 from (0, 0, 2.5), FP32 forward with analytic "
+                    "normals, 50 steps; back-to-back traces (inputs L2-resident)"}
+
 
 def five_views_rate(api, dec, z, stream, flush, steps=5):
     """Forward trace of 5 seeded viewpoints (radius 2.5) at 256x256 in one

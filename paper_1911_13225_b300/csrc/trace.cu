@@ -990,40 +990,44 @@ struct LossArgs {
 };
 
 // Per-pixel loss terms and upstream gradients (Sec. B.3; silhouette Eq. 4 of
-// Sec. A.3); FP64 block sums.
+// Sec. A.3); FP64 block sums.  The means' weights w / |M| and w / n are
+// formed once per thread (FP64 division is slow on B300) and each term's
+// pixel sum is scaled by them at the end.
 __global__ void loss_terms_kernel(LossArgs a) {
   __shared__ double sh[32];
-  const double nM = (double)max(*a.cnt, 1);
-  const double nA = (double)a.n;
-  double acc = 0.0;
+  const double sd = (double)a.w.w_depth / (double)max(*a.cnt, 1);
+  const double sn = (double)a.w.w_normal / (double)max(*a.cnt, 1);
+  const double ss = (double)a.w.w_sil / (double)a.n;
+  const float gd = (float)sd;
+  double acc_d = 0.0, acc_n = 0.0, acc_s = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < a.n;
        i += (long long)gridDim.x * blockDim.x) {
     const bool M = a.mask[i] && isfinite(a.tgt_depth[i]);
     if (a.w.w_depth != 0.f) {
       const double r = M ? (double)a.depth[i] - (double)a.tgt_depth[i] : 0.0;
-      acc += a.w.w_depth * fabs(r) / nM;
-      a.g_depth[i] = (float)(a.w.w_depth * (r > 0 ? 1.0 : (r < 0 ? -1.0 : 0.0)) / nM);
+      acc_d += fabs(r);
+      a.g_depth[i] = r > 0 ? gd : (r < 0 ? -gd : 0.f);
     } else if (a.g_depth) {
       a.g_depth[i] = 0.f;
     }
     if (a.w.w_normal != 0.f) {
       double dot = 0.0;
       for (int e = 0; e < 3; ++e) dot += (double)a.normal[3 * i + e] * (double)a.tgt_normal[3 * i + e];
-      if (M) acc += -a.w.w_normal * dot / nM;
+      if (M) acc_n -= dot;
       for (int e = 0; e < 3; ++e)
-        a.g_normal[3 * i + e] = M ? (float)(-a.w.w_normal * a.tgt_normal[3 * i + e] / nM) : 0.f;
+        a.g_normal[3 * i + e] = M ? (float)(-sn * a.tgt_normal[3 * i + e]) : 0.f;
     } else if (a.g_normal) {
       for (int e = 0; e < 3; ++e) a.g_normal[3 * i + e] = 0.f;
     }
     if (a.w.w_sil != 0.f) {
       const double S = a.sil[i], Sg = a.tgt_sil[i];
-      acc += a.w.w_sil * (Sg * fmax(0.0, S) + (1.0 - Sg) * fmax(0.0, -S)) / nA;
-      a.g_sil[i] = (float)(a.w.w_sil * (Sg * (S > 0 ? 1.0 : 0.0) - (1.0 - Sg) * (S < 0 ? 1.0 : 0.0)) / nA);
+      acc_s += Sg * fmax(0.0, S) + (1.0 - Sg) * fmax(0.0, -S);
+      a.g_sil[i] = (float)(ss * (Sg * (S > 0 ? 1.0 : 0.0) - (1.0 - Sg) * (S < 0 ? 1.0 : 0.0)));
     } else if (a.g_sil) {
       a.g_sil[i] = 0.f;
     }
   }
-  const double t = block_sum_d(acc, sh);
+  const double t = block_sum_d(sd * acc_d + sn * acc_n + ss * acc_s, sh);
   if (threadIdx.x == 0 && t != 0.0) atomicAdd(a.loss, t);
 }
 
@@ -1169,7 +1173,7 @@ dist_status validate_and_upload(const dist_decoder* dec, const float* z, int n_s
   }
   DIST_CHECK(n_pix <= ws->max_rays, DIST_E_INVALID, "more pixels than the workspace holds");
   const DecoderF32& d = dec->f32;
-  dim3 g(n_shapes, 2, (d.width + 63) / 64);
+  dim3 g(n_shapes, 2, (d.width + 7) / 8);   // one output per warp
   fold_bias_kernel<<<g, 256, 0, st>>>(d, z, n_shapes, ws->bfold, ws->bfold + kMaxShapes * 512);
   DIST_LAUNCH_CHECK();
   out->n_pix = n_pix;
@@ -1288,7 +1292,7 @@ dist_status normals_impl(const dist_decoder* dec, const dist_trace_params* p,
 // scratch memory instead of a workspace.
 cudaError_t launch_fold_bias(const DecoderF32& d, const float* z, int n_shapes, float* bfold0,
                              float* bfolds, cudaStream_t st) {
-  dim3 g(n_shapes, 2, (d.width + 63) / 64);
+  dim3 g(n_shapes, 2, (d.width + 7) / 8);   // one output per warp
   fold_bias_kernel<<<g, 256, 0, st>>>(d, z, n_shapes, bfold0, bfolds);
   count_launch(1);
   return cudaGetLastError();
@@ -1789,7 +1793,7 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
              "BF16 tensor-core MLP covers only the DeepSDF decoder shape");
   cudaStream_t st = (cudaStream_t)stream;
   const DecoderF32& d = dec->f32;
-  dim3 fg(n_shapes, 2, (d.width + 63) / 64);
+  dim3 fg(n_shapes, 2, (d.width + 7) / 8);
   fold_bias_kernel<<<fg, 256, 0, st>>>(d, z, n_shapes, ws->bfold, ws->bfold + kMaxShapes * 512);
   DIST_LAUNCH_CHECK();
   const float* b0 = ws->bfold;
