@@ -208,8 +208,7 @@ typedef struct {
                           sign with |f| < 16 eps_mid), so fewer queries pay
                           the FP32-class cost.  Needs refine_engine TC,
                           refine_steps 0, refine_rule MARCH, coarse_levels
-                          0; ignored for other precisions; the server
-                          rejects it.                                        */
+                          0; ignored for other precisions.                   */
 } dist_trace_params;
 
 /* Fill `p` with the paper's defaults: max_steps 50, eps 5e-5, alpha 1.5,
@@ -281,9 +280,11 @@ dist_status dist_render_normals(const dist_decoder* dec, const float* z, int n_s
 /* Evaluate the decoder f(p, z_shape) (Sec. 3.4: f_theta(p, z)) at n points:
  * pts: device float [n][3]; shape: device int32 [n] latent index per point;
  * f: device float [n]; grad: device float [n][3] = grad_p f, or NULL.
- * precision DIST_PREC_FP32 (SIMT kernels; grad allowed), DIST_PREC_BF16,
- * DIST_PREC_FP16 or DIST_PREC_FP32_TC (tensor-core kernels; grad must be
- * NULL).  n <= 10 * workspace max_rays.
+ * precision DIST_PREC_FP32 (SIMT kernels; grad allowed), DIST_PREC_BF16 or
+ * DIST_PREC_FP16 (tensor-core kernels; grad must be NULL), DIST_PREC_FP32_TC
+ * (tensor-core kernels with two-term FP16 operands; with grad, f and grad_p f
+ * both come from the FP32-class adjoint kernel, whose f may differ from the
+ * forward kernel's in the last bits).  n <= 10 * workspace max_rays.
  * Shape indices outside [0, n_shapes) are clamped into range.
  * Errors: DIST_E_INVALID, DIST_E_UNSUPPORTED, DIST_E_CUDA. */
 dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
@@ -373,7 +374,12 @@ dist_status dist_photo_loss(const dist_camera* cams, int n_cams, const float* de
  * (Sec. 3.4, B.2).  Silhouette: sign(f_min) df(p_min)/dz (Sec. A.3 with the
  * first-term rule).  Normal: needs normal_delta > 0; VJP of the central-
  * difference normal with the hit point held fixed.  The decoder is
- * re-evaluated at these points only (no per-step graph is stored).
+ * re-evaluated at these points only (no per-step graph is stored): the depth
+ * probes in the trace's precision (16-bit tensor-core adjoint after a BF16 or
+ * FP16 march, FP32-class tensor-core adjoint after FP32_TC, FP32 CUDA cores
+ * after FP32); the silhouette and central-difference probes at FP32-class
+ * accuracy whatever the march's (the FP32-class tensor-core adjoint where the
+ * trace's FP32-class queries run on the tensor cores, else FP32 CUDA cores).
  * Upstream gradients g_depth [n], g_normal [n][3], g_sil [n] are device
  * arrays or NULL.  Per-ray sums are reduced in FP64. */
 dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes,

@@ -147,6 +147,7 @@ struct DecoderTC {
   TCMaps bmaps;                  // W_l^T for the adjoint's backward GEMMs (bf16)
   TCMaps bmaps16;                // same, fp16
   TCMaps xmaps;                  // [N][2K] fp16 hi | lo split of 2^s_l W_l (FP32-class kernel)
+  TCMaps bxmaps;                 // [K][2N] its transpose (FP32-class adjoint)
   TCMaps wmaps, wmaps16, wxmaps; // the same three as 3D views [K/64][N][64] with boxes of
                                  // two 128-row x 64-column chunks (latency-mode kernel)
   float x_inv_scale[7];          // 2^-s_l
@@ -280,6 +281,7 @@ struct RayPool {
   dist_trace_out o;
   int K;
   float eps, alpha, eps_bf16, radius;
+  float eps_mid;      // FP16 stage of a BF16 march (0: none)
   int max_steps;
 };
 cudaError_t pool_write_cam(const CamDev& c, int slot, CamDev* dst, cudaStream_t st);
@@ -345,5 +347,28 @@ cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const floa
                            const int* count, const float* bfold0, const float* bfolds,
                            float* out4, double* gacc0, double* gaccs, int accumulate,
                            void* scratch, cudaStream_t st, bool f16);
+
+// Probes handed from the FP32-class adjoint to the FP32 one: device arrays
+// of `cap` entries, the device count (zeroed by the caller; it ends at most
+// at cap) and the |ReLU input| below which a probe is handed over.
+struct RedoList {
+  float4* p;
+  float4* q;
+  int* count;
+  int cap;
+  float tau;
+};
+
+// The same adjoint with FP32-class operands (two-term FP16 splits, 64 probes
+// per tile, four times a 16-bit probe's tensor work).  Its pre-activations
+// carry ~1e-6 of truncation error, so a ReLU input that close to 0 may take
+// the other side: with `redo`, such probes are left to the caller's FP32
+// adjoint (the gradient of a central-difference normal differences two
+// Jacobians 2 delta apart, and one flipped mask in either is amplified by
+// 1 / (2 delta)).
+cudaError_t mlp_tcx_adjoint(const dist_decoder* dec, const float4* pp, const float4* pq,
+                            const int* count, const float* bfold0, const float* bfolds,
+                            float* out4, double* gacc0, double* gaccs, int accumulate,
+                            void* scratch, cudaStream_t st, const RedoList* redo = nullptr);
 
 }  // namespace dist

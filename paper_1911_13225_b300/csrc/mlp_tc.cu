@@ -624,6 +624,13 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
 // The two column halves of a row meet through a small exchange buffer and
 // two mbarriers (half 1 -> half 0: head and gradient partial sums; half 0 ->
 // half 1: 1 - f^2 and the coefficient).
+//
+// FP32-class variant (X): 64 probes per tile in the forward kernel's hi / lo
+// row layout, every GEMM's K loop twice (W_lo, then W_hi; the backward
+// GEMMs over the transposed split), the lane pair of a probe adding its two
+// rows.  The backward operand g is scaled by 2^kGradExp before its split, so
+// that its lo parts stay normal FP16 numbers (the backward is linear in g;
+// the scale is exact and removed before any result leaves the kernel).
 
 constexpr int XFER_BYTES = 3 * BM * 4;
 constexpr int ADJ_SMEM_BYTES = 1024 + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES + XFER_BYTES;
@@ -633,6 +640,8 @@ constexpr size_t kMaskWordsPerCta = (size_t)8 * 128 * 2 * 8;
 // GEMM e of a tile: forward layers 1..7 (e < 7), then backward layers 7..1.
 __device__ __forceinline__ int adj_n(int e) { return e < 7 ? gemm_n(e) : gemm_k(13 - e); }
 __device__ __forceinline__ int adj_k(int e) { return e < 7 ? gemm_k(e) : gemm_n(13 - e); }
+
+constexpr int kGradExp = 8;   // FP32-class adjoint: g scaled by 2^8 before its split
 
 struct TCAdjArgs {
   const TCConst* K;
@@ -647,6 +656,15 @@ struct TCAdjArgs {
   int accumulate;
   uint8_t* scratch;   // gridDim.x * kTcAdjScratchPerCta bytes
   int* err;
+  float inv_scale[NUM_GEMM];   // X: 2^-s_l of GEMM layer g
+  // X, optional: probes with a ReLU input within redo_tau of 0 are appended
+  // to (redo_p, redo_q) instead of being accumulated (at most redo_cap; the
+  // rest are accumulated here), for an FP32 adjoint to redo
+  float4* redo_p;
+  float4* redo_q;
+  int* redo_count;
+  int redo_cap;
+  float redo_tau;
 };
 
 // Sum of v[0..31] over the 32 lanes of the warp, column by column: lane L
@@ -665,11 +683,14 @@ __device__ __forceinline__ float warp_column_sum(float (&v)[32], int lane) {
   return v[0];
 }
 
-template <bool F16>
+template <bool F16, bool X>
 __global__ void __launch_bounds__(THREADS, 1)
 mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ TCMaps bmaps,
                   const TCAdjArgs a) {
+  static_assert(!X || F16, "FP32-class operands are FP16 pairs");
   constexpr uint32_t kIdesc = instr_desc<F16>();
+  constexpr int QPT = X ? 64 : BM;     // probes per tile
+  constexpr int NPASS = X ? 2 : 1;     // K passes per GEMM (X: W_lo, then W_hi)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -690,7 +711,7 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
   const int n = *a.count;
-  const int n_tiles = (n + BM - 1) / BM;
+  const int n_tiles = (n + QPT - 1) / QPT;
   if ((int)blockIdx.x >= n_tiles) return;
   uint32_t* masks = reinterpret_cast<uint32_t*>(a.scratch + (size_t)blockIdx.x * kTcAdjScratchPerCta);
   float* g4s = reinterpret_cast<float*>(masks + kMaskWordsPerCta);
@@ -726,11 +747,14 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
         for (int e = 0; ok && e < NUM_ADJ_GEMM; ++e) {
           const CUtensorMap* map = e < 7 ? &fmaps.m[e] : &bmaps.m[13 - e];
+          const int nkc = adj_k(e) / BK;
           for (int nh = 0; ok && nh < adj_n(e) / BN; ++nh) {
-            for (int kc = 0; kc < adj_k(e) / BK; ++kc) {
+            for (int kc = 0; kc < NPASS * nkc; ++kc) {
               if (!mbar_wait(empty + stage, phase ^ 1u, abort_flag)) { ok = false; break; }
               mbar_expect_tx(full + stage, STAGE_BYTES);
-              tma_load_2d(wst + stage * STAGE_BYTES, map, full + stage, kc * BK, nh * BN);
+              // X: the split rows hold [hi | lo]; the lo half comes first
+              const int xk = !X ? kc : (kc < nkc ? nkc + kc : kc - nkc);
+              tma_load_2d(wst + stage * STAGE_BYTES, map, full + stage, xk * BK, nh * BN);
               issued[stage] = true;
               issued_parity[stage] = phase;
               if (++stage == STAGES) { stage = 0; phase ^= 1u; }
@@ -760,11 +784,12 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           if (!mbar_wait(act_full, act_phase, abort_flag)) { ok = false; break; }
           act_phase ^= 1u;
           tc_fence_after();
+          const int nkc = adj_k(e) / BK;
           for (int nh = 0; ok && nh < adj_n(e) / BN; ++nh) {
-            for (int kc = 0; kc < adj_k(e) / BK; ++kc) {
+            for (int kc = 0; kc < NPASS * nkc; ++kc) {
               if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
               tc_fence_after();
-              const uint32_t a_base = smem_u32(act + kc * CHUNK_BYTES);
+              const uint32_t a_base = smem_u32(act + (kc % nkc) * CHUNK_BYTES);
               const uint32_t b_base = smem_u32(wst + stage * STAGE_BYTES);
 #pragma unroll
               for (int k = 0; k < BK / 16; ++k)
@@ -786,7 +811,7 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
       while (!mbar_try_wait(drain, 0) && globaltimer() - t0 < kTimeoutNs) {
       }
     }
-  } else {
+  } else if constexpr (!X) {
     // --------------------------------------------------------- epilogue
     const int ew = warp - 2;
     const int quad = warp & 3;
@@ -1009,6 +1034,331 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
       *abort_flag = 1;
       atomicOr(a.err, 32);
     }
+  } else {
+    // ------------------------------------------- epilogue, FP32-class tiles
+    // Lane pair (i, i + 16) of quadrant q holds probe 16q + i: lane i the hi
+    // row, lane i + 16 the lo row.  After the pair sum each lane owns 16 of a
+    // 32-column chunk (`part`) and writes both rows of those columns.
+    const int ew = warp - 2;
+    const int quad = warp & 3;
+    const int half = ew >> 2;
+    const int part = lane >> 4;
+    const int jq = quad * 16 + (lane & 15);
+    const int rhi = quad * 32 + (lane & 15), rlo = rhi + 16;
+    const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
+    constexpr float kGS = (float)(1 << kGradExp), kInvGS = 1.f / (float)(1 << kGradExp);
+    uint32_t acc_phase = 0, h2l_phase = 0, l2h_phase = 0;
+    bool ok = true;
+    float vmax = 0.f;
+    auto mask_ptr = [&](int layer) { return masks + ((size_t)(layer * BM + jq) * 2 + half) * 8; };
+    // warp-uniform waits: the lane pairs exchange values after every wait, so
+    // a warp never splits on a wait that runs out
+    auto wait_all = [&](uint64_t* bar, uint32_t parity) {
+      return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag));
+    };
+    // hi / lo words of this lane's 16 columns from column cc into both rows
+    auto putx = [&](int cc, const uint32_t (&hi)[8], const uint32_t (&lo)[8]) {
+      const uint32_t base = smem_u32(act) + (uint32_t)((cc >> 6) * CHUNK_BYTES);
+      const int u = (cc & 63) >> 3;
+      st_shared_v4(base + swz(rhi, u), hi[0], hi[1], hi[2], hi[3]);
+      st_shared_v4(base + swz(rhi, u + 1), hi[4], hi[5], hi[6], hi[7]);
+      st_shared_v4(base + swz(rlo, u), lo[0], lo[1], lo[2], lo[3]);
+      st_shared_v4(base + swz(rlo, u + 1), lo[4], lo[5], lo[6], lo[7]);
+    };
+    // the two-term split of 16 signed values (backward operands)
+    auto splitx = [&](const float (&v)[16], uint32_t (&hi)[8], uint32_t (&lo)[8]) {
+#pragma unroll
+      for (int i = 0; i < 16; i += 2) {
+        vmax = fmaxf(vmax, fmaxf(fabsf(v[i]), fabsf(v[i + 1])));
+        split_pair(v[i], v[i + 1], hi[i / 2], lo[i / 2]);
+      }
+    };
+    // 32-bit mask word of a chunk from the pair's two 16-bit halves
+    auto join = [&](uint32_t b16) {
+      const uint32_t o = __shfl_xor_sync(0xffffffffu, b16, 16);
+      return part ? (o | (b16 << 16)) : (b16 | (o << 16));
+    };
+    auto store_masks = [&](int layer, const uint32_t (&mw)[8]) {
+      if (part == 0) {
+        uint4* mp = reinterpret_cast<uint4*>(mask_ptr(layer));
+        mp[0] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+        mp[1] = make_uint4(mw[4], mw[5], mw[6], mw[7]);
+      }
+    };
+    // this lane's accumulator columns cc..cc+15 of chunk c, times s
+    auto pair_acc = [&](int c, float s, float (&m)[16]) {
+      uint32_t r[32];
+      tmem_ld32(t_row + (uint32_t)c, r);
+      pair_sum16(r, part, m);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) m[i] *= s;
+    };
+    for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
+      const int j = tile * QPT + jq;
+      const bool valid = j < n;
+      float4 pv = valid ? a.pp[j] : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+      const float3 p = make_float3(pv.x, pv.y, pv.z);
+      const int shape = __float_as_int(pv.w);
+      const float* bf4 = a.bfold4 + (size_t)shape * 512;
+      float pmin = __builtin_huge_valf();   // smallest |ReLU input| of the probe
+      // ---- forward recompute with ReLU masks
+      {
+        const float* bf = a.bfold0 + (size_t)shape * 512;
+        uint32_t mw[8];
+        for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+          float v[16];
+          layer0_16(a.K, bf, c + 16 * part, p, v);
+          uint32_t bits = 0;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            bits |= (v[i] > 0.f ? 1u : 0u) << i;
+            pmin = fminf(pmin, fabsf(v[i]));
+          }
+          mw[w] = join(bits);
+          uint32_t hi[8], lo[8];
+          relu_split16(v, hi, lo, vmax);
+          putx(c + 16 * part, hi, lo);
+        }
+        store_masks(0, mw);
+        fence_async_shared();
+        mbar_arrive(act_full);
+      }
+      float head = 0.f;
+      for (int g = 0; g < NUM_GEMM; ++g) {
+        if (!wait_all(acc_full, acc_phase)) { ok = false; break; }
+        acc_phase ^= 1u;
+        tc_fence_after();
+        const int ncol = gemm_n(g) / 2;
+        const int c0 = half * ncol;
+        uint32_t mw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int c = c0, w = 0; c < c0 + ncol; c += 32, ++w) {
+          float m[16], v[16];
+          pair_acc(c, 1.f, m);
+          const int cc = c + 16 * part;
+          affine16(a.K, g, bf4, cc, p, a.inv_scale[g], m, v);
+          uint32_t bits = 0;
+#pragma unroll
+          for (int i = 0; i < 16; ++i) {
+            bits |= (v[i] > 0.f ? 1u : 0u) << i;
+            // (layer 3's padding columns 253..255 are no neurons)
+            if (g != 2 || cc + i < 253) pmin = fminf(pmin, fabsf(v[i]));
+          }
+          mw[w] = join(bits);
+          if (g < NUM_GEMM - 1) {
+            uint32_t hi[8], lo[8];
+            relu_split16(v, hi, lo, vmax);
+            putx(cc, hi, lo);
+          } else {
+#pragma unroll
+            for (int i = 0; i < 16; i += 4) {
+              const float4 wh = ldg4(a.K->w_head + cc + i);
+              head = fmaf(fmaxf(v[i], 0.f), wh.x,
+                          fmaf(fmaxf(v[i + 1], 0.f), wh.y,
+                               fmaf(fmaxf(v[i + 2], 0.f), wh.z, fmaf(fmaxf(v[i + 3], 0.f), wh.w, head))));
+            }
+          }
+        }
+        store_masks(g + 1, mw);
+        tc_fence_before();
+        if (g < NUM_GEMM - 1) {
+          fence_async_shared();
+          mbar_arrive(act_full);
+        }
+      }
+      if (!ok) break;
+      head += __shfl_xor_sync(0xffffffffu, head, 16);
+      pmin = fminf(pmin, __shfl_xor_sync(0xffffffffu, pmin, 16));
+      // ---- head: f, then 1 - f^2 to both halves (and half 1's pmin to half 0)
+      float fval = 0.f, dfs = 0.f;
+      if (half == 1) {
+        if (part == 0) {
+          xfer[jq] = head;
+          xfer[BM + jq] = pmin;
+        }
+        mbar_arrive(h2l);
+        if (!wait_all(l2h, l2h_phase)) { ok = false; break; }
+        dfs = xfer[jq];
+      } else {
+        if (!wait_all(h2l, h2l_phase)) { ok = false; break; }
+        pmin = fminf(pmin, xfer[BM + jq]);
+        fval = tanhf(head + xfer[jq] + __ldg(&a.K->b_head));
+        dfs = 1.f - fval * fval;
+        __syncwarp();
+        if (part == 0) xfer[jq] = dfs;
+        mbar_arrive(l2h);
+      }
+      h2l_phase ^= 1u;
+      l2h_phase ^= 1u;
+      // ---- g_7 = 2^kGradExp (1 - f^2) w_head * mask_7 into the A tile
+      {
+        const uint32_t* mw = mask_ptr(7);
+        const float ds = dfs * kGS;
+        for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+          const uint32_t bits = mw[w] >> (16 * part);
+          const int cc = c + 16 * part;
+          float v[16];
+#pragma unroll
+          for (int i = 0; i < 16; i += 4) {
+            const float4 wh = ldg4(a.K->w_head + cc + i);
+            v[i + 0] = ((bits >> (i + 0)) & 1u) ? ds * wh.x : 0.f;
+            v[i + 1] = ((bits >> (i + 1)) & 1u) ? ds * wh.y : 0.f;
+            v[i + 2] = ((bits >> (i + 2)) & 1u) ? ds * wh.z : 0.f;
+            v[i + 3] = ((bits >> (i + 3)) & 1u) ? ds * wh.w : 0.f;
+          }
+          uint32_t hi[8], lo[8];
+          splitx(v, hi, lo);
+          putx(cc, hi, lo);
+        }
+        fence_async_shared();
+        mbar_arrive(act_full);
+      }
+      // ---- backward GEMMs for layers 7..1: g_{l-1} = acc * mask_{l-1}
+      float gx = 0.f, gy = 0.f, gz = 0.f;
+      for (int l = 7; l >= 1; --l) {
+        if (!wait_all(acc_full, acc_phase)) { ok = false; break; }
+        acc_phase ^= 1u;
+        tc_fence_after();
+        const int nout = gemm_k(l - 1);
+        const int ncol = nout / 2;
+        const int c0 = half * ncol;
+        const uint32_t* mw = mask_ptr(l - 1);
+        for (int c = c0, w = 0; c < c0 + ncol; c += 32, ++w) {
+          float m[16];
+          pair_acc(c, a.inv_scale[l - 1], m);
+          const uint32_t bits = mw[w] >> (16 * part);
+          const int cc = c + 16 * part;
+          float v[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) v[i] = ((bits >> i) & 1u) ? m[i] : 0.f;
+          if (l == 5 || l == 1) {
+            const float(*Wx)[512] = l == 5 ? a.K->wx4 : a.K->wx0;
+#pragma unroll
+            for (int i = 0; i < 16; i += 4) {
+              const float4 x = ldg4(Wx[0] + cc + i), y = ldg4(Wx[1] + cc + i), z = ldg4(Wx[2] + cc + i);
+              gx = fmaf(v[i], x.x, fmaf(v[i + 1], x.y, fmaf(v[i + 2], x.z, fmaf(v[i + 3], x.w, gx))));
+              gy = fmaf(v[i], y.x, fmaf(v[i + 1], y.y, fmaf(v[i + 2], y.z, fmaf(v[i + 3], y.w, gy))));
+              gz = fmaf(v[i], z.x, fmaf(v[i + 1], z.y, fmaf(v[i + 2], z.z, fmaf(v[i + 3], z.w, gz))));
+            }
+            if (l == 5) {
+              float4* dst = reinterpret_cast<float4*>(g4s + (size_t)jq * 512 + cc);
+#pragma unroll
+              for (int i = 0; i < 16; i += 4) dst[i / 4] = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
+            }
+          }
+          if (l > 1) {
+            uint32_t hi[8], lo[8];
+            splitx(v, hi, lo);
+            putx(cc, hi, lo);
+          }
+        }
+        tc_fence_before();
+        if (l > 1) {
+          fence_async_shared();
+          mbar_arrive(act_full);
+        }
+      }
+      if (!ok) break;
+      gx += __shfl_xor_sync(0xffffffffu, gx, 16);
+      gy += __shfl_xor_sync(0xffffffffu, gy, 16);
+      gz += __shfl_xor_sync(0xffffffffu, gz, 16);
+      // ---- grad_p f and the probe coefficient
+      float coef = 0.f;
+      if (half == 1) {
+        if (part == 0) {
+          xfer[jq] = gx;
+          xfer[BM + jq] = gy;
+          xfer[2 * BM + jq] = gz;
+        }
+        mbar_arrive(h2l);
+        if (!wait_all(l2h, l2h_phase)) { ok = false; break; }
+        coef = xfer[jq];
+      } else {
+        if (!wait_all(h2l, h2l_phase)) { ok = false; break; }
+        gx = (gx + xfer[jq]) * kInvGS;
+        gy = (gy + xfer[BM + jq]) * kInvGS;
+        gz = (gz + xfer[2 * BM + jq]) * kInvGS;
+        if (valid) {
+          if (a.out4 && part == 0) reinterpret_cast<float4*>(a.out4)[j] = make_float4(fval, gx, gy, gz);
+          const float4 q4 = a.pq ? a.pq[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          coef = q4.w;
+          if (q4.x != 0.f || q4.y != 0.f || q4.z != 0.f) {
+            const float gv = gx * q4.x + gy * q4.y + gz * q4.z;
+            const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
+            coef = (fabsf(gv) >= 1e-3f * gn && gv != 0.f) ? -q4.w / gv : 0.f;
+          }
+        }
+        // a probe whose ReLU masks the FP32-class recompute may have got
+        // wrong goes to the FP32 redo list instead (its lane pair agrees)
+        int slot = -1;
+        if (a.redo_p && part == 0 && valid && pmin < a.redo_tau) {
+          slot = atomicAdd(a.redo_count, 1);
+          if (slot < a.redo_cap) {
+            a.redo_p[slot] = pv;
+            a.redo_q[slot] = a.pq ? a.pq[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+          } else {
+            atomicSub(a.redo_count, 1);   // the count settles at redo_cap
+            slot = -1;
+          }
+        }
+        slot = __shfl_sync(0xffffffffu, slot, lane & 15);
+        if (slot >= 0) coef = 0.f;
+        __syncwarp();
+        if (part == 0) xfer[jq] = coef;
+        mbar_arrive(l2h);
+      }
+      h2l_phase ^= 1u;
+      l2h_phase ^= 1u;
+      // ---- sum coef * g_0 and coef * g_4 over the tile's probes per shape
+      // (g carries 2^kGradExp: the coefficient takes it back)
+      if (a.accumulate) {
+        const uint32_t* m0 = mask_ptr(0);
+        const bool live = valid && coef != 0.f;
+        unsigned todo = __ballot_sync(0xffffffffu, live);
+        while (todo) {
+          const int leader = __ffs(todo) - 1;
+          const int s = __shfl_sync(0xffffffffu, shape, leader);
+          const bool mine = live && shape == s;
+          const float cc = mine ? coef * kInvGS : 0.f;
+          for (int which = 0; which < 2; ++which) {
+            double* dst = (which == 0 ? a.gacc0 : a.gacc4) + (size_t)s * 512;
+            for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+              float u[16];
+              if (which == 0) {
+                float m[16];
+                pair_acc(c, a.inv_scale[0], m);
+                const uint32_t bits = m0[w] >> (16 * part);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) u[i] = ((bits >> i) & 1u) ? cc * m[i] : 0.f;
+              } else {
+                const float4* src = reinterpret_cast<const float4*>(g4s + (size_t)jq * 512 + c + 16 * part);
+#pragma unroll
+                for (int i = 0; i < 16; i += 4) {
+                  const float4 t = src[i / 4];
+                  u[i] = cc * t.x; u[i + 1] = cc * t.y; u[i + 2] = cc * t.z; u[i + 3] = cc * t.w;
+                }
+              }
+              // the lane's 16 columns in its half of a 32-column row, zeros
+              // in the other half: column sums over the warp's 16 probes
+              float v[32];
+#pragma unroll
+              for (int i = 0; i < 16; ++i) {
+                v[i] = part ? 0.f : u[i];
+                v[16 + i] = part ? u[i] : 0.f;
+              }
+              const float colsum = warp_column_sum(v, lane);
+              if (colsum != 0.f) atomicAdd(dst + c + lane, (double)colsum);
+            }
+          }
+          todo &= ~__ballot_sync(0xffffffffu, mine);
+        }
+      }
+      tc_fence_before();
+    }
+    if (!ok) {
+      *abort_flag = 1;
+      atomicOr(a.err, 32);
+    }
+    if (!(vmax <= 65504.f)) atomicOr(a.err, 64);   // an FP32-class operand overflowed FP16
   }
   tc_fence_before();
   __syncthreads();
@@ -1082,6 +1432,24 @@ dist_status pack_tcx(dist_decoder* d, const float* const* W) {
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
       DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (split, 3D)");
     }
+    // the transposed split [K rows][2N cols] (W^T_hi | W^T_lo) for the
+    // FP32-class adjoint's backward GEMMs
+    std::vector<uint16_t> t((size_t)K * 2 * N, 0);
+    for (int nn = 0; nn < N; ++nn)
+      for (int k = 0; k < K; ++k) {
+        t[(size_t)k * 2 * N + nn] = h[(size_t)nn * 2 * K + k];
+        t[(size_t)k * 2 * N + N + nn] = h[(size_t)nn * 2 * K + K + k];
+      }
+    void* qt = nullptr;
+    DIST_CUDA_TRY(cudaMalloc(&qt, t.size() * sizeof(uint16_t)));
+    d->allocations.push_back(qt);
+    DIST_CUDA_TRY(cudaMemcpy(qt, t.data(), t.size() * sizeof(uint16_t), cudaMemcpyHostToDevice));
+    cuuint64_t tdims[2] = {(cuuint64_t)(2 * N), (cuuint64_t)K};
+    cuuint64_t tstrides[1] = {(cuuint64_t)(2 * N) * sizeof(uint16_t)};
+    r = enc(&d->tc.bxmaps.m[g], CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, qt, tdims, tstrides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    DIST_CHECK(r == CUDA_SUCCESS, DIST_E_CUDA, "cuTensorMapEncodeTiled failed (split transpose)");
   }
   return DIST_OK;
 }
@@ -1290,21 +1658,25 @@ cudaError_t mlp_tcx_forward(const dist_decoder* dec, const RowSrc& src, const fl
   return mlp_tc_fused(dec, none, nullptr, src, fout, bfold0, bfolds, st, false);
 }
 
-cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const float4* pq,
-                           const int* count, const float* bfold0, const float* bfolds,
-                           float* out4, double* gacc0, double* gaccs, int accumulate,
-                           void* scratch, cudaStream_t st, bool f16) {
-  if (!dec->tc.ok) return cudaErrorNotSupported;
-  static const cudaError_t configured = [] {
-    cudaError_t e = cudaFuncSetAttribute(mlp_tc_adj_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         ADJ_SMEM_BYTES);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mlp_tc_adj_kernel<true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM_BYTES);
-    return e;
-  }();
+namespace {
+
+template <bool F16, bool X>
+cudaError_t launch_adjoint(const TCMaps& fmaps, const TCMaps& bmaps, const TCAdjArgs& a,
+                           cudaStream_t st) {
+  // set once per process and variant (thread-safe static initialisation)
+  static const cudaError_t configured = cudaFuncSetAttribute(
+      mlp_tc_adj_kernel<F16, X>, cudaFuncAttributeMaxDynamicSharedMemorySize, ADJ_SMEM_BYTES);
   if (configured != cudaSuccess) return configured;
+  prof_mlp_begin(st, 2);
+  mlp_tc_adj_kernel<F16, X><<<num_sms(), THREADS, ADJ_SMEM_BYTES, st>>>(fmaps, bmaps, a);
+  prof_mlp_end(st);
+  count_launch(1);
+  return cudaGetLastError();
+}
+
+TCAdjArgs adj_args(const dist_decoder* dec, const float4* pp, const float4* pq, const int* count,
+                   const float* bfold0, const float* bfolds, float* out4, double* gacc0,
+                   double* gaccs, int accumulate, void* scratch) {
   TCAdjArgs a;
   a.K = dec->tc.cst;
   a.bfold0 = bfold0;
@@ -1318,16 +1690,43 @@ cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const floa
   a.accumulate = accumulate;
   a.scratch = static_cast<uint8_t*>(scratch);
   a.err = dec->tc.err;
-  prof_mlp_begin(st, 2);
-  if (f16)
-    mlp_tc_adj_kernel<true><<<num_sms(), THREADS, ADJ_SMEM_BYTES, st>>>(
-        dec->tc.maps16, dec->tc.bmaps16, a);
-  else
-    mlp_tc_adj_kernel<false><<<num_sms(), THREADS, ADJ_SMEM_BYTES, st>>>(
-        dec->tc.maps, dec->tc.bmaps, a);
-  prof_mlp_end(st);
-  count_launch(1);
-  return cudaGetLastError();
+  for (int g = 0; g < NUM_GEMM; ++g) a.inv_scale[g] = dec->tc.x_inv_scale[g];
+  a.redo_p = nullptr;
+  a.redo_q = nullptr;
+  a.redo_count = nullptr;
+  a.redo_cap = 0;
+  a.redo_tau = 0.f;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t mlp_tc_adjoint(const dist_decoder* dec, const float4* pp, const float4* pq,
+                           const int* count, const float* bfold0, const float* bfolds,
+                           float* out4, double* gacc0, double* gaccs, int accumulate,
+                           void* scratch, cudaStream_t st, bool f16) {
+  if (!dec->tc.ok) return cudaErrorNotSupported;
+  const TCAdjArgs a = adj_args(dec, pp, pq, count, bfold0, bfolds, out4, gacc0, gaccs,
+                               accumulate, scratch);
+  return f16 ? launch_adjoint<true, false>(dec->tc.maps16, dec->tc.bmaps16, a, st)
+             : launch_adjoint<false, false>(dec->tc.maps, dec->tc.bmaps, a, st);
+}
+
+cudaError_t mlp_tcx_adjoint(const dist_decoder* dec, const float4* pp, const float4* pq,
+                            const int* count, const float* bfold0, const float* bfolds,
+                            float* out4, double* gacc0, double* gaccs, int accumulate,
+                            void* scratch, cudaStream_t st, const RedoList* redo) {
+  if (!dec->tc.ok) return cudaErrorNotSupported;
+  TCAdjArgs a = adj_args(dec, pp, pq, count, bfold0, bfolds, out4, gacc0, gaccs, accumulate,
+                         scratch);
+  if (redo) {
+    a.redo_p = redo->p;
+    a.redo_q = redo->q;
+    a.redo_count = redo->count;
+    a.redo_cap = redo->cap;
+    a.redo_tau = redo->tau;
+  }
+  return launch_adjoint<true, true>(dec->tc.xmaps, dec->tc.bxmaps, a, st);
 }
 
 }  // namespace dist

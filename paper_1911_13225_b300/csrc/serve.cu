@@ -44,13 +44,15 @@ struct Req {
 // Requests per slot among the listed rays (camera index == slot), with a
 // shared-memory histogram per block.
 __global__ void count_slots_kernel(const int* l0, const int* c0, const int* l1, const int* c1,
-                                   const float4* st, int n_slots, int* active) {
+                                   const int* l2, const int* c2, const float4* st, int n_slots,
+                                   int* active) {
   extern __shared__ int hist[];
   for (int s = threadIdx.x; s < n_slots; s += blockDim.x) hist[s] = 0;
   __syncthreads();
-  const int n0 = *c0, n1 = *c1;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n0 + n1; j += gridDim.x * blockDim.x) {
-    const int ray = j < n0 ? l0[j] : l1[j - n0];
+  const int n0 = *c0, n1 = *c1, n2 = *c2;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n0 + n1 + n2;
+       j += gridDim.x * blockDim.x) {
+    const int ray = j < n0 ? l0[j] : (j < n0 + n1 ? l1[j - n0] : l2[j - n0 - n1]);
     atomicAdd(&hist[__float_as_int(st[ray].w)], 1);
   }
   __syncthreads();
@@ -61,7 +63,7 @@ __global__ void count_slots_kernel(const int* l0, const int* c0, const int* l1, 
 size_t bytes_per_pixel(int K) {
   // ray state (incl. the refinement samples), lists, MLP outputs, per-pixel
   // outputs, target, upstream gradient and backward probes
-  return 16 + 16 + 12 + 16 + 8 + (4 + 4 + 1 + 4 + 4 + 4 + 8 * K) + 4 + 4 + (16 + 16 + 4);
+  return 16 + 16 + 12 + 24 + 12 + (4 + 4 + 1 + 4 + 4 + 4 + 8 * K) + 4 + 4 + (16 + 16 + 4);
 }
 
 }  // namespace
@@ -83,9 +85,9 @@ struct dist_server {
   int* fq = nullptr;
   float* fprev = nullptr;
   float* dprev = nullptr;
-  int* act[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-  float* fbuf[2] = {nullptr, nullptr};
-  int* cnt = nullptr;             // [parity][list]
+  int* act[2][3] = {{nullptr, nullptr, nullptr}, {nullptr, nullptr, nullptr}};
+  float* fbuf[3] = {nullptr, nullptr, nullptr};
+  int* cnt = nullptr;             // [parity][list 0, 1], then [parity] of list 2 (FP16 stage)
   CamDev* cams = nullptr;         // [max_req]
   float* z = nullptr;             // [max_req][L]
   float* bfold = nullptr;         // [2][max_req][512]
@@ -128,6 +130,7 @@ struct dist_server {
     P.o.depth = depth; P.o.sil = sil; P.o.mask = mask; P.o.steps = steps; P.o.status = status;
     P.o.d_hit = d_hit; P.o.d_min = d_min; P.o.f_min = f_min; P.o.queries = queries;
     P.K = p.k_min; P.eps = p.eps; P.alpha = p.alpha; P.eps_bf16 = p.eps_bf16;
+    P.eps_mid = p.precision == DIST_PREC_BF16 ? p.eps_mid : 0.f;
     P.radius = p.radius; P.max_steps = p.max_steps;
     return P;
   }
@@ -214,18 +217,25 @@ struct dist_server {
     RowSrc sx = src;
     sx.count = cnt + 2 * par + 1;
     sx.idx = act[par][1];
+    RowSrc sm = src;                 // FP16 stage of a BF16 march (list 2)
+    sm.count = cnt + 4 + par;
+    sm.idx = act[par][2];
     int* out[2] = {act[par ^ 1][0], act[par ^ 1][1]};
     DIST_CUDA_TRY(cudaMemsetAsync(cnt + 2 * (par ^ 1), 0, 2 * sizeof(int), st));
+    DIST_CUDA_TRY(cudaMemsetAsync(cnt + 4 + (par ^ 1), 0, sizeof(int), st));
     if (fp32_on_tc(p)) {
-      // both lists in one launch (an empty 16-bit list for FP32_TC), which
+      // every list in one launch (an empty 16-bit list for FP32_TC), which
       // also applies the step update
       src.count = cnt + 2 * par;
       src.idx = act[par][0];
       StepFuse sf;
       pool_step_fuse(P, cnt + 2 * (par ^ 1), out, &sf);
+      sf.out[2] = act[par ^ 1][2];
+      sf.cnt_out[2] = cnt + 4 + (par ^ 1);
       if (p.latency_mode) sf.wide = static_cast<uint8_t*>(wide_scratch);
       DIST_CUDA_TRY(mlp_tc_fused(dec, src, fbuf[0], sx, fbuf[1], b0, bs, st,
-                                 p.precision == DIST_PREC_FP16, &sf));
+                                 p.precision == DIST_PREC_FP16, &sf,
+                                 P.eps_mid > 0.f ? &sm : nullptr, fbuf[2]));
     } else {
       if (is_tc(p.precision)) {
         src.count = cnt + 2 * par;
@@ -241,7 +251,8 @@ struct dist_server {
     par ^= 1;
     DIST_CUDA_TRY(cudaMemsetAsync(slot_active, 0, max_req * sizeof(int), st));
     count_slots_kernel<<<num_sms(), 256, max_req * sizeof(int), st>>>(
-        act[par][0], cnt + 2 * par, act[par][1], cnt + 2 * par + 1, stt, max_req, slot_active);
+        act[par][0], cnt + 2 * par, act[par][1], cnt + 2 * par + 1, act[par][2], cnt + 4 + par,
+        stt, max_req, slot_active);
     count_launch(1);
     DIST_CUDA_TRY(cudaGetLastError());
     DIST_CUDA_TRY(cudaMemcpyAsync(slot_active_host, slot_active, max_req * sizeof(int),
@@ -276,6 +287,9 @@ struct dist_server {
         DIST_CUDA_TRY(mlp_tc_adjoint(dec, pp, pq, pcount, bfold, bfold + (size_t)max_req * 512,
                                      nullptr, G0, Gs, 1, tc_scratch, st,
                                      p.precision == DIST_PREC_FP16));
+      else if (p.precision == DIST_PREC_FP32_TC)
+        DIST_CUDA_TRY(mlp_tcx_adjoint(dec, pp, pq, pcount, bfold, bfold + (size_t)max_req * 512,
+                                      nullptr, G0, Gs, 1, tc_scratch, st));
       else
         DIST_CUDA_TRY(mlp_fp32_adjoint(dec->f32, pp, pq, pcount, bfold,
                                        bfold + (size_t)max_req * 512, nullptr, G0, Gs, 1, st));
@@ -396,8 +410,12 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
              "the tensor-core decoder covers only the DeepSDF shape");
   DIST_CHECK(p->coarse_levels == 0, DIST_E_INVALID,
              "dist_serve_create: coarse-to-fine tracing is not supported by the server");
-  DIST_CHECK(p->eps_mid == 0.f || p->precision != DIST_PREC_BF16, DIST_E_INVALID,
-             "dist_serve_create: the server's march has no FP16 stage (eps_mid must be 0)");
+  DIST_CHECK(p->precision != DIST_PREC_BF16 || p->eps_mid == 0.f ||
+                 (p->eps_mid > 0.f && p->eps_mid < p->eps_bf16 && fp32_on_tc(*p) &&
+                  p->refine_steps == 0 && p->refine_rule == DIST_REFINE_MARCH),
+             DIST_E_INVALID,
+             "dist_serve_create: eps_mid must be 0, or in (0, eps_bf16) with the TC refine "
+             "engine, refine_steps 0 and the MARCH rule");
   dist_server* S = new dist_server();
   S->dec = dec;
   S->p = *p;
@@ -424,9 +442,12 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
   SV_ALLOC(act[0][1], n * sizeof(int));
   SV_ALLOC(act[1][0], n * sizeof(int));
   SV_ALLOC(act[1][1], n * sizeof(int));
+  SV_ALLOC(act[0][2], n * sizeof(int));
+  SV_ALLOC(act[1][2], n * sizeof(int));
   SV_ALLOC(fbuf[0], n * sizeof(float));
   SV_ALLOC(fbuf[1], n * sizeof(float));
-  SV_ALLOC(cnt, 4 * sizeof(int));
+  SV_ALLOC(fbuf[2], n * sizeof(float));
+  SV_ALLOC(cnt, 6 * sizeof(int));
   SV_ALLOC(cams, (size_t)max_requests * sizeof(CamDev));
   SV_ALLOC(z, (size_t)max_requests * S->L * sizeof(float));
   SV_ALLOC(bfold, (size_t)2 * max_requests * 512 * sizeof(float));
@@ -464,7 +485,7 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
     s = DIST_E_CUDA;
   }
   if (s == DIST_OK) {
-    cudaError_t e = cudaMemset(S->cnt, 0, 4 * sizeof(int));
+    cudaError_t e = cudaMemset(S->cnt, 0, 6 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(S->queries, 0, 2 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(S->z, 0, (size_t)max_requests * S->L * sizeof(float));
     if (e != cudaSuccess) {

@@ -1,6 +1,8 @@
 // Sphere tracing on the device: ray generation with unit-sphere
 // initialisation, the per-step converge/step/compact update, normals, the
 // backward probes and the image-plane losses, plus their C-ABI entry points.
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstring>
 
@@ -1231,8 +1233,9 @@ cudaError_t ordered_probes(ProbeArgs a, dist_workspace* ws, long long n_pix, cud
   return cudaGetLastError();
 }
 
-// The decoder adjoint in the trace's precision: tcgen05 (BF16 / FP16
-// operands) after a tensor-core march, FP32 SIMT otherwise.
+// The decoder adjoint in the trace's precision: tcgen05 with BF16 / FP16
+// operands after a tensor-core march, with FP32-class operands after an
+// FP32_TC trace, FP32 SIMT otherwise.
 cudaError_t adjoint(const dist_decoder* dec, const dist_trace_params* p, dist_workspace* ws,
                     const float4* pp, const float4* pq, const int* count, const float* b0,
                     const float* bs, float* out4, double* G0, double* Gs, int acc,
@@ -1240,7 +1243,33 @@ cudaError_t adjoint(const dist_decoder* dec, const dist_trace_params* p, dist_wo
   if (is_tc(p->precision) && dec->tc.ok)
     return mlp_tc_adjoint(dec, pp, pq, count, b0, bs, out4, G0, Gs, acc, ws->tc_scratch, st,
                           p->precision == DIST_PREC_FP16);
+  if (p->precision == DIST_PREC_FP32_TC && dec->tc.ok)
+    return mlp_tcx_adjoint(dec, pp, pq, count, b0, bs, out4, G0, Gs, acc, ws->tc_scratch, st);
   return mlp_fp32_adjoint(dec->f32, pp, pq, count, b0, bs, out4, G0, Gs, acc, st);
+}
+
+// The decoder adjoint at FP32-class accuracy whatever the march's precision
+// (silhouette probes, too few for 16-bit rounding errors to average out, and
+// the central-difference probes, whose gradients are differenced): the
+// FP32-class tensor-core adjoint where the trace runs its FP32-class queries
+// on the tensor cores, else the FP32 CUDA-core adjoint.
+// With `redo` (central-difference probes), the probes the FP32-class kernel
+// hands back (a ReLU input within kMaskMargin of 0) go through the FP32
+// adjoint after it.
+constexpr float kMaskMargin = 1e-5f;
+
+cudaError_t fine_adjoint(const dist_decoder* dec, const dist_trace_params* p, dist_workspace* ws,
+                         const float4* pp, const float4* pq, const int* count, const float* b0,
+                         const float* bs, double* G0, double* Gs, cudaStream_t st,
+                         const RedoList* redo = nullptr) {
+  if (fp32_on_tc(*p) && dec->tc.ok) {
+    cudaError_t e = mlp_tcx_adjoint(dec, pp, pq, count, b0, bs, nullptr, G0, Gs, 1,
+                                    ws->tc_scratch, st, redo);
+    if (e != cudaSuccess || !redo) return e;
+    return mlp_fp32_adjoint(dec->f32, redo->p, redo->q, redo->count, b0, bs, nullptr, G0, Gs, 1,
+                            st);
+  }
+  return mlp_fp32_adjoint(dec->f32, pp, pq, count, b0, bs, nullptr, G0, Gs, 1, st);
 }
 
 // Queries of the central-difference probes (normals and their gradient):
@@ -1322,7 +1351,7 @@ static TraceArgs pool_args(const RayPool& P) {
   a.max_steps = P.max_steps; a.o = P.o; a.st = P.st; a.dir = P.dir;
   a.fq = P.fq; a.fprev = P.fprev; a.dprev = P.dprev; a.refine = P.refine;
   a.secant = P.secant; a.alpha_fp32 = P.alpha_fp32;
-  a.eps_mid = 0.f;      // the server's march has no FP16 stage
+  a.eps_mid = P.eps_mid;
   a.c2f = 0; a.c2f_start = 0; a.last = 0;
   return a;
 }
@@ -1361,7 +1390,7 @@ cudaError_t pool_step(const RayPool& P, const int* cnt_in, int* cnt_out, int* co
 void pool_step_fuse(const RayPool& P, int* cnt_out, int* const out[2], StepFuse* sf) {
   sf->t = pool_args(P);
   for (int k = 0; k < 2; ++k) { sf->out[k] = out[k]; sf->cnt_out[k] = cnt_out + k; }
-  sf->out[2] = nullptr;   // no FP16 stage (eps_mid 0): nothing goes to list 2
+  sf->out[2] = nullptr;   // set by the caller when the march has an FP16 stage
   sf->cnt_out[2] = nullptr;
   sf->queries = P.o.queries;
   sf->wide = nullptr;
@@ -1611,19 +1640,19 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
   if (g_sil) {
     // silhouette probes (<= 1 per pixel) in [3, 4) max_rays: only rays whose
     // soft silhouette disagrees with the target contribute, too few for
-    // 16-bit rounding errors to average out, so the FP32 adjoint
+    // 16-bit rounding errors to average out, so an FP32-class adjoint
     const long long off = 3 * (long long)ws->max_rays;
     ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, off, 2);
     const float alpha = p->alpha;
     DIST_CUDA_TRY(ordered_probes(a, ws, n_pix, st, [&](const ProbeArgs& b) {
       probes_bwd_kernel<<<g, 256, 0, st>>>(b, nullptr, g_sil, 0, alpha);
     }));
-    DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p + off, ws->probe_q + off, ws->probe_count + 2,
-                                   b0, bs, nullptr, G0, Gs, 1, st));
+    DIST_CUDA_TRY(fine_adjoint(dec, p, ws, ws->probe_p + off, ws->probe_q + off,
+                               ws->probe_count + 2, b0, bs, G0, Gs, st));
   }
   if (g_normal) {
     // central-difference normals difference nearby values: FP32-class
-    // queries (fd_forward) and the FP32 adjoint whatever the march precision
+    // queries (fd_forward) and an FP32-class adjoint whatever the march precision
     const long long off = 4 * (long long)ws->max_rays;
     ProbeArgs a = make_probe_args(p, fwd, ws, n_cams, n_pix, off, 1);
     const float delta = p->normal_delta;
@@ -1638,8 +1667,14 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
     fd_coef_kernel<<<g, 256, 0, st>>>(f6, ws->probe_pix + off, ws->probe_count + 1,
                                       p->normal_delta, g_normal, ws->probe_q + off);
     DIST_LAUNCH_CHECK();
-    DIST_CUDA_TRY(mlp_fp32_adjoint(d, ws->probe_p + off, ws->probe_q + off, ws->probe_count + 1,
-                                   b0, bs, nullptr, G0, Gs, 1, st));
+    // the redo list lives in the probe outputs of these probes (their f,
+    // read by fd_coef_kernel, is no longer needed): two float4 arrays
+    const long long cap = ((long long)kProbesPerRay * ws->max_rays - off) / 2;
+    float4* redo_p = reinterpret_cast<float4*>(ws->probe_out + off * 4);
+    RedoList redo{redo_p, redo_p + cap, ws->probe_count + 4, (int)std::min<long long>(cap, INT_MAX),
+                  kMaskMargin};
+    DIST_CUDA_TRY(fine_adjoint(dec, p, ws, ws->probe_p + off, ws->probe_q + off,
+                               ws->probe_count + 1, b0, bs, G0, Gs, st, &redo));
   }
   dim3 fg((d.latent + 31) / 32, n_shapes);
   latent_finalize_kernel<<<fg, kFinalizeWarps * 32, 0, st>>>(d, G0, Gs, n_shapes, dz);
@@ -1787,8 +1822,10 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
   DIST_CHECK(n >= 1 && n <= ws->max_rays * kProbesPerRay, DIST_E_INVALID,
              "dist_sdf_eval: n must be 1..10 * workspace max_rays");
   DIST_CHECK(n_shapes >= 1 && n_shapes <= kMaxShapes, DIST_E_INVALID, "n_shapes out of range");
-  DIST_CHECK(precision == DIST_PREC_FP32 || (valid_precision(precision) && !grad),
-             DIST_E_INVALID, "dist_sdf_eval: bad precision (tensor-core kernels have no gradient)");
+  DIST_CHECK(precision == DIST_PREC_FP32 || precision == DIST_PREC_FP32_TC ||
+                 (valid_precision(precision) && !grad),
+             DIST_E_INVALID,
+             "dist_sdf_eval: bad precision (gradients need FP32 or FP32_TC)");
   DIST_CHECK(precision == DIST_PREC_FP32 || dec->tc.ok, DIST_E_UNSUPPORTED,
              "BF16 tensor-core MLP covers only the DeepSDF decoder shape");
   cudaStream_t st = (cudaStream_t)stream;
@@ -1806,8 +1843,14 @@ dist_status dist_sdf_eval(const dist_decoder* dec, const float* z, int n_shapes,
   src.pts = ws->probe_p;
   if (is_tc(precision)) {
     DIST_CUDA_TRY(mlp_tc_forward(dec, src, b0, bs, f, st, precision == DIST_PREC_FP16));
-  } else if (precision == DIST_PREC_FP32_TC) {
+  } else if (precision == DIST_PREC_FP32_TC && !grad) {
     DIST_CUDA_TRY(mlp_tcx_forward(dec, src, b0, bs, f, st));
+  } else if (precision == DIST_PREC_FP32_TC) {
+    // f and grad_p f from the FP32-class adjoint (its own forward recompute)
+    DIST_CUDA_TRY(mlp_tcx_adjoint(dec, ws->probe_p, nullptr, ws->probe_count, b0, bs,
+                                  ws->probe_out, nullptr, nullptr, 0, ws->tc_scratch, st));
+    unpack_grad_kernel<<<g, 256, 0, st>>>(ws->probe_out, n, f, grad);
+    DIST_LAUNCH_CHECK();
   } else if (!grad) {
     DIST_CUDA_TRY(mlp_fp32_forward(d, src, b0, bs, f, st));
   } else {

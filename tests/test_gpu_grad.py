@@ -87,6 +87,59 @@ def test_tensor_core_adjoint_gradients(cuda_device, precision, mode):
     assert _rel(to_np(dz).astype(np.float64), G) < 2e-2
 
 
+@pytest.mark.parametrize("precision,mode", [("bf16", "sil"), ("bf16", "normal"),
+                                            ("fp32_tc", "exact"), ("fp32_tc", "sil"),
+                                            ("fp32_tc", "normal")])
+def test_fp32_class_adjoint_gradients(cuda_device, precision, mode):
+    """FP32-class tcgen05 adjoint (two-term FP16 operands): the silhouette and
+    central-difference normal probes of a tensor-core march, and every probe
+    of an FP32_TC trace.  Latent gradient against the FP64 oracle at the FP32
+    bars (1e-3 relative l2; 2e-2 for the central-difference normal, whose
+    gradient differences Jacobians 2 delta apart), and against the FP32
+    CUDA-core adjoint on the same upstream gradients."""
+    from paper_1911_13225_b300 import api
+    spec = synth.DEEPSDF_SPEC
+    delta = 1e-3 if mode == "normal" else 0.0
+    Ws, bs, Z = workload(spec, seed=7, n_shapes=2)
+    dec = gpu_decoder(spec, Ws, bs)
+    cams = [synth.look_at_camera(v, 48, 48, shape=i % 2)
+            for i, v in enumerate(synth.random_viewpoints(2, seed=11))]
+    n = api.n_pixels(cams)
+    ws = api.Workspace(n, 60)
+    z = torch.from_numpy(Z).to(cuda_device)
+    p32 = api.TraceParams(max_steps=60, normal_delta=delta)
+    res = api.trace(dec, z, cams, p32, ws, normals=mode == "normal")
+    tgt = api.trace(dec, z, [dict(c, shape=1 - c["shape"]) for c in cams], p32, ws,
+                    normals=mode == "normal")
+    sdf = oracle_sdf(spec, Ws, bs, Z)
+    orc = tracer.render(sdf, cams, max_steps=60, normal_delta=delta, record=True)
+    amb = ambiguous_rays(orc, tol_f=1e-5, max_steps=60, normals=orc["normal"], near_miss=1e-3)
+    sil_gt = torch.from_numpy((to_np(tgt.mask) > 0).astype(np.float32)).to(cuda_device)
+    target = {"depth": tgt.depth, "sil": sil_gt}
+    if mode == "normal":
+        target["normal"] = tgt.normal
+    _, gd, gn, gs, _ = api.loss(res, target, z, ws, w_depth=1.0, w_sil=1.0,
+                                w_normal=1.0 if mode == "normal" else 0.0)
+    g = to_np({"exact": gd, "sil": gs, "normal": gn}[mode]).astype(np.float64)
+    g[amb] = 0.0
+    gt = torch.from_numpy(g.astype(np.float32)).to(cuda_device)
+    key = {"exact": "g_depth", "sil": "g_sil", "normal": "g_normal"}[mode]
+    dz = to_np(api.backward(dec, z, cams, api.TraceParams(max_steps=60, precision=precision,
+                                                          normal_delta=delta),
+                            ws, res, **{key: gt})).astype(np.float64)
+    dz32 = to_np(api.backward(dec, z, cams, p32, ws, res, **{key: gt})).astype(np.float64)
+    torch.cuda.synchronize()
+    assert dec.device_error() == 0
+    okw = {key: g.astype(np.float32).astype(np.float64)}
+    G = latent_vjp(sdf, orc, 2, spec.latent_dim, normal_delta=delta, **okw)
+    assert np.abs(G).max() > 0
+    bar = 2e-2 if mode == "normal" else GRAD_TOL
+    print(mode, precision, "vs oracle", _rel(dz, G), "vs fp32", _rel(dz, dz32),
+          "fp32 vs oracle", _rel(dz32, G))
+    assert _rel(dz, G) < bar
+    assert _rel(dz, dz32) < bar / 2
+
+
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 def test_tensor_core_normals(cuda_device, precision):
     from paper_1911_13225_b300 import api

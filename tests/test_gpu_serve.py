@@ -31,18 +31,20 @@ def _target(api, dec, cam, z_tgt, ws, params, dev):
     return to_np(api.trace(dec, z, [dict(cam, shape=0)], params, ws).depth)
 
 
-@pytest.mark.parametrize("precision,latency_mode", [("fp32", 1), ("bf16", 1), ("bf16", 0)])
-def test_mixed_load_equals_alone_and_direct_calls(cuda_device, precision, latency_mode):
+@pytest.mark.parametrize("precision,latency_mode,eps_mid", [("fp32", 1, 0.0), ("bf16", 1, 0.0),
+                                                           ("bf16", 0, 0.0), ("bf16", 1, 2e-4)])
+def test_mixed_load_equals_alone_and_direct_calls(cuda_device, precision, latency_mode, eps_mid):
     """(With latency_mode 0 the server decodes every step one tile per SM, the
     direct calls use the default latency mode: the results still agree bit
-    for bit.)"""
+    for bit.  eps_mid: the BF16 march with its FP16 stage, in the server and
+    in the direct calls.)"""
     from paper_1911_13225_b300 import api
     from paper_1911_13225_b300.serve import Server
     spec = synth.DEEPSDF_SPEC if precision == "bf16" else synth.SMALL_SPEC
     Ws, bs, _ = workload(spec)
     dec = gpu_decoder(spec, Ws, bs)
-    params = api.TraceParams(precision=precision)
-    srv_params = api.TraceParams(precision=precision, latency_mode=latency_mode)
+    params = api.TraceParams(precision=precision, eps_mid=eps_mid)
+    srv_params = api.TraceParams(precision=precision, latency_mode=latency_mode, eps_mid=eps_mid)
     reqs, z_tgt = _requests(spec, 12)
     ws = api.Workspace(48 * 48, 50)
     tgts = [_target(api, dec, c, z_tgt, ws, params, cuda_device) if k == "backward" else None

@@ -131,7 +131,8 @@ def test_static_scratch_rejects_sizes_beyond_its_limit(cuda_device):
     st, _, _ = _static(dec, z, pts[:10], shp[:10], "fp32", False)
     assert st == _abi.DIST_E_INVALID
     assert b"64" in _abi.lib().dist_last_error()
-    # the tensor-core kernels have no gradient; the small decoder no tensor-core path
+    # the static entry gives gradients in FP32 only; the small decoder has no
+    # tensor-core path
     deep = synth.DEEPSDF_SPEC
     Wd, bd, Zd = workload(deep, n_shapes=1)
     ddec = gpu_decoder(deep, Wd, bd)
