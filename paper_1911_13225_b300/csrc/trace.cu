@@ -1256,7 +1256,7 @@ cudaError_t adjoint(const dist_decoder* dec, const dist_trace_params* p, dist_wo
 // With `redo` (central-difference probes), the probes the FP32-class kernel
 // hands back (a ReLU input within kMaskMargin of 0) go through the FP32
 // adjoint after it.
-constexpr float kMaskMargin = 1e-5f;
+constexpr float kMaskMargin = 5e-7f;
 
 cudaError_t fine_adjoint(const dist_decoder* dec, const dist_trace_params* p, dist_workspace* ws,
                          const float4* pp, const float4* pq, const int* count, const float* b0,

@@ -96,7 +96,8 @@ def test_fp32_class_adjoint_gradients(cuda_device, precision, mode):
     of an FP32_TC trace.  Latent gradient against the FP64 oracle at the FP32
     bars (1e-3 relative l2; 2e-2 for the central-difference normal, whose
     gradient differences Jacobians 2 delta apart), and against the FP32
-    CUDA-core adjoint on the same upstream gradients."""
+    CUDA-core adjoint on the same upstream gradients (2e-3 for the normal,
+    measured 6.5e-4)."""
     from paper_1911_13225_b300 import api
     spec = synth.DEEPSDF_SPEC
     delta = 1e-3 if mode == "normal" else 0.0
@@ -137,7 +138,9 @@ def test_fp32_class_adjoint_gradients(cuda_device, precision, mode):
     print(mode, precision, "vs oracle", _rel(dz, G), "vs fp32", _rel(dz, dz32),
           "fp32 vs oracle", _rel(dz32, G))
     assert _rel(dz, G) < bar
-    assert _rel(dz, dz32) < bar / 2
+    # normal: without the hand-over of probes whose ReLU inputs sit within
+    # the margin of 0 to the FP32 adjoint this is 1.6e-2 (flipped masks)
+    assert _rel(dz, dz32) < (2e-3 if mode == "normal" else bar / 2)
 
 
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
