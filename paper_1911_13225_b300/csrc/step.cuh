@@ -147,8 +147,9 @@ __device__ __forceinline__ int apply_step(const TraceArgs& a, int list, int i, f
     outcome = DIST_RAY_HIT;
   } else if (low && (af < eps_lo || crossed)) {
     // switch to FP32-class queries at the same point (from a BF16 march with
-    // an FP16 stage: BF16 samples close to the surface go to FP16 first)
-    keep = (list == 0 && a.eps_mid > 0.f && !crossed) ? 2 : 1;
+    // an FP16 stage: BF16 rays close to the surface or across it go to FP16
+    // first)
+    keep = (list == 0 && a.eps_mid > 0.f) ? 2 : 1;
     if (a.c2f) a.o.status[i] = -2;
   } else {
     dn = fmaf(list == 1 ? a.alpha_fp32 : a.alpha, f, d);
