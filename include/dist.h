@@ -251,6 +251,14 @@ typedef struct {
   unsigned long long* queries;  /* optional, device [2]: += MLP queries made
                         while marching, [0] 16-bit (BF16 or FP16), [1] FP32
                         or FP32-class                                       */
+  float* grad_len;   /* (optional) written with `normal` when normal_delta >
+                        0: |g| of the central difference g_a = (f(p + delta
+                        e_a) - f(p - delta e_a)) / (2 delta) at the hit, 0
+                        elsewhere (Sec. 3.3; normal = g / |g|).  With it,
+                        dist_trace_bwd forms the normal loss's coefficients
+                        from `normal` and `grad_len` instead of evaluating
+                        the six probes again; both must then come from a
+                        forward with the same params                        */
 } dist_trace_out;
 
 /* Forward render: unit-sphere initialisation (Sec. 3.2), then up to
@@ -270,7 +278,8 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
 /* Surface normals at the hits of a previous dist_trace_fwd (same arguments;
  * reads out->mask and out->d_hit): the normalised analytic gradient of f
  * (normal_delta = 0) or the paper's central differences (Sec. 3.3).
- * normal: device float [n_pixels][3]; zero for non-hit pixels. */
+ * normal: device float [n_pixels][3]; zero for non-hit pixels.  When normal
+ * is out->normal, out->grad_len (if set) is written too. */
 dist_status dist_render_normals(const dist_decoder* dec, const float* z, int n_shapes,
                                 const dist_camera* cams, int n_cams,
                                 const dist_trace_params* params,

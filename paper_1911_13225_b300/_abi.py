@@ -64,7 +64,7 @@ class TraceOut(Structure):
     _fields_ = [("depth", c_void_p), ("sil", c_void_p), ("mask", c_void_p),
                 ("steps", c_void_p), ("status", c_void_p), ("d_hit", c_void_p),
                 ("d_min", c_void_p), ("f_min", c_void_p), ("normal", c_void_p),
-                ("queries", c_void_p)]
+                ("queries", c_void_p), ("grad_len", c_void_p)]
 
 
 class LossWeights(Structure):

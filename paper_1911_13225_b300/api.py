@@ -170,12 +170,14 @@ class TraceResult:
     f_min: torch.Tensor
     normal: Optional[torch.Tensor]
     queries: torch.Tensor
+    grad_len: Optional[torch.Tensor] = None   # |central-difference gradient| beside `normal`
     _c: _abi.TraceOut = field(default=None, repr=False)
 
     def c(self) -> _abi.TraceOut:
         return _abi.TraceOut(_ptr(self.depth), _ptr(self.sil), _ptr(self.mask), _ptr(self.steps),
                              _ptr(self.status), _ptr(self.d_hit), _ptr(self.d_min),
-                             _ptr(self.f_min), _ptr(self.normal), _ptr(self.queries))
+                             _ptr(self.f_min), _ptr(self.normal), _ptr(self.queries),
+                             _ptr(self.grad_len))
 
 
 def n_pixels(cams) -> int:
@@ -192,7 +194,8 @@ def alloc_result(n: int, k_min: int, device, normals: bool) -> TraceResult:
         d_hit=torch.empty(n, **f), d_min=torch.empty(n, k_min, **f),
         f_min=torch.empty(n, k_min, **f),
         normal=torch.empty(n, 3, **f) if normals else None,
-        queries=torch.zeros(2, device=device, dtype=torch.int64))
+        queries=torch.zeros(2, device=device, dtype=torch.int64),
+        grad_len=torch.empty(n, **f) if normals else None)
 
 
 def trace(dec: Decoder, z: torch.Tensor, cams, params: TraceParams, ws: Workspace,

@@ -505,7 +505,7 @@ __global__ void normals_from_grad_kernel(const float* out4, const int* pix, cons
 }
 
 __global__ void normals_from_fd_kernel(const float* f6, const int* pix, const int* count,
-                                       float delta, float* normal) {
+                                       float delta, float* normal, float* grad_len) {
   const int n = *count / 6;
   for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
     const float* f = f6 + 6 * h;
@@ -515,6 +515,7 @@ __global__ void normals_from_fd_kernel(const float* f6, const int* pix, const in
     const float s = nn > 0.f ? 1.f / nn : 0.f;
     const int i = pix[6 * h];
     normal[3 * i] = gx * s; normal[3 * i + 1] = gy * s; normal[3 * i + 2] = gz * s;
+    if (grad_len) grad_len[i] = nn;
   }
 }
 
@@ -899,6 +900,24 @@ __global__ void color_finalize_kernel(const float* cpart, const int* pix, const 
 // Normal-loss coefficients: with g = FD gradient from the six probe values
 // and n = g / |g|, dL/dg = (g_n - n (n . g_n)) / |g|; probe +a gets
 // dL/dg_a / (2 delta), probe -a its negative (hit point held fixed).
+// Probe coefficients of the central-difference normal n = g / |g|: the VJP
+// of dL/dn through the normalisation, (dL/dn - n (n . dL/dn)) / |g|, times
+// +-1 / (2 delta) for the probes at p +- delta e_a.
+__device__ __forceinline__ void fd_coef_store(const double (&nv)[3], double gn, double inv,
+                                              const float* g_normal, int i, float4* pq6) {
+  const double up[3] = {g_normal[3 * i], g_normal[3 * i + 1], g_normal[3 * i + 2]};
+  double c[3] = {0, 0, 0};
+  if (gn > 0) {
+    const double nu = nv[0] * up[0] + nv[1] * up[1] + nv[2] * up[2];
+    for (int e = 0; e < 3; ++e) c[e] = (up[e] - nv[e] * nu) / gn * inv;
+  }
+  for (int e = 0; e < 3; ++e) {
+    pq6[2 * e] = make_float4(0.f, 0.f, 0.f, (float)c[e]);
+    pq6[2 * e + 1] = make_float4(0.f, 0.f, 0.f, (float)-c[e]);
+  }
+}
+
+// ... from the six probe values.
 __global__ void fd_coef_kernel(const float* f6, const int* pix, const int* count, float delta,
                                const float* g_normal, float4* pq) {
   const int n = *count / 6;
@@ -907,18 +926,23 @@ __global__ void fd_coef_kernel(const float* f6, const int* pix, const int* count
     const double inv = 1.0 / (2.0 * (double)delta);
     const double g[3] = {(f[0] - f[1]) * inv, (f[2] - f[3]) * inv, (f[4] - f[5]) * inv};
     const double gn = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+    double nv[3] = {0, 0, 0};
+    if (gn > 0)
+      for (int e = 0; e < 3; ++e) nv[e] = g[e] / gn;
+    fd_coef_store(nv, gn, inv, g_normal, pix[6 * h], pq + 6 * h);
+  }
+}
+
+// ... from the forward's normal and |g| (dist_trace_out.grad_len).
+__global__ void fd_coef_from_normal_kernel(const float* normal, const float* grad_len,
+                                           const int* pix, const int* count, float delta,
+                                           const float* g_normal, float4* pq) {
+  const int n = *count / 6;
+  for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
     const int i = pix[6 * h];
-    const double up[3] = {g_normal[3 * i], g_normal[3 * i + 1], g_normal[3 * i + 2]};
-    double c[3] = {0, 0, 0};
-    if (gn > 0) {
-      const double nv[3] = {g[0] / gn, g[1] / gn, g[2] / gn};
-      const double nu = nv[0] * up[0] + nv[1] * up[1] + nv[2] * up[2];
-      for (int e = 0; e < 3; ++e) c[e] = (up[e] - nv[e] * nu) / gn * inv;
-    }
-    for (int e = 0; e < 3; ++e) {
-      pq[6 * h + 2 * e] = make_float4(0.f, 0.f, 0.f, (float)c[e]);
-      pq[6 * h + 2 * e + 1] = make_float4(0.f, 0.f, 0.f, (float)-c[e]);
-    }
+    const double inv = 1.0 / (2.0 * (double)delta);
+    const double nv[3] = {normal[3 * i], normal[3 * i + 1], normal[3 * i + 2]};
+    fd_coef_store(nv, (double)grad_len[i], inv, g_normal, i, pq + 6 * h);
   }
 }
 
@@ -1290,6 +1314,9 @@ dist_status normals_impl(const dist_decoder* dec, const dist_trace_params* p,
   const float* bs = ws->bfold + kMaxShapes * 512;
   DIST_CUDA_TRY(cudaMemsetAsync(normal, 0, (size_t)n_pix * 3 * sizeof(float), st));
   DIST_CUDA_TRY(cudaMemsetAsync(ws->probe_count, 0, 8 * sizeof(int), st));
+  // |g| beside the normal it belongs to (the forward's own normal buffer)
+  float* glen = o->grad_len && normal == o->normal ? o->grad_len : nullptr;
+  if (glen) DIST_CUDA_TRY(cudaMemsetAsync(glen, 0, (size_t)n_pix * sizeof(float), st));
   const int g = grid_for(n_pix, 256);
   if (p->normal_delta == 0.f) {
     ProbeArgs a = make_probe_args(p, o, ws, n_cams, n_pix, 0, 0);
@@ -1309,7 +1336,7 @@ dist_status normals_impl(const dist_decoder* dec, const dist_trace_params* p,
     src.pts = ws->probe_p;
     DIST_CUDA_TRY(fd_forward(dec, p, src, b0, bs, ws->probe_out, st));
     normals_from_fd_kernel<<<g, 256, 0, st>>>(ws->probe_out, ws->probe_pix, ws->probe_count,
-                                               p->normal_delta, normal);
+                                               p->normal_delta, normal, glen);
     DIST_LAUNCH_CHECK();
   }
   return DIST_OK;
@@ -1659,13 +1686,22 @@ dist_status dist_trace_bwd(const dist_decoder* dec, const float* z, int n_shapes
     DIST_CUDA_TRY(ordered_probes(a, ws, n_pix, st, [&](const ProbeArgs& b) {
       probes_fd_kernel<<<g, 256, 0, st>>>(b, delta, g_normal);
     }));
-    RowSrc src{};
-    src.count = ws->probe_count + 1;
-    src.pts = ws->probe_p + off;
-    float* f6 = ws->probe_out + off * 4;
-    DIST_CUDA_TRY(fd_forward(dec, p, src, b0, bs, f6, st));
-    fd_coef_kernel<<<g, 256, 0, st>>>(f6, ws->probe_pix + off, ws->probe_count + 1,
-                                      p->normal_delta, g_normal, ws->probe_q + off);
+    if (fwd->normal && fwd->grad_len) {
+      // the forward's central difference: its normal and |g| give the
+      // coefficients without evaluating the probes again
+      fd_coef_from_normal_kernel<<<g, 256, 0, st>>>(fwd->normal, fwd->grad_len,
+                                                    ws->probe_pix + off, ws->probe_count + 1,
+                                                    p->normal_delta, g_normal,
+                                                    ws->probe_q + off);
+    } else {
+      RowSrc src{};
+      src.count = ws->probe_count + 1;
+      src.pts = ws->probe_p + off;
+      float* f6 = ws->probe_out + off * 4;
+      DIST_CUDA_TRY(fd_forward(dec, p, src, b0, bs, f6, st));
+      fd_coef_kernel<<<g, 256, 0, st>>>(f6, ws->probe_pix + off, ws->probe_count + 1,
+                                        p->normal_delta, g_normal, ws->probe_q + off);
+    }
     DIST_LAUNCH_CHECK();
     // the redo list lives in the probe outputs of these probes (their f,
     // read by fd_coef_kernel, is no longer needed): two float4 arrays

@@ -143,6 +143,41 @@ def test_fp32_class_adjoint_gradients(cuda_device, precision, mode):
     assert _rel(dz, dz32) < (2e-3 if mode == "normal" else bar / 2)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_normal_gradient_from_forward_grad_len(cuda_device, precision):
+    """dist_trace_out.grad_len: the forward's |central-difference gradient|
+    beside its normal (0 off the hits) lets dist_trace_bwd skip the six probe
+    queries; the latent gradient equals the one from re-evaluated probes to
+    FP32 rounding."""
+    import dataclasses
+    from paper_1911_13225_b300 import api
+    spec = synth.DEEPSDF_SPEC
+    delta = 1e-3
+    Ws, bs, Z = workload(spec, seed=7, n_shapes=2)
+    dec = gpu_decoder(spec, Ws, bs)
+    cams = [synth.look_at_camera(v, 48, 48, shape=i % 2)
+            for i, v in enumerate(synth.random_viewpoints(2, seed=11))]
+    ws = api.Workspace(api.n_pixels(cams), 60)
+    z = torch.from_numpy(Z).to(cuda_device)
+    p = api.TraceParams(max_steps=60, normal_delta=delta, precision=precision)
+    res = api.trace(dec, z, cams, p, ws, normals=True)
+    tgt = api.trace(dec, z, [dict(c, shape=1 - c["shape"]) for c in cams], p, ws, normals=True)
+    mask = to_np(res.mask).astype(bool)
+    glen = to_np(res.grad_len)
+    assert np.all(glen[~mask] == 0) and np.all(glen[mask] > 0)
+    # |grad f| of an SDF-like decoder is near 1 at the surface
+    assert 0.5 < np.median(glen[mask]) < 2.0
+    _, _, gn, _, _ = api.loss(res, {"depth": tgt.depth, "normal": tgt.normal}, z, ws,
+                              w_depth=0.0, w_normal=1.0)
+    dz_reuse = to_np(api.backward(dec, z, cams, p, ws, res, g_normal=gn)).astype(np.float64)
+    bare = dataclasses.replace(res, grad_len=None)
+    dz_eval = to_np(api.backward(dec, z, cams, p, ws, bare, g_normal=gn)).astype(np.float64)
+    torch.cuda.synchronize()
+    assert dec.device_error() == 0
+    assert np.abs(dz_eval).max() > 0
+    assert _rel(dz_reuse, dz_eval) < 1e-5
+
+
 @pytest.mark.parametrize("precision", ["bf16", "fp16"])
 def test_tensor_core_normals(cuda_device, precision):
     from paper_1911_13225_b300 import api
