@@ -621,9 +621,14 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
 // g_0 and g_4, which are summed over rays into FP64 per-shape accumulators
 // (a warp transpose-reduction over 32 rays in FP32, then FP64 atomics).
 //
-// The two column halves of a row meet through a small exchange buffer and
-// two mbarriers (half 1 -> half 0: head and gradient partial sums; half 0 ->
-// half 1: 1 - f^2 and the coefficient).
+// Each GEMM's accumulator completes in two 256-column halves (acc_half[0],
+// acc_half[1]); the epilogue warps of a lane quadrant split every layer's
+// columns between two sides, each side taking 128 columns of each half, and
+// hold their half-0 results in registers until the half-1 MMAs (which still
+// read the operand tile) are done, so half 0's epilogue overlaps half 1's
+// MMAs.  The two sides of a row meet through a small exchange buffer and
+// two mbarriers (side 1 -> side 0: head and gradient partial sums; side 0 ->
+// side 1: 1 - f^2 and the coefficient).
 //
 // FP32-class variant (X): 64 probes per tile in the forward kernel's hi / lo
 // row layout, every GEMM's K loop twice (W_lo, then W_hi; the backward
@@ -699,12 +704,12 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
   uint64_t* bars = reinterpret_cast<uint64_t*>(wst + STAGES * STAGE_BYTES);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
-  uint64_t* acc_full = bars + 2 * STAGES;
-  uint64_t* act_full = bars + 2 * STAGES + 1;
-  uint64_t* drain = bars + 2 * STAGES + 2;
-  uint64_t* h2l = bars + 2 * STAGES + 3;      // half 1 -> half 0
-  uint64_t* l2h = bars + 2 * STAGES + 4;      // half 0 -> half 1
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  uint64_t* acc_half = bars + 2 * STAGES;     // [2]: accumulator columns 0..255, 256..511
+  uint64_t* act_full = bars + 2 * STAGES + 2;
+  uint64_t* drain = bars + 2 * STAGES + 3;
+  uint64_t* h2l = bars + 2 * STAGES + 4;      // side 1 -> side 0
+  uint64_t* l2h = bars + 2 * STAGES + 5;      // side 0 -> side 1
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* xfer = reinterpret_cast<float*>(smem + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES);
 
@@ -721,7 +726,8 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
-    mbar_init(acc_full, 1);
+    mbar_init(acc_half, 1);
+    mbar_init(acc_half + 1, 1);
     mbar_init(act_full, NUM_EPI * 32);
     mbar_init(drain, 1);
     mbar_init(h2l, NUM_EPI * 16);
@@ -798,8 +804,8 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
               mma_commit(empty + stage);
               if (++stage == STAGES) { stage = 0; phase ^= 1u; }
             }
+            if (ok) mma_commit(acc_half + nh);   // this 256-column half is done
           }
-          if (ok) mma_commit(acc_full);
         }
       }
       if (!ok) {
@@ -813,26 +819,56 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
     }
   } else if constexpr (!X) {
     // --------------------------------------------------------- epilogue
+    // Warp (lane quadrant q, side s) owns TMEM lanes 32q..32q+31, one probe
+    // row each, and of a layer's output columns the chunks col(w): of a
+    // 512-wide layer columns s*128 + [0, 128) of each 256-column accumulator
+    // half (chunks 0..3 in half 0, 4..7 in half 1), of a 256-wide layer
+    // chunks 0..3.  Half 0's results wait in registers while half 1's MMAs,
+    // which still read the operand tile, run; then both are written.
     const int ew = warp - 2;
     const int quad = warp & 3;
-    const int half = ew >> 2;
+    const int side = ew >> 2;
     const int row = quad * 32 + lane;
     const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
-    uint32_t acc_phase = 0, h2l_phase = 0, l2h_phase = 0;
+    uint32_t acc_phase[2] = {0u, 0u};
+    uint32_t h2l_phase = 0, l2h_phase = 0;
     bool ok = true;
-    // mask words of (layer, row, half): 8 words cover this thread's columns
-    auto mask_ptr = [&](int layer) { return masks + ((size_t)(layer * BM + row) * 2 + half) * 8; };
+    auto col = [&](int w) { return side * 128 + 32 * (w & 3) + 256 * (w >> 2); };
+    // mask words of (layer, row, side): word w covers chunk col(w)
+    auto mask_ptr = [&](int layer) { return masks + ((size_t)(layer * BM + row) * 2 + side) * 8; };
+    auto wait_acc = [&](int h) -> bool {
+      if (!mbar_wait(acc_half + h, acc_phase[h], abort_flag)) return false;
+      acc_phase[h] ^= 1u;
+      tc_fence_after();
+      return true;
+    };
+    auto store_masks = [&](int layer, const uint32_t (&mw)[8]) {
+      uint4* mp = reinterpret_cast<uint4*>(mask_ptr(layer));
+      mp[0] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
+      mp[1] = make_uint4(mw[4], mw[5], mw[6], mw[7]);
+    };
+    auto store_held = [&](const uint32_t (&held)[4][16]) {
+#pragma unroll
+      for (int w = 0; w < 4; ++w) store_packed<16>(act, row, col(w), held[w]);
+    };
+    auto release = [&]() {
+      fence_async_shared();
+      mbar_arrive(act_full);
+    };
     for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
       const int j = tile * BM + row;
       const bool valid = j < n;
       float4 pv = valid ? a.pp[j] : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
       const float3 p = make_float3(pv.x, pv.y, pv.z);
       const int shape = __float_as_int(pv.w);
-      // ---- forward recompute with ReLU masks
+      const float* bf4 = a.bfold4 + (size_t)shape * 512;
+      // ---- forward recompute with ReLU masks (the operand tile is free:
+      // the previous tile's last GEMM is complete)
       {
         const float* bf = a.bfold0 + (size_t)shape * 512;
         uint32_t mw[8];
-        for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+        for (int w = 0; w < 8; ++w) {
+          const int c = col(w);
           float v[32];
           layer0_32(a.K, bf, c, p, v);
           uint32_t bits = 0;
@@ -844,25 +880,18 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           mw[w] = bits;
           store_act32<F16>(act, row, c, v);
         }
-        uint4* mp = reinterpret_cast<uint4*>(mask_ptr(0));
-        mp[0] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
-        mp[1] = make_uint4(mw[4], mw[5], mw[6], mw[7]);
-        fence_async_shared();
-        mbar_arrive(act_full);
+        store_masks(0, mw);
+        release();
       }
       float head = 0.f;
       for (int g = 0; g < NUM_GEMM; ++g) {
-        if (!mbar_wait(acc_full, acc_phase, abort_flag)) { ok = false; break; }
-        acc_phase ^= 1u;
-        tc_fence_after();
-        const int ncol = gemm_n(g) / 2;
-        const int c0 = half * ncol;
-        const float* bf4 = a.bfold4 + (size_t)shape * 512;
+        const bool last = g == NUM_GEMM - 1;
         uint32_t mw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int c = c0, w = 0; c < c0 + ncol; c += 32, ++w) {
+        // chunk w: bias, ReLU mask, then the head term or the operand values
+        auto chunk = [&](int w, float (&v)[32]) {
+          const int c = col(w);
           uint32_t r[32];
           tmem_ld32(t_row + (uint32_t)c, r);
-          float v[32];
           bias32(a.K, g, bf4, c, p, r, v);
           uint32_t bits = 0;
 #pragma unroll
@@ -871,25 +900,36 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
             v[i] = fmaxf(v[i], 0.f);
           }
           mw[w] = bits;
-          if (g < NUM_GEMM - 1) {
-            store_act32<F16>(act, row, c, v);
-          } else {
-            head = head32(a.K, c, v, head);
+          if (last) head = head32(a.K, c, v, head);
+        };
+        uint32_t held[4][16];
+        if (!wait_acc(0)) { ok = false; break; }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          float v[32];
+          chunk(w, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) held[w][i] = pack16<F16>(v[2 * i], v[2 * i + 1]);
+        }
+        if (gemm_n(g) == 512) {
+          if (!wait_acc(1)) { ok = false; break; }
+          if (!last) store_held(held);
+          for (int w = 4; w < 8; ++w) {
+            float v[32];
+            chunk(w, v);
+            if (!last) store_act32<F16>(act, row, col(w), v);
           }
+        } else if (!last) {
+          store_held(held);
         }
-        uint4* mp = reinterpret_cast<uint4*>(mask_ptr(g + 1));
-        mp[0] = make_uint4(mw[0], mw[1], mw[2], mw[3]);
-        mp[1] = make_uint4(mw[4], mw[5], mw[6], mw[7]);
+        store_masks(g + 1, mw);
         tc_fence_before();
-        if (g < NUM_GEMM - 1) {
-          fence_async_shared();
-          mbar_arrive(act_full);
-        }
+        if (!last) release();
       }
       if (!ok) break;
-      // ---- head: f, then 1 - f^2 to both halves
+      // ---- head: f, then 1 - f^2 to both sides
       float fval = 0.f, dfs = 0.f;
-      if (half == 1) {
+      if (side == 1) {
         xfer[row] = head;
         mbar_arrive(h2l);
         if (!mbar_wait(l2h, l2h_phase, abort_flag)) { ok = false; break; }
@@ -906,37 +946,32 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
       // ---- g_7 = (1 - f^2) w_head * mask_7 into the A tile
       {
         const uint32_t* mw = mask_ptr(7);
-        for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+        for (int w = 0; w < 8; ++w) {
+          const int c = col(w);
           const uint32_t bits = mw[w];
           float v[32];
 #pragma unroll
           for (int i = 0; i < 32; i += 4) {
-            const float4 w = ldg4(a.K->w_head + c + i);
-            v[i + 0] = ((bits >> (i + 0)) & 1u) ? dfs * w.x : 0.f;
-            v[i + 1] = ((bits >> (i + 1)) & 1u) ? dfs * w.y : 0.f;
-            v[i + 2] = ((bits >> (i + 2)) & 1u) ? dfs * w.z : 0.f;
-            v[i + 3] = ((bits >> (i + 3)) & 1u) ? dfs * w.w : 0.f;
+            const float4 wh = ldg4(a.K->w_head + c + i);
+            v[i + 0] = ((bits >> (i + 0)) & 1u) ? dfs * wh.x : 0.f;
+            v[i + 1] = ((bits >> (i + 1)) & 1u) ? dfs * wh.y : 0.f;
+            v[i + 2] = ((bits >> (i + 2)) & 1u) ? dfs * wh.z : 0.f;
+            v[i + 3] = ((bits >> (i + 3)) & 1u) ? dfs * wh.w : 0.f;
           }
           store_act32<F16>(act, row, c, v);
         }
-        fence_async_shared();
-        mbar_arrive(act_full);
+        release();
       }
       // ---- backward GEMMs for layers 7..1: g_{l-1} = acc * mask_{l-1}
       float gx = 0.f, gy = 0.f, gz = 0.f;
       for (int l = 7; l >= 1; --l) {
-        if (!mbar_wait(acc_full, acc_phase, abort_flag)) { ok = false; break; }
-        acc_phase ^= 1u;
-        tc_fence_after();
-        const int nout = gemm_k(l - 1);   // width of layer l's h-input
-        const int ncol = nout / 2;
-        const int c0 = half * ncol;
         const uint32_t* mw = mask_ptr(l - 1);
-        for (int c = c0, w = 0; c < c0 + ncol; c += 32, ++w) {
+        const bool more = l > 1;              // g_{l-1} is the next GEMM's operand
+        auto chunk = [&](int w, float (&v)[32]) {
+          const int c = col(w);
           uint32_t r[32];
           tmem_ld32(t_row + (uint32_t)c, r);
           const uint32_t bits = mw[w];
-          float v[32];
 #pragma unroll
           for (int i = 0; i < 32; ++i) v[i] = ((bits >> i) & 1u) ? __uint_as_float(r[i]) : 0.f;
           if (l == 5 || l == 1) {
@@ -955,18 +990,34 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
               for (int i = 0; i < 32; i += 4) dst[i / 4] = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
             }
           }
-          if (l > 1) store_act32<F16>(act, row, c, v);
+        };
+        uint32_t held[4][16];
+        if (!wait_acc(0)) { ok = false; break; }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          float v[32];
+          chunk(w, v);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) held[w][i] = pack16<F16>(v[2 * i], v[2 * i + 1]);
+        }
+        if (gemm_k(l - 1) == 512) {
+          if (!wait_acc(1)) { ok = false; break; }
+          if (more) store_held(held);
+          for (int w = 4; w < 8; ++w) {
+            float v[32];
+            chunk(w, v);
+            if (more) store_act32<F16>(act, row, col(w), v);
+          }
+        } else if (more) {
+          store_held(held);
         }
         tc_fence_before();
-        if (l > 1) {
-          fence_async_shared();
-          mbar_arrive(act_full);
-        }
+        if (more) release();
       }
       if (!ok) break;
       // ---- grad_p f and the probe coefficient
       float coef = 0.f;
-      if (half == 1) {
+      if (side == 1) {
         xfer[row] = gx;
         xfer[BM + row] = gy;
         xfer[2 * BM + row] = gz;
@@ -1004,7 +1055,8 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           const float cc = mine ? coef : 0.f;
           for (int which = 0; which < 2; ++which) {
             double* dst = (which == 0 ? a.gacc0 : a.gacc4) + (size_t)s * 512;
-            for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+            for (int w = 0; w < 8; ++w) {
+              const int c = col(w);
               float v[32];
               if (which == 0) {
                 uint32_t r[32];
@@ -1038,23 +1090,32 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
     // ------------------------------------------- epilogue, FP32-class tiles
     // Lane pair (i, i + 16) of quadrant q holds probe 16q + i: lane i the hi
     // row, lane i + 16 the lo row.  After the pair sum each lane owns 16 of a
-    // 32-column chunk (`part`) and writes both rows of those columns.
+    // 32-column chunk (`part`) and writes both rows of those columns.  The
+    // chunks of a side and the hold-back of half 0 are the 16-bit epilogue's.
     const int ew = warp - 2;
     const int quad = warp & 3;
-    const int half = ew >> 2;
+    const int side = ew >> 2;
     const int part = lane >> 4;
     const int jq = quad * 16 + (lane & 15);
     const int rhi = quad * 32 + (lane & 15), rlo = rhi + 16;
     const uint32_t t_row = tmem + ((uint32_t)(quad * 32) << 16);
     constexpr float kGS = (float)(1 << kGradExp), kInvGS = 1.f / (float)(1 << kGradExp);
-    uint32_t acc_phase = 0, h2l_phase = 0, l2h_phase = 0;
+    uint32_t acc_phase[2] = {0u, 0u};
+    uint32_t h2l_phase = 0, l2h_phase = 0;
     bool ok = true;
     float vmax = 0.f;
-    auto mask_ptr = [&](int layer) { return masks + ((size_t)(layer * BM + jq) * 2 + half) * 8; };
+    auto col = [&](int w) { return side * 128 + 32 * (w & 3) + 256 * (w >> 2); };
+    auto mask_ptr = [&](int layer) { return masks + ((size_t)(layer * BM + jq) * 2 + side) * 8; };
     // warp-uniform waits: the lane pairs exchange values after every wait, so
     // a warp never splits on a wait that runs out
     auto wait_all = [&](uint64_t* bar, uint32_t parity) {
       return __all_sync(0xffffffffu, mbar_wait(bar, parity, abort_flag));
+    };
+    auto wait_acc = [&](int h) -> bool {
+      if (!wait_all(acc_half + h, acc_phase[h])) return false;
+      acc_phase[h] ^= 1u;
+      tc_fence_after();
+      return true;
     };
     // hi / lo words of this lane's 16 columns from column cc into both rows
     auto putx = [&](int cc, const uint32_t (&hi)[8], const uint32_t (&lo)[8]) {
@@ -1085,13 +1146,21 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
         mp[1] = make_uint4(mw[4], mw[5], mw[6], mw[7]);
       }
     };
-    // this lane's accumulator columns cc..cc+15 of chunk c, times s
-    auto pair_acc = [&](int c, float s, float (&m)[16]) {
+    // this lane's accumulator columns col(w) + 16 part .. + 15, times s
+    auto pair_acc = [&](int w, float s, float (&m)[16]) {
       uint32_t r[32];
-      tmem_ld32(t_row + (uint32_t)c, r);
+      tmem_ld32(t_row + (uint32_t)col(w), r);
       pair_sum16(r, part, m);
 #pragma unroll
       for (int i = 0; i < 16; ++i) m[i] *= s;
+    };
+    auto store_held = [&](const uint32_t (&hh)[4][8], const uint32_t (&hl)[4][8]) {
+#pragma unroll
+      for (int w = 0; w < 4; ++w) putx(col(w) + 16 * part, hh[w], hl[w]);
+    };
+    auto release = [&]() {
+      fence_async_shared();
+      mbar_arrive(act_full);
     };
     for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
       const int j = tile * QPT + jq;
@@ -1105,9 +1174,10 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
       {
         const float* bf = a.bfold0 + (size_t)shape * 512;
         uint32_t mw[8];
-        for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+        for (int w = 0; w < 8; ++w) {
+          const int cc = col(w) + 16 * part;
           float v[16];
-          layer0_16(a.K, bf, c + 16 * part, p, v);
+          layer0_16(a.K, bf, cc, p, v);
           uint32_t bits = 0;
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
@@ -1117,24 +1187,19 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           mw[w] = join(bits);
           uint32_t hi[8], lo[8];
           relu_split16(v, hi, lo, vmax);
-          putx(c + 16 * part, hi, lo);
+          putx(cc, hi, lo);
         }
         store_masks(0, mw);
-        fence_async_shared();
-        mbar_arrive(act_full);
+        release();
       }
       float head = 0.f;
       for (int g = 0; g < NUM_GEMM; ++g) {
-        if (!wait_all(acc_full, acc_phase)) { ok = false; break; }
-        acc_phase ^= 1u;
-        tc_fence_after();
-        const int ncol = gemm_n(g) / 2;
-        const int c0 = half * ncol;
+        const bool last = g == NUM_GEMM - 1;
         uint32_t mw[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-        for (int c = c0, w = 0; c < c0 + ncol; c += 32, ++w) {
+        auto chunk = [&](int w, uint32_t (&hi)[8], uint32_t (&lo)[8]) {
           float m[16], v[16];
-          pair_acc(c, 1.f, m);
-          const int cc = c + 16 * part;
+          pair_acc(w, 1.f, m);
+          const int cc = col(w) + 16 * part;
           affine16(a.K, g, bf4, cc, p, a.inv_scale[g], m, v);
           uint32_t bits = 0;
 #pragma unroll
@@ -1144,11 +1209,7 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
             if (g != 2 || cc + i < 253) pmin = fminf(pmin, fabsf(v[i]));
           }
           mw[w] = join(bits);
-          if (g < NUM_GEMM - 1) {
-            uint32_t hi[8], lo[8];
-            relu_split16(v, hi, lo, vmax);
-            putx(cc, hi, lo);
-          } else {
+          if (last) {
 #pragma unroll
             for (int i = 0; i < 16; i += 4) {
               const float4 wh = ldg4(a.K->w_head + cc + i);
@@ -1156,21 +1217,35 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
                           fmaf(fmaxf(v[i + 1], 0.f), wh.y,
                                fmaf(fmaxf(v[i + 2], 0.f), wh.z, fmaf(fmaxf(v[i + 3], 0.f), wh.w, head))));
             }
+          } else {
+            relu_split16(v, hi, lo, vmax);
           }
+        };
+        uint32_t hh[4][8], hl[4][8];
+        if (!wait_acc(0)) { ok = false; break; }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) chunk(w, hh[w], hl[w]);
+        if (gemm_n(g) == 512) {
+          if (!wait_acc(1)) { ok = false; break; }
+          if (!last) store_held(hh, hl);
+          for (int w = 4; w < 8; ++w) {
+            uint32_t hi[8], lo[8];
+            chunk(w, hi, lo);
+            if (!last) putx(col(w) + 16 * part, hi, lo);
+          }
+        } else if (!last) {
+          store_held(hh, hl);
         }
         store_masks(g + 1, mw);
         tc_fence_before();
-        if (g < NUM_GEMM - 1) {
-          fence_async_shared();
-          mbar_arrive(act_full);
-        }
+        if (!last) release();
       }
       if (!ok) break;
       head += __shfl_xor_sync(0xffffffffu, head, 16);
       pmin = fminf(pmin, __shfl_xor_sync(0xffffffffu, pmin, 16));
-      // ---- head: f, then 1 - f^2 to both halves (and half 1's pmin to half 0)
+      // ---- head: f, then 1 - f^2 to both sides (and side 1's pmin to side 0)
       float fval = 0.f, dfs = 0.f;
-      if (half == 1) {
+      if (side == 1) {
         if (part == 0) {
           xfer[jq] = head;
           xfer[BM + jq] = pmin;
@@ -1193,9 +1268,9 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
       {
         const uint32_t* mw = mask_ptr(7);
         const float ds = dfs * kGS;
-        for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+        for (int w = 0; w < 8; ++w) {
           const uint32_t bits = mw[w] >> (16 * part);
-          const int cc = c + 16 * part;
+          const int cc = col(w) + 16 * part;
           float v[16];
 #pragma unroll
           for (int i = 0; i < 16; i += 4) {
@@ -1209,24 +1284,18 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           splitx(v, hi, lo);
           putx(cc, hi, lo);
         }
-        fence_async_shared();
-        mbar_arrive(act_full);
+        release();
       }
       // ---- backward GEMMs for layers 7..1: g_{l-1} = acc * mask_{l-1}
       float gx = 0.f, gy = 0.f, gz = 0.f;
       for (int l = 7; l >= 1; --l) {
-        if (!wait_all(acc_full, acc_phase)) { ok = false; break; }
-        acc_phase ^= 1u;
-        tc_fence_after();
-        const int nout = gemm_k(l - 1);
-        const int ncol = nout / 2;
-        const int c0 = half * ncol;
         const uint32_t* mw = mask_ptr(l - 1);
-        for (int c = c0, w = 0; c < c0 + ncol; c += 32, ++w) {
+        const bool more = l > 1;
+        auto chunk = [&](int w, uint32_t (&hi)[8], uint32_t (&lo)[8]) {
           float m[16];
-          pair_acc(c, a.inv_scale[l - 1], m);
+          pair_acc(w, a.inv_scale[l - 1], m);
           const uint32_t bits = mw[w] >> (16 * part);
-          const int cc = c + 16 * part;
+          const int cc = col(w) + 16 * part;
           float v[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) v[i] = ((bits >> i) & 1u) ? m[i] : 0.f;
@@ -1245,17 +1314,25 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
               for (int i = 0; i < 16; i += 4) dst[i / 4] = make_float4(v[i], v[i + 1], v[i + 2], v[i + 3]);
             }
           }
-          if (l > 1) {
+          if (more) splitx(v, hi, lo);
+        };
+        uint32_t hh[4][8], hl[4][8];
+        if (!wait_acc(0)) { ok = false; break; }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) chunk(w, hh[w], hl[w]);
+        if (gemm_k(l - 1) == 512) {
+          if (!wait_acc(1)) { ok = false; break; }
+          if (more) store_held(hh, hl);
+          for (int w = 4; w < 8; ++w) {
             uint32_t hi[8], lo[8];
-            splitx(v, hi, lo);
-            putx(cc, hi, lo);
+            chunk(w, hi, lo);
+            if (more) putx(col(w) + 16 * part, hi, lo);
           }
+        } else if (more) {
+          store_held(hh, hl);
         }
         tc_fence_before();
-        if (l > 1) {
-          fence_async_shared();
-          mbar_arrive(act_full);
-        }
+        if (more) release();
       }
       if (!ok) break;
       gx += __shfl_xor_sync(0xffffffffu, gx, 16);
@@ -1263,7 +1340,7 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
       gz += __shfl_xor_sync(0xffffffffu, gz, 16);
       // ---- grad_p f and the probe coefficient
       float coef = 0.f;
-      if (half == 1) {
+      if (side == 1) {
         if (part == 0) {
           xfer[jq] = gx;
           xfer[BM + jq] = gy;
@@ -1321,11 +1398,12 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           const float cc = mine ? coef * kInvGS : 0.f;
           for (int which = 0; which < 2; ++which) {
             double* dst = (which == 0 ? a.gacc0 : a.gacc4) + (size_t)s * 512;
-            for (int c = half * 256, w = 0; c < half * 256 + 256; c += 32, ++w) {
+            for (int w = 0; w < 8; ++w) {
+              const int c = col(w);
               float u[16];
               if (which == 0) {
                 float m[16];
-                pair_acc(c, a.inv_scale[0], m);
+                pair_acc(w, a.inv_scale[0], m);
                 const uint32_t bits = m0[w] >> (16 * part);
 #pragma unroll
                 for (int i = 0; i < 16; ++i) u[i] = ((bits >> i) & 1u) ? cc * m[i] : 0.f;
