@@ -241,6 +241,12 @@ dist_status dist_workspace_create(int64_t max_rays, int max_steps, dist_workspac
   WS_ALLOC(tc_scratch, (size_t)num_sms() * kTcAdjScratchPerCta);
   WS_ALLOC(wide_scratch, tc_wide_scratch_bytes());
 #undef WS_ALLOC
+  w->step_seq = 0;
+  if (s == DIST_OK &&
+      cudaMemset(tc_wide_seq_flag(w->wide_scratch), 0, sizeof(unsigned long long)) != cudaSuccess) {
+    set_error("dist_workspace_create: cudaMemset failed");
+    s = DIST_E_CUDA;
+  }
   if (s != DIST_OK) {
     dist_workspace_destroy(w);
     return s;

@@ -199,6 +199,7 @@ struct dist_workspace {
   int* ired;          // [8] small integer scratch
   void* tc_scratch;   // num_sms() * kTcAdjScratchPerCta bytes (tensor-core adjoint)
   void* wide_scratch; // tc_wide_scratch_bytes(): latency-mode operand images
+  unsigned long long step_seq;  // host: sequence number of the last fused step
   std::vector<void*> allocations;
 };
 
@@ -332,6 +333,8 @@ cudaError_t mlp_tc_wide(const dist_decoder* dec, const RowSrc& src16, float* f16
                         void* scratch, const RowSrc* srcm = nullptr, float* fmout = nullptr);
 int tc_wide_max_tiles();
 size_t tc_wide_scratch_bytes();
+// The step sequence word inside that scratch (zeroed with it by its owner).
+unsigned long long* tc_wide_seq_flag(void* scratch);
 
 // Colour decoder on the tensor cores (16-bit rows only): per row the three
 // head dot products of its last hidden layer in four partial sums (one per

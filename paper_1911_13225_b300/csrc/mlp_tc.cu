@@ -136,6 +136,14 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   // launched early behind the previous grid (programmatic dependent
   // launch): nothing it writes is read before this wait
   grid_dep_wait();
+  if (a.wide_tiles > 0) {
+    // mlp_tc_wide_kernel, launched behind this grid, may run beside it: it
+    // acquires this step's inputs (complete and visible here) through the
+    // release of the step's sequence number, written before any CTA of this
+    // grid lets it launch
+    if (pid == 0 && threadIdx.x == 0) seq_release(a.step.seq_flag, a.step.seq);
+    __syncthreads();
+  }
   grid_dep_launch();
   const int n0 = rowsrc_count(a.src[0]);
   const int n1 = rowsrc_count(a.src[1]);
@@ -143,12 +151,13 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   const int t1 = (n1 + QPT_X - 1) / QPT_X;   // FP32-class tiles: [0, t1)
   const int t2 = t1 + (n2 + BM - 1) / BM;     // FP16-stage tiles: [t1, t2)
   const int n_tiles = t2 + (n0 + BM - 1) / BM;
-  if (pid >= n_tiles) return;
-  // a launch small enough for the latency mode (its tiles: 128 16-bit rows
-  // or 64 FP32-class queries) runs there instead, launched right behind this
-  if (a.wide_tiles > 0 &&
-      (n1 + 63) / 64 + (n2 + BM - 1) / BM + (n0 + BM - 1) / BM <= a.wide_tiles)
-    return;
+  // tiles [0, tb) go to the latency-mode kernel (all of a small launch, or
+  // the FP32-class tiles of a launch that leaves room for both, see
+  // wide_share); this grid takes [tb, n_tiles)
+  const int tb = wide_share(n_tiles, t1, a.wide_tiles, npid);
+  if (tb + pid >= n_tiles) return;
+  // tile of round r for this CTA
+  auto tile_at = [&](int r) { return tb + tile_of(r, pid, npid); };
   if (a.fuse_step && a.step.queries && pid == 0 && threadIdx.x == 0) {
     atomicAdd(a.step.queries + 0, (unsigned long long)(n0 + n2));
     atomicAdd(a.step.queries + 1, (unsigned long long)n1);
@@ -190,8 +199,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       bool ok = true;
       // (a.withhold, tests only: no copy is issued, so the MMA warp's first
       // wait for a weight stage runs out and the CTA takes its abort path)
-      for (int r = 0, tile = pid; ok && !a.withhold && tile < n_tiles;
-           tile = tile_of(++r, pid, npid)) {
+      for (int r = 0, tile = tile_at(0); ok && !a.withhold && tile < n_tiles; tile = tile_at(++r)) {
         const bool xt = tile < t1;
         const bool mid = tile_list(tile) == 2;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
@@ -231,7 +239,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       uint32_t act_phase[4] = {0u, 0u, 0u, 0u};
       bool ok = true;
       auto commit = [&](uint64_t* bar) { mma_commit(bar); };
-      for (int r = 0, tile = pid; ok && tile < n_tiles; tile = tile_of(++r, pid, npid)) {
+      for (int r = 0, tile = tile_at(0); ok && tile < n_tiles; tile = tile_at(++r)) {
         const bool xt = tile < t1;
         const uint32_t idesc = instr_desc_m(xt || F16 || tile_list(tile) == 2, BM);
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
@@ -281,7 +289,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       constexpr int RPT = BM / SW;   // rows per step thread
       const int s = threadIdx.x - (2 + FWD_EPI) * 32;
       uint32_t sphase = 0;
-      for (int r = 0, t = pid; t < n_tiles; t = tile_of(++r, pid, npid)) {
+      for (int r = 0, t = tile_at(0); t < n_tiles; t = tile_at(++r)) {
         const bool xt = t < t1;
         const int list = tile_list(t);
         const int j0 = tile_row0(t);
@@ -456,7 +464,7 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     };
 
     uint32_t step_phase = 0;   // column group 1: step_empty parity
-    int tile = pid;
+    int tile = tile_at(0);
     int rnd = 0;
     load_rows(tile);
     for (int q = 0; q < 4; ++q) {
@@ -465,9 +473,9 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
       put(q, h);
       release(q);
     }
-    for (; tile < n_tiles; tile = tile_of(++rnd, pid, npid)) {
+    for (; tile < n_tiles; tile = tile_at(++rnd)) {
       const float* bf4 = a.bfold4 + (size_t)shape * 512;
-      const int next = tile_of(rnd + 1, pid, npid);
+      const int next = tile_at(rnd + 1);
       const bool has_next = next < n_tiles;
       for (int g = 0; g < NUM_GEMM - 1; ++g) {
         if (!wait_acc(0)) { ok = false; break; }

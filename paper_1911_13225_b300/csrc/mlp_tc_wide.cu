@@ -48,6 +48,7 @@ struct WideArgs {
   StepFuse step;
   uint8_t* stage_g;    // [clusters][2][ACT_BYTES] operand images
   float* head_g;       // [clusters][BM][16] head chunk sums
+  int nsm;             // CTAs of the mlp_tc_kernel launch of the same step
 };
 
 __device__ __forceinline__ uint32_t wide_idesc(bool f16, int n) {
@@ -108,8 +109,13 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   static_assert((2 * W_NST + 8) * 8 + 8 <= W_BAR_BYTES, "barrier block");
 
-  // launched behind the previous grid (programmatic dependent launch)
-  grid_dep_wait();
+  // Launched behind this step's mlp_tc_kernel (programmatic dependent
+  // launch), possibly to decode some of the step's tiles beside it.  This
+  // step's inputs are acquired through the sequence number that grid
+  // releases before it lets this one launch (so the bounded wait below finds
+  // it at once; it never waits for the other grid to make progress).  Each
+  // CTA that decodes, and CTA 0, waits for that grid before it exits, so the
+  // next step, launched behind this grid, starts only once both are done.
   grid_dep_launch();
 
   const int warp = threadIdx.x >> 5;
@@ -117,16 +123,33 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
   const int rank = (int)cluster_rank();
   const int cid = (int)(blockIdx.x / WC);
   const int ncl = (int)(gridDim.x / WC);
-  const int n0 = rowsrc_count(a.src[0]);
-  const int n1 = rowsrc_count(a.src[1]);
-  const int n2 = rowsrc_count(a.src[2]);
+  int fresh = 1;
+  if (threadIdx.x == 0) {
+    const unsigned long long t0 = globaltimer();
+    while (seq_acquire(a.step.seq_flag) != a.step.seq) {
+      if (globaltimer() - t0 > kTimeoutNs) {
+        fresh = 0;
+        atomicOr(a.err, 4);
+        break;
+      }
+    }
+  }
+  fresh = __syncthreads_or(fresh && threadIdx.x == 0);
+  const int n0 = fresh ? rowsrc_count(a.src[0]) : 0;
+  const int n1 = fresh ? rowsrc_count(a.src[1]) : 0;
+  const int n2 = fresh ? rowsrc_count(a.src[2]) : 0;
   const int t1 = (n1 + QPT_XW - 1) / QPT_XW;         // FP32-class tiles: [0, t1)
   const int t2 = t1 + (n2 + BM - 1) / BM;            // FP16-stage tiles: [t1, t2)
   const int n_tiles = t2 + (n0 + BM - 1) / BM;
-  // launches with more tiles than clusters go to mlp_tc_kernel, which makes
-  // the same decision from the same counts; uniform over a cluster
-  if (n_tiles == 0 || n_tiles > ncl || cid >= n_tiles) return;
-  if (a.fuse_step && a.step.queries && cid == 0 && rank == 0 && threadIdx.x == 0) {
+  // this kernel's tiles [0, nw): the same decision as mlp_tc_kernel's from
+  // the same counts (wide_share); uniform over a cluster
+  const int nw = wide_share(n_tiles, t1, ncl, a.nsm);
+  if (cid >= nw) {
+    if (blockIdx.x == 0) grid_dep_wait();
+    return;
+  }
+  if (nw == n_tiles && a.fuse_step && a.step.queries && cid == 0 && rank == 0 &&
+      threadIdx.x == 0) {
     atomicAdd(a.step.queries + 0, (unsigned long long)(n0 + n2));
     atomicAdd(a.step.queries + 1, (unsigned long long)n1);
   }
@@ -165,7 +188,7 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
       bool issued[W_NST];
       for (int s = 0; s < W_NST; ++s) issued[s] = false;
       bool ok = true;
-      for (int tile = cid; ok && tile < n_tiles; tile += ncl) {
+      for (int tile = cid; ok && tile < nw; tile += ncl) {
         const bool xt = tile < t1;
         const bool mid = tile_list(tile) == 2;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
@@ -202,7 +225,7 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
       int stage = 0;
       uint32_t phase = 0, act_phase = 0;
       bool ok = true;
-      for (int tile = cid; ok && tile < n_tiles; tile += ncl) {
+      for (int tile = cid; ok && tile < nw; tile += ncl) {
         const bool xt = tile < t1;
         const bool f16 = xt || F16 || tile_list(tile) == 2;
         for (int g = 0; ok && g < NUM_GEMM; ++g) {
@@ -387,7 +410,7 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
     };
 
     stage_base = a.stage_g + ((size_t)cid * 2 + (xs & 1)) * ACT_BYTES;
-    for (int tile = cid; ok && tile < n_tiles; tile += ncl) {
+    for (int tile = cid; ok && tile < nw; tile += ncl) {
       list = tile_list(tile);
       xt = list == 1;
       f16 = F16 || list == 2;
@@ -487,6 +510,7 @@ mlp_tc_wide_kernel(const __grid_constant__ TCMaps wmaps, const __grid_constant__
     tmem_dealloc(tmem, 128);
   }
   cluster_sync_all();   // no CTA leaves while a peer may still arrive on its barriers
+  grid_dep_wait();      // this step's mlp_tc_kernel is complete
 }
 
 }  // namespace
@@ -545,6 +569,7 @@ cudaError_t mlp_tc_wide(const dist_decoder* dec, const RowSrc& src16, float* f16
   if (step) a.step = *step;
   a.stage_g = static_cast<uint8_t*>(scratch);
   a.head_g = reinterpret_cast<float*>(a.stage_g + (size_t)WT_MAX * 2 * ACT_BYTES);
+  a.nsm = num_sms();
   const int wt = tc_wide_max_tiles();
   if (wt <= 0) return cudaErrorNotSupported;
   auto kern = f16 ? mlp_tc_wide_kernel<true> : mlp_tc_wide_kernel<false>;
@@ -570,7 +595,12 @@ cudaError_t mlp_tc_wide(const dist_decoder* dec, const RowSrc& src16, float* f16
 }
 
 size_t tc_wide_scratch_bytes() {
-  return (size_t)WT_MAX * 2 * ACT_BYTES + (size_t)WT_MAX * BM * 16 * sizeof(float);
+  return (size_t)WT_MAX * 2 * ACT_BYTES + (size_t)WT_MAX * BM * 16 * sizeof(float) + 256;
+}
+
+unsigned long long* tc_wide_seq_flag(void* scratch) {
+  return reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(scratch) +
+                                               tc_wide_scratch_bytes() - 256);
 }
 
 }  // namespace dist

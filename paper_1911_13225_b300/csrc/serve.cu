@@ -103,6 +103,7 @@ struct dist_server {
   unsigned long long* queries = nullptr;
   void* tc_scratch = nullptr;
   void* wide_scratch = nullptr;
+  unsigned long long step_seq = 0;   // sequence number of the last fused step
   std::vector<void*> allocs;
   // host state
   std::mutex mu;
@@ -232,7 +233,11 @@ struct dist_server {
       pool_step_fuse(P, cnt + 2 * (par ^ 1), out, &sf);
       sf.out[2] = act[par ^ 1][2];
       sf.cnt_out[2] = cnt + 4 + (par ^ 1);
-      if (p.latency_mode) sf.wide = static_cast<uint8_t*>(wide_scratch);
+      if (p.latency_mode) {
+        sf.wide = static_cast<uint8_t*>(wide_scratch);
+        sf.seq_flag = tc_wide_seq_flag(wide_scratch);
+        sf.seq = ++step_seq;
+      }
       DIST_CUDA_TRY(mlp_tc_fused(dec, src, fbuf[0], sx, fbuf[1], b0, bs, st,
                                  p.precision == DIST_PREC_FP16, &sf,
                                  P.eps_mid > 0.f ? &sm : nullptr, fbuf[2]));
@@ -474,6 +479,11 @@ dist_status dist_serve_create(const dist_decoder* dec, const dist_trace_params* 
   SV_ALLOC(tc_scratch, (size_t)num_sms() * kTcAdjScratchPerCta);
   SV_ALLOC(wide_scratch, tc_wide_scratch_bytes());
 #undef SV_ALLOC
+  if (s == DIST_OK &&
+      cudaMemset(tc_wide_seq_flag(S->wide_scratch), 0, sizeof(unsigned long long)) != cudaSuccess) {
+    set_error("dist_serve_create: cudaMemset failed");
+    s = DIST_E_CUDA;
+  }
   if (s == DIST_OK && cudaMallocHost(&S->slot_active_host, max_requests * sizeof(int)) != cudaSuccess) {
     S->slot_active_host = nullptr;
     set_error("dist_serve_create: cudaMallocHost failed");

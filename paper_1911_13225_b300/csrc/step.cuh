@@ -47,7 +47,34 @@ struct StepFuse {
   unsigned long long* queries;   // per-list query counters, or null
   uint8_t* wide;                 // latency-mode scratch (tc_wide_scratch_bytes()), or
                                  // null: every launch on the one-tile-per-SM kernel
+  unsigned long long* seq_flag;  // with `wide`: device word through which mlp_tc_kernel
+  unsigned long long seq;        // hands this step's inputs to mlp_tc_wide_kernel
+                                 // (seq: distinct per fused step on this word)
 };
+
+// Tiles of a fused step that mlp_tc_wide_kernel decodes: the first ones in
+// tile order (FP32-class tiles first), mlp_tc_kernel the rest.  All of them
+// when they fit on the resident clusters (wt); the FP32-class tiles alone
+// (a four-SM cluster each) when those fit too and the other tiles take one
+// round on the SMs left over (4 t1 + (n_tiles - t1) <= nsm): the two kernels
+// then run side by side; else none.  Both kernels make this decision from
+// the same counts.
+__host__ __device__ __forceinline__ int wide_share(int n_tiles, int t1, int wt, int nsm) {
+  if (wt <= 0) return 0;
+  if (n_tiles <= wt) return n_tiles;
+  if (t1 > 0 && t1 <= wt && 3 * t1 + n_tiles <= nsm) return t1;
+  return 0;
+}
+
+// Release / acquire of the step sequence word (gpu scope).
+__device__ __forceinline__ void seq_release(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long seq_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
 
 __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
 

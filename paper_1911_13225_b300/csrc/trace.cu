@@ -1421,6 +1421,8 @@ void pool_step_fuse(const RayPool& P, int* cnt_out, int* const out[2], StepFuse*
   sf->cnt_out[2] = nullptr;
   sf->queries = P.o.queries;
   sf->wide = nullptr;
+  sf->seq_flag = nullptr;   // set with `wide` by the caller
+  sf->seq = 0;
 }
 
 cudaError_t pool_probes_depth(const RayPool& P, int cam, long long pix0, long long n,
@@ -1546,6 +1548,8 @@ dist_status dist_trace_fwd(const dist_decoder* dec, const float* z, int n_shapes
       sf.cnt_out[0] = cA + s + 1; sf.cnt_out[1] = cB + s + 1; sf.cnt_out[2] = cC + s + 1;
       sf.queries = o->queries;
       sf.wide = p->latency_mode ? static_cast<uint8_t*>(ws->wide_scratch) : nullptr;
+      sf.seq_flag = tc_wide_seq_flag(ws->wide_scratch);
+      sf.seq = ++ws->step_seq;
       prof_mlp_begin(st, 0);
       DIST_CUDA_TRY(mlp_tc_fused(dec, src, ws->fbuf[0], sx, ws->fbuf[1], b0, bs, st,
                                  p->precision == DIST_PREC_FP16, &sf, mid ? &sm : nullptr,
