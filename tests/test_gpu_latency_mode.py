@@ -70,6 +70,20 @@ def test_bitwise_same_trace_with_and_without(cuda_device, precision, levels):
     _assert_identical(out)
 
 
+def test_split_steps_bitwise_benchmark_view(cuda_device):
+    """The 512 x 512 benchmark view with the FP16 stage: its middle steps
+    (about 16..24) fit their FP32-class tiles on the latency-mode clusters
+    and their 16-bit tiles on the SMs left over, so the two decoder kernels
+    decode them side by side.  Identical results (query counts included:
+    only one of the two kernels counts a step's queries) with the mode on
+    and off."""
+    spec = synth.DEEPSDF_SPEC
+    cam = synth.look_at_camera(synth.random_viewpoints(5, seed=0)[0], 512, 512, shape=0)
+    out, _ = _run(cuda_device, spec, [cam], n_shapes=2, precision="bf16", eps_mid=2e-4)
+    assert out[1]["mask"].sum() > 40000
+    _assert_identical(out)
+
+
 @pytest.mark.parametrize("precision", ["bf16", "fp32_tc"])
 def test_benchmark_view_bitwise(cuda_device, precision):
     """One 256 x 256 view of the benchmark's kind (its tail is where the
