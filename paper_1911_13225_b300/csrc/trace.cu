@@ -1006,6 +1006,8 @@ __global__ void loss_count_kernel(long long n, const uint8_t* mask, const float*
 }
 
 struct LossArgs {
+  double* part;            // [gridDim.x] block sums and
+  unsigned int* ticket;    // a zeroed counter: fixed-order sum; or null: FP64 atomics
   long long n;
   const float *depth, *sil, *normal, *tgt_depth, *tgt_normal, *tgt_sil;
   const uint8_t* mask;
@@ -1054,7 +1056,30 @@ __global__ void loss_terms_kernel(LossArgs a) {
     }
   }
   const double t = block_sum_d(sd * acc_d + sn * acc_n + ss * acc_s, sh);
-  if (threadIdx.x == 0 && t != 0.0) atomicAdd(a.loss, t);
+  if (!a.part) {
+    if (threadIdx.x == 0 && t != 0.0) atomicAdd(a.loss, t);
+    return;
+  }
+  // block sums to part[], the last block to finish adds them in block order
+  // (one FP64 atomic per block on one word serialised at the L2; this sum
+  // is also the same on every run)
+  __shared__ bool last;
+  if (threadIdx.x == 0) {
+    a.part[blockIdx.x] = t;
+    __threadfence();
+    last = atomicAdd(a.ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double v = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x)
+    v += reinterpret_cast<volatile const double*>(a.part)[b];
+  const double tot = block_sum_d(v, sh);
+  if (threadIdx.x == 0) {
+    *a.loss += tot;
+    *a.ticket = 0u;
+  }
 }
 
 // ||z||^2 regulariser (Sec. B.4): loss += w sum z^2, dz = 2 w z.
@@ -1919,15 +1944,19 @@ dist_status dist_loss(int64_t n, const float* depth, const uint8_t* mask, const 
              "dist_loss: regulariser needs z");
   cudaStream_t st = (cudaStream_t)stream;
   DIST_CUDA_TRY(cudaMemsetAsync(loss, 0, sizeof(double), st));
-  DIST_CUDA_TRY(cudaMemsetAsync(ws->ired, 0, sizeof(int), st));
+  DIST_CUDA_TRY(cudaMemsetAsync(ws->ired, 0, 2 * sizeof(int), st));
   const int g = grid_for(n, 256);
   loss_count_kernel<<<g, 256, 0, st>>>(n, mask, tgt_depth, ws->ired);
   DIST_LAUNCH_CHECK();
   LossArgs a;
+  // block sums in the FP64 accumulators of the backward pass, which zeroes
+  // them before its own use
+  a.part = ws->gacc;
+  a.ticket = reinterpret_cast<unsigned int*>(ws->ired + 1);
   a.n = n; a.depth = depth; a.sil = sil; a.normal = normal; a.tgt_depth = tgt_depth;
   a.tgt_normal = tgt_normal; a.tgt_sil = tgt_sil; a.mask = mask; a.w = *w; a.cnt = ws->ired;
   a.loss = loss; a.g_depth = g_depth; a.g_normal = g_normal; a.g_sil = g_sil;
-  loss_terms_kernel<<<g, 256, 0, st>>>(a);
+  loss_terms_kernel<<<std::min(g, 2 * num_sms()), 256, 0, st>>>(a);
   DIST_LAUNCH_CHECK();
   if (dz && z && n_shapes > 0 && latent_dim > 0) {
     const long long nz = (long long)n_shapes * latent_dim;
