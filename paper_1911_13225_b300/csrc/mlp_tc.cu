@@ -713,11 +713,12 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
   uint64_t* acc_half = bars + 2 * STAGES;     // [2]: accumulator columns 0..255, 256..511
-  uint64_t* act_full = bars + 2 * STAGES + 2;
-  uint64_t* drain = bars + 2 * STAGES + 3;
-  uint64_t* h2l = bars + 2 * STAGES + 4;      // side 1 -> side 0
-  uint64_t* l2h = bars + 2 * STAGES + 5;      // side 0 -> side 1
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 6);
+  uint64_t* act_lo = bars + 2 * STAGES + 2;   // operand columns 0..255 written
+  uint64_t* act_hi = bars + 2 * STAGES + 3;   // operand columns 256..511 written
+  uint64_t* drain = bars + 2 * STAGES + 4;
+  uint64_t* h2l = bars + 2 * STAGES + 5;      // side 1 -> side 0
+  uint64_t* l2h = bars + 2 * STAGES + 6;      // side 0 -> side 1
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 7);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   float* xfer = reinterpret_cast<float*>(smem + ACT_BYTES + STAGES * STAGE_BYTES + BAR_BYTES);
 
@@ -736,7 +737,8 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
     }
     mbar_init(acc_half, 1);
     mbar_init(acc_half + 1, 1);
-    mbar_init(act_full, NUM_EPI * 32);
+    mbar_init(act_lo, NUM_EPI * 32);
+    mbar_init(act_hi, NUM_EPI * 32);
     mbar_init(drain, 1);
     mbar_init(h2l, NUM_EPI * 16);
     mbar_init(l2h, NUM_EPI * 16);
@@ -791,16 +793,22 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
     // ------------------------------------------------------- MMA issuer
     if (lane == 0) {
       int stage = 0;
-      uint32_t phase = 0, act_phase = 0;
+      uint32_t phase = 0, lo_phase = 0, hi_phase = 0;
       bool ok = true;
       for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
         for (int e = 0; ok && e < NUM_ADJ_GEMM; ++e) {
-          if (!mbar_wait(act_full, act_phase, abort_flag)) { ok = false; break; }
-          act_phase ^= 1u;
-          tc_fence_after();
           const int nkc = adj_k(e) / BK;
           for (int nh = 0; ok && nh < adj_n(e) / BN; ++nh) {
             for (int kc = 0; kc < NPASS * nkc; ++kc) {
+              // the operand arrives in two 256-column halves: the first K
+              // chunks start as soon as their half is written
+              if (nh == 0 && (kc == 0 || (kc == 4 && nkc == 8))) {
+                uint64_t* bar = kc == 0 ? act_lo : act_hi;
+                uint32_t& ph = kc == 0 ? lo_phase : hi_phase;
+                if (!mbar_wait(bar, ph, abort_flag)) { ok = false; break; }
+                ph ^= 1u;
+                tc_fence_after();
+              }
               if (!mbar_wait(full + stage, phase, abort_flag)) { ok = false; break; }
               tc_fence_after();
               const uint32_t a_base = smem_u32(act + (kc % nkc) * CHUNK_BYTES);
@@ -859,9 +867,11 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
 #pragma unroll
       for (int w = 0; w < 4; ++w) store_packed<16>(act, row, col(w), held[w]);
     };
-    auto release = [&]() {
+    // operand columns 0..255 (lo) or 256..511 (hi) of this thread written
+    auto release = [&](uint64_t* bar) {
+      tc_fence_before();
       fence_async_shared();
-      mbar_arrive(act_full);
+      mbar_arrive(bar);
     };
     for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
       const int j = tile * BM + row;
@@ -887,9 +897,10 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           }
           mw[w] = bits;
           store_act32<F16>(act, row, c, v);
+          if (w == 3) release(act_lo);
         }
         store_masks(0, mw);
-        release();
+        release(act_hi);
       }
       float head = 0.f;
       for (int g = 0; g < NUM_GEMM; ++g) {
@@ -921,18 +932,22 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
         }
         if (gemm_n(g) == 512) {
           if (!wait_acc(1)) { ok = false; break; }
-          if (!last) store_held(held);
+          if (!last) {
+            store_held(held);
+            release(act_lo);
+          }
           for (int w = 4; w < 8; ++w) {
             float v[32];
             chunk(w, v);
             if (!last) store_act32<F16>(act, row, col(w), v);
           }
+          if (!last) release(act_hi);
         } else if (!last) {
           store_held(held);
+          release(act_lo);
         }
         store_masks(g + 1, mw);
         tc_fence_before();
-        if (!last) release();
       }
       if (!ok) break;
       // ---- head: f, then 1 - f^2 to both sides
@@ -967,8 +982,9 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
             v[i + 3] = ((bits >> (i + 3)) & 1u) ? dfs * wh.w : 0.f;
           }
           store_act32<F16>(act, row, c, v);
+          if (w == 3) release(act_lo);
         }
-        release();
+        release(act_hi);
       }
       // ---- backward GEMMs for layers 7..1: g_{l-1} = acc * mask_{l-1}
       float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -1010,17 +1026,21 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
         }
         if (gemm_k(l - 1) == 512) {
           if (!wait_acc(1)) { ok = false; break; }
-          if (more) store_held(held);
+          if (more) {
+            store_held(held);
+            release(act_lo);
+          }
           for (int w = 4; w < 8; ++w) {
             float v[32];
             chunk(w, v);
             if (more) store_act32<F16>(act, row, col(w), v);
           }
+          if (more) release(act_hi);
         } else if (more) {
           store_held(held);
+          release(act_lo);
         }
         tc_fence_before();
-        if (more) release();
       }
       if (!ok) break;
       // ---- grad_p f and the probe coefficient
@@ -1166,9 +1186,10 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
 #pragma unroll
       for (int w = 0; w < 4; ++w) putx(col(w) + 16 * part, hh[w], hl[w]);
     };
-    auto release = [&]() {
+    auto release = [&](uint64_t* bar) {
+      tc_fence_before();
       fence_async_shared();
-      mbar_arrive(act_full);
+      mbar_arrive(bar);
     };
     for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
       const int j = tile * QPT + jq;
@@ -1196,9 +1217,10 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           uint32_t hi[8], lo[8];
           relu_split16(v, hi, lo, vmax);
           putx(cc, hi, lo);
+          if (w == 3) release(act_lo);
         }
         store_masks(0, mw);
-        release();
+        release(act_hi);
       }
       float head = 0.f;
       for (int g = 0; g < NUM_GEMM; ++g) {
@@ -1235,18 +1257,22 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
         for (int w = 0; w < 4; ++w) chunk(w, hh[w], hl[w]);
         if (gemm_n(g) == 512) {
           if (!wait_acc(1)) { ok = false; break; }
-          if (!last) store_held(hh, hl);
+          if (!last) {
+            store_held(hh, hl);
+            release(act_lo);
+          }
           for (int w = 4; w < 8; ++w) {
             uint32_t hi[8], lo[8];
             chunk(w, hi, lo);
             if (!last) putx(col(w) + 16 * part, hi, lo);
           }
+          if (!last) release(act_hi);
         } else if (!last) {
           store_held(hh, hl);
+          release(act_lo);
         }
         store_masks(g + 1, mw);
         tc_fence_before();
-        if (!last) release();
       }
       if (!ok) break;
       head += __shfl_xor_sync(0xffffffffu, head, 16);
@@ -1291,8 +1317,9 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           uint32_t hi[8], lo[8];
           splitx(v, hi, lo);
           putx(cc, hi, lo);
+          if (w == 3) release(act_lo);
         }
-        release();
+        release(act_hi);
       }
       // ---- backward GEMMs for layers 7..1: g_{l-1} = acc * mask_{l-1}
       float gx = 0.f, gy = 0.f, gz = 0.f;
@@ -1330,17 +1357,21 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
         for (int w = 0; w < 4; ++w) chunk(w, hh[w], hl[w]);
         if (gemm_k(l - 1) == 512) {
           if (!wait_acc(1)) { ok = false; break; }
-          if (more) store_held(hh, hl);
+          if (more) {
+            store_held(hh, hl);
+            release(act_lo);
+          }
           for (int w = 4; w < 8; ++w) {
             uint32_t hi[8], lo[8];
             chunk(w, hi, lo);
             if (more) putx(col(w) + 16 * part, hi, lo);
           }
+          if (more) release(act_hi);
         } else if (more) {
           store_held(hh, hl);
+          release(act_lo);
         }
         tc_fence_before();
-        if (more) release();
       }
       if (!ok) break;
       gx += __shfl_xor_sync(0xffffffffu, gx, 16);
