@@ -224,6 +224,35 @@ def test_loss_terms_match_oracle_on_gpu_render(cuda_device):
     np.testing.assert_allclose(to_np(dz), 1.0 * to_np(z), rtol=1e-6)
 
 
+def test_loss_is_the_same_on_every_run(cuda_device):
+    """dist_loss adds its block sums in block order (no FP64 atomics on one
+    word): the loss of a 512 x 512 image comes out bit for bit the same on
+    repeated calls, and matches the oracle's loss terms to 1e-9."""
+    from paper_1911_13225_b300 import api
+    rng = np.random.default_rng(3)
+    n = 512 * 512
+    dev = cuda_device
+    depth = rng.uniform(1.0, 3.0, n).astype(np.float32)
+    tgt = rng.uniform(1.0, 3.0, n).astype(np.float32)
+    mask = (rng.random(n) < 0.4).astype(np.uint8)
+    tgt[rng.random(n) < 0.3] = np.inf
+    res = api.alloc_result(n, 1, dev, normals=False)
+    res.depth.copy_(torch.from_numpy(depth))
+    res.mask.copy_(torch.from_numpy(mask))
+    z = torch.zeros(1, 256, device=dev)
+    ws = api.Workspace(n)
+    vals = []
+    for _ in range(4):
+        L, gd, _, _, _ = api.loss(res, {"depth": torch.from_numpy(tgt).to(dev)}, z, ws,
+                                  w_depth=10.0)
+        torch.cuda.synchronize()
+        vals.append(float(L.item()))
+    assert len({np.float64(v).tobytes() for v in vals}) == 1
+    out_np = {"depth": depth.astype(np.float64), "mask": mask.astype(bool)}
+    Lo, _, _, _ = loss_terms(out_np, {"depth": tgt.astype(np.float64)}, w_depth=10.0)
+    assert abs(vals[0] - Lo) <= 1e-9 * abs(Lo)
+
+
 @pytest.mark.parametrize("spec", [synth.SMALL_SPEC, synth.DEEPSDF_SPEC])
 def test_exact_depth_gradient(cuda_device, spec):
     api, dec, ws, z, params, cams, res, tgt, sdf, orc, amb = _setup(cuda_device, spec)
