@@ -84,6 +84,23 @@ def test_split_steps_bitwise_benchmark_view(cuda_device):
     _assert_identical(out)
 
 
+@pytest.mark.parametrize("kw", [dict(precision="fp16", eps_bf16=2e-4),
+                                dict(precision="bf16", coarse_levels=2),
+                                dict(precision="bf16", eps_mid=2e-4, k_min=3)],
+                         ids=["fp16", "bf16-coarse-to-fine", "bf16-fp16-stage-k3"])
+def test_split_steps_bitwise_other_marches(cuda_device, kw):
+    """Other marches whose middle steps the two decoder kernels may share (a
+    second 512 x 512 viewpoint, two shapes in one call): identical results
+    with the latency mode on and off."""
+    spec = synth.DEEPSDF_SPEC
+    vps = synth.random_viewpoints(5, seed=0)
+    cams = [synth.look_at_camera(vps[1], 512, 512, shape=0),
+            synth.look_at_camera(vps[2], 256, 256, shape=1)]
+    out, _ = _run(cuda_device, spec, cams, n_shapes=2, **kw)
+    assert out[1]["mask"].sum() > 20000
+    _assert_identical(out)
+
+
 @pytest.mark.parametrize("precision", ["bf16", "fp32_tc"])
 def test_benchmark_view_bitwise(cuda_device, precision):
     """One 256 x 256 view of the benchmark's kind (its tail is where the
