@@ -224,6 +224,33 @@ def test_loss_terms_match_oracle_on_gpu_render(cuda_device):
     np.testing.assert_allclose(to_np(dz), 1.0 * to_np(z), rtol=1e-6)
 
 
+@pytest.mark.parametrize("precision", ["fp32", "bf16"])
+def test_normal_gradient_of_an_image_without_hits(cuda_device, precision):
+    """A view that misses the shape: central-difference normals and their
+    gradient length are 0 everywhere, and the normal loss's latent gradient
+    is exactly 0 (no probes; nothing handed to the FP32 adjoint)."""
+    from paper_1911_13225_b300 import api
+    spec = synth.DEEPSDF_SPEC
+    Ws, bs, Z = workload(spec, seed=7, n_shapes=1)
+    dec = gpu_decoder(spec, Ws, bs)
+    # turned half a turn about its own y axis, it looks away from the origin:
+    # every ray misses the unit sphere
+    cam = synth.look_at_camera((0.0, 0.0, 2.5), 24, 24)
+    R = np.asarray(cam["R"], dtype=np.float64) @ np.diag([-1.0, 1.0, -1.0])
+    cam = dict(cam, R=R)
+    z = torch.from_numpy(Z).to(cuda_device)
+    ws = api.Workspace(24 * 24, 50)
+    p = api.TraceParams(precision=precision, normal_delta=1e-3)
+    res = api.trace(dec, z, [cam], p, ws, normals=True)
+    assert int(res.mask.sum()) == 0
+    assert float(res.grad_len.abs().max()) == 0.0 and float(res.normal.abs().max()) == 0.0
+    g = torch.ones(24 * 24, 3, device=cuda_device)
+    dz = api.backward(dec, z, [cam], p, ws, res, g_normal=g)
+    torch.cuda.synchronize()
+    assert dec.device_error() == 0
+    assert float(dz.abs().max()) == 0.0
+
+
 def test_loss_is_the_same_on_every_run(cuda_device):
     """dist_loss adds its block sums in block order (no FP64 atomics on one
     word): the loss of a 512 x 512 image comes out bit for bit the same on
