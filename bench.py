@@ -977,7 +977,7 @@ def main():
                     help="skip the 5-view 256x256 and the 32x8x224^2 inverse-step lines")
     ap.add_argument("--inverse-steps", type=int, default=3,
                     help="timed Adam steps of the 32x8x224^2 inverse-step line")
-    ap.add_argument("--serve-requests", type=int, default=400)
+    ap.add_argument("--serve-requests", type=int, default=2000)
     ap.add_argument("--serve-loads", default="0.5,0.95",
                     help="further Poisson loads reported under serving.by_load")
     ap.add_argument("--serve-load", type=float, default=0.8,
