@@ -133,6 +133,30 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   const unsigned long long wlim = a.wait_ns;
   const int pid = (int)blockIdx.x;
   const int npid = (int)gridDim.x;
+  // shared-memory barriers and TMEM read nothing the previous grid writes:
+  // set them up before waiting for it (the other TMEM users of this library
+  // need as much shared memory as this kernel, so none of their CTAs shares
+  // an SM with this one and holds TMEM it would wait for)
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NST; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, 1);
+    }
+    for (int h = 0; h < 2; ++h) mbar_init(acc_full + h, 1);
+    for (int q = 0; q < 4; ++q) mbar_init(act_full + q, FWD_EPI);
+    mbar_init(drain, 1);
+    mbar_init(head_bar, (FWD_EPI - 4) * 32);
+    mbar_init(step_full, 4);
+    mbar_init(step_empty, FWD_STEP_WARPS);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) tmem_alloc(tmem_slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
   // launched early behind the previous grid (programmatic dependent
   // launch): nothing it writes is read before this wait
   grid_dep_wait();
@@ -155,7 +179,10 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
   // the FP32-class tiles of a launch that leaves room for both, see
   // wide_share); this grid takes [tb, n_tiles)
   const int tb = wide_share(n_tiles, t1, a.wide_tiles, npid);
-  if (tb + pid >= n_tiles) return;
+  if (tb + pid >= n_tiles) {
+    if (warp == 1) tmem_dealloc(tmem, 512);
+    return;
+  }
   // tile of round r for this CTA
   auto tile_at = [&](int r) { return tb + tile_of(r, pid, npid); };
   if (a.fuse_step && a.step.queries && pid == 0 && threadIdx.x == 0) {
@@ -168,25 +195,6 @@ mlp_tc_kernel(const __grid_constant__ TCMaps maps, const __grid_constant__ TCMap
     return t < t1 ? t * QPT_X : (t - (t < t2 ? t1 : t2)) * BM;
   };
 
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) {
-      mbar_init(full + s, 1);
-      mbar_init(empty + s, 1);
-    }
-    for (int h = 0; h < 2; ++h) mbar_init(acc_full + h, 1);
-    for (int q = 0; q < 4; ++q) mbar_init(act_full + q, FWD_EPI);
-    mbar_init(drain, 1);
-    mbar_init(head_bar, (FWD_EPI - 4) * 32);
-    mbar_init(step_full, 4);
-    mbar_init(step_empty, FWD_STEP_WARPS);
-    *abort_flag = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 1) tmem_alloc(tmem_slot, 512);
-  tc_fence_before();
-  __syncthreads();
-  tc_fence_after();
-  const uint32_t tmem = *tmem_slot;
 
   if (warp == 0) {
     // ------------------------------------------------------ TMA producer
