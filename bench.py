@@ -32,7 +32,7 @@ EPS_MID = 2e-4                      # FP16 stage of the BF16 march (hand-over to
 # dram__bytes_read.sum + dram__bytes_write.sum of one mlp_tc_kernel launch (ncu, the
 # first march launch of a 256x256 trace: 65,536 rows); the weights dominate it, so it
 # is not scaled by rows.  Taken on the current kernel; None once the kernel changes.
-TC_TRAFFIC_BYTES = 6318080 + 8192
+TC_TRAFFIC_BYTES = 6317056 + 5888
 TC_TRAFFIC_NOTE = ("ncu dram read+write, first march launch of a 256x256 BF16 trace "
                    "(65,536 rows; weights once + ray state read and written by the step "
                    "warps), not scaled")
