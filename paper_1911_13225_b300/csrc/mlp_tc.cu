@@ -1127,7 +1127,8 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
     // Lane pair (i, i + 16) of quadrant q holds probe 16q + i: lane i the hi
     // row, lane i + 16 the lo row.  After the pair sum each lane owns 16 of a
     // 32-column chunk (`part`) and writes both rows of those columns.  The
-    // chunks of a side and the hold-back of half 0 are the 16-bit epilogue's.
+    // chunks of a side are the 16-bit epilogue's; the operand is written once
+    // a layer's MMAs are all done (no hold-back of half 0, see below).
     const int ew = warp - 2;
     const int quad = warp & 3;
     const int side = ew >> 2;
@@ -1189,10 +1190,6 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
       pair_sum16(r, part, m);
 #pragma unroll
       for (int i = 0; i < 16; ++i) m[i] *= s;
-    };
-    auto store_held = [&](const uint32_t (&hh)[4][8], const uint32_t (&hl)[4][8]) {
-#pragma unroll
-      for (int w = 0; w < 4; ++w) putx(col(w) + 16 * part, hh[w], hl[w]);
     };
     auto release = [&](uint64_t* bar) {
       tc_fence_before();
@@ -1259,26 +1256,19 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
             relu_split16(v, hi, lo, vmax);
           }
         };
-        uint32_t hh[4][8], hl[4][8];
+        // (FP32-class tiles write straight after the layer's last MMAs: holding
+        // half 0 in registers spilled at the 168-register cap and measured no
+        // faster)
         if (!wait_acc(0)) { ok = false; break; }
-#pragma unroll
-        for (int w = 0; w < 4; ++w) chunk(w, hh[w], hl[w]);
-        if (gemm_n(g) == 512) {
-          if (!wait_acc(1)) { ok = false; break; }
-          if (!last) {
-            store_held(hh, hl);
-            release(act_lo);
-          }
-          for (int w = 4; w < 8; ++w) {
-            uint32_t hi[8], lo[8];
-            chunk(w, hi, lo);
-            if (!last) putx(col(w) + 16 * part, hi, lo);
-          }
-          if (!last) release(act_hi);
-        } else if (!last) {
-          store_held(hh, hl);
-          release(act_lo);
+        const bool wide_out = gemm_n(g) == 512;
+        if (wide_out && !wait_acc(1)) { ok = false; break; }
+        for (int w = 0; w < (wide_out ? 8 : 4); ++w) {
+          uint32_t hi[8], lo[8];
+          chunk(w, hi, lo);
+          if (!last) putx(col(w) + 16 * part, hi, lo);
+          if (!last && w == 3) release(act_lo);
         }
+        if (!last && wide_out) release(act_hi);
         store_masks(g + 1, mw);
         tc_fence_before();
       }
@@ -1359,26 +1349,16 @@ mlp_tc_adj_kernel(const __grid_constant__ TCMaps fmaps, const __grid_constant__ 
           }
           if (more) splitx(v, hi, lo);
         };
-        uint32_t hh[4][8], hl[4][8];
         if (!wait_acc(0)) { ok = false; break; }
-#pragma unroll
-        for (int w = 0; w < 4; ++w) chunk(w, hh[w], hl[w]);
-        if (gemm_k(l - 1) == 512) {
-          if (!wait_acc(1)) { ok = false; break; }
-          if (more) {
-            store_held(hh, hl);
-            release(act_lo);
-          }
-          for (int w = 4; w < 8; ++w) {
-            uint32_t hi[8], lo[8];
-            chunk(w, hi, lo);
-            if (more) putx(col(w) + 16 * part, hi, lo);
-          }
-          if (more) release(act_hi);
-        } else if (more) {
-          store_held(hh, hl);
-          release(act_lo);
+        const bool wide_out = gemm_k(l - 1) == 512;
+        if (wide_out && !wait_acc(1)) { ok = false; break; }
+        for (int w = 0; w < (wide_out ? 8 : 4); ++w) {
+          uint32_t hi[8], lo[8];
+          chunk(w, hi, lo);
+          if (more) putx(col(w) + 16 * part, hi, lo);
+          if (more && w == 3) release(act_lo);
         }
+        if (more && wide_out) release(act_hi);
         tc_fence_before();
       }
       if (!ok) break;
